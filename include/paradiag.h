@@ -1,0 +1,223 @@
+/*
+ * paradiag.h - C ABI of the GB300 (sm_103a) ParaDIAG step with the additive
+ * element-wise Vanka multigrid of He & Liu, "A Vanka-type multigrid solver for
+ * complex-shifted Laplacian systems from diagonalization-based parallel-in-time
+ * algorithms" (arXiv 2203.11154).
+ *
+ * The problem (Sec. 1, eq. (1)): (B kron I_h + I_t kron A) u = f, with B = V D V^{-1}
+ * and A the five-point Laplacian (1/h^2)[.,-1,.;-1,4,-1;.,-1,.] on the N x N interior
+ * of the unit square, homogeneous Dirichlet values, h = 1/(N+1), N = 2^k - 1.
+ * The step: g = (V^{-1} kron I_h) f, then the n independent shifted systems of eq. (2)
+ * (A + lam_j I) z_j = g_j solved by multigrid (Sec. 3 components, smoother of
+ * eq. (3)/(6)), then u = (V kron I_h) z.
+ *
+ * Conventions for every call:
+ *   - Grid vectors are row-major [n][N][N] (shift or time index outermost), no
+ *     padding, point (i,j) at i*N + j.  Complex values are interleaved (re, im)
+ *     pairs of the context's working type: double for precision 0 (FP64), float for
+ *     the FP32 multigrid of precision 1.  Real vectors of paradiag_solve are double.
+ *   - Pointers named d_* are device pointers owned by the caller; h_* are host
+ *     pointers owned by the caller.  The context owns all other device memory.
+ *   - Calls are ordered on the context's CUDA stream.  Calls that return counts or
+ *     residuals to the host synchronise that stream before returning.
+ *   - Errors are returned as pd_status; nothing throws across the ABI.  After a
+ *     PD_ERR_CUDA the context must be destroyed.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef PARADIAG_H
+#define PARADIAG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pd_ctx pd_ctx;
+
+typedef enum {
+    PD_OK = 0,
+    PD_ERR_ARG = 1,     /* invalid argument (sizes, NULL, unsupported option) */
+    PD_ERR_CUDA = 2,    /* a CUDA runtime call failed or the extension is unusable */
+    PD_ERR_NOMEM = 3,   /* device or pinned host allocation failed */
+    PD_ERR_NOCONV = 4,  /* tolerance not reached within maxit / max_refine */
+    PD_ERR_NAN = 5,     /* a residual norm became NaN or Inf */
+    PD_ERR_SING = 6,    /* a coarsest-grid matrix is singular */
+    PD_ERR_STATE = 7    /* call not valid for this context (e.g. no V given) */
+} pd_status;
+
+typedef struct {
+    int cycle_gamma;   /* 1 = V-cycle, 2 = W-cycle (Sec. 3 uses W) */
+    int nu1, nu2;      /* pre- and post-smoothing steps (Sec. 3 uses 1, 0) */
+    int coarsest_n;    /* interior size of the coarsest grid, 1, 3, 7 or 15 (h0 = 1/(n+1)) */
+    int maxit;         /* cycles per shifted solve */
+    double tol;        /* precision 0: relative residual per shift;
+                          precision 1: relative residual of eq. (1) */
+    int omega_mode;    /* 0: 24/25 (Vanka) or 4/5 (Jacobi), Sec. 2.1 and Sec. 3;
+                          1: LFA optimum of eq. (5) per shift and level;
+                          2: the caller's table given to paradiag_setup */
+    int precision;     /* 0: FP64 throughout; 1: FP32 cycles inside FP64 refinement */
+    int smoother;      /* 0: additive element-wise Vanka (eq. (6)); 1: damped Jacobi */
+    double inner_tol;  /* precision 1: relative residual of each inner FP32 solve */
+    int max_refine;    /* precision 1: maximum refinement steps */
+    int imag_check;    /* paradiag_solve: also form Im((V kron I) z) and report max |Im| */
+} pd_config;
+
+/* Fills cfg with V(1,1), coarsest 3, maxit 100, tol 1e-10, omega_mode 1, FP64,
+ * Vanka, inner_tol 1e-6, max_refine 12, imag_check 1. */
+void pd_config_default(pd_config *cfg);
+
+/*
+ * The alpha-circulant backward-Euler time matrix (a circulant-type B, Sec. 1):
+ * B = (1/tau)(I - C_alpha), C_alpha the cyclic down-shift with alpha in the top-right
+ * corner, and B = V D V^{-1} in closed form:
+ *   lam_j = (1 - alpha^{1/n} e^{2 pi i (j-1)/n}) / tau,
+ *   V = Gamma^{-1} Fbar, Fbar_{kj} = e^{-2 pi i (k-1)(j-1)/n}, V^{-1} = (1/n) F Gamma,
+ *   Gamma = diag(alpha^{(k-1)/n}).
+ * Outputs (host, caller-allocated, any may be NULL): h_B n*n real row-major,
+ * h_shifts 2n doubles (re, im), h_V and h_Vinv 2*n*n doubles (row-major complex),
+ * h_u0_coef n doubles (1/tau, 0, ..., 0: the initial value enters the first step).
+ * Errors: PD_ERR_ARG for n < 1, tau <= 0 or alpha not in (0, 1].
+ */
+pd_status pd_alpha_circulant(int n, double tau, double alpha, double *h_B, double *h_shifts,
+                             double *h_V, double *h_Vinv, double *h_u0_coef);
+
+/*
+ * Creates a context for N x N grids and n shifts (Sec. 1, eq. (1)-(2)).
+ *   N         interior points per side, 2^k - 1 with N >= cfg->coarsest_n.
+ *   h         mesh step; must equal 1/(N+1) (the unit square).
+ *   n         number of shifts / time steps, 1 <= n <= 128.
+ *   h_shifts  2n doubles: lam_j (re, im).  Required.
+ *   h_V, h_Vinv  2*n*n doubles each (complex row-major) or both NULL (then only the
+ *             shifted-solve calls are valid).
+ *   h_B       n*n real time matrix, row-major, or NULL.  Required by precision 1
+ *             (the refinement residual uses B directly, never V).
+ *   h_u0_coef n doubles or NULL (zeros): fhat_k = f_k + u0_coef[k] u0.
+ *   h_omega   [n][levels] relaxation parameters for omega_mode 2, else NULL.
+ *   cfg       options (NULL = pd_config_default).
+ *   stream    the cudaStream_t every call of this context is ordered on (NULL = the
+ *             legacy default stream).  The context never creates or destroys streams.
+ * Setup runs on the host (shift tables, LFA, coarsest-grid inverses) and allocates
+ * all device memory.  Errors: PD_ERR_ARG, PD_ERR_NOMEM, PD_ERR_CUDA, PD_ERR_SING.
+ */
+pd_status paradiag_setup(pd_ctx **ctx, int N, double h, int n, const double *h_shifts,
+                         const double *h_V, const double *h_Vinv, const double *h_B,
+                         const double *h_u0_coef, const double *h_omega,
+                         const pd_config *cfg, void *stream);
+
+/* Number of grid levels (finest N down to the coarsest) and the relaxation
+ * parameter table [n][levels] the context uses (host copy). */
+int pd_num_levels(const pd_ctx *ctx);
+pd_status pd_get_omega(const pd_ctx *ctx, double *h_omega);
+
+/*
+ * One multigrid cycle (Sec. 3: nu1 smoothing steps, full-weighting restriction of
+ * the residual, gamma recursive cycles on the problem re-discretised at 2h with zero
+ * initial guess, linear interpolation of the correction, nu2 smoothing steps) for all
+ * n shifts at grid level `level` (0 = finest, N_l = (N_{l-1}-1)/2), in place:
+ * d_z [n][N_l][N_l] holds the iterate on entry and on return; d_b the right-hand
+ * side.  Working type per precision (see above).  Asynchronous.
+ */
+pd_status mg_vcycle(pd_ctx *ctx, int level, void *d_z, const void *d_b);
+
+/*
+ * Solves L_j z_j = b_j (eq. (2)) for all n shifts by cycles from z = 0 until
+ * ||b_j - L_j z_j||_2 / ||b_j||_2 <= cfg.tol (checked before the first cycle and after
+ * each one) or maxit cycles; converged shifts stop while others continue.
+ * d_b, d_z: [n][N][N] complex of the working type.  h_iters, h_relres (n each, may be
+ * NULL) receive cycles and final relative residual per shift.  Synchronises.
+ * Returns PD_ERR_NOCONV if any shift missed the tolerance, PD_ERR_NAN on NaN/Inf.
+ */
+pd_status shifted_solve_batched(pd_ctx *ctx, void *d_z, const void *d_b, int *h_iters,
+                                double *h_relres);
+
+/* Indices of the values paradiag_solve writes to h_stats (PD_STATS_LEN doubles). */
+enum {
+    PD_STAT_RELRES_ALLATONCE = 0, /* ||fhat - (B kron I + I kron A) u|| / ||fhat||, or -1 without B */
+    PD_STAT_REFINE_STEPS = 1,     /* refinement steps (precision 1), 0 for FP64 */
+    PD_STAT_IMAG_MAX = 2,         /* max |Im((V kron I) z)| of the last step (imag_check) */
+    PD_STAT_CYCLES_TOTAL = 3,     /* multigrid cycles summed over shifts and steps */
+    PD_STAT_CYCLES_MAX = 4,       /* max over shifts of cycles, summed over steps */
+    PD_STAT_RELRES_SHIFT_MAX = 5, /* max over shifts of the last shifted relative residual */
+    PD_STATS_LEN = 8
+};
+
+/*
+ * One ParaDIAG solve of eq. (1) (device buffers):
+ *   fhat_k = f_k + u0_coef[k] u0                      (right-hand side)
+ *   g = (V^{-1} kron I_h) fhat                        (eq. (1))
+ *   z_j = L_j^{-1} g_j by multigrid to cfg.tol        (eq. (2))
+ *   u = Re (V kron I_h) z                             (eq. (1))
+ * precision 1 wraps FP32 multigrid and compensated transforms in FP64 iterative
+ * refinement on eq. (1) itself: r = fhat - (B kron I + I kron A) u in FP64, a step
+ * above on r, u += d, until ||r|| / ||fhat|| <= cfg.tol.
+ *   d_u   [n][N][N] double, output (precision 0 and 1).
+ *   d_f   [n][N][N] double.   d_u0  [N][N] double (may be NULL: zero).
+ *   h_iters/h_relres  per-shift cycles (summed over refinement steps) and last
+ *                     relative residual, n each, may be NULL.
+ *   h_stats           PD_STATS_LEN doubles, may be NULL.
+ * Synchronises.  Errors: PD_ERR_STATE without V, PD_ERR_NOCONV, PD_ERR_NAN, CUDA.
+ */
+pd_status paradiag_solve(pd_ctx *ctx, double *d_u, const double *d_f, const double *d_u0,
+                         int *h_iters, double *h_relres, double *h_stats);
+
+/*
+ * paradiag_solve on host buffers: copies h_f (and h_u0) to context-owned device
+ * buffers with cudaMemcpyAsync on the context stream, solves, and copies u back to
+ * h_u.  Pinned (page-locked) host memory gives full copy bandwidth; pageable memory
+ * works but is slower.  Same outputs and errors as paradiag_solve.
+ */
+pd_status paradiag_solve_host(pd_ctx *ctx, double *h_u, const double *h_f, const double *h_u0,
+                              int *h_iters, double *h_relres, double *h_stats);
+
+/*
+ * Component entry points (one kernel each, all shifts of one level, asynchronous),
+ * exposed so that each kernel can be checked against the oracle on its own.  Grid
+ * arrays are [n][N_l][N_l] complex of the working type unless stated otherwise.
+ *   pd_smooth             d_z_out = d_z_in + omega_{j,l} M_{e,j} (d_b - L_j d_z_in):
+ *                         one step of S_j = I - omega M_{e,j} L_j (Sec. 2), stencil of
+ *                         eq. (6); d_z_out must not alias d_z_in.
+ *   pd_residual_restrict  d_bc [n][N_{l+1}]^2 = full weighting (Sec. 3) of
+ *                         d_b - L_j d_z at grid level l.
+ *   pd_prolong_add        d_z += linear interpolation (Sec. 3) of d_ec [n][N_{l+1}]^2.
+ *   pd_coarse_solve       d_z = L_j^{-1} d_b on the coarsest level (inverse formed at
+ *                         setup by Gauss-Jordan elimination with partial pivoting).
+ *   pd_transform_forward  d_g = (V^{-1} kron I_h)(d_f + u0_coef kron d_u0), eq. (1):
+ *                         d_f [n][N][N] double, d_u0 [N][N] double or NULL, d_g complex
+ *                         of the working type.
+ *   pd_transform_inverse  d_u = Re (V kron I_h) d_z (accumulate = 0) or
+ *                         d_u += Re (V kron I_h) d_z (accumulate = 1), eq. (1): d_z
+ *                         complex of the working type, d_u [n][N][N] double.
+ *   pd_allatonce_residual d_r = fhat - (B kron I_h + I_t kron A) d_u, fhat as above,
+ *                         in FP64 with the B given at setup; h_norms[0] = ||d_r||_2,
+ *                         h_norms[1] = ||fhat||_2.  Synchronises.
+ */
+pd_status pd_smooth(pd_ctx *ctx, int level, void *d_z_out, const void *d_z_in, const void *d_b);
+pd_status pd_residual_restrict(pd_ctx *ctx, int level, void *d_bc, const void *d_z,
+                               const void *d_b);
+pd_status pd_prolong_add(pd_ctx *ctx, int level, void *d_z, const void *d_ec);
+pd_status pd_coarse_solve(pd_ctx *ctx, void *d_z, const void *d_b);
+pd_status pd_transform_forward(pd_ctx *ctx, void *d_g, const double *d_f, const double *d_u0);
+pd_status pd_transform_inverse(pd_ctx *ctx, double *d_u, const void *d_z, int accumulate);
+pd_status pd_allatonce_residual(pd_ctx *ctx, double *d_r, const double *d_u, const double *d_f,
+                                const double *d_u0, double *h_norms);
+
+/* Waits for the context stream. */
+pd_status pd_synchronize(pd_ctx *ctx);
+
+/* Kernel launches issued by this context since creation (for launch accounting). */
+long long pd_launch_count(const pd_ctx *ctx);
+
+/* Waits for the context stream, then frees all device and pinned host memory of the
+ * context. */
+pd_status paradiag_destroy(pd_ctx *ctx);
+
+/* Static description of a status code. */
+const char *pd_status_str(pd_status s);
+
+/* Text of the last error recorded in the context (CUDA error string or argument). */
+const char *pd_last_error(const pd_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PARADIAG_H */

@@ -1,0 +1,317 @@
+"""Thin ctypes binding of libparadiag.so (include/paradiag.h), same names as the C ABI.
+
+Only argument marshalling happens here: torch CUDA tensors become device pointers,
+numpy arrays become host pointers, status codes become exceptions.  Every step of a
+solve runs in the library's kernels.  The library must have been built (see
+`build.build()`); if it is missing or cannot be loaded this module raises instead of
+falling back to anything else.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+PD_STAT_RELRES_ALLATONCE = 0
+PD_STAT_REFINE_STEPS = 1
+PD_STAT_IMAG_MAX = 2
+PD_STAT_CYCLES_TOTAL = 3
+PD_STAT_CYCLES_MAX = 4
+PD_STAT_RELRES_SHIFT_MAX = 5
+PD_STATS_LEN = 8
+
+STATUS = {0: "PD_OK", 1: "PD_ERR_ARG", 2: "PD_ERR_CUDA", 3: "PD_ERR_NOMEM", 4: "PD_ERR_NOCONV",
+          5: "PD_ERR_NAN", 6: "PD_ERR_SING", 7: "PD_ERR_STATE"}
+
+EXPORTS = ["pd_config_default", "pd_alpha_circulant", "paradiag_setup", "pd_num_levels",
+           "pd_get_omega", "mg_vcycle", "shifted_solve_batched", "paradiag_solve",
+           "paradiag_solve_host", "pd_smooth", "pd_residual_restrict", "pd_prolong_add",
+           "pd_coarse_solve", "pd_transform_forward", "pd_transform_inverse",
+           "pd_allatonce_residual", "pd_synchronize", "pd_launch_count", "paradiag_destroy",
+           "pd_status_str", "pd_last_error"]
+
+
+class PDError(RuntimeError):
+    def __init__(self, code, where, detail=""):
+        self.code = code
+        self.status = STATUS.get(code, str(code))
+        super().__init__("%s: %s%s" % (where, self.status, (" (%s)" % detail) if detail else ""))
+
+
+class pd_config(C.Structure):
+    _fields_ = [("cycle_gamma", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
+                ("coarsest_n", C.c_int), ("maxit", C.c_int), ("tol", C.c_double),
+                ("omega_mode", C.c_int), ("precision", C.c_int), ("smoother", C.c_int),
+                ("inner_tol", C.c_double), ("max_refine", C.c_int), ("imag_check", C.c_int)]
+
+
+_P = C.c_void_p
+_I = C.c_int
+_D = C.c_double
+
+
+def lib(path=None):
+    """Loads libparadiag.so (building it first if it is out of date)."""
+    global _lib
+    if _lib is None:
+        if path is None:
+            path = _build.LIB
+            if not _build.up_to_date():
+                _build.build()
+        if not os.path.exists(path):
+            raise ImportError("libparadiag.so not found at %s" % path)
+        L = C.CDLL(path)
+        sig = {
+            "pd_config_default": (None, [C.POINTER(pd_config)]),
+            "pd_alpha_circulant": (_I, [_I, _D, _D, _P, _P, _P, _P, _P]),
+            "paradiag_setup": (_I, [C.POINTER(_P), _I, _D, _I, _P, _P, _P, _P, _P, _P,
+                                    C.POINTER(pd_config), _P]),
+            "pd_num_levels": (_I, [_P]),
+            "pd_get_omega": (_I, [_P, _P]),
+            "mg_vcycle": (_I, [_P, _I, _P, _P]),
+            "shifted_solve_batched": (_I, [_P, _P, _P, _P, _P]),
+            "paradiag_solve": (_I, [_P, _P, _P, _P, _P, _P, _P]),
+            "paradiag_solve_host": (_I, [_P, _P, _P, _P, _P, _P, _P]),
+            "pd_smooth": (_I, [_P, _I, _P, _P, _P]),
+            "pd_residual_restrict": (_I, [_P, _I, _P, _P, _P]),
+            "pd_prolong_add": (_I, [_P, _I, _P, _P]),
+            "pd_coarse_solve": (_I, [_P, _P, _P]),
+            "pd_transform_forward": (_I, [_P, _P, _P, _P]),
+            "pd_transform_inverse": (_I, [_P, _P, _P, _I]),
+            "pd_allatonce_residual": (_I, [_P, _P, _P, _P, _P, _P]),
+            "pd_synchronize": (_I, [_P]),
+            "pd_launch_count": (C.c_longlong, [_P]),
+            "paradiag_destroy": (_I, [_P]),
+            "pd_status_str": (C.c_char_p, [_I]),
+            "pd_last_error": (C.c_char_p, [_P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def config(**kw):
+    """pd_config with the library defaults, then the given fields."""
+    c = pd_config()
+    lib().pd_config_default(C.byref(c))
+    for k, v in kw.items():
+        if not hasattr(c, k):
+            raise AttributeError("pd_config has no field %r" % k)
+        setattr(c, k, v)
+    return c
+
+
+def _dptr(t, dtype=None, numel=None):
+    """Device pointer of a contiguous CUDA tensor (checked)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("expected %s, got %s" % (dtype, t.dtype))
+    if numel is not None and t.numel() != numel:
+        raise ValueError("expected %d elements, got %d" % (numel, t.numel()))
+    return C.c_void_p(t.data_ptr())
+
+
+def _hptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _check(code, where, ctx=None):
+    if code != 0:
+        detail = ""
+        if ctx is not None:
+            detail = (lib().pd_last_error(ctx) or b"").decode(errors="replace")
+        raise PDError(code, where, detail)
+
+
+def pd_alpha_circulant(n, tau, alpha):
+    """(B [n][n], shifts [n] complex, V, Vinv [n][n] complex, u0_coef [n])."""
+    B = np.zeros((n, n))
+    sh = np.zeros(2 * n)
+    V = np.zeros(2 * n * n)
+    Vi = np.zeros(2 * n * n)
+    c0 = np.zeros(n)
+    _check(lib().pd_alpha_circulant(n, float(tau), float(alpha), _hptr(B), _hptr(sh), _hptr(V),
+                                    _hptr(Vi), _hptr(c0)), "pd_alpha_circulant")
+    return B, sh.view(np.complex128), V.view(np.complex128).reshape(n, n), \
+        Vi.view(np.complex128).reshape(n, n), c0
+
+
+class Context:
+    """A paradiag context (one GPU, the caller's current torch stream)."""
+
+    def __init__(self, N, n, shifts, V=None, Vinv=None, B=None, u0_coef=None, omega=None,
+                 cfg=None, stream=None):
+        import torch
+        self.N, self.n = int(N), int(n)
+        self.cfg = cfg if cfg is not None else config()
+        sh = np.ascontiguousarray(np.asarray(shifts, dtype=np.complex128).reshape(n))
+        self._keep = [sh]
+        args = [_hptr(sh.view(np.float64))]
+        for a in (V, Vinv):
+            if a is None:
+                args.append(None)
+            else:
+                a = np.ascontiguousarray(np.asarray(a, dtype=np.complex128).reshape(n, n))
+                self._keep.append(a)
+                args.append(_hptr(a.view(np.float64)))
+        for a in (B, u0_coef, omega):
+            if a is None:
+                args.append(None)
+            else:
+                a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+                self._keep.append(a)
+                args.append(_hptr(a))
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = stream
+        h = C.c_void_p()
+        _check(lib().paradiag_setup(C.byref(h), self.N, 1.0 / (self.N + 1), self.n, *args,
+                                    C.byref(self.cfg), C.c_void_p(stream)), "paradiag_setup")
+        self.h = h
+        self.levels = lib().pd_num_levels(h)
+        self.Ns = [self.N]
+        while len(self.Ns) < self.levels:
+            self.Ns.append((self.Ns[-1] - 1) // 2)
+        self.ctype = torch.complex128 if self.cfg.precision == 0 else torch.complex64
+
+    # -- helpers -------------------------------------------------------------------
+    def omega(self):
+        out = np.zeros((self.n, self.levels))
+        _check(lib().pd_get_omega(self.h, _hptr(out)), "pd_get_omega", self.h)
+        return out
+
+    def _grid(self, t, level=0, dtype=None):
+        N = self.Ns[level]
+        return _dptr(t, dtype or self.ctype, self.n * N * N)
+
+    def synchronize(self):
+        _check(lib().pd_synchronize(self.h), "pd_synchronize", self.h)
+
+    def launch_count(self):
+        return int(lib().pd_launch_count(self.h))
+
+    def destroy(self):
+        if getattr(self, "h", None):
+            lib().paradiag_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    # -- the C ABI -----------------------------------------------------------------
+    def mg_vcycle(self, level, z, b):
+        _check(lib().mg_vcycle(self.h, level, self._grid(z, level), self._grid(b, level)),
+               "mg_vcycle", self.h)
+
+    def shifted_solve_batched(self, z, b, raise_on_noconv=True):
+        it = np.zeros(self.n, np.int32)
+        rr = np.zeros(self.n)
+        code = lib().shifted_solve_batched(self.h, self._grid(z), self._grid(b), _hptr(it), _hptr(rr))
+        if code != 0 and not (code == 4 and not raise_on_noconv):
+            _check(code, "shifted_solve_batched", self.h)
+        return it, rr
+
+    def _solve_out(self, code, it, rr, stats, where, raise_on_noconv):
+        if code != 0 and not (code == 4 and not raise_on_noconv):
+            _check(code, where, self.h)
+        return dict(iters=it, relres=rr, relres_allatonce=stats[PD_STAT_RELRES_ALLATONCE],
+                    refine_steps=int(stats[PD_STAT_REFINE_STEPS]), imag_max=stats[PD_STAT_IMAG_MAX],
+                    cycles_total=int(stats[PD_STAT_CYCLES_TOTAL]),
+                    cycles_max=int(stats[PD_STAT_CYCLES_MAX]),
+                    relres_shift_max=stats[PD_STAT_RELRES_SHIFT_MAX], status=STATUS.get(code))
+
+    def paradiag_solve(self, u, f, u0=None, raise_on_noconv=True):
+        import torch
+        it = np.zeros(self.n, np.int32)
+        rr = np.zeros(self.n)
+        stats = np.zeros(PD_STATS_LEN)
+        m = self.n * self.N * self.N
+        code = lib().paradiag_solve(self.h, _dptr(u, torch.float64, m), _dptr(f, torch.float64, m),
+                                    _dptr(u0, torch.float64, self.N * self.N), _hptr(it),
+                                    _hptr(rr), _hptr(stats))
+        return self._solve_out(code, it, rr, stats, "paradiag_solve", raise_on_noconv)
+
+    def paradiag_solve_host(self, u, f, u0=None, raise_on_noconv=True):
+        """u, f, u0: contiguous float64 host tensors or numpy arrays (pinned is fastest)."""
+        def hp(a, numel):
+            if a is None:
+                return None
+            if hasattr(a, "data_ptr"):
+                if a.is_cuda or not a.is_contiguous() or a.numel() != numel:
+                    raise ValueError("expected a contiguous host tensor of %d elements" % numel)
+                return C.c_void_p(a.data_ptr())
+            a = np.asarray(a)
+            if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != numel:
+                raise ValueError("expected a contiguous float64 array of %d elements" % numel)
+            return _hptr(a)
+        it = np.zeros(self.n, np.int32)
+        rr = np.zeros(self.n)
+        stats = np.zeros(PD_STATS_LEN)
+        m = self.n * self.N * self.N
+        code = lib().paradiag_solve_host(self.h, hp(u, m), hp(f, m), hp(u0, self.N * self.N),
+                                         _hptr(it), _hptr(rr), _hptr(stats))
+        return self._solve_out(code, it, rr, stats, "paradiag_solve_host", raise_on_noconv)
+
+    def pd_smooth(self, level, z_out, z_in, b):
+        _check(lib().pd_smooth(self.h, level, self._grid(z_out, level), self._grid(z_in, level),
+                               self._grid(b, level)), "pd_smooth", self.h)
+
+    def pd_residual_restrict(self, level, bc, z, b):
+        _check(lib().pd_residual_restrict(self.h, level, self._grid(bc, level + 1),
+                                          self._grid(z, level), self._grid(b, level)),
+               "pd_residual_restrict", self.h)
+
+    def pd_prolong_add(self, level, z, ec):
+        _check(lib().pd_prolong_add(self.h, level, self._grid(z, level), self._grid(ec, level + 1)),
+               "pd_prolong_add", self.h)
+
+    def pd_coarse_solve(self, z, b):
+        L = self.levels - 1
+        _check(lib().pd_coarse_solve(self.h, self._grid(z, L), self._grid(b, L)),
+               "pd_coarse_solve", self.h)
+
+    def pd_transform_forward(self, g, f, u0=None):
+        import torch
+        m = self.n * self.N * self.N
+        _check(lib().pd_transform_forward(self.h, self._grid(g), _dptr(f, torch.float64, m),
+                                          _dptr(u0, torch.float64, self.N * self.N)),
+               "pd_transform_forward", self.h)
+
+    def pd_transform_inverse(self, u, z, accumulate=False):
+        import torch
+        m = self.n * self.N * self.N
+        _check(lib().pd_transform_inverse(self.h, _dptr(u, torch.float64, m), self._grid(z),
+                                          int(bool(accumulate))), "pd_transform_inverse", self.h)
+
+    def pd_allatonce_residual(self, r, u, f, u0=None):
+        import torch
+        m = self.n * self.N * self.N
+        norms = np.zeros(2)
+        _check(lib().pd_allatonce_residual(self.h, _dptr(r, torch.float64, m),
+                                           _dptr(u, torch.float64, m), _dptr(f, torch.float64, m),
+                                           _dptr(u0, torch.float64, self.N * self.N), _hptr(norms)),
+               "pd_allatonce_residual", self.h)
+        return norms[0], norms[1]
+
+
+def paradiag_setup(N, n, shifts, V=None, Vinv=None, B=None, u0_coef=None, omega=None, cfg=None,
+                   stream=None):
+    return Context(N, n, shifts, V, Vinv, B, u0_coef, omega, cfg, stream)
+
+
+def alpha_circulant_context(N, n, tau, alpha, **cfg_fields):
+    """Context for the backward-Euler alpha-circulant ParaDIAG step on an N x N grid."""
+    B, sh, V, Vi, c0 = pd_alpha_circulant(n, tau, alpha)
+    return Context(N, n, sh, V, Vi, B, c0, None, config(**cfg_fields))

@@ -1,0 +1,895 @@
+// C ABI of libparadiag.so: context setup and the orchestration of the ParaDIAG step
+// (Sec. 1, eq. (1)-(2)) around the multigrid of Sec. 2-3.  Every arithmetic step of
+// a solve runs in the kernels of mg_kernels.cu and transforms.cu; this file only
+// allocates, launches and reads back convergence information.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pd_internal.h"
+
+using namespace pd;
+
+namespace {
+
+constexpr size_t kCoarseSmemLimit = 200 * 1024;
+
+struct LevelBufs {
+  int N = 0;
+  long long P = 0;        // row pitch (elements) of the internal arrays
+  void *z[2] = {nullptr, nullptr};
+  void *b = nullptr;
+};
+
+template <typename T> struct Prec {
+  using C = typename Cx<T>::type;
+  std::vector<LevelBufs> lv;
+  Coef<T> *coef = nullptr;  // [L][n]
+  C *cinv = nullptr;        // [n][mc*mc]
+  C *Wf = nullptr;          // V^{-1}, n x n
+  C *Wi = nullptr;          // V, n x n
+};
+
+}  // namespace
+
+struct pd_ctx {
+  int N = 0, n = 0, L = 0, lc = 0;
+  pd_config cfg{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<double> shifts, omega, V, Vinv, B, u0coef;
+  bool have_V = false, have_B = false;
+  std::vector<int> Ns;
+  CoarsePlan plan{};
+  Prec<double> p64;
+  Prec<float> p32;
+  int cur[kMaxLevels] = {0};
+  SolveState st{};
+  void *state_mem = nullptr;
+  int *h_pinned = nullptr;     // [2] nactive slots, [2..] flags
+  int *h_iters = nullptr;      // pinned [n]
+  double *h_relres = nullptr;  // pinned [n]
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  double *d_u0coef = nullptr;
+  int *d_Bptr = nullptr, *d_Bcol = nullptr;
+  double *d_Bval = nullptr;
+  double *d_r = nullptr;       // refinement residual [n][N][N]
+  double *d_part = nullptr;    // all-at-once residual partial sums
+  double *h_part = nullptr;    // pinned copy
+  unsigned long long *d_imag = nullptr;
+  double *d_stage_f = nullptr, *d_stage_u = nullptr, *d_stage_u0 = nullptr;
+  long long launches = 0;
+  std::string err;
+  std::vector<void *> allocs;
+};
+
+namespace {
+
+struct CudaFail {
+  cudaError_t e;
+};
+
+void ck(pd_ctx *c, cudaError_t e) {
+  if (e != cudaSuccess) {
+    if (c) c->err = cudaGetErrorString(e);
+    throw CudaFail{e};
+  }
+}
+
+void ck_launch(pd_ctx *c, int count = 1) {
+  c->launches += count;
+  ck(c, cudaGetLastError());
+}
+
+template <typename P> P dalloc(pd_ctx *c, size_t bytes) {
+  void *p = nullptr;
+  cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 16));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    c->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+    throw std::bad_alloc();
+  }
+  c->allocs.push_back(p);
+  return reinterpret_cast<P>(p);
+}
+
+View view(void *p, int N, long long P) { return View{p, P, (long long)N * P}; }
+View uview(const void *p, int N) { return View{const_cast<void *>(p), N, (long long)N * N}; }
+
+template <typename T> Prec<T> &prec(pd_ctx *c);
+template <> Prec<double> &prec<double>(pd_ctx *c) { return c->p64; }
+template <> Prec<float> &prec<float>(pd_ctx *c) { return c->p32; }
+
+double hl(const pd_ctx *c, int l) { return 1.0 / (c->Ns[l] + 1); }
+
+template <typename T>
+void alloc_prec(pd_ctx *c) {
+  using C = typename Cx<T>::type;
+  Prec<T> &P = prec<T>(c);
+  const int n = c->n, L = c->L;
+  P.lv.resize(L);
+  for (int l = 0; l < L; l++) {
+    LevelBufs &B = P.lv[l];
+    B.N = c->Ns[l];
+    B.P = B.N + 1;
+    const size_t bytes = (size_t)n * B.N * B.P * sizeof(C);
+    B.z[0] = dalloc<void *>(c, bytes);
+    B.z[1] = dalloc<void *>(c, bytes);
+    B.b = dalloc<void *>(c, bytes);
+  }
+  // smoother coefficients in the scaled form of pd_internal.h
+  std::vector<Coef<T>> cf((size_t)L * n);
+  for (int l = 0; l < L; l++) {
+    const double h = hl(c, l);
+    for (int j = 0; j < n; j++) {
+      const std::complex<double> lam(c->shifts[2 * j], c->shifts[2 * j + 1]);
+      const std::complex<double> eta = lam * h * h, d = 4.0 + eta;
+      const double w = c->omega[(size_t)j * L + l];
+      double abc[6];
+      vanka_abc(eta.real(), eta.imag(), abc);
+      std::complex<double> ca, cb, cc;
+      if (c->cfg.smoother == 1) {
+        ca = w / d;
+        cb = cc = 0.0;
+      } else {
+        ca = w * std::complex<double>(abc[0], abc[1]);
+        cb = w * std::complex<double>(abc[2], abc[3]) * 0.5;
+        cc = w * std::complex<double>(abc[4], abc[5]) * 0.25;
+      }
+      Coef<T> &k = cf[(size_t)l * n + j];
+      k.d.x = (T)d.real(); k.d.y = (T)d.imag();
+      k.ca.x = (T)ca.real(); k.ca.y = (T)ca.imag();
+      k.cb.x = (T)cb.real(); k.cb.y = (T)cb.imag();
+      k.cc.x = (T)cc.real(); k.cc.y = (T)cc.imag();
+    }
+  }
+  P.coef = dalloc<Coef<T> *>(c, cf.size() * sizeof(Coef<T>));
+  ck(c, cudaMemcpy(P.coef, cf.data(), cf.size() * sizeof(Coef<T>), cudaMemcpyHostToDevice));
+  // inverse of the scaled coarsest matrix h^2 L_j = (4 + eta) I - (neighbours)
+  const int Nc = c->Ns[L - 1], m = Nc * Nc;
+  const double h = hl(c, L - 1);
+  std::vector<C> inv((size_t)n * m * m);
+  for (int j = 0; j < n; j++) {
+    const std::complex<double> lam(c->shifts[2 * j], c->shifts[2 * j + 1]);
+    const std::complex<double> d = 4.0 + lam * h * h;
+    std::vector<double> A((size_t)2 * m * m, 0.0);
+    for (int i = 0; i < Nc; i++)
+      for (int q = 0; q < Nc; q++) {
+        const int p = i * Nc + q;
+        A[2 * ((size_t)p * m + p)] = d.real();
+        A[2 * ((size_t)p * m + p) + 1] = d.imag();
+        if (i > 0) A[2 * ((size_t)p * m + p - Nc)] = -1.0;
+        if (i < Nc - 1) A[2 * ((size_t)p * m + p + Nc)] = -1.0;
+        if (q > 0) A[2 * ((size_t)p * m + p - 1)] = -1.0;
+        if (q < Nc - 1) A[2 * ((size_t)p * m + p + 1)] = -1.0;
+      }
+    if (invert_dense(m, A) != 0) throw PD_ERR_SING;
+    for (size_t e = 0; e < (size_t)m * m; e++) {
+      inv[(size_t)j * m * m + e].x = (T)A[2 * e];
+      inv[(size_t)j * m * m + e].y = (T)A[2 * e + 1];
+    }
+  }
+  P.cinv = dalloc<C *>(c, inv.size() * sizeof(C));
+  ck(c, cudaMemcpy(P.cinv, inv.data(), inv.size() * sizeof(C), cudaMemcpyHostToDevice));
+  if (c->have_V) {
+    std::vector<C> wf((size_t)n * n), wi((size_t)n * n);
+    for (size_t e = 0; e < (size_t)n * n; e++) {
+      wf[e].x = (T)c->Vinv[2 * e];
+      wf[e].y = (T)c->Vinv[2 * e + 1];
+      wi[e].x = (T)c->V[2 * e];
+      wi[e].y = (T)c->V[2 * e + 1];
+    }
+    P.Wf = dalloc<C *>(c, wf.size() * sizeof(C));
+    P.Wi = dalloc<C *>(c, wi.size() * sizeof(C));
+    ck(c, cudaMemcpy(P.Wf, wf.data(), wf.size() * sizeof(C), cudaMemcpyHostToDevice));
+    ck(c, cudaMemcpy(P.Wi, wi.data(), wi.size() * sizeof(C), cudaMemcpyHostToDevice));
+  }
+  // the attributes are per kernel, shared by all contexts: set the largest any context
+  // can use (coarse launches never exceed kCoarseSmemLimit; transforms need n <= 128)
+  ck(c, prepare_coarse<T>(kCoarseSmemLimit));
+  ck(c, prepare_transforms<T>(kMaxShifts));
+}
+
+// ---- one cycle on the global-memory levels (Sec. 3), recursing to the coarse kernel ----
+template <typename T>
+void run_cycle(pd_ctx *c, int l, bool zzero, bool top, const int *active, double tol, int maxit) {
+  Prec<T> &P = prec<T>(c);
+  LevelBufs &B = P.lv[l];
+  const int N = B.N, n = c->n;
+  const View b = view(B.b, N, B.P);
+  View z[2] = {view(B.z[0], N, B.P), view(B.z[1], N, B.P)};
+  const Coef<T> *cf = P.coef + (size_t)l * n;
+  const bool jac = c->cfg.smoother == 1;
+  int &cur = c->cur[l];
+  if (l >= c->lc) {
+    launch_coarse<T>(c->stream, c->plan, l, n, b, (T)1, z[cur], P.coef, P.cinv, active, 1,
+                     zzero ? 0 : 1, 0, 0.0, 0, c->st);
+    ck_launch(c);
+    return;
+  }
+  int s = 0;
+  if (top) {
+    if (c->cfg.nu1 >= 1) {
+      launch_smooth<T>(c->stream, N, n, z[cur], z[cur ^ 1], b, (T)1, cf, active, zzero, jac,
+                       c->st.partials, c->st.max_tiles);
+      launch_converge(c->stream, n, smooth_tiles(N), c->st, tol, maxit, cur);
+      ck_launch(c, 2);
+      cur ^= 1;
+      zzero = false;
+      s = 1;
+    } else {
+      launch_resnorm<T>(c->stream, N, n, z[cur], b, (T)1, cf, active, zzero, c->st.partials,
+                        c->st.max_tiles);
+      launch_converge(c->stream, n, smooth_tiles(N), c->st, tol, maxit, cur);
+      ck_launch(c, 2);
+    }
+  }
+  for (; s < c->cfg.nu1; s++) {
+    launch_smooth<T>(c->stream, N, n, z[cur], z[cur ^ 1], b, (T)1, cf, active, zzero, jac,
+                     nullptr, 0);
+    ck_launch(c);
+    cur ^= 1;
+    zzero = false;
+  }
+  LevelBufs &Bc = P.lv[l + 1];
+  launch_residual_restrict<T>(c->stream, N, n, z[cur], b, (T)1, view(Bc.b, Bc.N, Bc.P), (T)1, cf,
+                              active, zzero);
+  ck_launch(c);
+  c->cur[l + 1] = 0;
+  if (l + 1 >= c->lc) {
+    launch_coarse<T>(c->stream, c->plan, l + 1, n, view(Bc.b, Bc.N, Bc.P), (T)1,
+                     view(Bc.z[0], Bc.N, Bc.P), P.coef, P.cinv, active, c->cfg.cycle_gamma, 0, 0,
+                     0.0, 0, c->st);
+    ck_launch(c);
+  } else {
+    bool zz = true;
+    for (int g = 0; g < c->cfg.cycle_gamma; g++) {
+      run_cycle<T>(c, l + 1, zz, false, active, tol, maxit);
+      zz = false;
+    }
+  }
+  if (zzero) {
+    ck(c, cudaMemsetAsync(z[cur].p, 0, (size_t)n * z[cur].plane * sizeof(typename Cx<T>::type),
+                          c->stream));
+  }
+  launch_prolong_add<T>(c->stream, N, n, z[cur], view(Bc.z[c->cur[l + 1]], Bc.N, Bc.P), active);
+  ck_launch(c);
+  for (s = 0; s < c->cfg.nu2; s++) {
+    launch_smooth<T>(c->stream, N, n, z[cur], z[cur ^ 1], b, (T)1, cf, active, false, jac, nullptr,
+                     0);
+    ck_launch(c);
+    cur ^= 1;
+  }
+}
+
+// Solve of eq. (2) for all shifts with the right-hand side already in lv[0].b
+// (scaled by h^2).  On return the per-shift answers are in lv[0].z[final_buf[j]],
+// and h_iters/h_relres (pinned copies) hold cycles and relative residuals.
+template <typename T>
+pd_status solve_levels(pd_ctx *c, double tol, int maxit) {
+  Prec<T> &P = prec<T>(c);
+  LevelBufs &B = P.lv[0];
+  const int n = c->n;
+  launch_reset_state(c->stream, n, c->st);
+  ck_launch(c);
+  if (c->lc == 0) {
+    launch_coarse<T>(c->stream, c->plan, 0, n, view(B.b, B.N, B.P), (T)1, view(B.z[0], B.N, B.P),
+                     P.coef, P.cinv, nullptr, 0, 0, 1, tol, maxit, c->st);
+    ck_launch(c);
+  } else {
+    ck(c, cudaMemsetAsync(B.z[0], 0, (size_t)n * B.N * B.P * sizeof(typename Cx<T>::type),
+                          c->stream));
+    c->cur[0] = 0;
+    for (int cyc = 0; cyc <= maxit; cyc++) {
+      run_cycle<T>(c, 0, cyc == 0, true, c->st.active, tol, maxit);
+      ck(c, cudaMemcpyAsync(&c->h_pinned[cyc & 1], c->st.nactive, sizeof(int),
+                            cudaMemcpyDeviceToHost, c->stream));
+      ck(c, cudaEventRecord(c->ev[cyc & 1], c->stream));
+      if (cyc >= 1) {
+        ck(c, cudaEventSynchronize(c->ev[(cyc - 1) & 1]));
+        if (c->h_pinned[(cyc - 1) & 1] == 0) break;
+      }
+    }
+  }
+  ck(c, cudaMemcpyAsync(c->h_iters, c->st.iters, n * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  ck(c, cudaMemcpyAsync(c->h_relres, c->st.relres, n * sizeof(double), cudaMemcpyDeviceToHost,
+                        c->stream));
+  ck(c, cudaMemcpyAsync(&c->h_pinned[2], c->st.flags, sizeof(int), cudaMemcpyDeviceToHost,
+                        c->stream));
+  ck(c, cudaStreamSynchronize(c->stream));
+  if (c->h_pinned[2] & 1) return PD_ERR_NAN;
+  for (int j = 0; j < n; j++)
+    if (!(c->h_relres[j] <= tol)) return PD_ERR_NOCONV;
+  return PD_OK;
+}
+
+// ||fhat - A u|| and ||fhat|| from the per-CTA partial sums (fixed order)
+void allatonce_norms(pd_ctx *c, double *r, const double *u, const double *f, const double *u0,
+                     double *rn, double *fn) {
+  launch_allatonce_residual(c->stream, c->N, c->n, r, u, f, u0, c->d_u0coef, c->d_Bptr,
+                            c->d_Bcol, c->d_Bval, c->d_part);
+  ck_launch(c);
+  const int nb = allatonce_blocks();
+  ck(c, cudaMemcpyAsync(c->h_part, c->d_part, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost,
+                        c->stream));
+  ck(c, cudaStreamSynchronize(c->stream));
+  double a = 0.0, b = 0.0;
+  for (int k = 0; k < nb; k++) {
+    a += c->h_part[2 * k];
+    b += c->h_part[2 * k + 1];
+  }
+  *rn = std::sqrt(a);
+  *fn = std::sqrt(b);
+}
+
+template <typename T>
+pd_status paradiag_impl(pd_ctx *c, double *u, const double *f, const double *u0, int *h_iters,
+                        double *h_relres, double *stats) {
+  Prec<T> &P = prec<T>(c);
+  LevelBufs &B = P.lv[0];
+  const int N = c->N, n = c->n;
+  const double h2 = hl(c, 0) * hl(c, 0);
+  const View g = view(B.b, N, B.P);
+  const View z0 = view(B.z[0], N, B.P), z1 = view(B.z[1], N, B.P);
+  std::vector<int> it_sum(n, 0);
+  int cyc_max_sum = 0;
+  double st_local[PD_STATS_LEN];
+  for (int k = 0; k < PD_STATS_LEN; k++) st_local[k] = 0.0;
+  st_local[PD_STAT_RELRES_ALLATONCE] = -1.0;
+  pd_status rc = PD_OK;
+  const bool imag = c->cfg.imag_check != 0;
+  auto accumulate_iters = [&]() {
+    int mx = 0;
+    for (int j = 0; j < n; j++) {
+      it_sum[j] += c->h_iters[j];
+      mx = std::max(mx, c->h_iters[j]);
+    }
+    cyc_max_sum += mx;
+  };
+  if (imag) ck(c, cudaMemsetAsync(c->d_imag, 0, sizeof(unsigned long long), c->stream));
+  if (c->cfg.precision == 0) {
+    launch_transform_forward<T>(c->stream, N, n, g, f, u0, c->d_u0coef, P.Wf, h2);
+    ck_launch(c);
+    rc = solve_levels<T>(c, c->cfg.tol, c->cfg.maxit);
+    accumulate_iters();
+    launch_transform_inverse<T>(c->stream, N, n, u, z0, z1, c->st.final_buf, P.Wi, false, imag,
+                                c->d_imag);
+    ck_launch(c);
+    if (c->have_B) {
+      double rn, fn;
+      allatonce_norms(c, nullptr, u, f, u0, &rn, &fn);
+      st_local[PD_STAT_RELRES_ALLATONCE] = fn > 0 ? rn / fn : 0.0;
+    }
+  } else {
+    // FP64 iterative refinement on eq. (1) around FP32 ParaDIAG steps.  Step 1 transforms
+    // fhat itself; later steps transform the FP64 residual r = fhat - A u.
+    double relres = 1.0;
+    int steps = 0;
+    for (int step = 0; step < std::max(1, c->cfg.max_refine); step++) {
+      if (step == 0)
+        launch_transform_forward<T>(c->stream, N, n, g, f, u0, c->d_u0coef, P.Wf, h2);
+      else
+        launch_transform_forward<T>(c->stream, N, n, g, c->d_r, nullptr, c->d_u0coef, P.Wf, h2);
+      ck_launch(c);
+      pd_status s = solve_levels<T>(c, c->cfg.inner_tol, c->cfg.maxit);
+      if (s == PD_ERR_NAN) {
+        rc = s;
+        break;
+      }
+      accumulate_iters();
+      launch_transform_inverse<T>(c->stream, N, n, u, z0, z1, c->st.final_buf, P.Wi, step > 0,
+                                  imag, c->d_imag);
+      ck_launch(c);
+      double rn, fn;
+      allatonce_norms(c, c->d_r, u, f, u0, &rn, &fn);
+      steps = step + 1;
+      relres = fn > 0 ? rn / fn : 0.0;
+      if (!std::isfinite(relres)) {
+        rc = PD_ERR_NAN;
+        break;
+      }
+      if (relres <= c->cfg.tol) break;
+    }
+    st_local[PD_STAT_RELRES_ALLATONCE] = relres;
+    st_local[PD_STAT_REFINE_STEPS] = steps;
+    if (rc == PD_OK && !(relres <= c->cfg.tol)) rc = PD_ERR_NOCONV;
+  }
+  if (imag) {
+    unsigned long long bits = 0;
+    ck(c, cudaMemcpy(&bits, c->d_imag, sizeof(bits), cudaMemcpyDeviceToHost));
+    double v;
+    std::memcpy(&v, &bits, sizeof(v));
+    st_local[PD_STAT_IMAG_MAX] = v;
+  }
+  double tot = 0.0, rmax = 0.0;
+  for (int j = 0; j < n; j++) {
+    tot += it_sum[j];
+    rmax = std::max(rmax, c->h_relres[j]);
+    if (h_iters) h_iters[j] = it_sum[j];
+    if (h_relres) h_relres[j] = c->h_relres[j];
+  }
+  st_local[PD_STAT_CYCLES_TOTAL] = tot;
+  st_local[PD_STAT_CYCLES_MAX] = cyc_max_sum;
+  st_local[PD_STAT_RELRES_SHIFT_MAX] = rmax;
+  if (stats)
+    for (int k = 0; k < PD_STATS_LEN; k++) stats[k] = st_local[k];
+  return rc;
+}
+
+bool is_pow2m1(int N) { return N >= 1 && ((N + 1) & N) == 0; }
+
+#define PD_TRY(ctx, ...)                    \
+  try {                                     \
+    __VA_ARGS__                             \
+  } catch (const CudaFail &) {              \
+    return PD_ERR_CUDA;                     \
+  } catch (const std::bad_alloc &) {        \
+    return PD_ERR_NOMEM;                    \
+  } catch (pd_status s_) {                  \
+    return s_;                              \
+  }
+
+void free_ctx(pd_ctx *c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (void *p : c->allocs) cudaFree(p);
+  if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  if (c->h_iters) cudaFreeHost(c->h_iters);
+  if (c->h_relres) cudaFreeHost(c->h_relres);
+  if (c->h_part) cudaFreeHost(c->h_part);
+  for (int k = 0; k < 2; k++)
+    if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pd_config_default(pd_config *cfg) {
+  if (!cfg) return;
+  cfg->cycle_gamma = 1;
+  cfg->nu1 = 1;
+  cfg->nu2 = 1;
+  cfg->coarsest_n = 3;
+  cfg->maxit = 100;
+  cfg->tol = 1e-10;
+  cfg->omega_mode = 1;
+  cfg->precision = 0;
+  cfg->smoother = 0;
+  cfg->inner_tol = 1e-6;
+  cfg->max_refine = 12;
+  cfg->imag_check = 1;
+}
+
+pd_status pd_alpha_circulant(int n, double tau, double alpha, double *B, double *shifts,
+                             double *V, double *Vinv, double *u0coef) {
+  if (n < 1 || !(tau > 0) || !(alpha > 0) || alpha > 1) return PD_ERR_ARG;
+  const double an = std::pow(alpha, 1.0 / n);
+  for (int j = 0; j < n; j++) {
+    const std::complex<double> e = std::polar(1.0, 2.0 * M_PI * j / n);
+    const std::complex<double> lam = (1.0 - an * e) / tau;
+    if (shifts) {
+      shifts[2 * j] = lam.real();
+      shifts[2 * j + 1] = lam.imag();
+    }
+  }
+  for (int k = 0; k < n; k++)
+    for (int j = 0; j < n; j++) {
+      const size_t e = (size_t)k * n + j;
+      const double ang = 2.0 * M_PI * (double)((long long)k * j % n) / n;
+      if (V) {
+        const std::complex<double> v = std::pow(alpha, -(double)k / n) * std::polar(1.0, -ang);
+        V[2 * e] = v.real();
+        V[2 * e + 1] = v.imag();
+      }
+      if (Vinv) {
+        const std::complex<double> v = std::polar(1.0, ang) * std::pow(alpha, (double)j / n) / (double)n;
+        Vinv[2 * e] = v.real();
+        Vinv[2 * e + 1] = v.imag();
+      }
+      if (B) {
+        double b = 0.0;
+        if (k == j) b = 1.0 / tau;
+        if (k == j + 1) b = -1.0 / tau;
+        if (k == 0 && j == n - 1) b += -alpha / tau;
+        B[e] = b;
+      }
+    }
+  if (u0coef)
+    for (int k = 0; k < n; k++) u0coef[k] = (k == 0) ? 1.0 / tau : 0.0;
+  return PD_OK;
+}
+
+pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shifts,
+                         const double *V, const double *Vinv, const double *B,
+                         const double *u0coef, const double *omega, const pd_config *cfg_in,
+                         void *stream) {
+  if (!out) return PD_ERR_ARG;
+  *out = nullptr;
+  pd_config cfg;
+  if (cfg_in) cfg = *cfg_in;
+  else pd_config_default(&cfg);
+  if (!is_pow2m1(N) || !shifts || n < 1 || n > kMaxShifts) return PD_ERR_ARG;
+  if (!(std::fabs(h * (N + 1) - 1.0) <= 1e-12)) return PD_ERR_ARG;
+  if ((V == nullptr) != (Vinv == nullptr)) return PD_ERR_ARG;
+  if (!(cfg.coarsest_n == 1 || cfg.coarsest_n == 3 || cfg.coarsest_n == 7 || cfg.coarsest_n == 15))
+    return PD_ERR_ARG;
+  if (N < cfg.coarsest_n || cfg.cycle_gamma < 1 || cfg.cycle_gamma > 2 || cfg.nu1 < 0 ||
+      cfg.nu2 < 0 || cfg.nu1 + cfg.nu2 < 1 || cfg.nu1 > 8 || cfg.nu2 > 8 || cfg.maxit < 0 ||
+      cfg.maxit > 100000 || !(cfg.tol >= 0) || cfg.omega_mode < 0 || cfg.omega_mode > 2 ||
+      cfg.precision < 0 || cfg.precision > 1 || cfg.smoother < 0 || cfg.smoother > 1 ||
+      !(cfg.inner_tol >= 0) || cfg.max_refine < 1)
+    return PD_ERR_ARG;
+  if (cfg.omega_mode == 2 && !omega) return PD_ERR_ARG;
+  if (cfg.precision == 1 && (!B || !V)) return PD_ERR_ARG;
+  for (int k = 0; k < 2 * n; k++)
+    if (!std::isfinite(shifts[k])) return PD_ERR_ARG;
+  pd_ctx *c = new (std::nothrow) pd_ctx();
+  if (!c) return PD_ERR_NOMEM;
+  c->N = N;
+  c->n = n;
+  c->cfg = cfg;
+  int Nl = N;
+  c->Ns.push_back(Nl);
+  while (Nl > cfg.coarsest_n) {
+    Nl = (Nl - 1) / 2;
+    c->Ns.push_back(Nl);
+  }
+  c->L = (int)c->Ns.size();
+  if (c->L > kMaxLevels) {
+    delete c;
+    return PD_ERR_ARG;
+  }
+  c->shifts.assign(shifts, shifts + 2 * n);
+  c->have_V = V != nullptr;
+  if (V) {
+    c->V.assign(V, V + 2 * (size_t)n * n);
+    c->Vinv.assign(Vinv, Vinv + 2 * (size_t)n * n);
+  }
+  c->have_B = B != nullptr;
+  if (B) c->B.assign(B, B + (size_t)n * n);
+  c->u0coef.assign(n, 0.0);
+  if (u0coef) c->u0coef.assign(u0coef, u0coef + n);
+  // relaxation parameters per shift and level
+  c->omega.assign((size_t)n * c->L, 0.0);
+  for (int j = 0; j < n; j++)
+    for (int l = 0; l < c->L; l++) {
+      double w;
+      if (cfg.omega_mode == 2) w = omega[(size_t)j * c->L + l];
+      else if (cfg.omega_mode == 0) w = cfg.smoother == 1 ? 0.8 : 24.0 / 25.0;
+      else {
+        const double hh = 1.0 / (c->Ns[l] + 1);
+        w = lfa_omega_opt(shifts[2 * j] * hh * hh, shifts[2 * j + 1] * hh * hh, cfg.smoother);
+      }
+      c->omega[(size_t)j * c->L + l] = w;
+    }
+  // plan of the coarse levels run inside one CTA per shift
+  c->plan.L = c->L;
+  for (int l = 0; l < c->L; l++) c->plan.Ns[l] = c->Ns[l];
+  c->plan.gamma = cfg.cycle_gamma;
+  c->plan.nu1 = cfg.nu1;
+  c->plan.nu2 = cfg.nu2;
+  c->plan.jacobi = cfg.smoother == 1;
+  const int cap = cfg.precision == 0 ? 31 : 63;
+  c->lc = c->L - 1;
+  for (int l = c->L - 1; l >= 0; l--) {
+    const size_t bytes = cfg.precision == 0 ? coarse_smem_bytes<double>(c->plan, l)
+                                            : coarse_smem_bytes<float>(c->plan, l);
+    if (bytes <= kCoarseSmemLimit && c->Ns[l] <= cap) c->lc = l;
+    else break;
+  }
+  c->plan.lc = c->lc;
+  try {
+    c->stream = (cudaStream_t)stream;
+    for (int k = 0; k < 2; k++) ck(c, cudaEventCreateWithFlags(&c->ev[k], cudaEventDisableTiming));
+    ck(c, cudaMallocHost(&c->h_pinned, 4 * sizeof(int)));
+    ck(c, cudaMallocHost(&c->h_iters, n * sizeof(int)));
+    ck(c, cudaMallocHost(&c->h_relres, n * sizeof(double)));
+    ck(c, cudaMallocHost(&c->h_part, 2 * allatonce_blocks() * sizeof(double)));
+    // solve state
+    const int tiles = smooth_tiles(N);
+    c->st.max_tiles = tiles;
+    c->st.active = dalloc<int *>(c, n * sizeof(int));
+    c->st.iters = dalloc<int *>(c, n * sizeof(int));
+    c->st.final_buf = dalloc<int *>(c, n * sizeof(int));
+    c->st.nactive = dalloc<int *>(c, 2 * sizeof(int));
+    c->st.flags = c->st.nactive + 1;
+    c->st.bn2 = dalloc<double *>(c, n * sizeof(double));
+    c->st.relres = dalloc<double *>(c, n * sizeof(double));
+    c->st.partials = dalloc<double *>(c, (size_t)n * tiles * sizeof(double));
+    c->d_u0coef = dalloc<double *>(c, n * sizeof(double));
+    ck(c, cudaMemcpy(c->d_u0coef, c->u0coef.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    c->d_part = dalloc<double *>(c, 2 * allatonce_blocks() * sizeof(double));
+    c->d_imag = dalloc<unsigned long long *>(c, sizeof(unsigned long long));
+    if (B) {
+      std::vector<int> ptr(n + 1, 0), col;
+      std::vector<double> val;
+      for (int k = 0; k < n; k++) {
+        for (int l = 0; l < n; l++)
+          if (B[(size_t)k * n + l] != 0.0) {
+            col.push_back(l);
+            val.push_back(B[(size_t)k * n + l]);
+          }
+        ptr[k + 1] = (int)col.size();
+      }
+      c->d_Bptr = dalloc<int *>(c, ptr.size() * sizeof(int));
+      c->d_Bcol = dalloc<int *>(c, std::max<size_t>(col.size(), 1) * sizeof(int));
+      c->d_Bval = dalloc<double *>(c, std::max<size_t>(val.size(), 1) * sizeof(double));
+      ck(c, cudaMemcpy(c->d_Bptr, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice));
+      if (!col.empty()) {
+        ck(c, cudaMemcpy(c->d_Bcol, col.data(), col.size() * sizeof(int), cudaMemcpyHostToDevice));
+        ck(c, cudaMemcpy(c->d_Bval, val.data(), val.size() * sizeof(double), cudaMemcpyHostToDevice));
+      }
+    }
+    if (cfg.precision == 0) {
+      alloc_prec<double>(c);
+    } else {
+      alloc_prec<float>(c);
+      c->d_r = dalloc<double *>(c, (size_t)n * N * N * sizeof(double));
+    }
+    ck(c, cudaDeviceSynchronize());
+  } catch (const CudaFail &) {
+    free_ctx(c);
+    return PD_ERR_CUDA;
+  } catch (const std::bad_alloc &) {
+    free_ctx(c);
+    return PD_ERR_NOMEM;
+  } catch (pd_status s) {
+    free_ctx(c);
+    return s;
+  }
+  *out = c;
+  return PD_OK;
+}
+
+int pd_num_levels(const pd_ctx *c) { return c ? c->L : 0; }
+
+pd_status pd_get_omega(const pd_ctx *c, double *h_omega) {
+  if (!c || !h_omega) return PD_ERR_ARG;
+  std::memcpy(h_omega, c->omega.data(), c->omega.size() * sizeof(double));
+  return PD_OK;
+}
+
+pd_status mg_vcycle(pd_ctx *c, int level, void *z, const void *b) {
+  if (!c || !z || !b || level < 0 || level >= c->L) return PD_ERR_ARG;
+  PD_TRY(c, {
+    const int N = c->Ns[level], n = c->n;
+    const double h = hl(c, level);
+    if (c->cfg.precision == 0) {
+      LevelBufs &B = c->p64.lv[level];
+      launch_copy_scale<double>(c->stream, N, n, view(B.b, N, B.P), uview(b, N), h * h);
+      launch_copy_scale<double>(c->stream, N, n, view(B.z[0], N, B.P), uview(z, N), 1.0);
+      ck_launch(c, 2);
+      c->cur[level] = 0;
+      run_cycle<double>(c, level, false, false, nullptr, 0.0, 0);
+      launch_copy_scale<double>(c->stream, N, n, uview(z, N), view(B.z[c->cur[level]], N, B.P), 1.0);
+    } else {
+      LevelBufs &B = c->p32.lv[level];
+      launch_copy_scale<float>(c->stream, N, n, view(B.b, N, B.P), uview(b, N), (float)(h * h));
+      launch_copy_scale<float>(c->stream, N, n, view(B.z[0], N, B.P), uview(z, N), 1.0f);
+      ck_launch(c, 2);
+      c->cur[level] = 0;
+      run_cycle<float>(c, level, false, false, nullptr, 0.0, 0);
+      launch_copy_scale<float>(c->stream, N, n, uview(z, N), view(B.z[c->cur[level]], N, B.P), 1.0f);
+    }
+    ck_launch(c);
+    return PD_OK;
+  })
+}
+
+pd_status shifted_solve_batched(pd_ctx *c, void *z, const void *b, int *h_iters, double *h_relres) {
+  if (!c || !z || !b) return PD_ERR_ARG;
+  PD_TRY(c, {
+    const int N = c->N, n = c->n;
+    const double h = hl(c, 0);
+    pd_status rc;
+    if (c->cfg.precision == 0) {
+      LevelBufs &B = c->p64.lv[0];
+      launch_copy_scale<double>(c->stream, N, n, view(B.b, N, B.P), uview(b, N), h * h);
+      ck_launch(c);
+      rc = solve_levels<double>(c, c->cfg.tol, c->cfg.maxit);
+      launch_gather_final<double>(c->stream, N, n, uview(z, N), view(B.z[0], N, B.P),
+                                  view(B.z[1], N, B.P), c->st.final_buf);
+    } else {
+      LevelBufs &B = c->p32.lv[0];
+      launch_copy_scale<float>(c->stream, N, n, view(B.b, N, B.P), uview(b, N), (float)(h * h));
+      ck_launch(c);
+      rc = solve_levels<float>(c, c->cfg.tol, c->cfg.maxit);
+      launch_gather_final<float>(c->stream, N, n, uview(z, N), view(B.z[0], N, B.P),
+                                 view(B.z[1], N, B.P), c->st.final_buf);
+    }
+    ck_launch(c);
+    ck(c, cudaStreamSynchronize(c->stream));
+    for (int j = 0; j < n; j++) {
+      if (h_iters) h_iters[j] = c->h_iters[j];
+      if (h_relres) h_relres[j] = c->h_relres[j];
+    }
+    return rc;
+  })
+}
+
+pd_status paradiag_solve(pd_ctx *c, double *u, const double *f, const double *u0, int *h_iters,
+                         double *h_relres, double *h_stats) {
+  if (!c || !u || !f) return PD_ERR_ARG;
+  if (!c->have_V) return PD_ERR_STATE;
+  PD_TRY(c, {
+    if (c->cfg.precision == 0) return paradiag_impl<double>(c, u, f, u0, h_iters, h_relres, h_stats);
+    return paradiag_impl<float>(c, u, f, u0, h_iters, h_relres, h_stats);
+  })
+}
+
+pd_status paradiag_solve_host(pd_ctx *c, double *h_u, const double *h_f, const double *h_u0,
+                              int *h_iters, double *h_relres, double *h_stats) {
+  if (!c || !h_u || !h_f) return PD_ERR_ARG;
+  if (!c->have_V) return PD_ERR_STATE;
+  PD_TRY(c, {
+    const size_t bytes = (size_t)c->n * c->N * c->N * sizeof(double);
+    const size_t b0 = (size_t)c->N * c->N * sizeof(double);
+    if (!c->d_stage_f) {
+      c->d_stage_f = dalloc<double *>(c, bytes);
+      c->d_stage_u = dalloc<double *>(c, bytes);
+      c->d_stage_u0 = dalloc<double *>(c, b0);
+    }
+    ck(c, cudaMemcpyAsync(c->d_stage_f, h_f, bytes, cudaMemcpyHostToDevice, c->stream));
+    if (h_u0) ck(c, cudaMemcpyAsync(c->d_stage_u0, h_u0, b0, cudaMemcpyHostToDevice, c->stream));
+    pd_status rc = paradiag_solve(c, c->d_stage_u, c->d_stage_f, h_u0 ? c->d_stage_u0 : nullptr,
+                                  h_iters, h_relres, h_stats);
+    if (rc == PD_ERR_CUDA) return rc;
+    ck(c, cudaMemcpyAsync(h_u, c->d_stage_u, bytes, cudaMemcpyDeviceToHost, c->stream));
+    ck(c, cudaStreamSynchronize(c->stream));
+    return rc;
+  })
+}
+
+pd_status pd_smooth(pd_ctx *c, int level, void *zout, const void *zin, const void *b) {
+  if (!c || !zout || !zin || !b || zout == zin || level < 0 || level >= c->L) return PD_ERR_ARG;
+  PD_TRY(c, {
+    const int N = c->Ns[level], n = c->n;
+    const double h = hl(c, level);
+    const bool jac = c->cfg.smoother == 1;
+    if (c->cfg.precision == 0)
+      launch_smooth<double>(c->stream, N, n, uview(zin, N), uview(zout, N), uview(b, N), h * h,
+                            c->p64.coef + (size_t)level * n, nullptr, false, jac, nullptr, 0);
+    else
+      launch_smooth<float>(c->stream, N, n, uview(zin, N), uview(zout, N), uview(b, N),
+                           (float)(h * h), c->p32.coef + (size_t)level * n, nullptr, false, jac,
+                           nullptr, 0);
+    ck_launch(c);
+    return PD_OK;
+  })
+}
+
+pd_status pd_residual_restrict(pd_ctx *c, int level, void *bc, const void *z, const void *b) {
+  if (!c || !bc || !z || !b || level < 0 || level >= c->L - 1) return PD_ERR_ARG;
+  PD_TRY(c, {
+    const int N = c->Ns[level], Nc = c->Ns[level + 1], n = c->n;
+    const double h = hl(c, level), hc = hl(c, level + 1);
+    if (c->cfg.precision == 0)
+      launch_residual_restrict<double>(c->stream, N, n, uview(z, N), uview(b, N), h * h,
+                                       uview(bc, Nc), 1.0 / (hc * hc),
+                                       c->p64.coef + (size_t)level * n, nullptr, false);
+    else
+      launch_residual_restrict<float>(c->stream, N, n, uview(z, N), uview(b, N), (float)(h * h),
+                                      uview(bc, Nc), (float)(1.0 / (hc * hc)),
+                                      c->p32.coef + (size_t)level * n, nullptr, false);
+    ck_launch(c);
+    return PD_OK;
+  })
+}
+
+pd_status pd_prolong_add(pd_ctx *c, int level, void *z, const void *ec) {
+  if (!c || !z || !ec || level < 0 || level >= c->L - 1) return PD_ERR_ARG;
+  PD_TRY(c, {
+    const int N = c->Ns[level], Nc = c->Ns[level + 1], n = c->n;
+    if (c->cfg.precision == 0)
+      launch_prolong_add<double>(c->stream, N, n, uview(z, N), uview(ec, Nc), nullptr);
+    else
+      launch_prolong_add<float>(c->stream, N, n, uview(z, N), uview(ec, Nc), nullptr);
+    ck_launch(c);
+    return PD_OK;
+  })
+}
+
+pd_status pd_coarse_solve(pd_ctx *c, void *z, const void *b) {
+  if (!c || !z || !b) return PD_ERR_ARG;
+  PD_TRY(c, {
+    const int l = c->L - 1, N = c->Ns[l], n = c->n;
+    const double h = hl(c, l);
+    if (c->cfg.precision == 0)
+      launch_coarse<double>(c->stream, c->plan, l, n, uview(b, N), h * h, uview(z, N), c->p64.coef,
+                            c->p64.cinv, nullptr, 1, 0, 0, 0.0, 0, c->st);
+    else
+      launch_coarse<float>(c->stream, c->plan, l, n, uview(b, N), (float)(h * h), uview(z, N),
+                           c->p32.coef, c->p32.cinv, nullptr, 1, 0, 0, 0.0, 0, c->st);
+    ck_launch(c);
+    return PD_OK;
+  })
+}
+
+pd_status pd_transform_forward(pd_ctx *c, void *g, const double *f, const double *u0) {
+  if (!c || !g || !f) return PD_ERR_ARG;
+  if (!c->have_V) return PD_ERR_STATE;
+  PD_TRY(c, {
+    if (c->cfg.precision == 0)
+      launch_transform_forward<double>(c->stream, c->N, c->n, uview(g, c->N), f, u0, c->d_u0coef,
+                                       c->p64.Wf, 1.0);
+    else
+      launch_transform_forward<float>(c->stream, c->N, c->n, uview(g, c->N), f, u0, c->d_u0coef,
+                                      c->p32.Wf, 1.0);
+    ck_launch(c);
+    return PD_OK;
+  })
+}
+
+pd_status pd_transform_inverse(pd_ctx *c, double *u, const void *z, int accumulate) {
+  if (!c || !u || !z) return PD_ERR_ARG;
+  if (!c->have_V) return PD_ERR_STATE;
+  PD_TRY(c, {
+    const View zv = uview(z, c->N);
+    if (c->cfg.precision == 0)
+      launch_transform_inverse<double>(c->stream, c->N, c->n, u, zv, zv, nullptr, c->p64.Wi,
+                                       accumulate != 0, false, nullptr);
+    else
+      launch_transform_inverse<float>(c->stream, c->N, c->n, u, zv, zv, nullptr, c->p32.Wi,
+                                      accumulate != 0, false, nullptr);
+    ck_launch(c);
+    return PD_OK;
+  })
+}
+
+pd_status pd_allatonce_residual(pd_ctx *c, double *r, const double *u, const double *f,
+                                const double *u0, double *h_norms) {
+  if (!c || !u || !f) return PD_ERR_ARG;
+  if (!c->have_B) return PD_ERR_STATE;
+  PD_TRY(c, {
+    double rn, fn;
+    allatonce_norms(c, r, u, f, u0, &rn, &fn);
+    if (h_norms) {
+      h_norms[0] = rn;
+      h_norms[1] = fn;
+    }
+    return PD_OK;
+  })
+}
+
+pd_status pd_synchronize(pd_ctx *c) {
+  if (!c) return PD_ERR_ARG;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    c->err = cudaGetErrorString(e);
+    return PD_ERR_CUDA;
+  }
+  return PD_OK;
+}
+
+long long pd_launch_count(const pd_ctx *c) { return c ? c->launches : 0; }
+
+pd_status paradiag_destroy(pd_ctx *c) {
+  if (!c) return PD_ERR_ARG;
+  free_ctx(c);
+  return PD_OK;
+}
+
+const char *pd_status_str(pd_status s) {
+  switch (s) {
+    case PD_OK: return "ok";
+    case PD_ERR_ARG: return "invalid argument";
+    case PD_ERR_CUDA: return "CUDA error";
+    case PD_ERR_NOMEM: return "out of memory";
+    case PD_ERR_NOCONV: return "tolerance not reached";
+    case PD_ERR_NAN: return "NaN or Inf in a residual";
+    case PD_ERR_SING: return "singular coarsest-grid matrix";
+    case PD_ERR_STATE: return "call not valid for this context";
+  }
+  return "unknown status";
+}
+
+const char *pd_last_error(const pd_ctx *c) { return c ? c->err.c_str() : ""; }
+
+}  // extern "C"

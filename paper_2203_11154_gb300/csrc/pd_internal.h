@@ -1,0 +1,119 @@
+// Internal declarations shared by the translation units of libparadiag.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/paradiag.h"
+
+namespace pd {
+
+constexpr int kMaxLevels = 16;
+constexpr int kMaxShifts = 128;
+
+template <typename T> struct Cx;
+template <> struct Cx<double> { using type = double2; };
+template <> struct Cx<float> { using type = float2; };
+
+// A strided grid array: element (shift j, row i, col c) at p[j*plane + i*pitch + c].
+struct View {
+  void *p;
+  long long pitch;
+  long long plane;
+};
+
+// Smoother coefficients of one (level, shift) in the h^2-scaled form used by every
+// kernel: with rt = h^2 (b - L z) = h^2 b - d z + (sum of the 4 neighbours of z),
+//   Vanka (eq. (6)):  z += ca rt + cb (sum of 4 edge neighbours of rt)
+//                             + cc (sum of 4 corner neighbours of rt),
+//   with d = 4 + eta, ca = omega a, cb = omega b / 2, cc = omega c / 4;
+//   Jacobi: ca = omega / (4 + eta), cb = cc = 0.
+template <typename T> struct Coef {
+  typename Cx<T>::type d, ca, cb, cc;
+};
+
+// Per-shift state of a batched solve, device resident.
+struct SolveState {
+  int *active;        // [n] 1 while the shift still iterates
+  int *iters;         // [n] cycles done
+  int *final_buf;     // [n] ping-pong index holding the answer of level 0
+  int *nactive;       // [1] number of active shifts
+  int *flags;         // [1] bit 0: NaN/Inf seen
+  double *bn2;        // [n] ||b_j||^2 (scaled)
+  double *relres;     // [n] last relative residual
+  double *partials;   // [n][max_tiles] per-CTA squared residual sums
+  int max_tiles;
+};
+
+// ---- multigrid kernels (mg_kernels.cu), T = double or float ----
+template <typename T>
+void launch_smooth(cudaStream_t s, int N, int n, View zin, View zout, View b, T bscale,
+                   const Coef<T> *coef, const int *active, bool z_zero, bool jacobi,
+                   double *partials, int part_stride);
+template <typename T>
+void launch_resnorm(cudaStream_t s, int N, int n, View z, View b, T bscale, const Coef<T> *coef,
+                    const int *active, bool z_zero, double *partials, int part_stride);
+int smooth_tiles(int N);
+void launch_reset_state(cudaStream_t s, int n, SolveState st);
+void launch_converge(cudaStream_t s, int n, int ntiles, SolveState st, double tol, int maxit,
+                     int cur_buf);
+template <typename T>
+void launch_residual_restrict(cudaStream_t s, int Nf, int n, View z, View b, T bscale, View bc,
+                              T oscale, const Coef<T> *coef, const int *active, bool z_zero);
+template <typename T>
+void launch_prolong_add(cudaStream_t s, int Nf, int n, View z, View ec, const int *active);
+
+struct CoarsePlan {
+  int lc;                   // first level handled inside one CTA per shift
+  int L;                    // total levels
+  int Ns[kMaxLevels];       // interior sizes per level
+  int gamma, nu1, nu2;
+  int jacobi;
+};
+template <typename T>
+size_t coarse_smem_bytes(const CoarsePlan &plan, int start);
+template <typename T>
+cudaError_t prepare_coarse(size_t smem);
+// Levels start..L-1 in one CTA per shift; see k_coarse for the two modes.
+template <typename T>
+void launch_coarse(cudaStream_t s, const CoarsePlan &plan, int start, int n, View b, T bscale,
+                   View z, const Coef<T> *coef /*[L][n]*/, const typename Cx<T>::type *cinv,
+                   const int *active, int ncycles, int load_z, int solve_mode, double tol,
+                   int maxit, SolveState st);
+template <typename T>
+void launch_copy_scale(cudaStream_t s, int N, int n, View dst, View src, T scale);
+template <typename T>
+void launch_gather_final(cudaStream_t s, int N, int n, View dst, View z0, View z1,
+                         const int *final_buf);
+
+// ---- transforms (transforms.cu) ----
+template <typename T>
+cudaError_t prepare_transforms(int n);
+// g (view, working type) = scale * W fhat, fhat_k = f_k + u0coef[k] u0 (f, u0 double)
+template <typename T>
+void launch_transform_forward(cudaStream_t s, int N, int n, View g, const double *f,
+                              const double *u0, const double *u0coef,
+                              const typename Cx<T>::type *W, double scale);
+// u (double, [n][N][N]) = or += Re(W z); z_j read from z1 where final_buf[j] != 0
+// (final_buf may be NULL: all from z0); imag_check: atomicMax of max|Im| bits
+template <typename T>
+void launch_transform_inverse(cudaStream_t s, int N, int n, double *u, View z0, View z1,
+                              const int *final_buf, const typename Cx<T>::type *W,
+                              bool accumulate, bool imag_check, unsigned long long *imag_max_bits);
+// r = fhat - (B kron I + I kron A) u in FP64 (r may be NULL); part[2b], part[2b+1] =
+// per-CTA sums of r^2 and fhat^2 over allatonce_blocks() CTAs
+int allatonce_blocks();
+void launch_allatonce_residual(cudaStream_t s, int N, int n, double *r, const double *u,
+                               const double *f, const double *u0, const double *u0coef,
+                               const int *Bptr, const int *Bcol, const double *Bval,
+                               double *part);
+
+// ---- host-side setup (setup.cpp) ----
+void vanka_abc(double er, double ei, double out[6]);
+double lfa_omega_opt(double er, double ei, int jacobi);
+int invert_dense(int m, std::vector<double> &A /* 2*m*m, complex row-major */);
+
+}  // namespace pd

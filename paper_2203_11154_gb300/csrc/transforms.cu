@@ -1,0 +1,236 @@
+// Time-direction transforms of eq. (1), (V^{-1} kron I_h) and (V kron I_h), applied to
+// every grid point, and the FP64 residual of the all-at-once system (1).
+//
+// Layout: time/shift index outermost, [n][N][N]; one CTA owns kPts consecutive grid
+// points, stages their n values in shared memory and forms all n outputs for them.
+#include "cplx.cuh"
+#include "pd_internal.h"
+
+namespace pd {
+
+namespace {
+
+constexpr int kPts = 32, kGroups = 4, kThreads = kPts * kGroups;
+
+template <typename C>
+__device__ __forceinline__ C ldv(const View &v, int j, long long i, long long c) {
+  return reinterpret_cast<const C *>(v.p)[j * v.plane + i * v.pitch + c];
+}
+template <typename C>
+__device__ __forceinline__ void stv(const View &v, int j, long long i, long long c, C x) {
+  reinterpret_cast<C *>(v.p)[j * v.plane + i * v.pitch + c] = x;
+}
+
+// g_j = scale * sum_k W[j][k] fhat_k, fhat_k = f_k + u0coef[k] u0 (real input).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_transform_forward(int N, int n, View g, const double *__restrict__ f,
+                    const double *__restrict__ u0, const double *__restrict__ u0coef,
+                    const typename Cx<T>::type *__restrict__ W, T scale) {
+  using C = typename Cx<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *xs = reinterpret_cast<T *>(smem_raw);  // [n][kPts]
+  const long long m = (long long)N * N;
+  const long long x0 = (long long)blockIdx.x * kPts;
+  for (int t = threadIdx.x; t < n * kPts; t += kThreads) {
+    const int k = t / kPts, p = t - k * kPts;
+    const long long x = x0 + p;
+    double v = 0.0;
+    if (x < m) {
+      v = f[k * m + x];
+      if (u0) v += u0coef[k] * u0[x];
+    }
+    xs[t] = (T)v;
+  }
+  __syncthreads();
+  const int p = threadIdx.x % kPts, jg = threadIdx.x / kPts;
+  const long long x = x0 + p;
+  if (x >= m) return;
+  const int i = (int)(x / N), c = (int)(x - (long long)i * N);
+  for (int j = jg; j < n; j += kGroups) {
+    const C *w = W + (long long)j * n;
+    T re = 0, im = 0;
+    for (int k = 0; k < n; k++) {
+      const C wk = w[k];
+      const T xv = xs[k * kPts + p];
+      re = fmadd(wk.x, xv, re);
+      im = fmadd(wk.y, xv, im);
+    }
+    stv<C>(g, j, i, c, cx<C>(re * scale, im * scale));
+  }
+}
+
+// u_k (+)= Re sum_j W[k][j] z_j; with imag_check also max |Im sum_j W[k][j] z_j|.
+// z_j is read from z1 where final_buf[j] is set, else from z0.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_transform_inverse(int N, int n, double *__restrict__ u, View z0, View z1,
+                    const int *__restrict__ final_buf, const typename Cx<T>::type *__restrict__ W,
+                    int accumulate, int imag_check, unsigned long long *imag_bits) {
+  using C = typename Cx<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *zs = reinterpret_cast<C *>(smem_raw);  // [n][kPts]
+  __shared__ double red[kThreads / 32];
+  const long long m = (long long)N * N;
+  const long long x0 = (long long)blockIdx.x * kPts;
+  for (int t = threadIdx.x; t < n * kPts; t += kThreads) {
+    const int j = t / kPts, p = t - j * kPts;
+    const long long x = x0 + p;
+    C v = czero<C>();
+    if (x < m) {
+      const int i = (int)(x / N), c = (int)(x - (long long)i * N);
+      v = (final_buf && final_buf[j]) ? ldv<C>(z1, j, i, c) : ldv<C>(z0, j, i, c);
+    }
+    zs[t] = v;
+  }
+  __syncthreads();
+  const int p = threadIdx.x % kPts, kg = threadIdx.x / kPts;
+  const long long x = x0 + p;
+  double imax = 0.0;
+  if (x < m) {
+    for (int k = kg; k < n; k += kGroups) {
+      const C *w = W + (long long)k * n;
+      T re = 0, im = 0;
+      for (int j = 0; j < n; j++) {
+        const C wj = w[j];
+        const C zv = zs[j * kPts + p];
+        re = fmadd(wj.x, zv.x, re);
+        re = fmadd(-wj.y, zv.y, re);
+        if (imag_check) {
+          im = fmadd(wj.x, zv.y, im);
+          im = fmadd(wj.y, zv.x, im);
+        }
+      }
+      double out = (double)re;
+      if (accumulate) out += u[k * m + x];
+      u[k * m + x] = out;
+      imax = fmax(imax, fabs((double)im));
+    }
+  }
+  if (imag_check) {
+    for (int o = 16; o > 0; o >>= 1) imax = fmax(imax, __shfl_down_sync(0xffffffffu, imax, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = imax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double mx = 0.0;
+      for (int k = 0; k < kThreads / 32; k++) mx = fmax(mx, red[k]);
+      atomicMax(imag_bits, (unsigned long long)__double_as_longlong(mx));
+    }
+  }
+}
+
+constexpr int kResThreads = 256;
+
+// r_k = fhat_k - sum_l B[k][l] u_l - A u_k (eq. (1)), A = (1/h^2) 5-point, FP64.
+// part[2b], part[2b+1]: this CTA's sums of r^2 and fhat^2 (fixed grid, fixed order).
+__global__ void __launch_bounds__(kResThreads)
+k_allatonce_residual(int N, int n, double *__restrict__ r, const double *__restrict__ u,
+                     const double *__restrict__ f, const double *__restrict__ u0,
+                     const double *__restrict__ u0coef, const int *__restrict__ Bptr,
+                     const int *__restrict__ Bcol, const double *__restrict__ Bval, double ih2,
+                     double *__restrict__ part) {
+  __shared__ double red[2][kResThreads / 32];
+  const long long m = (long long)N * N, total = m * n;
+  double ar = 0.0, af = 0.0;
+  for (long long q = (long long)blockIdx.x * kResThreads + threadIdx.x; q < total;
+       q += (long long)gridDim.x * kResThreads) {
+    const int k = (int)(q / m);
+    const long long x = q - (long long)k * m;
+    const int i = (int)(x / N), c = (int)(x - (long long)i * N);
+    double fh = f[q];
+    if (u0) fh += u0coef[k] * u0[x];
+    double bu = 0.0;
+    for (int e = Bptr[k]; e < Bptr[k + 1]; e++) bu += Bval[e] * u[(long long)Bcol[e] * m + x];
+    const double *uk = u + (long long)k * m;
+    double nb = 0.0;
+    if (i > 0) nb += uk[x - N];
+    if (i < N - 1) nb += uk[x + N];
+    if (c > 0) nb += uk[x - 1];
+    if (c < N - 1) nb += uk[x + 1];
+    const double rv = fh - bu - ih2 * (4.0 * uk[x] - nb);
+    if (r) r[q] = rv;
+    ar += rv * rv;
+    af += fh * fh;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ar += __shfl_down_sync(0xffffffffu, ar, o);
+    af += __shfl_down_sync(0xffffffffu, af, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = ar;
+    red[1][threadIdx.x >> 5] = af;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int w = 0; w < kResThreads / 32; w++) {
+      s0 += red[0][w];
+      s1 += red[1][w];
+    }
+    part[2 * blockIdx.x] = s0;
+    part[2 * blockIdx.x + 1] = s1;
+  }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t prepare_transforms(int n) {
+  using C = typename Cx<T>::type;
+  cudaError_t e = cudaFuncSetAttribute(k_transform_forward<T>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(n * kPts * sizeof(T)));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_transform_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(n * kPts * sizeof(C)));
+}
+
+template <typename T>
+void launch_transform_forward(cudaStream_t s, int N, int n, View g, const double *f,
+                              const double *u0, const double *u0coef,
+                              const typename Cx<T>::type *W, double scale) {
+  const long long m = (long long)N * N;
+  const unsigned blocks = (unsigned)((m + kPts - 1) / kPts);
+  k_transform_forward<T><<<blocks, kThreads, n * kPts * sizeof(T), s>>>(N, n, g, f, u0, u0coef, W,
+                                                                        (T)scale);
+}
+
+template <typename T>
+void launch_transform_inverse(cudaStream_t s, int N, int n, double *u, View z0, View z1,
+                              const int *final_buf, const typename Cx<T>::type *W,
+                              bool accumulate, bool imag_check,
+                              unsigned long long *imag_max_bits) {
+  using C = typename Cx<T>::type;
+  const long long m = (long long)N * N;
+  const unsigned blocks = (unsigned)((m + kPts - 1) / kPts);
+  k_transform_inverse<T><<<blocks, kThreads, n * kPts * sizeof(C), s>>>(
+      N, n, u, z0, z1, final_buf, W, accumulate ? 1 : 0, imag_check ? 1 : 0, imag_max_bits);
+}
+
+int allatonce_blocks() { return 4 * 152; }
+
+void launch_allatonce_residual(cudaStream_t s, int N, int n, double *r, const double *u,
+                               const double *f, const double *u0, const double *u0coef,
+                               const int *Bptr, const int *Bcol, const double *Bval,
+                               double *part) {
+  const double h = 1.0 / (N + 1);
+  k_allatonce_residual<<<allatonce_blocks(), kResThreads, 0, s>>>(
+      N, n, r, u, f, u0, u0coef, Bptr, Bcol, Bval, 1.0 / (h * h), part);
+}
+
+template cudaError_t prepare_transforms<double>(int);
+template cudaError_t prepare_transforms<float>(int);
+template void launch_transform_forward<double>(cudaStream_t, int, int, View, const double *,
+                                               const double *, const double *, const double2 *,
+                                               double);
+template void launch_transform_forward<float>(cudaStream_t, int, int, View, const double *,
+                                              const double *, const double *, const float2 *,
+                                              double);
+template void launch_transform_inverse<double>(cudaStream_t, int, int, double *, View, View,
+                                               const int *, const double2 *, bool, bool,
+                                               unsigned long long *);
+template void launch_transform_inverse<float>(cudaStream_t, int, int, double *, View, View,
+                                              const int *, const float2 *, bool, bool,
+                                              unsigned long long *);
+
+}  // namespace pd

@@ -1,0 +1,81 @@
+"""The C-ABI library builds, loads and exports every entry point of include/paradiag.h;
+host-only entry points behave (no GPU needed)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import core
+from paper_2203_11154_gb300 import api, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    with open(os.path.join(ROOT, "include", "paradiag.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = [m for m in re.findall(r"\b([a-z_][a-z0-9_]*)\s*\(", text)
+             if m.startswith(("pd_", "paradiag_", "mg_", "shifted_"))]
+    return sorted(set(names))
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = build.build()
+    L = C.CDLL(path)
+    names = declared_functions()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(L, name), name
+    assert sorted(api.EXPORTS) == names
+
+
+def test_config_defaults():
+    c = api.config()
+    assert (c.cycle_gamma, c.nu1, c.nu2, c.coarsest_n, c.maxit) == (1, 1, 1, 3, 100)
+    assert c.tol == 1e-10 and c.omega_mode == 1 and c.precision == 0 and c.smoother == 0
+
+
+def test_alpha_circulant_matches_oracle():
+    for n, tau, alpha in [(16, 1 / 16, 1e-2), (64, 1 / 64, 1e-3), (5, 0.3, 0.5)]:
+        B, sh, V, Vi, c0 = api.pd_alpha_circulant(n, tau, alpha)
+        lam, Vo, Vio = core.alpha_circulant(n, tau, alpha)
+        assert np.allclose(sh, lam, rtol=1e-14, atol=1e-12)
+        assert np.allclose(V, Vo, rtol=1e-13, atol=1e-13)
+        assert np.allclose(Vi, Vio, rtol=1e-13, atol=1e-16)
+        Cm = np.eye(n, k=-1)
+        Cm[0, n - 1] = alpha
+        assert np.array_equal(B, (np.eye(n) - Cm) / tau)
+        assert c0[0] == 1 / tau and not np.any(c0[1:])
+
+
+def test_setup_rejects_bad_arguments_before_touching_the_gpu():
+    L = api.lib()
+    h = C.c_void_p()
+    sh = np.zeros(8)
+    cfg = api.config()
+    p = sh.ctypes.data_as(C.c_void_p)
+    # N not 2^k - 1, wrong h, n out of range, missing shifts, bad cycle options
+    assert L.paradiag_setup(C.byref(h), 10, 1 / 11, 4, p, None, None, None, None, None, C.byref(cfg), None) == 1
+    assert L.paradiag_setup(C.byref(h), 7, 0.1, 4, p, None, None, None, None, None, C.byref(cfg), None) == 1
+    assert L.paradiag_setup(C.byref(h), 7, 1 / 8, 0, p, None, None, None, None, None, C.byref(cfg), None) == 1
+    assert L.paradiag_setup(C.byref(h), 7, 1 / 8, 4, None, None, None, None, None, None, C.byref(cfg), None) == 1
+    bad = api.config(cycle_gamma=3)
+    assert L.paradiag_setup(C.byref(h), 7, 1 / 8, 4, p, None, None, None, None, None, C.byref(bad), None) == 1
+    bad = api.config(coarsest_n=5)
+    assert L.paradiag_setup(C.byref(h), 7, 1 / 8, 4, p, None, None, None, None, None, C.byref(bad), None) == 1
+    bad = api.config(precision=1)  # needs B and V
+    assert L.paradiag_setup(C.byref(h), 7, 1 / 8, 4, p, None, None, None, None, None, C.byref(bad), None) == 1
+    nan = np.array([np.nan] * 8)
+    assert L.paradiag_setup(C.byref(h), 7, 1 / 8, 4, nan.ctypes.data_as(C.c_void_p), None, None, None,
+                            None, None, C.byref(cfg), None) == 1
+    assert h.value is None
+
+
+def test_status_strings():
+    L = api.lib()
+    for code in range(8):
+        assert L.pd_status_str(code)
+    assert L.pd_status_str(99) == b"unknown status"

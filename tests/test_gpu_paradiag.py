@@ -1,0 +1,129 @@
+"""GPU parity of the time transforms, the all-at-once residual and the whole ParaDIAG
+step (FP64 and the FP32 + FP64-refinement form) against the FP64 oracle."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import core, lfa  # noqa: E402
+from paper_2203_11154_gb300 import api, inputs  # noqa: E402
+
+
+def rel_per_vector(x, ref):
+    x = np.asarray(x).reshape(ref.shape[0], -1)
+    ref = ref.reshape(ref.shape[0], -1)
+    return np.max(np.linalg.norm(x - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), 1e-300))
+
+
+def dev(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def oracle_paradiag(N, n, tau, alpha, f, u0, omega_mode="lfa", tol=1e-10):
+    lam, V, Vinv = core.alpha_circulant(n, tau, alpha)
+    om = lfa.omega_table(lam, N, mode=omega_mode)
+    fhat = core.assemble_rhs(N, n, tau, f, u0)
+    u, im, iters, relres = core.paradiag_solve(N, lam, V, Vinv, om, fhat, tol=tol)
+    return u, fhat, iters, relres
+
+
+@pytest.mark.parametrize("N,n,alpha", [(15, 4, 1e-2), (63, 16, 1e-3), (127, 8, 1e-3)])
+def test_transforms_fp64(N, n, alpha):
+    rng = np.random.default_rng(N)
+    c = api.alpha_circulant_context(N, n, 1.0 / n, alpha)
+    lam, V, Vinv = core.alpha_circulant(n, 1.0 / n, alpha)
+    f = rng.uniform(-1, 1, (n, N, N))
+    u0 = inputs.sine_initial_value(N)
+    g = torch.empty(n, N, N, dtype=torch.complex128, device="cuda")
+    c.pd_transform_forward(g, dev(f), dev(u0))
+    fhat = core.assemble_rhs(N, n, 1.0 / n, f, u0)
+    ref = core.time_transform(Vinv, fhat.reshape(n, -1)).reshape(n, N, N)
+    assert rel_per_vector(host(g), ref) < 1e-13
+    z = rng.uniform(-1, 1, (n, N, N)) + 1j * rng.uniform(-1, 1, (n, N, N))
+    u = torch.full((n, N, N), 0.5, dtype=torch.float64, device="cuda")
+    c.pd_transform_inverse(u, dev(z, torch.complex128), accumulate=True)
+    ref = core.time_transform(V, z.reshape(n, -1)).real.reshape(n, N, N) + 0.5
+    assert rel_per_vector(host(u), ref) < 1e-13
+
+
+def test_allatonce_residual_fp64():
+    N, n, tau, alpha = 31, 8, 1 / 8, 1e-3
+    rng = np.random.default_rng(2)
+    c = api.alpha_circulant_context(N, n, tau, alpha)
+    u = rng.standard_normal((n, N, N))
+    f = rng.standard_normal((n, N, N))
+    u0 = rng.standard_normal((N, N))
+    r = torch.empty(n, N, N, dtype=torch.float64, device="cuda")
+    rn, fn = c.pd_allatonce_residual(r, dev(u), dev(f), dev(u0))
+    fhat = core.assemble_rhs(N, n, tau, f, u0)
+    rno, fno, ro = core.allatonce_residual(N, n, tau, alpha, u, fhat, want_r=True)
+    assert rel_per_vector(host(r), ro) < 1e-14 * 100
+    assert abs(rn - rno) < 1e-12 * rno and abs(fn - fno) < 1e-12 * fno
+
+
+@pytest.mark.parametrize("N,n,alpha", [(31, 4, 1e-2), (63, 16, 1e-3), (127, 8, 1e-3)])
+def test_paradiag_fp64(N, n, alpha):
+    tau = 1.0 / n
+    f, u0 = inputs.paradiag_problem(N, n, seed=1)
+    c = api.alpha_circulant_context(N, n, tau, alpha)
+    u = torch.empty(n, N, N, dtype=torch.float64, device="cuda")
+    out = c.paradiag_solve(u, dev(f), dev(u0))
+    uo, fhat, ito, rro = oracle_paradiag(N, n, tau, alpha, f, u0)
+    assert np.array_equal(out["iters"], ito)
+    assert np.all(out["relres"] <= 1e-10)
+    assert rel_per_vector(host(u), uo) < 1e-12
+    rn, fn = core.allatonce_residual(N, n, tau, alpha, host(u), fhat)
+    assert abs(out["relres_allatonce"] - rn / fn) <= 1e-3 * rn / fn
+    assert out["imag_max"] < 1e-10 * np.max(np.abs(uo))
+
+
+@pytest.mark.parametrize("N,n,alpha", [(63, 16, 1e-3), (127, 8, 1e-3), (255, 16, 1e-3)])
+def test_paradiag_precision_form(N, n, alpha):
+    """FP32 cycles inside FP64 refinement reach ||fhat - A u|| / ||fhat|| <= 1e-10 on eq. (1)."""
+    tau = 1.0 / n
+    f, u0 = inputs.paradiag_problem(N, n, seed=1)
+    c = api.alpha_circulant_context(N, n, tau, alpha, precision=1)
+    u = torch.empty(n, N, N, dtype=torch.float64, device="cuda")
+    out = c.paradiag_solve(u, dev(f), dev(u0))
+    uh = host(u)
+    fhat = core.assemble_rhs(N, n, tau, f, u0)
+    rn, fn = core.allatonce_residual(N, n, tau, alpha, uh, fhat)
+    assert rn / fn <= 1e-10 and out["relres_allatonce"] <= 1e-10
+    assert abs(out["relres_allatonce"] - rn / fn) <= 1e-3 * rn / fn
+    assert 1 <= out["refine_steps"] <= 8
+    uo, _, _, _ = oracle_paradiag(N, n, tau, alpha, f, u0, tol=1e-12)
+    assert rel_per_vector(uh, uo) < 1e-8
+
+
+def test_paradiag_host_api_matches_device():
+    N, n = 63, 8
+    f, u0 = inputs.paradiag_problem(N, n, seed=4)
+    c = api.alpha_circulant_context(N, n, 1.0 / n, 1e-3)
+    u = torch.empty(n, N, N, dtype=torch.float64, device="cuda")
+    out = c.paradiag_solve(u, dev(f), dev(u0))
+    uh = torch.empty(n, N, N, dtype=torch.float64).pin_memory()
+    fh = torch.from_numpy(f).pin_memory()
+    u0h = torch.from_numpy(u0).pin_memory()
+    out2 = c.paradiag_solve_host(uh, fh, u0h)
+    assert np.array_equal(uh.numpy(), host(u))
+    assert np.array_equal(out["iters"], out2["iters"])
+
+
+def test_paradiag_without_V_is_a_state_error():
+    c = api.Context(15, 2, [1.0, 2.0])
+    u = torch.empty(2, 15, 15, dtype=torch.float64, device="cuda")
+    with pytest.raises(api.PDError) as e:
+        c.paradiag_solve(u, u.clone())
+    assert e.value.status == "PD_ERR_STATE"
