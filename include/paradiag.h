@@ -200,6 +200,33 @@ pd_status pd_transform_inverse(pd_ctx *ctx, double *d_u, const void *d_z, int ac
 pd_status pd_allatonce_residual(pd_ctx *ctx, double *d_r, const double *d_u, const double *d_f,
                                 const double *d_u0, double *h_norms);
 
+/*
+ * Instrumentation (no counterpart in the paper).  While enabled, the context records a
+ * CUDA event pair on its stream around every kernel launch and attributes it to one of
+ * the classes below, together with the algorithmic bytes of the launch (each array
+ * element read or written once, counting only shifts that are still iterating).
+ * pd_profile_enable(ctx, 1) clears the totals; pd_profile_read synchronises and
+ * returns the totals of one class (any output pointer may be NULL).
+ */
+enum {
+    PD_KC_SMOOTH0 = 0,   /* smoothing steps on the finest grid */
+    PD_KC_RESTRICT0 = 1, /* residual + full weighting from the finest grid */
+    PD_KC_PROLONG0 = 2,  /* interpolation + correction on the finest grid */
+    PD_KC_SMOOTH_C = 3,  /* the same three on the other global-memory levels */
+    PD_KC_RESTRICT_C = 4,
+    PD_KC_PROLONG_C = 5,
+    PD_KC_COARSE = 6,    /* coarse levels and coarsest solve, one CTA per shift */
+    PD_KC_CONVERGE = 7,  /* per-shift convergence test */
+    PD_KC_FORWARD = 8,   /* (V^{-1} kron I_h) */
+    PD_KC_INVERSE = 9,   /* (V kron I_h) */
+    PD_KC_RESIDUAL = 10, /* FP64 residual of eq. (1) */
+    PD_KC_OTHER = 11,    /* copies, state reset */
+    PD_KC_COUNT = 12
+};
+pd_status pd_profile_enable(pd_ctx *ctx, int on);
+pd_status pd_profile_read(pd_ctx *ctx, int kclass, double *total_ms, long long *launches,
+                          double *alg_bytes);
+
 /* Waits for the context stream. */
 pd_status pd_synchronize(pd_ctx *ctx);
 

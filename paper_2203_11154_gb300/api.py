@@ -23,6 +23,9 @@ PD_STAT_CYCLES_MAX = 4
 PD_STAT_RELRES_SHIFT_MAX = 5
 PD_STATS_LEN = 8
 
+KERNEL_CLASSES = ["smooth0", "restrict0", "prolong0", "smooth_c", "restrict_c", "prolong_c",
+                  "coarse", "converge", "forward", "inverse", "residual", "other"]
+
 STATUS = {0: "PD_OK", 1: "PD_ERR_ARG", 2: "PD_ERR_CUDA", 3: "PD_ERR_NOMEM", 4: "PD_ERR_NOCONV",
           5: "PD_ERR_NAN", 6: "PD_ERR_SING", 7: "PD_ERR_STATE"}
 
@@ -30,7 +33,7 @@ EXPORTS = ["pd_config_default", "pd_alpha_circulant", "paradiag_setup", "pd_num_
            "pd_get_omega", "mg_vcycle", "shifted_solve_batched", "paradiag_solve",
            "paradiag_solve_host", "pd_smooth", "pd_residual_restrict", "pd_prolong_add",
            "pd_coarse_solve", "pd_transform_forward", "pd_transform_inverse",
-           "pd_allatonce_residual", "pd_synchronize", "pd_launch_count", "paradiag_destroy",
+           "pd_allatonce_residual", "pd_profile_enable", "pd_profile_read", "pd_synchronize", "pd_launch_count", "paradiag_destroy",
            "pd_status_str", "pd_last_error"]
 
 
@@ -82,6 +85,8 @@ def lib(path=None):
             "pd_transform_forward": (_I, [_P, _P, _P, _P]),
             "pd_transform_inverse": (_I, [_P, _P, _P, _I]),
             "pd_allatonce_residual": (_I, [_P, _P, _P, _P, _P, _P]),
+            "pd_profile_enable": (_I, [_P, _I]),
+            "pd_profile_read": (_I, [_P, _I, _P, _P, _P]),
             "pd_synchronize": (_I, [_P]),
             "pd_launch_count": (C.c_longlong, [_P]),
             "paradiag_destroy": (_I, [_P]),
@@ -198,6 +203,21 @@ class Context:
 
     def launch_count(self):
         return int(lib().pd_launch_count(self.h))
+
+    def profile_enable(self, on=True):
+        _check(lib().pd_profile_enable(self.h, int(bool(on))), "pd_profile_enable", self.h)
+
+    def profile_read(self):
+        """{class: (total_ms, launches, algorithmic_bytes)} since profile_enable."""
+        out = {}
+        for k, name in enumerate(KERNEL_CLASSES):
+            ms = C.c_double()
+            nl = C.c_longlong()
+            by = C.c_double()
+            _check(lib().pd_profile_read(self.h, k, C.byref(ms), C.byref(nl), C.byref(by)),
+                   "pd_profile_read", self.h)
+            out[name] = (ms.value, nl.value, by.value)
+        return out
 
     def destroy(self):
         if getattr(self, "h", None):

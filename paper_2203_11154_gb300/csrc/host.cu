@@ -63,6 +63,19 @@ struct pd_ctx {
   unsigned long long *d_imag = nullptr;
   double *d_stage_f = nullptr, *d_stage_u = nullptr, *d_stage_u0 = nullptr;
   long long launches = 0;
+  // instrumentation: event pairs around launches, resolved after each solve
+  bool prof_on = false;
+  int cur_cyc = -1;                 // cycle of the running batched solve, -1 outside
+  int *h_hist = nullptr;            // pinned [maxit + 2]: active shifts after each cycle's test
+  std::vector<cudaEvent_t> prof_ev; // 2 per pair
+  std::vector<int> prof_free;
+  struct ProfRec {
+    int kc, idx, cyc, phase;
+    double bytes_per_shift;
+  };
+  std::vector<ProfRec> prof_pending;
+  double prof_ms[PD_KC_COUNT] = {0}, prof_bytes[PD_KC_COUNT] = {0};
+  long long prof_n[PD_KC_COUNT] = {0};
   std::string err;
   std::vector<void *> allocs;
 };
@@ -84,6 +97,55 @@ void ck_launch(pd_ctx *c, int count = 1) {
   c->launches += count;
   ck(c, cudaGetLastError());
 }
+
+// phase of a launch for byte accounting: 0 all n shifts, 1 the shifts active when the
+// cycle started (before its convergence test), 2 those active after it
+int prof_begin(pd_ctx *c) {
+  if (!c->prof_on) return -1;
+  if (c->prof_free.empty()) {
+    const int idx = (int)c->prof_ev.size() / 2;
+    cudaEvent_t a, b;
+    ck(c, cudaEventCreate(&a));
+    ck(c, cudaEventCreate(&b));
+    c->prof_ev.push_back(a);
+    c->prof_ev.push_back(b);
+    c->prof_free.push_back(idx);
+  }
+  const int idx = c->prof_free.back();
+  c->prof_free.pop_back();
+  ck(c, cudaEventRecord(c->prof_ev[2 * idx], c->stream));
+  return idx;
+}
+
+void prof_end(pd_ctx *c, int idx, int kc, double bytes_per_shift, int phase) {
+  if (idx < 0) return;
+  ck(c, cudaEventRecord(c->prof_ev[2 * idx + 1], c->stream));
+  if (c->cur_cyc < 0) phase = 0;
+  c->prof_pending.push_back({kc, idx, c->cur_cyc, phase, bytes_per_shift});
+}
+
+// after a stream synchronisation: turn pending event pairs into totals
+void prof_resolve(pd_ctx *c) {
+  for (const auto &r : c->prof_pending) {
+    float ms = 0.f;
+    ck(c, cudaEventElapsedTime(&ms, c->prof_ev[2 * r.idx], c->prof_ev[2 * r.idx + 1]));
+    double cnt = c->n;
+    if (r.phase == 1) cnt = r.cyc == 0 ? c->n : c->h_hist[r.cyc - 1];
+    if (r.phase == 2) cnt = c->h_hist[r.cyc];
+    c->prof_ms[r.kc] += ms;
+    c->prof_n[r.kc] += 1;
+    c->prof_bytes[r.kc] += cnt * r.bytes_per_shift;
+    c->prof_free.push_back(r.idx);
+  }
+  c->prof_pending.clear();
+}
+
+#define PD_PROF(kc, bytes, phase, ...)          \
+  do {                                         \
+    const int pi_ = prof_begin(c);             \
+    __VA_ARGS__;                               \
+    prof_end(c, pi_, (kc), (bytes), (phase));  \
+  } while (0)
 
 template <typename P> P dalloc(pd_ctx *c, size_t bytes) {
   void *p = nullptr;
@@ -205,45 +267,56 @@ void run_cycle(pd_ctx *c, int l, bool zzero, bool top, const int *active, double
   const Coef<T> *cf = P.coef + (size_t)l * n;
   const bool jac = c->cfg.smoother == 1;
   int &cur = c->cur[l];
+  const double w = sizeof(typename Cx<T>::type), pts = (double)N * N;
+  const int ks = l == 0 ? PD_KC_SMOOTH0 : PD_KC_SMOOTH_C;
   if (l >= c->lc) {
-    launch_coarse<T>(c->stream, c->plan, l, n, b, (T)1, z[cur], P.coef, P.cinv, active, 1,
-                     zzero ? 0 : 1, 0, 0.0, 0, c->st);
+    PD_PROF(PD_KC_COARSE, (zzero ? 2 : 3) * w * pts, 2,
+            launch_coarse<T>(c->stream, c->plan, l, n, b, (T)1, z[cur], P.coef, P.cinv, active, 1,
+                             zzero ? 0 : 1, 0, 0.0, 0, c->st));
     ck_launch(c);
     return;
   }
   int s = 0;
   if (top) {
     if (c->cfg.nu1 >= 1) {
-      launch_smooth<T>(c->stream, N, n, z[cur], z[cur ^ 1], b, (T)1, cf, active, zzero, jac,
-                       c->st.partials, c->st.max_tiles);
-      launch_converge(c->stream, n, smooth_tiles(N), c->st, tol, maxit, cur);
+      PD_PROF(ks, (zzero ? 2 : 3) * w * pts, 1,
+              launch_smooth<T>(c->stream, N, n, z[cur], z[cur ^ 1], b, (T)1, cf, active, zzero, jac,
+                               c->st.partials, c->st.max_tiles));
+      PD_PROF(PD_KC_CONVERGE, 8.0 * smooth_tiles(N), 1,
+              launch_converge(c->stream, n, smooth_tiles(N), c->st, tol, maxit, cur));
       ck_launch(c, 2);
       cur ^= 1;
       zzero = false;
       s = 1;
     } else {
-      launch_resnorm<T>(c->stream, N, n, z[cur], b, (T)1, cf, active, zzero, c->st.partials,
-                        c->st.max_tiles);
-      launch_converge(c->stream, n, smooth_tiles(N), c->st, tol, maxit, cur);
+      PD_PROF(ks, (zzero ? 1 : 2) * w * pts, 1,
+              launch_resnorm<T>(c->stream, N, n, z[cur], b, (T)1, cf, active, zzero,
+                                c->st.partials, c->st.max_tiles));
+      PD_PROF(PD_KC_CONVERGE, 8.0 * smooth_tiles(N), 1,
+              launch_converge(c->stream, n, smooth_tiles(N), c->st, tol, maxit, cur));
       ck_launch(c, 2);
     }
   }
   for (; s < c->cfg.nu1; s++) {
-    launch_smooth<T>(c->stream, N, n, z[cur], z[cur ^ 1], b, (T)1, cf, active, zzero, jac,
-                     nullptr, 0);
+    PD_PROF(ks, (zzero ? 2 : 3) * w * pts, 2,
+            launch_smooth<T>(c->stream, N, n, z[cur], z[cur ^ 1], b, (T)1, cf, active, zzero, jac,
+                             nullptr, 0));
     ck_launch(c);
     cur ^= 1;
     zzero = false;
   }
   LevelBufs &Bc = P.lv[l + 1];
-  launch_residual_restrict<T>(c->stream, N, n, z[cur], b, (T)1, view(Bc.b, Bc.N, Bc.P), (T)1, cf,
-                              active, zzero);
+  const double ptsc = (double)Bc.N * Bc.N;
+  PD_PROF(l == 0 ? PD_KC_RESTRICT0 : PD_KC_RESTRICT_C, (zzero ? 1 : 2) * w * pts + w * ptsc, 2,
+          launch_residual_restrict<T>(c->stream, N, n, z[cur], b, (T)1, view(Bc.b, Bc.N, Bc.P),
+                                      (T)1, cf, active, zzero));
   ck_launch(c);
   c->cur[l + 1] = 0;
   if (l + 1 >= c->lc) {
-    launch_coarse<T>(c->stream, c->plan, l + 1, n, view(Bc.b, Bc.N, Bc.P), (T)1,
-                     view(Bc.z[0], Bc.N, Bc.P), P.coef, P.cinv, active, c->cfg.cycle_gamma, 0, 0,
-                     0.0, 0, c->st);
+    PD_PROF(PD_KC_COARSE, 2 * w * ptsc, 2,
+            launch_coarse<T>(c->stream, c->plan, l + 1, n, view(Bc.b, Bc.N, Bc.P), (T)1,
+                             view(Bc.z[0], Bc.N, Bc.P), P.coef, P.cinv, active, c->cfg.cycle_gamma,
+                             0, 0, 0.0, 0, c->st));
     ck_launch(c);
   } else {
     bool zz = true;
@@ -256,11 +329,14 @@ void run_cycle(pd_ctx *c, int l, bool zzero, bool top, const int *active, double
     ck(c, cudaMemsetAsync(z[cur].p, 0, (size_t)n * z[cur].plane * sizeof(typename Cx<T>::type),
                           c->stream));
   }
-  launch_prolong_add<T>(c->stream, N, n, z[cur], view(Bc.z[c->cur[l + 1]], Bc.N, Bc.P), active);
+  PD_PROF(l == 0 ? PD_KC_PROLONG0 : PD_KC_PROLONG_C, 2 * w * pts + w * ptsc, 2,
+          launch_prolong_add<T>(c->stream, N, n, z[cur], view(Bc.z[c->cur[l + 1]], Bc.N, Bc.P),
+                                active));
   ck_launch(c);
   for (s = 0; s < c->cfg.nu2; s++) {
-    launch_smooth<T>(c->stream, N, n, z[cur], z[cur ^ 1], b, (T)1, cf, active, false, jac, nullptr,
-                     0);
+    PD_PROF(ks, 3 * w * pts, 2,
+            launch_smooth<T>(c->stream, N, n, z[cur], z[cur ^ 1], b, (T)1, cf, active, false, jac,
+                             nullptr, 0));
     ck_launch(c);
     cur ^= 1;
   }
@@ -274,24 +350,29 @@ pd_status solve_levels(pd_ctx *c, double tol, int maxit) {
   Prec<T> &P = prec<T>(c);
   LevelBufs &B = P.lv[0];
   const int n = c->n;
-  launch_reset_state(c->stream, n, c->st);
+  const double w = sizeof(typename Cx<T>::type), pts = (double)B.N * B.N;
+  PD_PROF(PD_KC_OTHER, 0.0, 0, launch_reset_state(c->stream, n, c->st));
   ck_launch(c);
   if (c->lc == 0) {
-    launch_coarse<T>(c->stream, c->plan, 0, n, view(B.b, B.N, B.P), (T)1, view(B.z[0], B.N, B.P),
-                     P.coef, P.cinv, nullptr, 0, 0, 1, tol, maxit, c->st);
+    PD_PROF(PD_KC_COARSE, 2 * w * pts, 0,
+            launch_coarse<T>(c->stream, c->plan, 0, n, view(B.b, B.N, B.P), (T)1,
+                             view(B.z[0], B.N, B.P), P.coef, P.cinv, nullptr, 0, 0, 1, tol, maxit,
+                             c->st));
     ck_launch(c);
   } else {
     ck(c, cudaMemsetAsync(B.z[0], 0, (size_t)n * B.N * B.P * sizeof(typename Cx<T>::type),
                           c->stream));
     c->cur[0] = 0;
-    for (int cyc = 0; cyc <= maxit; cyc++) {
-      run_cycle<T>(c, 0, cyc == 0, true, c->st.active, tol, maxit);
-      ck(c, cudaMemcpyAsync(&c->h_pinned[cyc & 1], c->st.nactive, sizeof(int),
-                            cudaMemcpyDeviceToHost, c->stream));
+    const int cmax = std::min(maxit, c->cfg.maxit);
+    for (int cyc = 0; cyc <= cmax; cyc++) {
+      c->cur_cyc = cyc;
+      run_cycle<T>(c, 0, cyc == 0, true, c->st.active, tol, cmax);
+      ck(c, cudaMemcpyAsync(&c->h_hist[cyc], c->st.nactive, sizeof(int), cudaMemcpyDeviceToHost,
+                            c->stream));
       ck(c, cudaEventRecord(c->ev[cyc & 1], c->stream));
       if (cyc >= 1) {
         ck(c, cudaEventSynchronize(c->ev[(cyc - 1) & 1]));
-        if (c->h_pinned[(cyc - 1) & 1] == 0) break;
+        if (c->h_hist[cyc - 1] == 0) break;
       }
     }
   }
@@ -301,6 +382,8 @@ pd_status solve_levels(pd_ctx *c, double tol, int maxit) {
   ck(c, cudaMemcpyAsync(&c->h_pinned[2], c->st.flags, sizeof(int), cudaMemcpyDeviceToHost,
                         c->stream));
   ck(c, cudaStreamSynchronize(c->stream));
+  prof_resolve(c);
+  c->cur_cyc = -1;
   if (c->h_pinned[2] & 1) return PD_ERR_NAN;
   for (int j = 0; j < n; j++)
     if (!(c->h_relres[j] <= tol)) return PD_ERR_NOCONV;
@@ -310,8 +393,10 @@ pd_status solve_levels(pd_ctx *c, double tol, int maxit) {
 // ||fhat - A u|| and ||fhat|| from the per-CTA partial sums (fixed order)
 void allatonce_norms(pd_ctx *c, double *r, const double *u, const double *f, const double *u0,
                      double *rn, double *fn) {
-  launch_allatonce_residual(c->stream, c->N, c->n, r, u, f, u0, c->d_u0coef, c->d_Bptr,
-                            c->d_Bcol, c->d_Bval, c->d_part);
+  const double m = (double)c->N * c->N;
+  PD_PROF(PD_KC_RESIDUAL, (r ? 24.0 : 16.0) * m + (u0 ? 8.0 * m / c->n : 0.0), 0,
+          launch_allatonce_residual(c->stream, c->N, c->n, r, u, f, u0, c->d_u0coef, c->d_Bptr,
+                                    c->d_Bcol, c->d_Bval, c->d_part));
   ck_launch(c);
   const int nb = allatonce_blocks();
   ck(c, cudaMemcpyAsync(c->h_part, c->d_part, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost,
@@ -324,6 +409,7 @@ void allatonce_norms(pd_ctx *c, double *r, const double *u, const double *f, con
   }
   *rn = std::sqrt(a);
   *fn = std::sqrt(b);
+  prof_resolve(c);
 }
 
 template <typename T>
@@ -351,13 +437,17 @@ pd_status paradiag_impl(pd_ctx *c, double *u, const double *f, const double *u0,
     cyc_max_sum += mx;
   };
   if (imag) ck(c, cudaMemsetAsync(c->d_imag, 0, sizeof(unsigned long long), c->stream));
+  const double w = sizeof(typename Cx<T>::type), m = (double)N * N;
+  const double fwd_bytes = (8.0 + w) * m, fwd_u0 = 8.0 * m / n;
   if (c->cfg.precision == 0) {
-    launch_transform_forward<T>(c->stream, N, n, g, f, u0, c->d_u0coef, P.Wf, h2);
+    PD_PROF(PD_KC_FORWARD, fwd_bytes + (u0 ? fwd_u0 : 0.0), 0,
+            launch_transform_forward<T>(c->stream, N, n, g, f, u0, c->d_u0coef, P.Wf, h2));
     ck_launch(c);
     rc = solve_levels<T>(c, c->cfg.tol, c->cfg.maxit);
     accumulate_iters();
-    launch_transform_inverse<T>(c->stream, N, n, u, z0, z1, c->st.final_buf, P.Wi, false, imag,
-                                c->d_imag);
+    PD_PROF(PD_KC_INVERSE, (w + 8.0) * m, 0,
+            launch_transform_inverse<T>(c->stream, N, n, u, z0, z1, c->st.final_buf, P.Wi, false,
+                                        imag, c->d_imag));
     ck_launch(c);
     if (c->have_B) {
       double rn, fn;
@@ -371,9 +461,12 @@ pd_status paradiag_impl(pd_ctx *c, double *u, const double *f, const double *u0,
     int steps = 0;
     for (int step = 0; step < std::max(1, c->cfg.max_refine); step++) {
       if (step == 0)
-        launch_transform_forward<T>(c->stream, N, n, g, f, u0, c->d_u0coef, P.Wf, h2);
+        PD_PROF(PD_KC_FORWARD, fwd_bytes + (u0 ? fwd_u0 : 0.0), 0,
+                launch_transform_forward<T>(c->stream, N, n, g, f, u0, c->d_u0coef, P.Wf, h2));
       else
-        launch_transform_forward<T>(c->stream, N, n, g, c->d_r, nullptr, c->d_u0coef, P.Wf, h2);
+        PD_PROF(PD_KC_FORWARD, fwd_bytes, 0,
+                launch_transform_forward<T>(c->stream, N, n, g, c->d_r, nullptr, c->d_u0coef, P.Wf,
+                                            h2));
       ck_launch(c);
       pd_status s = solve_levels<T>(c, c->cfg.inner_tol, c->cfg.maxit);
       if (s == PD_ERR_NAN) {
@@ -381,8 +474,9 @@ pd_status paradiag_impl(pd_ctx *c, double *u, const double *f, const double *u0,
         break;
       }
       accumulate_iters();
-      launch_transform_inverse<T>(c->stream, N, n, u, z0, z1, c->st.final_buf, P.Wi, step > 0,
-                                  imag, c->d_imag);
+      PD_PROF(PD_KC_INVERSE, (w + (step > 0 ? 16.0 : 8.0)) * m, 0,
+              launch_transform_inverse<T>(c->stream, N, n, u, z0, z1, c->st.final_buf, P.Wi,
+                                          step > 0, imag, c->d_imag));
       ck_launch(c);
       double rn, fn;
       allatonce_norms(c, c->d_r, u, f, u0, &rn, &fn);
@@ -441,6 +535,8 @@ void free_ctx(pd_ctx *c) {
   if (c->h_iters) cudaFreeHost(c->h_iters);
   if (c->h_relres) cudaFreeHost(c->h_relres);
   if (c->h_part) cudaFreeHost(c->h_part);
+  if (c->h_hist) cudaFreeHost(c->h_hist);
+  for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
   for (int k = 0; k < 2; k++)
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -581,7 +677,7 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
   for (int l = c->L - 1; l >= 0; l--) {
     const size_t bytes = cfg.precision == 0 ? coarse_smem_bytes<double>(c->plan, l)
                                             : coarse_smem_bytes<float>(c->plan, l);
-    if (bytes <= kCoarseSmemLimit && c->Ns[l] <= cap) c->lc = l;
+    if (bytes <= kCoarseSmemLimit && c->Ns[l] <= cap && c->L - 1 - l <= kMaxCoarseDepth) c->lc = l;
     else break;
   }
   c->plan.lc = c->lc;
@@ -592,6 +688,7 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
     ck(c, cudaMallocHost(&c->h_iters, n * sizeof(int)));
     ck(c, cudaMallocHost(&c->h_relres, n * sizeof(double)));
     ck(c, cudaMallocHost(&c->h_part, 2 * allatonce_blocks() * sizeof(double)));
+    ck(c, cudaMallocHost(&c->h_hist, (cfg.maxit + 2) * sizeof(int)));
     // solve state
     const int tiles = smooth_tiles(N);
     c->st.max_tiles = tiles;
@@ -854,6 +951,33 @@ pd_status pd_allatonce_residual(pd_ctx *c, double *r, const double *u, const dou
       h_norms[0] = rn;
       h_norms[1] = fn;
     }
+    return PD_OK;
+  })
+}
+
+pd_status pd_profile_enable(pd_ctx *c, int on) {
+  if (!c) return PD_ERR_ARG;
+  PD_TRY(c, {
+    ck(c, cudaStreamSynchronize(c->stream));
+    prof_resolve(c);
+    c->prof_on = on != 0;
+    for (int k = 0; k < PD_KC_COUNT; k++) {
+      c->prof_ms[k] = 0.0;
+      c->prof_bytes[k] = 0.0;
+      c->prof_n[k] = 0;
+    }
+    return PD_OK;
+  })
+}
+
+pd_status pd_profile_read(pd_ctx *c, int kc, double *ms, long long *launches, double *bytes) {
+  if (!c || kc < 0 || kc >= PD_KC_COUNT) return PD_ERR_ARG;
+  PD_TRY(c, {
+    ck(c, cudaStreamSynchronize(c->stream));
+    prof_resolve(c);
+    if (ms) *ms = c->prof_ms[kc];
+    if (launches) *launches = c->prof_n[kc];
+    if (bytes) *bytes = c->prof_bytes[kc];
     return PD_OK;
   })
 }

@@ -255,13 +255,11 @@ k_prolong_add(int Nf, View z, View ec, const int *__restrict__ active) {
 }
 
 // ---------------------------------------------------------------------------------
-// Coarse levels inside one CTA per shift: z_l, bt_l, rt_l of levels lc..L-1 live in
-// shared memory; the cycle recursion (gamma, nu1, nu2) is the one of Sec. 3.
+// Coarse levels inside one CTA per shift: z_l, bt_l, rt_l of levels start..L-1 live in
+// shared memory; the cycle recursion (gamma, nu1, nu2) is the one of Sec. 3.  The
+// recursion is unrolled at compile time over at most kMaxCoarseDepth levels, so the
+// kernel needs no runtime call stack.
 constexpr int kCoThreads = 512;
-
-template <typename T> struct CtaGrid {
-  typename Cx<T>::type *z[kMaxLevels], *b[kMaxLevels], *r[kMaxLevels];
-};
 
 template <typename T>
 __device__ void cta_residual(int N, const typename Cx<T>::type *z, const typename Cx<T>::type *b,
@@ -310,67 +308,80 @@ template <typename T> struct CoarseArgs {
   const typename Cx<T>::type *cinv;
 };
 
-template <typename T>
-__device__ void cta_cycle(int l, const CoarseArgs<T> &a, CtaGrid<T> &g) {
+// shared-memory base and per-level element offsets of z_l (bt_l = z_l + N_l^2,
+// rt_l = z_l + 2 N_l^2)
+template <typename T> struct CtaMem {
+  typename Cx<T>::type *base;
+  const int *off;
+  __device__ typename Cx<T>::type *z(int l, int N) const { return base + off[l]; }
+  __device__ typename Cx<T>::type *b(int l, int N) const { return base + off[l] + N * N; }
+  __device__ typename Cx<T>::type *r(int l, int N) const { return base + off[l] + 2 * N * N; }
+};
+
+template <typename T, int D>
+__device__ __forceinline__ void cta_cycle(int l, const CoarseArgs<T> &a, const CtaMem<T> &g) {
   using C = typename Cx<T>::type;
   const int j = blockIdx.x;
   const int N = a.plan.Ns[l];
   if (l == a.plan.L - 1) {
     const int m = N * N;
     const C *inv = a.cinv + (long long)j * m * m;
+    const C *bl = g.b(l, N);
+    C *zl = g.z(l, N);
     for (int p = threadIdx.x; p < m; p += kCoThreads) {
       C s = czero<C>();
-      for (int q = 0; q < m; q++) s = cfma(inv[(long long)p * m + q], g.b[l][q], s);
-      g.z[l][p] = s;
+      for (int q = 0; q < m; q++) s = cfma(inv[(long long)p * m + q], bl[q], s);
+      zl[p] = s;
     }
     __syncthreads();
     return;
   }
-  const Coef<T> cf = a.coef[(long long)l * a.n + j];
-  for (int s = 0; s < a.plan.nu1; s++) cta_smooth<T>(N, g.z[l], g.b[l], g.r[l], cf, a.plan.jacobi);
-  cta_residual<T>(N, g.z[l], g.b[l], g.r[l], cf.d);
-  __syncthreads();
-  const int Nc = (N - 1) / 2;
-  C *bc = g.b[l + 1], *zc = g.z[l + 1];
-  const C *r = g.r[l];
-  for (int p = threadIdx.x; p < Nc * Nc; p += kCoThreads) {
-    const int I = p / Nc, J = p - I * Nc;
-    const C *rc = r + (2 * I + 1) * N + 2 * J + 1;
-    const C e = cadd(cadd(rc[-N], rc[N]), cadd(rc[-1], rc[1]));
-    const C k = cadd(cadd(rc[-N - 1], rc[-N + 1]), cadd(rc[N - 1], rc[N + 1]));
-    bc[p] = cscale(cadd(cadd(cscale(rc[0], (T)4), cscale(e, (T)2)), k), (T)0.25);
-    zc[p] = czero<C>();
-  }
-  __syncthreads();
-  for (int gm = 0; gm < a.plan.gamma; gm++) cta_cycle<T>(l + 1, a, g);
-  C *z = g.z[l];
-  for (int p = threadIdx.x; p < N * N; p += kCoThreads) {
-    const int i = p / N, c = p - i * N;
-    auto get = [&](int I, int J) -> C {
-      return ((unsigned)I < (unsigned)Nc && (unsigned)J < (unsigned)Nc) ? zc[I * Nc + J] : czero<C>();
-    };
-    C v;
-    if (i & 1) {
-      const int I = (i - 1) >> 1;
-      if (c & 1) v = get(I, (c - 1) >> 1);
-      else v = cscale(cadd(get(I, (c >> 1) - 1), get(I, c >> 1)), (T)0.5);
-    } else {
-      const int I1 = (i >> 1) - 1, I2 = i >> 1;
-      if (c & 1) {
-        const int J = (c - 1) >> 1;
-        v = cscale(cadd(get(I1, J), get(I2, J)), (T)0.5);
-      } else {
-        const int J1 = (c >> 1) - 1, J2 = c >> 1;
-        v = cscale(cadd(cadd(get(I1, J1), get(I1, J2)), cadd(get(I2, J1), get(I2, J2))), (T)0.25);
-      }
+  if constexpr (D > 0) {
+    const Coef<T> cf = a.coef[(long long)l * a.n + j];
+    C *z = g.z(l, N), *b = g.b(l, N), *r = g.r(l, N);
+    for (int s = 0; s < a.plan.nu1; s++) cta_smooth<T>(N, z, b, r, cf, a.plan.jacobi);
+    cta_residual<T>(N, z, b, r, cf.d);
+    __syncthreads();
+    const int Nc = (N - 1) / 2;
+    C *bc = g.b(l + 1, Nc), *zc = g.z(l + 1, Nc);
+    for (int p = threadIdx.x; p < Nc * Nc; p += kCoThreads) {
+      const int I = p / Nc, J = p - I * Nc;
+      const C *rc = r + (2 * I + 1) * N + 2 * J + 1;
+      const C e = cadd(cadd(rc[-N], rc[N]), cadd(rc[-1], rc[1]));
+      const C k = cadd(cadd(rc[-N - 1], rc[-N + 1]), cadd(rc[N - 1], rc[N + 1]));
+      bc[p] = cscale(cadd(cadd(cscale(rc[0], (T)4), cscale(e, (T)2)), k), (T)0.25);
+      zc[p] = czero<C>();
     }
-    z[p] = cadd(z[p], v);
+    __syncthreads();
+    for (int gm = 0; gm < a.plan.gamma; gm++) cta_cycle<T, D - 1>(l + 1, a, g);
+    for (int p = threadIdx.x; p < N * N; p += kCoThreads) {
+      const int i = p / N, c = p - i * N;
+      auto get = [&](int I, int J) -> C {
+        return ((unsigned)I < (unsigned)Nc && (unsigned)J < (unsigned)Nc) ? zc[I * Nc + J] : czero<C>();
+      };
+      C v;
+      if (i & 1) {
+        const int I = (i - 1) >> 1;
+        if (c & 1) v = get(I, (c - 1) >> 1);
+        else v = cscale(cadd(get(I, (c >> 1) - 1), get(I, c >> 1)), (T)0.5);
+      } else {
+        const int I1 = (i >> 1) - 1, I2 = i >> 1;
+        if (c & 1) {
+          const int J = (c - 1) >> 1;
+          v = cscale(cadd(get(I1, J), get(I2, J)), (T)0.5);
+        } else {
+          const int J1 = (c >> 1) - 1, J2 = c >> 1;
+          v = cscale(cadd(cadd(get(I1, J1), get(I1, J2)), cadd(get(I2, J1), get(I2, J2))), (T)0.25);
+        }
+      }
+      z[p] = cadd(z[p], v);
+    }
+    __syncthreads();
+    for (int s = 0; s < a.plan.nu2; s++) cta_smooth<T>(N, z, b, r, cf, a.plan.jacobi);
   }
-  __syncthreads();
-  for (int s = 0; s < a.plan.nu2; s++) cta_smooth<T>(N, g.z[l], g.b[l], g.r[l], cf, a.plan.jacobi);
 }
 
-// mode 0: ncycles cycles at level `start` from z = 0 (or from z_io when load_z);
+// mode 0: ncycles cycles at level `start` from z = 0 (or from zio when load_z);
 // mode 1: the whole solve of eq. (2) at level start = 0 with the relative-residual
 // test of Sec. 3 before each cycle; writes iters/relres/final_buf of the state.
 template <typename T>
@@ -380,36 +391,38 @@ k_coarse(CoarseArgs<T> a, View b, T bscale, View zio, const int *__restrict__ ac
   using C = typename Cx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[kCoThreads / 32];
+  __shared__ int off[kMaxLevels];
+  __shared__ int stop;
   const int j = blockIdx.x;
   if (active && !active[j]) return;
-  CtaGrid<T> g;
-  C *p = reinterpret_cast<C *>(smem_raw);
-  for (int l = a.start; l < a.plan.L; l++) {
-    const int m = a.plan.Ns[l] * a.plan.Ns[l];
-    g.z[l] = p;
-    g.b[l] = p + m;
-    g.r[l] = p + 2 * m;
-    p += 3 * m;
+  if (threadIdx.x == 0) {
+    int o = 0;
+    for (int l = a.start; l < a.plan.L; l++) {
+      off[l] = o;
+      o += 3 * a.plan.Ns[l] * a.plan.Ns[l];
+    }
   }
+  __syncthreads();
+  const CtaMem<T> g{reinterpret_cast<C *>(smem_raw), off};
   const int l0 = a.start, N = a.plan.Ns[l0];
+  C *z0 = g.z(l0, N), *b0 = g.b(l0, N), *r0 = g.r(l0, N);
   for (int q = threadIdx.x; q < N * N; q += kCoThreads) {
     const int i = q / N, c = q - i * N;
-    g.b[l0][q] = cscale(ldv<C>(b, j, i, c), bscale);
-    g.z[l0][q] = load_z ? ldv<C>(zio, j, i, c) : czero<C>();
+    b0[q] = cscale(ldv<C>(b, j, i, c), bscale);
+    z0[q] = load_z ? ldv<C>(zio, j, i, c) : czero<C>();
   }
   __syncthreads();
   if (!solve_mode) {
-    for (int k = 0; k < ncycles; k++) cta_cycle<T>(l0, a, g);
+    for (int k = 0; k < ncycles; k++) cta_cycle<T, kMaxCoarseDepth>(l0, a, g);
   } else {
     const Coef<T> cf = a.coef[(long long)l0 * a.n + j];
     double bn2 = 0.0, rr = 0.0;
     int k = 0;
-    __shared__ int stop;
     for (;;) {
-      cta_residual<T>(N, g.z[l0], g.b[l0], g.r[l0], cf.d);
+      cta_residual<T>(N, z0, b0, r0, cf.d);
       __syncthreads();
       double acc = 0.0;
-      for (int q = threadIdx.x; q < N * N; q += kCoThreads) acc += cabs2(g.r[l0][q]);
+      for (int q = threadIdx.x; q < N * N; q += kCoThreads) acc += cabs2(r0[q]);
       const double s = block_sum<kCoThreads>(acc, red);
       if (threadIdx.x == 0) {
         if (k == 0) bn2 = s;
@@ -420,7 +433,7 @@ k_coarse(CoarseArgs<T> a, View b, T bscale, View zio, const int *__restrict__ ac
       }
       __syncthreads();
       if (stop) break;
-      cta_cycle<T>(l0, a, g);
+      cta_cycle<T, kMaxCoarseDepth>(l0, a, g);
       k++;
     }
     if (threadIdx.x == 0) {
@@ -434,7 +447,7 @@ k_coarse(CoarseArgs<T> a, View b, T bscale, View zio, const int *__restrict__ ac
   }
   for (int q = threadIdx.x; q < N * N; q += kCoThreads) {
     const int i = q / N, c = q - i * N;
-    stv<C>(zio, j, i, c, g.z[l0][q]);
+    stv<C>(zio, j, i, c, z0[q]);
   }
 }
 

@@ -12,6 +12,7 @@
 namespace pd {
 
 constexpr int kMaxLevels = 16;
+constexpr int kMaxCoarseDepth = 7;  // levels below the first one of the coarse CTA kernel
 constexpr int kMaxShifts = 128;
 
 template <typename T> struct Cx;
