@@ -1,0 +1,321 @@
+#!/usr/bin/env python
+"""Throughput of the ParaDIAG step (alpha-circulant backward Euler, heat equation on the
+unit square) on one GB300: shifted solves per second to relative residual 1e-10, for
+the FP32-multigrid + FP64-refinement form (the value) and the plain FP64 form (beside
+it), with the roofline of the dominant kernel and the FP64 CPU oracle as a baseline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload paradiag-1023]
+  python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
+
+One step = one whole paradiag_solve: transforms, n batched multigrid solves, refinement.
+Under torchrun every rank solves its own independent problem (weak scaling, no
+collective on the data path); the time is the maximum over ranks.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "shifted solves/s to rel.res 1e-10: FP32+IR vs FP64 on GB300; % HBM peak"
+HBM_FALLBACK_GBS = 6800.0
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def traffic_table():
+    """Per-launch DRAM bytes from the committed ncu summaries (kernel class -> bytes)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    out = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            for line in f:
+                p = line.split()
+                if len(p) >= 3 and not line.startswith("#"):
+                    out[(p[0], p[1])] = float(p[2])
+    return out
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.file.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        smax = float(rows[0][2])
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip() == "Active"})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows)}
+
+
+def oracle_sample(workload, threads):
+    """Times the FP64 CPU oracle on a bounded sample of the workload and scales it to the
+    whole step: the forward transform on 1/16 of the grid points (x16, and x2 for the
+    inverse transform of the same size) plus the multigrid solves of `threads` of the n
+    shifted systems on the full grid, one per thread (x n/threads)."""
+    from oracle import core, lfa
+    from paper_2203_11154_gb300 import inputs
+
+    w = inputs.WORKLOADS[workload]
+    N, n, tau, alpha = w["N"], w["n"], w["tau"], w["alpha"]
+    s = max(1, min(threads, n))
+    core.set_threads(threads)
+    f, u0 = inputs.paradiag_problem(N, n, seed=w["seed"])
+    lam, V, Vinv = core.alpha_circulant(n, tau, alpha)
+    fhat = core.assemble_rhs(N, n, tau, f, u0).reshape(n, -1)
+    m = fhat.shape[1]
+    ms = m // 16
+    x = np.ascontiguousarray(fhat[:, :ms])
+    t0 = time.perf_counter()
+    core.time_transform(Vinv, x)
+    t_tr = time.perf_counter() - t0
+    sel = np.linspace(0, n - 1, s).astype(int)
+    g = (Vinv[sel] @ fhat).reshape(s, N, N)
+    om = lfa.omega_table(lam[sel], N, mode="lfa")
+    t0 = time.perf_counter()
+    core.shifted_solve_batch(N, lam[sel], om, g, tol=1e-10)
+    t_mg = time.perf_counter() - t0
+    step = 2 * t_tr * (m / ms) + t_mg * (n / s)
+    desc = ("forward transform of %d of %d grid points (x%.0f, x2 for the inverse) and multigrid "
+            "solves of %d of %d shifted systems on the full %dx%d grid (x%.1f); %s workload"
+            % (ms, m, m / ms, s, n, N, N, n / s, workload))
+    return n / step, t_tr + t_mg, desc
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    vals, secs = [], []
+    for k in range(args.warmup + args.steps):
+        v, sec, desc = oracle_sample(args.workload, cores)
+        if k >= args.warmup:
+            vals.append(v)
+            secs.append(sec)
+    v = float(np.median(vals))
+    from paper_2203_11154_gb300 import inputs
+    w = inputs.WORKLOADS[args.workload]
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * w["n"] / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "N": w["N"], "n": w["n"], "tau": w["tau"],
+                       "alpha": w["alpha"]},
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": v, "unit": "solves/s",
+                             "sample": desc, "sample_seconds_median": float(np.median(secs))},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="paradiag-1023",
+                    choices=["paradiag-1023", "paradiag-2047"])
+    ap.add_argument("--fp64-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2203_11154_gb300 import api, inputs
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    w = inputs.WORKLOADS[args.workload]
+    N, n, tau, alpha = w["N"], w["n"], w["tau"], w["alpha"]
+    f, u0 = inputs.paradiag_problem(N, n, seed=w["seed"] + rank)
+    fd = torch.from_numpy(f).cuda()
+    u0d = torch.from_numpy(u0).cuda()
+    u = torch.empty_like(fd)
+    stream = torch.cuda.current_stream()
+
+    def timed(ctx, steps, warmup, profile=False, clocks=None):
+        out = None
+        for _ in range(warmup):
+            out = ctx.paradiag_solve(u, fd, u0d)
+        barrier()
+        torch.cuda.synchronize()
+        if profile:
+            ctx.profile_enable(True)
+        l0 = ctx.launch_count()
+        if clocks:
+            clocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            out = ctx.paradiag_solve(u, fd, u0d)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ck = clocks.stop() if clocks else None
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        prof = ctx.profile_read() if profile else None
+        if profile:
+            ctx.profile_enable(False)
+        return ms, out, prof, ctx.launch_count() - l0, ck
+
+    # FP32 multigrid inside FP64 refinement (the value)
+    ctx = api.alpha_circulant_context(N, n, tau, alpha, precision=1, imag_check=0)
+    clocks = Clocks(local)
+    ms_ir, out_ir, prof, launches, ck = timed(ctx, args.steps, args.warmup, profile=True,
+                                                clocks=clocks)
+    value = n * args.steps * world / (ms_ir / 1e3)
+
+    # end to end through the host-buffer C ABI call (pinned host memory, copies timed)
+    e2e = None
+    if not args.no_e2e:
+        fh = torch.from_numpy(f).pin_memory()
+        u0h = torch.from_numpy(u0).pin_memory()
+        uh = torch.empty_like(fh).pin_memory()
+        for _ in range(max(1, args.warmup)):
+            ctx.paradiag_solve_host(uh, fh, u0h)
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            ctx.paradiag_solve_host(uh, fh, u0h)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms_e2e = max_over_ranks(e0.elapsed_time(e1))
+        e2e = {"value": n * args.steps * world / (ms_e2e / 1e3), "unit": "solves/s",
+               "h2d_bytes_per_step": int(fh.numel() * 8 + u0h.numel() * 8),
+               "d2h_bytes_per_step": int(uh.numel() * 8), "ms_per_step": ms_e2e / args.steps}
+        del fh, u0h, uh
+    ctx.destroy()
+
+    # plain FP64 (beside the value)
+    ctx64 = api.alpha_circulant_context(N, n, tau, alpha, precision=0, imag_check=0)
+    k64 = args.fp64_steps or args.steps
+    ms64, out64, _, _, _ = timed(ctx64, k64, args.warmup)
+    ctx64.destroy()
+    value64 = n * k64 * world / (ms64 / 1e3)
+
+    # roofline of the dominant kernel class (its own launch times, live in the timed region)
+    peak, peak_src = measured_peaks()
+    total = sum(v[0] for v in prof.values())
+    kernels = []
+    for name, (kms, nl, by) in sorted(prof.items(), key=lambda kv: -kv[1][0]):
+        if nl == 0:
+            continue
+        kernels.append({"kernel": name, "launches": nl, "ms": round(kms, 3),
+                        "share": round(kms / total, 4),
+                        "gbs": round(by / (kms * 1e-3) / 1e9, 1) if kms > 0 else None})
+    top = kernels[0]
+    tname = top["kernel"]
+    tms, tn, tby = prof[tname]
+    achieved = tby / (tms * 1e-3) / 1e9
+    traffic = traffic_table().get((args.workload, tname))
+    roofline = {"bound": "hbm", "kernel": tname, "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
+                "traffic": traffic, "alg_bytes_per_launch": tby / tn,
+                "avg_launch_us": 1e3 * tms / tn}
+
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_ir / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": args.workload, "N": N, "n": n, "tau": tau, "alpha": alpha,
+                       "cycle": "V(1,1)", "smoother": "additive element-wise Vanka",
+                       "omega": "LFA per shift and level", "tol_allatonce": 1e-10,
+                       "precision": "FP32 multigrid + FP64 refinement on eq. (1)",
+                       "l2": "inputs larger than L2 (f: %d MB)" % (f.nbytes >> 20),
+                       "parallelism": "one independent problem per rank"},
+            "relres_allatonce": out_ir["relres_allatonce"],
+            "refine_steps": out_ir["refine_steps"], "cycles_max": out_ir["cycles_max"],
+            "fp64": {"value": value64, "unit": "solves/s", "ms_per_step": ms64 / k64,
+                     "steps": k64, "relres_shift_max": out64["relres_shift_max"],
+                     "relres_allatonce": out64["relres_allatonce"],
+                     "cycles_max": out64["cycles_max"]},
+            "speedup_vs_fp64": value / value64,
+            "clocks": ck, "e2e": e2e, "gpu_launches": launches,
+            "roofline": roofline, "kernels": kernels}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        v, sec, desc = oracle_sample(args.workload, cores)
+        line["cpu_baseline"] = {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                                "sample": desc, "sample_seconds": round(sec, 2)}
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

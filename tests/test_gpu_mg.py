@@ -156,10 +156,11 @@ def shifted_case(N, n, lam, omega_mode, seed, **cfg):
     c = ctx_for(N, lam, omega_mode=omega_mode, **cfg)
     z = torch.empty(n, N, N, dtype=torch.complex128, device="cuda")
     it, rr = c.shifted_solve_batched(z, dev(b))
+    smoother = "jacobi" if cfg.get("smoother", 0) == 1 else "vanka"
     om = lfa.omega_table(lam, N, coarsest_n=cfg.get("coarsest_n", 3),
-                         mode="lfa" if omega_mode == 1 else "fixed")
+                         mode="lfa" if omega_mode == 1 else "fixed", smoother=smoother)
     prm = core.mg_params(cfg.get("cycle_gamma", 1), cfg.get("nu1", 1), cfg.get("nu2", 1),
-                         cfg.get("coarsest_n", 3))
+                         cfg.get("coarsest_n", 3), cfg.get("smoother", 0))
     zo, ito, rro = core.shifted_solve_batch(N, lam, om, b, tol=cfg.get("tol", 1e-10),
                                             maxit=cfg.get("maxit", 100), prm=prm)
     return host(z), it, rr, zo, ito, rro
