@@ -59,10 +59,14 @@ typedef struct {
     double inner_tol;  /* precision 1: relative residual of each inner FP32 solve */
     int max_refine;    /* precision 1: maximum refinement steps */
     int imag_check;    /* paradiag_solve: also form Im((V kron I) z) and report max |Im| */
+    int inner_maxit;   /* precision 1: cycles per inner FP32 solve at most */
+    double stall_ratio;/* precision 1: an inner solve also stops once a cycle reduces its
+                          relative residual by less than this factor (FP32 rounding of z
+                          bounds the attainable residual near cond(L) * 6e-8); 0 = off */
 } pd_config;
 
 /* Fills cfg with V(1,1), coarsest 3, maxit 100, tol 1e-10, omega_mode 1, FP64,
- * Vanka, inner_tol 1e-6, max_refine 12, imag_check 1. */
+ * Vanka, inner_tol 1e-6, max_refine 12, imag_check 1, inner_maxit 8, stall_ratio 0.5. */
 void pd_config_default(pd_config *cfg);
 
 /*

@@ -48,7 +48,8 @@ class pd_config(C.Structure):
     _fields_ = [("cycle_gamma", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
                 ("coarsest_n", C.c_int), ("maxit", C.c_int), ("tol", C.c_double),
                 ("omega_mode", C.c_int), ("precision", C.c_int), ("smoother", C.c_int),
-                ("inner_tol", C.c_double), ("max_refine", C.c_int), ("imag_check", C.c_int)]
+                ("inner_tol", C.c_double), ("max_refine", C.c_int), ("imag_check", C.c_int),
+                ("inner_maxit", C.c_int), ("stall_ratio", C.c_double)]
 
 
 _P = C.c_void_p

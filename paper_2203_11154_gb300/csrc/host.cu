@@ -66,6 +66,7 @@ struct pd_ctx {
   // instrumentation: event pairs around launches, resolved after each solve
   bool prof_on = false;
   int cur_cyc = -1;                 // cycle of the running batched solve, -1 outside
+  double stall = 0.0;               // stall ratio of the running solve (0: off)
   int *h_hist = nullptr;            // pinned [maxit + 2]: active shifts after each cycle's test
   std::vector<cudaEvent_t> prof_ev; // 2 per pair
   std::vector<int> prof_free;
@@ -283,7 +284,7 @@ void run_cycle(pd_ctx *c, int l, bool zzero, bool top, const int *active, double
               launch_smooth<T>(c->stream, N, n, z[cur], z[cur ^ 1], b, (T)1, cf, active, zzero, jac,
                                c->st.partials, c->st.max_tiles));
       PD_PROF(PD_KC_CONVERGE, 8.0 * smooth_tiles(N), 1,
-              launch_converge(c->stream, n, smooth_tiles(N), c->st, tol, maxit, cur));
+              launch_converge(c->stream, n, smooth_tiles(N), c->st, tol, maxit, c->stall, cur));
       ck_launch(c, 2);
       cur ^= 1;
       zzero = false;
@@ -293,7 +294,7 @@ void run_cycle(pd_ctx *c, int l, bool zzero, bool top, const int *active, double
               launch_resnorm<T>(c->stream, N, n, z[cur], b, (T)1, cf, active, zzero,
                                 c->st.partials, c->st.max_tiles));
       PD_PROF(PD_KC_CONVERGE, 8.0 * smooth_tiles(N), 1,
-              launch_converge(c->stream, n, smooth_tiles(N), c->st, tol, maxit, cur));
+              launch_converge(c->stream, n, smooth_tiles(N), c->st, tol, maxit, c->stall, cur));
       ck_launch(c, 2);
     }
   }
@@ -346,8 +347,9 @@ void run_cycle(pd_ctx *c, int l, bool zzero, bool top, const int *active, double
 // (scaled by h^2).  On return the per-shift answers are in lv[0].z[final_buf[j]],
 // and h_iters/h_relres (pinned copies) hold cycles and relative residuals.
 template <typename T>
-pd_status solve_levels(pd_ctx *c, double tol, int maxit) {
+pd_status solve_levels(pd_ctx *c, double tol, int maxit, double stall = 0.0) {
   Prec<T> &P = prec<T>(c);
+  c->stall = stall;
   LevelBufs &B = P.lv[0];
   const int n = c->n;
   const double w = sizeof(typename Cx<T>::type), pts = (double)B.N * B.N;
@@ -363,7 +365,7 @@ pd_status solve_levels(pd_ctx *c, double tol, int maxit) {
     ck(c, cudaMemsetAsync(B.z[0], 0, (size_t)n * B.N * B.P * sizeof(typename Cx<T>::type),
                           c->stream));
     c->cur[0] = 0;
-    const int cmax = std::min(maxit, c->cfg.maxit);
+    const int cmax = std::min(maxit, std::max(c->cfg.maxit, c->cfg.inner_maxit));
     for (int cyc = 0; cyc <= cmax; cyc++) {
       c->cur_cyc = cyc;
       run_cycle<T>(c, 0, cyc == 0, true, c->st.active, tol, cmax);
@@ -457,7 +459,7 @@ pd_status paradiag_impl(pd_ctx *c, double *u, const double *f, const double *u0,
   } else {
     // FP64 iterative refinement on eq. (1) around FP32 ParaDIAG steps.  Step 1 transforms
     // fhat itself; later steps transform the FP64 residual r = fhat - A u.
-    double relres = 1.0;
+    double relres = 1.0, prev_relres = 1.0;
     int steps = 0;
     for (int step = 0; step < std::max(1, c->cfg.max_refine); step++) {
       if (step == 0)
@@ -468,7 +470,7 @@ pd_status paradiag_impl(pd_ctx *c, double *u, const double *f, const double *u0,
                 launch_transform_forward<T>(c->stream, N, n, g, c->d_r, nullptr, c->d_u0coef, P.Wf,
                                             h2));
       ck_launch(c);
-      pd_status s = solve_levels<T>(c, c->cfg.inner_tol, c->cfg.maxit);
+      pd_status s = solve_levels<T>(c, c->cfg.inner_tol, c->cfg.inner_maxit, c->cfg.stall_ratio);
       if (s == PD_ERR_NAN) {
         rc = s;
         break;
@@ -487,6 +489,8 @@ pd_status paradiag_impl(pd_ctx *c, double *u, const double *f, const double *u0,
         break;
       }
       if (relres <= c->cfg.tol) break;
+      if (step >= 2 && relres > 0.9 * prev_relres) break;  // refinement no longer contracts
+      prev_relres = relres;
     }
     st_local[PD_STAT_RELRES_ALLATONCE] = relres;
     st_local[PD_STAT_REFINE_STEPS] = steps;
@@ -561,6 +565,8 @@ void pd_config_default(pd_config *cfg) {
   cfg->inner_tol = 1e-6;
   cfg->max_refine = 12;
   cfg->imag_check = 1;
+  cfg->inner_maxit = 8;
+  cfg->stall_ratio = 0.5;
 }
 
 pd_status pd_alpha_circulant(int n, double tau, double alpha, double *B, double *shifts,
@@ -620,7 +626,8 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
       cfg.nu2 < 0 || cfg.nu1 + cfg.nu2 < 1 || cfg.nu1 > 8 || cfg.nu2 > 8 || cfg.maxit < 0 ||
       cfg.maxit > 100000 || !(cfg.tol >= 0) || cfg.omega_mode < 0 || cfg.omega_mode > 2 ||
       cfg.precision < 0 || cfg.precision > 1 || cfg.smoother < 0 || cfg.smoother > 1 ||
-      !(cfg.inner_tol >= 0) || cfg.max_refine < 1)
+      !(cfg.inner_tol >= 0) || cfg.max_refine < 1 || cfg.inner_maxit < 1 ||
+      cfg.inner_maxit > 100000 || !(cfg.stall_ratio >= 0))
     return PD_ERR_ARG;
   if (cfg.omega_mode == 2 && !omega) return PD_ERR_ARG;
   if (cfg.precision == 1 && (!B || !V)) return PD_ERR_ARG;
@@ -688,7 +695,7 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
     ck(c, cudaMallocHost(&c->h_iters, n * sizeof(int)));
     ck(c, cudaMallocHost(&c->h_relres, n * sizeof(double)));
     ck(c, cudaMallocHost(&c->h_part, 2 * allatonce_blocks() * sizeof(double)));
-    ck(c, cudaMallocHost(&c->h_hist, (cfg.maxit + 2) * sizeof(int)));
+    ck(c, cudaMallocHost(&c->h_hist, (std::max(cfg.maxit, cfg.inner_maxit) + 2) * sizeof(int)));
     // solve state
     const int tiles = smooth_tiles(N);
     c->st.max_tiles = tiles;

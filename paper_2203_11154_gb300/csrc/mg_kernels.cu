@@ -146,7 +146,10 @@ k_resnorm(int N, View z, View b, T bscale, const Coef<T> *__restrict__ coef,
 
 // Convergence test of Sec. 3 per shift (relative residual before each cycle), in a
 // fixed summation order so that the stopping cycle is reproducible.
-__global__ void k_converge(int n, int ntiles, SolveState st, double tol, int maxit, int cur_buf) {
+// stall > 0: also stop once a cycle reduced the relative residual by less than `stall`
+// (the floor set by the rounding of z in the working precision has been reached).
+__global__ void k_converge(int n, int ntiles, SolveState st, double tol, int maxit, double stall,
+                           int cur_buf) {
   const int j = threadIdx.x;
   if (j >= n || !st.active[j]) return;
   double s = 0.0;
@@ -155,10 +158,12 @@ __global__ void k_converge(int n, int ntiles, SolveState st, double tol, int max
   if (k == 0) st.bn2[j] = s;
   const double bn2 = st.bn2[j];
   const double rr = bn2 > 0.0 ? sqrt(s / bn2) : 0.0;
+  const double prev = st.relres[j];
   st.relres[j] = rr;
   const bool bad = !isfinite(s);
   if (bad) atomicOr(st.flags, 1);
-  if (bad || rr <= tol || k >= maxit) {
+  const bool stalled = stall > 0.0 && k >= 2 && rr > stall * prev;
+  if (bad || rr <= tol || k >= maxit || stalled) {
     st.active[j] = 0;
     st.final_buf[j] = cur_buf;
     atomicSub(st.nactive, 1);
@@ -521,8 +526,8 @@ void launch_resnorm(cudaStream_t s, int N, int n, View z, View b, T bscale, cons
 }
 
 void launch_converge(cudaStream_t s, int n, int ntiles, SolveState st, double tol, int maxit,
-                     int cur_buf) {
-  k_converge<<<1, 128, 0, s>>>(n, ntiles, st, tol, maxit, cur_buf);
+                     double stall, int cur_buf) {
+  k_converge<<<1, 128, 0, s>>>(n, ntiles, st, tol, maxit, stall, cur_buf);
 }
 
 template <typename T>

@@ -60,7 +60,7 @@ void launch_resnorm(cudaStream_t s, int N, int n, View z, View b, T bscale, cons
 int smooth_tiles(int N);
 void launch_reset_state(cudaStream_t s, int n, SolveState st);
 void launch_converge(cudaStream_t s, int n, int ntiles, SolveState st, double tol, int maxit,
-                     int cur_buf);
+                     double stall, int cur_buf);
 template <typename T>
 void launch_residual_restrict(cudaStream_t s, int Nf, int n, View z, View b, T bscale, View bc,
                               T oscale, const Coef<T> *coef, const int *active, bool z_zero);
