@@ -63,10 +63,15 @@ typedef struct {
     double stall_ratio;/* precision 1: an inner solve also stops once a cycle reduces its
                           relative residual by less than this factor (FP32 rounding of z
                           bounds the attainable residual near cond(L) * 6e-8); 0 = off */
+    int fused;         /* 1: on the global-memory levels the last pre-smoothing step is fused
+                          with residual and restriction, and interpolation with the first
+                          post-smoothing step (same arithmetic, fewer memory passes);
+                          0: one kernel per operation */
 } pd_config;
 
 /* Fills cfg with V(1,1), coarsest 3, maxit 100, tol 1e-10, omega_mode 1, FP64,
- * Vanka, inner_tol 1e-6, max_refine 12, imag_check 1, inner_maxit 8, stall_ratio 0.5. */
+ * Vanka, inner_tol 1e-6, max_refine 12, imag_check 1, inner_maxit 8, stall_ratio 0.5,
+ * fused 1. */
 void pd_config_default(pd_config *cfg);
 
 /*
@@ -225,7 +230,11 @@ enum {
     PD_KC_INVERSE = 9,   /* (V kron I_h) */
     PD_KC_RESIDUAL = 10, /* FP64 residual of eq. (1) */
     PD_KC_OTHER = 11,    /* copies, state reset */
-    PD_KC_COUNT = 12
+    PD_KC_SR0 = 12,      /* fused smoothing + residual + restriction, finest grid */
+    PD_KC_PS0 = 13,      /* fused interpolation + smoothing, finest grid */
+    PD_KC_SR_C = 14,     /* the same two on the other global-memory levels */
+    PD_KC_PS_C = 15,
+    PD_KC_COUNT = 16
 };
 pd_status pd_profile_enable(pd_ctx *ctx, int on);
 pd_status pd_profile_read(pd_ctx *ctx, int kclass, double *total_ms, long long *launches,

@@ -24,7 +24,8 @@ PD_STAT_RELRES_SHIFT_MAX = 5
 PD_STATS_LEN = 8
 
 KERNEL_CLASSES = ["smooth0", "restrict0", "prolong0", "smooth_c", "restrict_c", "prolong_c",
-                  "coarse", "converge", "forward", "inverse", "residual", "other"]
+                  "coarse", "converge", "forward", "inverse", "residual", "other",
+                  "smooth_restrict0", "prolong_smooth0", "smooth_restrict_c", "prolong_smooth_c"]
 
 STATUS = {0: "PD_OK", 1: "PD_ERR_ARG", 2: "PD_ERR_CUDA", 3: "PD_ERR_NOMEM", 4: "PD_ERR_NOCONV",
           5: "PD_ERR_NAN", 6: "PD_ERR_SING", 7: "PD_ERR_STATE"}
@@ -49,7 +50,7 @@ class pd_config(C.Structure):
                 ("coarsest_n", C.c_int), ("maxit", C.c_int), ("tol", C.c_double),
                 ("omega_mode", C.c_int), ("precision", C.c_int), ("smoother", C.c_int),
                 ("inner_tol", C.c_double), ("max_refine", C.c_int), ("imag_check", C.c_int),
-                ("inner_maxit", C.c_int), ("stall_ratio", C.c_double)]
+                ("inner_maxit", C.c_int), ("stall_ratio", C.c_double), ("fused", C.c_int)]
 
 
 _P = C.c_void_p

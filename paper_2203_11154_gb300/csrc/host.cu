@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "pd_internal.h"
 
 using namespace pd;
@@ -23,6 +25,10 @@ struct LevelBufs {
   long long P = 0;        // row pitch (elements) of the internal arrays
   void *z[2] = {nullptr, nullptr};
   void *b = nullptr;
+  // TMA maps of the fused kernels (boxes with halos, zero fill outside the grid)
+  CUtensorMap sr_z[2], sr_b;          // smooth+restrict: z and bt of this level
+  CUtensorMap ps_z[2], ps_e[2], ps_b; // prolong+smooth: z of this level, z of the next, bt
+  bool maps = false;
 };
 
 template <typename T> struct Prec {
@@ -63,6 +69,7 @@ struct pd_ctx {
   unsigned long long *d_imag = nullptr;
   double *d_stage_f = nullptr, *d_stage_u = nullptr, *d_stage_u0 = nullptr;
   long long launches = 0;
+  int num_sms = 0;
   // instrumentation: event pairs around launches, resolved after each solve
   bool prof_on = false;
   int cur_cyc = -1;                 // cycle of the running batched solve, -1 outside
@@ -160,6 +167,41 @@ template <typename P> P dalloc(pd_ctx *c, size_t bytes) {
   return reinterpret_cast<P>(p);
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder(pd_ctx *c) {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    ck(c, cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p) {
+      c->err = "cuTensorMapEncodeTiled unavailable";
+      throw CudaFail{cudaErrorNotSupported};
+    }
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 3D map of a [n][N][P] array of complex values (e 8-byte words each) with a box of
+// bw x bh complex elements of one shift; reads outside [0,N)^2 return zeros
+CUtensorMap grid_map(pd_ctx *c, void *base, int N, long long P, int n, int e, int bw, int bh) {
+  CUtensorMap m;
+  cuuint64_t dims[3] = {(cuuint64_t)N * e, (cuuint64_t)N, (cuuint64_t)n};
+  cuuint64_t strides[2] = {(cuuint64_t)P * 8 * e, (cuuint64_t)N * P * 8 * e};
+  cuuint32_t box[3] = {(cuuint32_t)(bw * e), (cuuint32_t)bh, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  const CUresult r = tensor_map_encoder(c)(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, base, dims, strides,
+                                           box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                           CU_TENSOR_MAP_SWIZZLE_NONE,
+                                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    c->err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+    throw CudaFail{cudaErrorInvalidValue};
+  }
+  return m;
+}
+
 View view(void *p, int N, long long P) { return View{p, P, (long long)N * P}; }
 View uview(const void *p, int N) { return View{const_cast<void *>(p), N, (long long)N * N}; }
 
@@ -183,6 +225,22 @@ void alloc_prec(pd_ctx *c) {
     B.z[0] = dalloc<void *>(c, bytes);
     B.z[1] = dalloc<void *>(c, bytes);
     B.b = dalloc<void *>(c, bytes);
+  }
+  if (c->cfg.fused) {
+    const FusedGeom g = fused_geom<T>();
+    const int e = (int)(sizeof(C) / 8);
+    for (int l = 0; l + 1 < L && l < c->lc; l++) {
+      LevelBufs &B = P.lv[l], &Bc = P.lv[l + 1];
+      for (int q = 0; q < 2; q++) {
+        B.sr_z[q] = grid_map(c, B.z[q], B.N, B.P, n, e, g.sr_zw, g.sr_zh);
+        B.ps_z[q] = grid_map(c, B.z[q], B.N, B.P, n, e, g.ps_zw, g.ps_zh);
+        B.ps_e[q] = grid_map(c, Bc.z[q], Bc.N, Bc.P, n, e, g.ps_ew, g.ps_eh);
+      }
+      B.sr_b = grid_map(c, B.b, B.N, B.P, n, e, g.sr_bw, g.sr_bh);
+      B.ps_b = grid_map(c, B.b, B.N, B.P, n, e, g.ps_bw, g.ps_bh);
+      B.maps = true;
+    }
+    ck(c, prepare_fused<T>());
   }
   // smoother coefficients in the scaled form of pd_internal.h
   std::vector<Coef<T>> cf((size_t)L * n);
@@ -257,6 +315,81 @@ void alloc_prec(pd_ctx *c) {
   ck(c, prepare_transforms<T>(kMaxShifts));
 }
 
+template <typename T>
+void run_cycle(pd_ctx *c, int l, bool zzero, bool top, const int *active, double tol, int maxit);
+
+// The same cycle with the last pre-smoothing step fused with residual and restriction
+// and the interpolation fused with the first post-smoothing step (fused_kernels.cu).
+template <typename T>
+void run_cycle_fused(pd_ctx *c, int l, bool zzero, bool top, const int *active, double tol,
+                     int maxit) {
+  Prec<T> &P = prec<T>(c);
+  LevelBufs &B = P.lv[l], &Bc = P.lv[l + 1];
+  const int N = B.N, n = c->n;
+  const View b = view(B.b, N, B.P);
+  View z[2] = {view(B.z[0], N, B.P), view(B.z[1], N, B.P)};
+  const Coef<T> *cf = P.coef + (size_t)l * n;
+  const bool jac = c->cfg.smoother == 1;
+  int &cur = c->cur[l];
+  const double w = sizeof(typename Cx<T>::type), pts = (double)N * N, ptsc = (double)Bc.N * Bc.N;
+  const FusedGeom g = fused_geom<T>();
+  const int ftiles = fused_tiles(N, g.TX, g.TY);
+  const int grid = std::max(1, std::min(c->num_sms, n * ftiles));
+  int *err = c->st.flags;
+  bool norm = top;
+  for (int s = 0; s + 1 < c->cfg.nu1; s++) {
+    PD_PROF(l == 0 ? PD_KC_SMOOTH0 : PD_KC_SMOOTH_C, (zzero ? 2 : 3) * w * pts, norm ? 1 : 2,
+            launch_smooth<T>(c->stream, N, n, z[cur], z[cur ^ 1], b, (T)1, cf, active, zzero, jac,
+                             norm ? c->st.partials : nullptr, c->st.max_tiles));
+    ck_launch(c);
+    if (norm) {
+      PD_PROF(PD_KC_CONVERGE, 8.0 * smooth_tiles(N), 1,
+              launch_converge(c->stream, n, smooth_tiles(N), c->st, tol, maxit, c->stall, cur));
+      ck_launch(c);
+      norm = false;
+    }
+    cur ^= 1;
+    zzero = false;
+  }
+  PD_PROF(l == 0 ? PD_KC_SR0 : PD_KC_SR_C, (zzero ? 2 : 3) * w * pts + w * ptsc, norm ? 1 : 2,
+          launch_smooth_restrict<T>(c->stream, grid, B.sr_z[cur], B.sr_b, N, n, z[cur ^ 1],
+                                    view(Bc.b, Bc.N, Bc.P), cf, active, zzero,
+                                    norm ? c->st.partials : nullptr, c->st.max_tiles, err));
+  ck_launch(c);
+  if (norm) {
+    PD_PROF(PD_KC_CONVERGE, 8.0 * ftiles, 1,
+            launch_converge(c->stream, n, ftiles, c->st, tol, maxit, c->stall, cur));
+    ck_launch(c);
+  }
+  cur ^= 1;
+  c->cur[l + 1] = 0;
+  if (l + 1 >= c->lc) {
+    PD_PROF(PD_KC_COARSE, 2 * w * ptsc, 2,
+            launch_coarse<T>(c->stream, c->plan, l + 1, n, view(Bc.b, Bc.N, Bc.P), (T)1,
+                             view(Bc.z[0], Bc.N, Bc.P), P.coef, P.cinv, active, c->cfg.cycle_gamma,
+                             0, 0, 0.0, 0, c->st));
+    ck_launch(c);
+  } else {
+    bool zz = true;
+    for (int gm = 0; gm < c->cfg.cycle_gamma; gm++) {
+      run_cycle<T>(c, l + 1, zz, false, active, tol, maxit);
+      zz = false;
+    }
+  }
+  PD_PROF(l == 0 ? PD_KC_PS0 : PD_KC_PS_C, 3 * w * pts + w * ptsc, 2,
+          launch_prolong_smooth<T>(c->stream, grid, B.ps_z[cur], B.ps_e[c->cur[l + 1]], B.ps_b, N,
+                                   n, z[cur ^ 1], cf, active, err));
+  ck_launch(c);
+  cur ^= 1;
+  for (int s = 1; s < c->cfg.nu2; s++) {
+    PD_PROF(l == 0 ? PD_KC_SMOOTH0 : PD_KC_SMOOTH_C, 3 * w * pts, 2,
+            launch_smooth<T>(c->stream, N, n, z[cur], z[cur ^ 1], b, (T)1, cf, active, false, jac,
+                             nullptr, 0));
+    ck_launch(c);
+    cur ^= 1;
+  }
+}
+
 // ---- one cycle on the global-memory levels (Sec. 3), recursing to the coarse kernel ----
 template <typename T>
 void run_cycle(pd_ctx *c, int l, bool zzero, bool top, const int *active, double tol, int maxit) {
@@ -275,6 +408,10 @@ void run_cycle(pd_ctx *c, int l, bool zzero, bool top, const int *active, double
             launch_coarse<T>(c->stream, c->plan, l, n, b, (T)1, z[cur], P.coef, P.cinv, active, 1,
                              zzero ? 0 : 1, 0, 0.0, 0, c->st));
     ck_launch(c);
+    return;
+  }
+  if (c->cfg.fused && B.maps && c->cfg.nu1 >= 1 && c->cfg.nu2 >= 1) {
+    run_cycle_fused<T>(c, l, zzero, top, active, tol, maxit);
     return;
   }
   int s = 0;
@@ -386,6 +523,10 @@ pd_status solve_levels(pd_ctx *c, double tol, int maxit, double stall = 0.0) {
   ck(c, cudaStreamSynchronize(c->stream));
   prof_resolve(c);
   c->cur_cyc = -1;
+  if (c->h_pinned[2] & 2) {
+    c->err = "a bounded TMA wait ran out in a fused kernel";
+    throw CudaFail{cudaErrorLaunchTimeout};
+  }
   if (c->h_pinned[2] & 1) return PD_ERR_NAN;
   for (int j = 0; j < n; j++)
     if (!(c->h_relres[j] <= tol)) return PD_ERR_NOCONV;
@@ -567,6 +708,7 @@ void pd_config_default(pd_config *cfg) {
   cfg->imag_check = 1;
   cfg->inner_maxit = 8;
   cfg->stall_ratio = 0.5;
+  cfg->fused = 1;
 }
 
 pd_status pd_alpha_circulant(int n, double tau, double alpha, double *B, double *shifts,
@@ -627,7 +769,7 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
       cfg.maxit > 100000 || !(cfg.tol >= 0) || cfg.omega_mode < 0 || cfg.omega_mode > 2 ||
       cfg.precision < 0 || cfg.precision > 1 || cfg.smoother < 0 || cfg.smoother > 1 ||
       !(cfg.inner_tol >= 0) || cfg.max_refine < 1 || cfg.inner_maxit < 1 ||
-      cfg.inner_maxit > 100000 || !(cfg.stall_ratio >= 0))
+      cfg.inner_maxit > 100000 || !(cfg.stall_ratio >= 0) || cfg.fused < 0 || cfg.fused > 1)
     return PD_ERR_ARG;
   if (cfg.omega_mode == 2 && !omega) return PD_ERR_ARG;
   if (cfg.precision == 1 && (!B || !V)) return PD_ERR_ARG;
@@ -697,7 +839,12 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
     ck(c, cudaMallocHost(&c->h_part, 2 * allatonce_blocks() * sizeof(double)));
     ck(c, cudaMallocHost(&c->h_hist, (std::max(cfg.maxit, cfg.inner_maxit) + 2) * sizeof(int)));
     // solve state
-    const int tiles = smooth_tiles(N);
+    int dev = 0;
+    ck(c, cudaGetDevice(&dev));
+    ck(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    const FusedGeom g32 = fused_geom<float>(), g64 = fused_geom<double>();
+    const int tiles = std::max({smooth_tiles(N), fused_tiles(N, g32.TX, g32.TY),
+                                fused_tiles(N, g64.TX, g64.TY)});
     c->st.max_tiles = tiles;
     c->st.active = dalloc<int *>(c, n * sizeof(int));
     c->st.iters = dalloc<int *>(c, n * sizeof(int));

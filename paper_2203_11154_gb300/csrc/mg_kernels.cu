@@ -86,7 +86,7 @@ k_smooth(int N, View zin, View zout, View b, T bscale, const Coef<T> *__restrict
     sr[t] = r;
   }
   __syncthreads();
-  double acc = 0.0;
+  T acc = 0;
   for (int t = tid; t < TY * TX; t += kSmThreads) {
     const int ty = t / TX, tx = t - ty * TX;
     const int gi = y0 + ty, gj = x0 + tx;
@@ -102,11 +102,11 @@ k_smooth(int N, View zin, View zout, View b, T bscale, const Coef<T> *__restrict
       }
       const C zold = ZZERO ? czero<C>() : sz[(ty + 2) * ZW + tx + 2];
       stv<C>(zout, j, gi, gj, cadd(zold, upd));
-      if (NORM) acc += cabs2(rv);
+      if (NORM) acc += rv.x * rv.x + rv.y * rv.y;
     }
   }
   if (NORM) {
-    const double s = block_sum<kSmThreads>(acc, red);
+    const double s = block_sum<kSmThreads>((double)acc, red);
     if (tid == 0) partials[(long long)j * part_stride + tile] = s;
   }
 }
@@ -148,12 +148,15 @@ k_resnorm(int N, View z, View b, T bscale, const Coef<T> *__restrict__ coef,
 // fixed summation order so that the stopping cycle is reproducible.
 // stall > 0: also stop once a cycle reduced the relative residual by less than `stall`
 // (the floor set by the rounding of z in the working precision has been reached).
+// One warp per shift; the lanes' strided sums are combined in a fixed order.
 __global__ void k_converge(int n, int ntiles, SolveState st, double tol, int maxit, double stall,
                            int cur_buf) {
-  const int j = threadIdx.x;
+  const int j = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (j >= n || !st.active[j]) return;
   double s = 0.0;
-  for (int t = 0; t < ntiles; t++) s += st.partials[(long long)j * st.max_tiles + t];
+  for (int t = lane; t < ntiles; t += 32) s += st.partials[(long long)j * st.max_tiles + t];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane != 0) return;
   const int k = st.iters[j];
   if (k == 0) st.bn2[j] = s;
   const double bn2 = st.bn2[j];
@@ -527,7 +530,7 @@ void launch_resnorm(cudaStream_t s, int N, int n, View z, View b, T bscale, cons
 
 void launch_converge(cudaStream_t s, int n, int ntiles, SolveState st, double tol, int maxit,
                      double stall, int cur_buf) {
-  k_converge<<<1, 128, 0, s>>>(n, ntiles, st, tol, maxit, stall, cur_buf);
+  k_converge<<<(n + 3) / 4, 128, 0, s>>>(n, ntiles, st, tol, maxit, stall, cur_buf);
 }
 
 template <typename T>

@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libparadiag.so.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -89,6 +90,25 @@ void launch_copy_scale(cudaStream_t s, int N, int n, View dst, View src, T scale
 template <typename T>
 void launch_gather_final(cudaStream_t s, int N, int n, View dst, View z0, View z1,
                          const int *final_buf);
+
+// ---- fused TMA kernels (fused_kernels.cu) ----
+struct FusedGeom {
+  int TX, TY;                 // output tile (columns, rows)
+  int sr_zw, sr_zh, sr_bw, sr_bh;                 // smooth+restrict boxes (complex elements)
+  int ps_zw, ps_zh, ps_ew, ps_eh, ps_bw, ps_bh;   // prolong+smooth boxes
+};
+template <typename T> FusedGeom fused_geom();
+template <typename T> cudaError_t prepare_fused();
+int fused_tiles(int N, int TX, int TY);
+template <typename T>
+void launch_smooth_restrict(cudaStream_t s, int grid, const CUtensorMap &zmap,
+                            const CUtensorMap &bmap, int N, int n, View zout, View bc,
+                            const Coef<T> *coef, const int *active, bool z_zero, double *partials,
+                            int part_stride, int *errflag);
+template <typename T>
+void launch_prolong_smooth(cudaStream_t s, int grid, const CUtensorMap &zmap,
+                           const CUtensorMap &emap, const CUtensorMap &bmap, int N, int n,
+                           View zout, const Coef<T> *coef, const int *active, int *errflag);
 
 // ---- transforms (transforms.cu) ----
 template <typename T>
