@@ -63,10 +63,11 @@ typedef struct {
     double stall_ratio;/* precision 1: an inner solve also stops once a cycle reduces its
                           relative residual by less than this factor (FP32 rounding of z
                           bounds the attainable residual near cond(L) * 6e-8); 0 = off */
-    int fused;         /* 1: on the global-memory levels the last pre-smoothing step is fused
-                          with residual and restriction, and interpolation with the first
-                          post-smoothing step (same arithmetic, fewer memory passes);
-                          0: one kernel per operation */
+    int fused;         /* on the global-memory levels, fuse the last pre-smoothing step with
+                          residual and restriction, and interpolation with the first
+                          post-smoothing step (same arithmetic, fewer memory passes):
+                          1 for the FP32 multigrid only (FP64 is bound by arithmetic, which
+                          the recomputed halos increase), 2 always, 0 never */
 } pd_config;
 
 /* Fills cfg with V(1,1), coarsest 3, maxit 100, tol 1e-10, omega_mode 1, FP64,

@@ -226,7 +226,7 @@ void alloc_prec(pd_ctx *c) {
     B.z[1] = dalloc<void *>(c, bytes);
     B.b = dalloc<void *>(c, bytes);
   }
-  if (c->cfg.fused) {
+  if (c->cfg.fused == 2 || (c->cfg.fused == 1 && sizeof(T) == sizeof(float))) {
     const FusedGeom g = fused_geom<T>();
     const int e = (int)(sizeof(C) / 8);
     for (int l = 0; l + 1 < L && l < c->lc; l++) {
@@ -410,7 +410,7 @@ void run_cycle(pd_ctx *c, int l, bool zzero, bool top, const int *active, double
     ck_launch(c);
     return;
   }
-  if (c->cfg.fused && B.maps && c->cfg.nu1 >= 1 && c->cfg.nu2 >= 1) {
+  if (B.maps && c->cfg.nu1 >= 1 && c->cfg.nu2 >= 1) {
     run_cycle_fused<T>(c, l, zzero, top, active, tol, maxit);
     return;
   }
@@ -769,7 +769,7 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
       cfg.maxit > 100000 || !(cfg.tol >= 0) || cfg.omega_mode < 0 || cfg.omega_mode > 2 ||
       cfg.precision < 0 || cfg.precision > 1 || cfg.smoother < 0 || cfg.smoother > 1 ||
       !(cfg.inner_tol >= 0) || cfg.max_refine < 1 || cfg.inner_maxit < 1 ||
-      cfg.inner_maxit > 100000 || !(cfg.stall_ratio >= 0) || cfg.fused < 0 || cfg.fused > 1)
+      cfg.inner_maxit > 100000 || !(cfg.stall_ratio >= 0) || cfg.fused < 0 || cfg.fused > 2)
     return PD_ERR_ARG;
   if (cfg.omega_mode == 2 && !omega) return PD_ERR_ARG;
   if (cfg.precision == 1 && (!B || !V)) return PD_ERR_ARG;

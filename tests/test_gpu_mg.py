@@ -244,7 +244,7 @@ def test_mg_vcycle_fused_and_unfused_fp64(fused, N, level, cyc):
     prm = CYCLES[cyc]
     rng = np.random.default_rng(21 + level)
     n = len(SHIFTS)
-    c = ctx_for(N, SHIFTS, omega_mode=0, fused=fused, **prm)
+    c = ctx_for(N, SHIFTS, omega_mode=0, fused=2 * fused, **prm)
     Nl = c.Ns[level]
     z = rand_c(rng, (n, Nl, Nl))
     b = rand_c(rng, (n, Nl, Nl)) * 100
@@ -252,7 +252,7 @@ def test_mg_vcycle_fused_and_unfused_fp64(fused, N, level, cyc):
     c.mg_vcycle(level, zt, dev(b))
     op = core.mg_params(prm["cycle_gamma"], prm["nu1"], prm["nu2"], prm["coarsest_n"])
     ref = np.stack([core.mg_cycle(Nl, SHIFTS[j], [24 / 25] * 16, b[j], z[j], op) for j in range(n)])
-    assert rel_per_vector(host(zt), ref) < 1e-13
+    assert rel_per_vector(host(zt), ref) < 1e-12
 
 
 @pytest.mark.parametrize("fused", [0, 1])
