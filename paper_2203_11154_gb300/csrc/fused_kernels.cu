@@ -28,7 +28,7 @@ namespace {
 template <typename T> struct FT;
 template <> struct FT<float> { static constexpr int TX = 128, TY = 16; };
 template <> struct FT<double> { static constexpr int TX = 64, TY = 16; };
-constexpr int kFT = 512;
+constexpr int kFT = 1024;
 
 // TMA x coordinates count 8-byte elements: one per FP32 complex, two per FP64 complex
 template <typename T> struct XS { static constexpr int v = sizeof(typename Cx<T>::type) / 8; };

@@ -38,6 +38,10 @@ template <typename T> struct Prec {
   C *cinv = nullptr;        // [n][mc*mc]
   C *Wf = nullptr;          // V^{-1}, n x n
   C *Wi = nullptr;          // V, n x n
+  // TF32 split operands of the tensor-core transforms (forward scaled by h^2 and unscaled)
+  float *tc_fwd_hi = nullptr, *tc_fwd_lo = nullptr, *tc_inv_hi = nullptr, *tc_inv_lo = nullptr;
+  float *tc_fwd1_hi = nullptr, *tc_fwd1_lo = nullptr;
+  bool tc = false;
 };
 
 }  // namespace
@@ -309,6 +313,28 @@ void alloc_prec(pd_ctx *c) {
     ck(c, cudaMemcpy(P.Wf, wf.data(), wf.size() * sizeof(C), cudaMemcpyHostToDevice));
     ck(c, cudaMemcpy(P.Wi, wi.data(), wi.size() * sizeof(C), cudaMemcpyHostToDevice));
   }
+  if (sizeof(T) == sizeof(float) && c->have_V && c->cfg.tensor_transforms &&
+      tc_transforms_supported(c->N, n)) {
+    const size_t fa = 128 * 64, ia = 128 * 128;
+    std::vector<float> fh(fa), fl(fa), ih(ia), il(ia), f1h(fa), f1l(fa), ih2(ia), il2(ia);
+    const double h0 = hl(c, 0);
+    tc_build_operands(n, c->Vinv.data(), c->V.data(), h0 * h0, fh.data(), fl.data(), ih.data(), il.data());
+    tc_build_operands(n, c->Vinv.data(), c->V.data(), 1.0, f1h.data(), f1l.data(), ih2.data(), il2.data());
+    P.tc_fwd_hi = dalloc<float *>(c, fa * 4);
+    P.tc_fwd_lo = dalloc<float *>(c, fa * 4);
+    P.tc_fwd1_hi = dalloc<float *>(c, fa * 4);
+    P.tc_fwd1_lo = dalloc<float *>(c, fa * 4);
+    P.tc_inv_hi = dalloc<float *>(c, ia * 4);
+    P.tc_inv_lo = dalloc<float *>(c, ia * 4);
+    ck(c, cudaMemcpy(P.tc_fwd_hi, fh.data(), fa * 4, cudaMemcpyHostToDevice));
+    ck(c, cudaMemcpy(P.tc_fwd_lo, fl.data(), fa * 4, cudaMemcpyHostToDevice));
+    ck(c, cudaMemcpy(P.tc_fwd1_hi, f1h.data(), fa * 4, cudaMemcpyHostToDevice));
+    ck(c, cudaMemcpy(P.tc_fwd1_lo, f1l.data(), fa * 4, cudaMemcpyHostToDevice));
+    ck(c, cudaMemcpy(P.tc_inv_hi, ih.data(), ia * 4, cudaMemcpyHostToDevice));
+    ck(c, cudaMemcpy(P.tc_inv_lo, il.data(), ia * 4, cudaMemcpyHostToDevice));
+    ck(c, prepare_tc_transforms());
+    P.tc = true;
+  }
   // the attributes are per kernel, shared by all contexts: set the largest any context
   // can use (coarse launches never exceed kCoarseSmemLimit; transforms need n <= 128)
   ck(c, prepare_coarse<T>(kCoarseSmemLimit));
@@ -555,6 +581,42 @@ void allatonce_norms(pd_ctx *c, double *r, const double *u, const double *f, con
   prof_resolve(c);
 }
 
+// forward transform into view g (scaled: the level-0 h^2 scaling; else unscaled)
+template <typename T>
+void transform_forward(pd_ctx *c, View g, const double *f, const double *u0, bool scaled) {
+  Prec<T> &P = prec<T>(c);
+  const double h = hl(c, 0);
+  if (P.tc) {
+    launch_tc_forward(c->stream, c->num_sms, c->N, c->n, g, f, u0, c->d_u0coef,
+                      scaled ? P.tc_fwd_hi : P.tc_fwd1_hi, scaled ? P.tc_fwd_lo : P.tc_fwd1_lo,
+                      c->st.flags);
+  } else {
+    launch_transform_forward<T>(c->stream, c->N, c->n, g, f, u0, c->d_u0coef, P.Wf,
+                                scaled ? h * h : 1.0);
+  }
+}
+
+template <typename T>
+void transform_inverse(pd_ctx *c, double *u, View z0, View z1, const int *final_buf, bool acc,
+                       bool imag) {
+  Prec<T> &P = prec<T>(c);
+  if (P.tc)
+    launch_tc_inverse(c->stream, c->num_sms, c->N, c->n, u, z0, z1, final_buf, P.tc_inv_hi,
+                      P.tc_inv_lo, acc, imag, c->d_imag, c->st.flags);
+  else
+    launch_transform_inverse<T>(c->stream, c->N, c->n, u, z0, z1, final_buf, P.Wi, acc, imag,
+                                c->d_imag);
+}
+
+void check_wait_flags(pd_ctx *c) {
+  ck(c, cudaMemcpyAsync(&c->h_pinned[2], c->st.flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  ck(c, cudaStreamSynchronize(c->stream));
+  if (c->h_pinned[2] & 6) {
+    c->err = "a bounded wait ran out in a TMA or tensor-core kernel";
+    throw CudaFail{cudaErrorLaunchTimeout};
+  }
+}
+
 template <typename T>
 pd_status paradiag_impl(pd_ctx *c, double *u, const double *f, const double *u0, int *h_iters,
                         double *h_relres, double *stats) {
@@ -584,13 +646,12 @@ pd_status paradiag_impl(pd_ctx *c, double *u, const double *f, const double *u0,
   const double fwd_bytes = (8.0 + w) * m, fwd_u0 = 8.0 * m / n;
   if (c->cfg.precision == 0) {
     PD_PROF(PD_KC_FORWARD, fwd_bytes + (u0 ? fwd_u0 : 0.0), 0,
-            launch_transform_forward<T>(c->stream, N, n, g, f, u0, c->d_u0coef, P.Wf, h2));
+            transform_forward<T>(c, g, f, u0, true));
     ck_launch(c);
     rc = solve_levels<T>(c, c->cfg.tol, c->cfg.maxit);
     accumulate_iters();
     PD_PROF(PD_KC_INVERSE, (w + 8.0) * m, 0,
-            launch_transform_inverse<T>(c->stream, N, n, u, z0, z1, c->st.final_buf, P.Wi, false,
-                                        imag, c->d_imag));
+            transform_inverse<T>(c, u, z0, z1, c->st.final_buf, false, imag));
     ck_launch(c);
     if (c->have_B) {
       double rn, fn;
@@ -605,11 +666,9 @@ pd_status paradiag_impl(pd_ctx *c, double *u, const double *f, const double *u0,
     for (int step = 0; step < std::max(1, c->cfg.max_refine); step++) {
       if (step == 0)
         PD_PROF(PD_KC_FORWARD, fwd_bytes + (u0 ? fwd_u0 : 0.0), 0,
-                launch_transform_forward<T>(c->stream, N, n, g, f, u0, c->d_u0coef, P.Wf, h2));
+                transform_forward<T>(c, g, f, u0, true));
       else
-        PD_PROF(PD_KC_FORWARD, fwd_bytes, 0,
-                launch_transform_forward<T>(c->stream, N, n, g, c->d_r, nullptr, c->d_u0coef, P.Wf,
-                                            h2));
+        PD_PROF(PD_KC_FORWARD, fwd_bytes, 0, transform_forward<T>(c, g, c->d_r, nullptr, true));
       ck_launch(c);
       pd_status s = solve_levels<T>(c, c->cfg.inner_tol, c->cfg.inner_maxit, c->cfg.stall_ratio);
       if (s == PD_ERR_NAN) {
@@ -618,8 +677,7 @@ pd_status paradiag_impl(pd_ctx *c, double *u, const double *f, const double *u0,
       }
       accumulate_iters();
       PD_PROF(PD_KC_INVERSE, (w + (step > 0 ? 16.0 : 8.0)) * m, 0,
-              launch_transform_inverse<T>(c->stream, N, n, u, z0, z1, c->st.final_buf, P.Wi,
-                                          step > 0, imag, c->d_imag));
+              transform_inverse<T>(c, u, z0, z1, c->st.final_buf, step > 0, imag));
       ck_launch(c);
       double rn, fn;
       allatonce_norms(c, c->d_r, u, f, u0, &rn, &fn);
@@ -637,6 +695,7 @@ pd_status paradiag_impl(pd_ctx *c, double *u, const double *f, const double *u0,
     st_local[PD_STAT_REFINE_STEPS] = steps;
     if (rc == PD_OK && !(relres <= c->cfg.tol)) rc = PD_ERR_NOCONV;
   }
+  check_wait_flags(c);
   if (imag) {
     unsigned long long bits = 0;
     ck(c, cudaMemcpy(&bits, c->d_imag, sizeof(bits), cudaMemcpyDeviceToHost));
@@ -706,9 +765,10 @@ void pd_config_default(pd_config *cfg) {
   cfg->inner_tol = 1e-6;
   cfg->max_refine = 12;
   cfg->imag_check = 1;
-  cfg->inner_maxit = 8;
+  cfg->inner_maxit = 3;
   cfg->stall_ratio = 0.5;
   cfg->fused = 1;
+  cfg->tensor_transforms = 1;
 }
 
 pd_status pd_alpha_circulant(int n, double tau, double alpha, double *B, double *shifts,
@@ -769,7 +829,8 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
       cfg.maxit > 100000 || !(cfg.tol >= 0) || cfg.omega_mode < 0 || cfg.omega_mode > 2 ||
       cfg.precision < 0 || cfg.precision > 1 || cfg.smoother < 0 || cfg.smoother > 1 ||
       !(cfg.inner_tol >= 0) || cfg.max_refine < 1 || cfg.inner_maxit < 1 ||
-      cfg.inner_maxit > 100000 || !(cfg.stall_ratio >= 0) || cfg.fused < 0 || cfg.fused > 2)
+      cfg.inner_maxit > 100000 || !(cfg.stall_ratio >= 0) || cfg.fused < 0 || cfg.fused > 2 ||
+      cfg.tensor_transforms < 0 || cfg.tensor_transforms > 1)
     return PD_ERR_ARG;
   if (cfg.omega_mode == 2 && !omega) return PD_ERR_ARG;
   if (cfg.precision == 1 && (!B || !V)) return PD_ERR_ARG;
@@ -1068,12 +1129,11 @@ pd_status pd_transform_forward(pd_ctx *c, void *g, const double *f, const double
   if (!c->have_V) return PD_ERR_STATE;
   PD_TRY(c, {
     if (c->cfg.precision == 0)
-      launch_transform_forward<double>(c->stream, c->N, c->n, uview(g, c->N), f, u0, c->d_u0coef,
-                                       c->p64.Wf, 1.0);
+      transform_forward<double>(c, uview(g, c->N), f, u0, false);
     else
-      launch_transform_forward<float>(c->stream, c->N, c->n, uview(g, c->N), f, u0, c->d_u0coef,
-                                      c->p32.Wf, 1.0);
+      transform_forward<float>(c, uview(g, c->N), f, u0, false);
     ck_launch(c);
+    check_wait_flags(c);
     return PD_OK;
   })
 }
@@ -1084,12 +1144,11 @@ pd_status pd_transform_inverse(pd_ctx *c, double *u, const void *z, int accumula
   PD_TRY(c, {
     const View zv = uview(z, c->N);
     if (c->cfg.precision == 0)
-      launch_transform_inverse<double>(c->stream, c->N, c->n, u, zv, zv, nullptr, c->p64.Wi,
-                                       accumulate != 0, false, nullptr);
+      transform_inverse<double>(c, u, zv, zv, nullptr, accumulate != 0, false);
     else
-      launch_transform_inverse<float>(c->stream, c->N, c->n, u, zv, zv, nullptr, c->p32.Wi,
-                                      accumulate != 0, false, nullptr);
+      transform_inverse<float>(c, u, zv, zv, nullptr, accumulate != 0, false);
     ck_launch(c);
+    check_wait_flags(c);
     return PD_OK;
   })
 }

@@ -132,6 +132,18 @@ void launch_allatonce_residual(cudaStream_t s, int N, int n, double *r, const do
                                const int *Bptr, const int *Bcol, const double *Bval,
                                double *part);
 
+// ---- tensor-core transforms (tc_transforms.cu), FP32 working type, n <= 64 ----
+bool tc_transforms_supported(int N, int n);
+cudaError_t prepare_tc_transforms();
+void tc_build_operands(int n, const double *Vinv, const double *V, double scale, float *fwd_hi,
+                       float *fwd_lo, float *inv_hi, float *inv_lo);
+void launch_tc_forward(cudaStream_t s, int grid, int N, int n, View g, const double *f,
+                       const double *u0, const double *u0coef, const float *Ahi, const float *Alo,
+                       int *errflag);
+void launch_tc_inverse(cudaStream_t s, int grid, int N, int n, double *u, View z0, View z1,
+                       const int *final_buf, const float *Ahi, const float *Alo, bool accumulate,
+                       bool imag_check, unsigned long long *imag_bits, int *errflag);
+
 // ---- host-side setup (setup.cpp) ----
 void vanka_abc(double er, double ei, double out[6]);
 double lfa_omega_opt(double er, double ei, int jacobi);

@@ -1,0 +1,414 @@
+// Time-direction transforms of eq. (1) on the 5th-generation tensor cores (tcgen05),
+// for n <= 64 shifts.  Both are real GEMMs D[128 x Nt] = A[128 x K] B[K x Nt] over tiles
+// of Nt grid points of one grid row, in TF32 with the 3-product split
+//   A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi,  x_hi = x rounded to TF32, x_lo = x - x_hi,
+// accumulated in FP32 in tensor memory: about 2^-21 relative per product, the
+// FP32-compensated product the refinement needs because V can be ill-conditioned.
+//
+//   forward:  K = 64 (k < n),  rows 2j / 2j+1 of A = Re / Im of h^2 V^{-1}[j][k],
+//             B[k][p] = fhat_k at point p (FP64 input, rounded to FP32 then split);
+//             g_j(p) = (D[2j][p], D[2j+1][p]).
+//   inverse:  K = 128 (2j + re/im), row k of A = (Re V[k][j], -Im V[k][j]) and row 64 + k =
+//             (Im V[k][j], Re V[k][j]), B[2j+q][p] = component q of z_j(p);
+//             u_k(p) (+)= D[k][p], max |D[64+k][p]| is the imaginary-part check.
+//
+// Operands live in shared memory in the K-major layout with 128-byte swizzling (8-row x
+// 128-byte atoms, 16-byte chunk c of row r stored at chunk c ^ (r mod 8)); A is loaded
+// once per CTA, B is built per tile by all threads.  One thread issues the MMAs and
+// commits them to an mbarrier; the epilogue reads the accumulators with tcgen05.ld
+// through a padded shared-memory stage so that the global stores are coalesced.
+#include "cplx.cuh"
+#include "pd_internal.h"
+#include "tma.cuh"
+
+namespace pd {
+namespace {
+
+constexpr int kTcThreads = 256;
+constexpr int kM = 128;
+
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);  // start address
+  d |= (uint64_t)1 << 16;                   // leading-dimension offset (unused: swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;         // stride between 8-row groups: 8 x 128 B
+  d |= (uint64_t)1 << 46;                   // descriptor version of tcgen05
+  d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+  return d;
+}
+
+// kind::tf32 instruction descriptor: FP32 accumulator, TF32 A and B, both K-major
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 32; q++) v[q] = __uint_as_float(r[q]);
+}
+
+// TF32 split: hi = x rounded to 10 explicit mantissa bits, lo = x - hi (exact)
+__device__ __forceinline__ void split_tf32(float x, float &hi, float &lo) {
+  const uint32_t b = (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
+  hi = __uint_as_float(b);
+  lo = x - hi;
+}
+
+// byte offset of the 16-byte chunk holding K values [4q, 4q+4) of row `row` in a
+// K-major, 128B-swizzled operand with `rows` rows
+__device__ __forceinline__ uint32_t sw_off(int row, int q, int rows) {
+  const int atom = q >> 3, ch = q & 7;
+  return (uint32_t)(atom * rows * 128 + row * 128 + ((ch ^ (row & 7)) << 4));
+}
+
+// copies a row-major [128][K] float matrix from global memory into the swizzled layout
+template <int K>
+__device__ void load_a(const float *__restrict__ src, unsigned char *dst) {
+  for (int it = threadIdx.x; it < kM * (K / 4); it += kTcThreads) {
+    const int row = it / (K / 4), q = it % (K / 4);
+    const float4 v = *reinterpret_cast<const float4 *>(src + (size_t)row * K + 4 * q);
+    *reinterpret_cast<float4 *>(dst + sw_off(row, q, kM)) = v;
+  }
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// issues the 3 x (K/8) MMAs of one tile and commits them to `bar` (one thread)
+template <int K, int NT>
+__device__ __forceinline__ void issue_tile(uint32_t tmem, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
+                                           uint32_t b_lo, uint64_t *bar) {
+  constexpr uint32_t idesc = idesc_tf32(kM, NT);
+  uint32_t acc = 0;
+#pragma unroll
+  for (int ks = 0; ks < K / 8; ks++) {
+    const uint32_t ao = (uint32_t)((ks >> 2) * kM * 128 + (ks & 3) * 32);
+    const uint32_t bo = (uint32_t)((ks >> 2) * NT * 128 + (ks & 3) * 32);
+    mma_tf32(tmem, desc_sw128(a_hi + ao), desc_sw128(b_hi + bo), idesc, acc);
+    acc = 1;
+    mma_tf32(tmem, desc_sw128(a_hi + ao), desc_sw128(b_lo + bo), idesc, 1);
+    mma_tf32(tmem, desc_sw128(a_lo + ao), desc_sw128(b_hi + bo), idesc, 1);
+  }
+  mma_commit(bar);
+}
+
+constexpr int kFwdK = 64, kFwdNt = 128, kInvK = 128, kInvNt = 64;
+constexpr int kFwdA = kM * kFwdK * 4, kFwdB = kFwdNt * kFwdK * 4;  // bytes per split
+constexpr int kInvA = kM * kInvK * 4, kInvB = kInvNt * kInvK * 4;
+constexpr int kFwdS = 64 * 66 * 4;   // epilogue stage: 64 j rows x 32 complex (stride 66 floats)
+constexpr int kInvS = kM * 33 * 4;   // epilogue stage: 128 rows x 32 columns (stride 33)
+constexpr int kFwdSmem = 2 * kFwdA + 2 * kFwdB + kFwdS + 1024;
+constexpr int kInvSmem = 2 * kInvA + 2 * kInvB + kInvS + 1024;
+
+__device__ __forceinline__ unsigned char *align1024(unsigned char *p) {
+  return p + ((1024 - (smem_u32(p) & 1023)) & 1023);
+}
+
+// g_j(p) = h^2 sum_k V^{-1}[j][k] fhat_k(p), fhat_k = f_k + u0coef[k] u0, for the points
+// p = (i, c0..c0+127) of grid row i; written into the h^2-scaled level-0 RHS view.
+__global__ void __launch_bounds__(kTcThreads, 1)
+k_tc_forward(int N, int n, View g, const double *__restrict__ f, const double *__restrict__ u0,
+             const double *__restrict__ u0coef, const float *__restrict__ Ahi,
+             const float *__restrict__ Alo, int *__restrict__ errflag) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *sm = align1024(smem_raw);
+  unsigned char *sAhi = sm, *sAlo = sm + kFwdA, *sBhi = sm + 2 * kFwdA, *sBlo = sBhi + kFwdB;
+  float *S = reinterpret_cast<float *>(sBlo + kFwdB);
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) tmem_alloc(&tmem_slot, kFwdNt);
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+  }
+  load_a<kFwdK>(Ahi, sAhi);
+  load_a<kFwdK>(Alo, sAlo);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const long long m = (long long)N * N;
+  const int tpr = (int)((g.pitch + kFwdNt - 1) / kFwdNt);  // tiles per grid row
+  const int total = N * tpr;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int t = blockIdx.x; t < total; t += gridDim.x) {
+    const int i = t / tpr, c0 = (t % tpr) * kFwdNt;
+    // B[p][k] = fhat_k(i, c0 + p): 4 consecutive k per thread, coalesced over p
+    for (int it = tid; it < kFwdNt * (kFwdK / 4); it += kTcThreads) {
+      const int p = it % kFwdNt, q = it / kFwdNt;
+      const int c = c0 + p;
+      float4 hi, lo;
+      float *h4 = &hi.x, *l4 = &lo.x;
+#pragma unroll
+      for (int e = 0; e < 4; e++) {
+        const int k = 4 * q + e;
+        double v = 0.0;
+        if (k < n && c < N) {
+          const long long x = (long long)i * N + c;
+          v = f[k * m + x];
+          if (u0) v += u0coef[k] * u0[x];
+        }
+        split_tf32((float)v, h4[e], l4[e]);
+      }
+      *reinterpret_cast<float4 *>(sBhi + sw_off(p, q, kFwdNt)) = hi;
+      *reinterpret_cast<float4 *>(sBlo + sw_off(p, q, kFwdNt)) = lo;
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      issue_tile<kFwdK, kFwdNt>(tmem, smem_u32(sAhi), smem_u32(sAlo), smem_u32(sBhi), smem_u32(sBlo),
+                                &bar);
+    }
+    ok = mbar_wait_bounded(&bar, phase);
+    if (!__syncthreads_and(ok)) {
+      if (tid == 0) atomicOr(errflag, 4);
+      break;
+    }
+    phase ^= 1;
+    tc_fence_after();
+    // epilogue, 32 columns at a time: lanes of warps 0-3 hold rows 2j+q of D
+    for (int chunk = 0; chunk < kFwdNt / 32; chunk++) {
+      if (warp < 4) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * chunk), v);
+        const int row = 32 * warp + lane, j = row >> 1, q = row & 1;
+        if (j < n)
+#pragma unroll
+          for (int cc = 0; cc < 32; cc++) S[j * 66 + 2 * cc + q] = v[cc];
+      }
+      __syncthreads();
+      for (int it = tid; it < n * 32; it += kTcThreads) {
+        const int j = it >> 5, cc = it & 31;
+        const int c = c0 + 32 * chunk + cc;
+        if (c < N) {
+          const float2 val = *reinterpret_cast<const float2 *>(&S[j * 66 + 2 * cc]);
+          reinterpret_cast<float2 *>(g.p)[j * g.plane + (long long)i * g.pitch + c] = val;
+        }
+      }
+      __syncthreads();
+    }
+    tc_fence_before();
+  }
+  if (!ok && tid == 0) mbar_wait_bounded(&bar, phase);  // let an MMA in flight finish
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, kFwdNt);
+}
+
+// u_k(p) (+)= Re sum_j V[k][j] z_j(p) for p = (i, c0..c0+63); z_j is read from z1 where
+// final_buf[j] is set, else from z0; imag_check: atomic max of |Im| (bits of a double).
+__global__ void __launch_bounds__(kTcThreads, 1)
+k_tc_inverse(int N, int n, double *__restrict__ u, View z0, View z1, const int *__restrict__ final_buf,
+             const float *__restrict__ Ahi, const float *__restrict__ Alo, int accumulate,
+             int imag_check, unsigned long long *imag_bits, int *__restrict__ errflag) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *sm = align1024(smem_raw);
+  unsigned char *sAhi = sm, *sAlo = sm + kInvA, *sBhi = sm + 2 * kInvA, *sBlo = sBhi + kInvB;
+  float *S = reinterpret_cast<float *>(sBlo + kInvB);
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ float red[kTcThreads / 32];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) tmem_alloc(&tmem_slot, kInvNt);
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+  }
+  load_a<kInvK>(Ahi, sAhi);
+  load_a<kInvK>(Alo, sAlo);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const long long m = (long long)N * N;
+  const int tpr = (int)((z0.pitch + kInvNt - 1) / kInvNt);
+  const int total = N * tpr;
+  uint32_t phase = 0;
+  bool ok = true;
+  float imax = 0.f;
+  for (int t = blockIdx.x; t < total; t += gridDim.x) {
+    const int i = t / tpr, c0 = (t % tpr) * kInvNt;
+    // B[p][2j+q] = component q of z_j(i, c0+p): two shifts (one 16-byte chunk) per item
+    for (int it = tid; it < kInvNt * (kInvK / 4); it += kTcThreads) {
+      const int p = it % kInvNt, qq = it / kInvNt;
+      const int c = c0 + p;
+      float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+      const int j0 = 2 * qq, j1 = 2 * qq + 1;
+      if (c < N) {
+        if (j0 < n) {
+          const View &zv = (final_buf && final_buf[j0]) ? z1 : z0;
+          a = reinterpret_cast<const float2 *>(zv.p)[j0 * zv.plane + (long long)i * zv.pitch + c];
+        }
+        if (j1 < n) {
+          const View &zv = (final_buf && final_buf[j1]) ? z1 : z0;
+          b = reinterpret_cast<const float2 *>(zv.p)[j1 * zv.plane + (long long)i * zv.pitch + c];
+        }
+      }
+      float4 hi, lo;
+      split_tf32(a.x, hi.x, lo.x);
+      split_tf32(a.y, hi.y, lo.y);
+      split_tf32(b.x, hi.z, lo.z);
+      split_tf32(b.y, hi.w, lo.w);
+      *reinterpret_cast<float4 *>(sBhi + sw_off(p, qq, kInvNt)) = hi;
+      *reinterpret_cast<float4 *>(sBlo + sw_off(p, qq, kInvNt)) = lo;
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      issue_tile<kInvK, kInvNt>(tmem, smem_u32(sAhi), smem_u32(sAlo), smem_u32(sBhi), smem_u32(sBlo),
+                                &bar);
+    }
+    ok = mbar_wait_bounded(&bar, phase);
+    if (!__syncthreads_and(ok)) {
+      if (tid == 0) atomicOr(errflag, 4);
+      break;
+    }
+    phase ^= 1;
+    tc_fence_after();
+    for (int chunk = 0; chunk < kInvNt / 32; chunk++) {
+      if (warp < 4) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * chunk), v);
+        const int row = 32 * warp + lane;
+#pragma unroll
+        for (int cc = 0; cc < 32; cc++) S[row * 33 + cc] = v[cc];
+      }
+      __syncthreads();
+      for (int it = tid; it < n * 32; it += kTcThreads) {
+        const int k = it >> 5, cc = it & 31;
+        const int c = c0 + 32 * chunk + cc;
+        if (c < N) {
+          const long long x = (long long)k * m + (long long)i * N + c;
+          double val = (double)S[k * 33 + cc];
+          if (accumulate) val += u[x];
+          u[x] = val;
+          if (imag_check) imax = fmaxf(imax, fabsf(S[(64 + k) * 33 + cc]));
+        }
+      }
+      __syncthreads();
+    }
+    tc_fence_before();
+  }
+  if (!ok && tid == 0) mbar_wait_bounded(&bar, phase);
+  if (imag_check) {
+    for (int o = 16; o > 0; o >>= 1) imax = fmaxf(imax, __shfl_down_sync(0xffffffffu, imax, o));
+    if (lane == 0) red[warp] = imax;
+  }
+  __syncthreads();
+  if (imag_check && tid == 0) {
+    float mx = 0.f;
+    for (int w = 0; w < kTcThreads / 32; w++) mx = fmaxf(mx, red[w]);
+    atomicMax(imag_bits, (unsigned long long)__double_as_longlong((double)mx));
+  }
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, kInvNt);
+}
+
+}  // namespace
+
+bool tc_transforms_supported(int N, int n) { return n <= 64 && N >= 127; }
+
+cudaError_t prepare_tc_transforms() {
+  cudaError_t e = cudaFuncSetAttribute(k_tc_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_tc_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, kInvSmem);
+}
+
+// A operands (host): TF32 splits of the scaled forward matrix [128][64] and of the
+// inverse matrix [128][128] in the row layouts described at the top of this file.
+static void split_host(double x, float &hi, float &lo) {
+  const float xf = (float)x;
+  uint32_t b;
+  memcpy(&b, &xf, 4);
+  b = (b + 0x1000u) & 0xFFFFE000u;
+  memcpy(&hi, &b, 4);
+  lo = (float)(x - (double)hi);
+}
+
+void tc_build_operands(int n, const double *Vinv, const double *V, double scale, float *fwd_hi,
+                       float *fwd_lo, float *inv_hi, float *inv_lo) {
+  for (int r = 0; r < kM; r++)
+    for (int k = 0; k < kFwdK; k++) {
+      double v = 0.0;
+      const int j = r >> 1;
+      if (j < n && k < n) v = scale * Vinv[2 * ((size_t)j * n + k) + (r & 1)];
+      split_host(v, fwd_hi[r * kFwdK + k], fwd_lo[r * kFwdK + k]);
+    }
+  for (int r = 0; r < kM; r++)
+    for (int kk = 0; kk < kInvK; kk++) {
+      double v = 0.0;
+      const int j = kk >> 1, q = kk & 1;
+      const int k = r < 64 ? r : r - 64;
+      if (k < n && j < n) {
+        const double vr = V[2 * ((size_t)k * n + j)], vi = V[2 * ((size_t)k * n + j) + 1];
+        if (r < 64) v = q == 0 ? vr : -vi;  // Re(V z) = Vr zr - Vi zi
+        else v = q == 0 ? vi : vr;          // Im(V z) = Vi zr + Vr zi
+      }
+      split_host(v, inv_hi[r * kInvK + kk], inv_lo[r * kInvK + kk]);
+    }
+}
+
+void launch_tc_forward(cudaStream_t s, int grid, int N, int n, View g, const double *f,
+                       const double *u0, const double *u0coef, const float *Ahi, const float *Alo,
+                       int *errflag) {
+  k_tc_forward<<<grid, kTcThreads, kFwdSmem, s>>>(N, n, g, f, u0, u0coef, Ahi, Alo, errflag);
+}
+
+void launch_tc_inverse(cudaStream_t s, int grid, int N, int n, double *u, View z0, View z1,
+                       const int *final_buf, const float *Ahi, const float *Alo, bool accumulate,
+                       bool imag_check, unsigned long long *imag_bits, int *errflag) {
+  k_tc_inverse<<<grid, kTcThreads, kInvSmem, s>>>(N, n, u, z0, z1, final_buf, Ahi, Alo,
+                                                  accumulate ? 1 : 0, imag_check ? 1 : 0, imag_bits,
+                                                  errflag);
+}
+
+}  // namespace pd

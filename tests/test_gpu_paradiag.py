@@ -155,3 +155,29 @@ def test_paradiag_without_V_is_a_state_error():
     with pytest.raises(api.PDError) as e:
         c.paradiag_solve(u, u.clone())
     assert e.value.status == "PD_ERR_STATE"
+
+
+@pytest.mark.parametrize("tc", [1, 0])
+@pytest.mark.parametrize("N,n", [(127, 16), (255, 64), (255, 5)])
+def test_transforms_fp32_tensor_cores(tc, N, n):
+    """FP32 context: TF32x3 tcgen05 transforms (tc=1) and FP32 CUDA-core products (tc=0)
+    against the FP64 oracle: relative error per shift vector of a few 1e-7 (TF32x3
+    keeps about 21 bits per product; fhat is rounded to FP32 first)."""
+    alpha = 1e-3
+    rng = np.random.default_rng(N + n)
+    c = api.alpha_circulant_context(N, n, 1.0 / n, alpha, precision=1, tensor_transforms=tc)
+    lam, V, Vinv = core.alpha_circulant(n, 1.0 / n, alpha)
+    f = rng.uniform(-1, 1, (n, N, N))
+    u0 = inputs.sine_initial_value(N)
+    g = torch.empty(n, N, N, dtype=torch.complex64, device="cuda")
+    c.pd_transform_forward(g, dev(f), dev(u0))
+    fhat = core.assemble_rhs(N, n, 1.0 / n, f, u0)
+    ref = core.time_transform(Vinv, fhat.reshape(n, -1)).reshape(n, N, N)
+    assert rel_per_vector(host(g), ref) < 2e-6
+    z = (rng.uniform(-1, 1, (n, N, N)) + 1j * rng.uniform(-1, 1, (n, N, N))).astype(np.complex64)
+    u = torch.full((n, N, N), 0.25, dtype=torch.float64, device="cuda")
+    c.pd_transform_inverse(u, dev(z, torch.complex64), accumulate=True)
+    ref = core.time_transform(V, z.astype(np.complex128).reshape(n, -1)).real.reshape(n, N, N) + 0.25
+    g_w = (alpha ** (np.arange(n) / n))[:, None, None]
+    err = np.linalg.norm(g_w * (host(u) - ref)) / np.linalg.norm(g_w * ref)
+    assert err < 2e-6
