@@ -213,6 +213,33 @@ pd_status pd_allatonce_residual(pd_ctx *ctx, double *d_r, const double *d_u, con
                                 const double *d_u0, double *h_norms);
 
 /*
+ * Allocation-free residual check for the alpha-circulant backward-Euler system (the
+ * paper has no counterpart; it is a service for callers of this library).
+ *
+ * For callers that cannot call cudaMalloc where they need this check - a framework that
+ * owns all device memory through its own pool or arena and forbids other allocations,
+ * or a time-critical loop that cannot afford cudaMalloc's device-wide synchronisation.
+ * It needs no context and allocates nothing: the caller passes every input and output,
+ * and the only scratch (per-CTA partial sums) lives in a fixed 128 KiB array in device
+ * memory inside the library, which every GPU that loads the library keeps until exit.
+ *
+ * Computes, for B = (1/tau)(I - C_alpha) and fhat_1 = f_1 + u0 / tau, fhat_k = f_k else:
+ *   d_r = fhat - (B kron I_h + I_t kron A) d_u      (d_r may be NULL: norms only)
+ *   d_norms[0] = ||d_r||_2,  d_norms[1] = ||fhat||_2   (two doubles, device memory)
+ * d_u, d_f, d_r: [n][N][N] double, device; d_u0: [N][N] double or NULL; stream: the
+ * cudaStream_t the two kernels run on (NULL = legacy default stream).  Asynchronous.
+ * Limits: n <= 128 (the size of the scratch array); larger n returns PD_ERR_ARG, as do
+ * N < 1, tau <= 0, alpha outside (0, 1] and NULL d_u, d_f or d_norms.
+ * The first call on a device looks up the scratch array's device address (with that
+ * device current) and caches it; make that first call before any stream capture.
+ * All calls share the scratch array: calls whose kernels may overlap on the GPU (on
+ * different streams without ordering between them) race and must not be issued.
+ */
+pd_status pd_allatonce_residual_static(int N, int n, double tau, double alpha, const double *d_u,
+                                       const double *d_f, const double *d_u0, double *d_r,
+                                       double *d_norms, void *stream);
+
+/*
  * Instrumentation (no counterpart in the paper).  While enabled, the context records a
  * CUDA event pair on its stream around every kernel launch and attributes it to one of
  * the classes below, together with the algorithmic bytes of the launch (each array

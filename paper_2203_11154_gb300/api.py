@@ -34,7 +34,7 @@ EXPORTS = ["pd_config_default", "pd_alpha_circulant", "paradiag_setup", "pd_num_
            "pd_get_omega", "mg_vcycle", "shifted_solve_batched", "paradiag_solve",
            "paradiag_solve_host", "pd_smooth", "pd_residual_restrict", "pd_prolong_add",
            "pd_coarse_solve", "pd_transform_forward", "pd_transform_inverse",
-           "pd_allatonce_residual", "pd_profile_enable", "pd_profile_read", "pd_synchronize", "pd_launch_count", "paradiag_destroy",
+           "pd_allatonce_residual", "pd_allatonce_residual_static", "pd_profile_enable", "pd_profile_read", "pd_synchronize", "pd_launch_count", "paradiag_destroy",
            "pd_status_str", "pd_last_error"]
 
 
@@ -88,6 +88,7 @@ def lib(path=None):
             "pd_transform_forward": (_I, [_P, _P, _P, _P]),
             "pd_transform_inverse": (_I, [_P, _P, _P, _I]),
             "pd_allatonce_residual": (_I, [_P, _P, _P, _P, _P, _P]),
+            "pd_allatonce_residual_static": (_I, [_I, _I, _D, _D, _P, _P, _P, _P, _P, _P]),
             "pd_profile_enable": (_I, [_P, _I]),
             "pd_profile_read": (_I, [_P, _I, _P, _P, _P]),
             "pd_synchronize": (_I, [_P]),

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "libparadiag.so")
-CU_SOURCES = ["mg_kernels.cu", "fused_kernels.cu", "transforms.cu", "host.cu", "tc_transforms.cu"]
+CU_SOURCES = ["mg_kernels.cu", "fused_kernels.cu", "transforms.cu", "host.cu", "tc_transforms.cu", "static_residual.cu"]
 CPP_SOURCES = ["setup.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
