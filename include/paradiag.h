@@ -70,11 +70,14 @@ typedef struct {
                           the recomputed halos increase), 2 always, 0 never */
     int tensor_transforms; /* precision 1, n <= 64, N >= 127: the time transforms as TF32x3
                           tensor-core GEMMs (tcgen05); 0: FP32 CUDA-core products */
+    int fused_variant; /* implementation of the fused kernels: 0 = chosen at set-up by timing
+                          both on the context's own levels, 1 = TMA-staged shared-memory
+                          tiles, 2 = warp-streaming strips (cp.async ring, shuffles) */
 } pd_config;
 
 /* Fills cfg with V(1,1), coarsest 3, maxit 100, tol 1e-10, omega_mode 1, FP64,
  * Vanka, inner_tol 1e-6, max_refine 12, imag_check 1, inner_maxit 3, stall_ratio 0.5,
- * fused 1, tensor_transforms 1. */
+ * fused 1, tensor_transforms 1, fused_variant 0. */
 void pd_config_default(pd_config *cfg);
 
 /*

@@ -51,7 +51,7 @@ class pd_config(C.Structure):
                 ("omega_mode", C.c_int), ("precision", C.c_int), ("smoother", C.c_int),
                 ("inner_tol", C.c_double), ("max_refine", C.c_int), ("imag_check", C.c_int),
                 ("inner_maxit", C.c_int), ("stall_ratio", C.c_double), ("fused", C.c_int),
-                ("tensor_transforms", C.c_int)]
+                ("tensor_transforms", C.c_int), ("fused_variant", C.c_int)]
 
 
 _P = C.c_void_p

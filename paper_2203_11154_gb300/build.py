@@ -11,7 +11,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "libparadiag.so")
-CU_SOURCES = ["mg_kernels.cu", "fused_kernels.cu", "transforms.cu", "host.cu", "tc_transforms.cu", "static_residual.cu"]
+CU_SOURCES = ["mg_kernels.cu", "fused_kernels.cu", "stream_kernels.cu", "transforms.cu",
+              "tc_transforms.cu", "host.cu", "static_residual.cu"]
 CPP_SOURCES = ["setup.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -61,7 +62,7 @@ def build(force=False, verbose=False):
     if failed:
         raise RuntimeError("nvcc failed:\n" + "\n".join(failed))
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
+    cmd = [nvcc] + ARCH + ["-shared", "-Xlinker", "--no-undefined", "-o", tmp] + objs
     subprocess.check_call(cmd)
     os.replace(tmp, LIB)
     return LIB

@@ -74,6 +74,8 @@ struct pd_ctx {
   double *d_stage_f = nullptr, *d_stage_u = nullptr, *d_stage_u0 = nullptr;
   long long launches = 0;
   int num_sms = 0;
+  int fused_impl = 2;     // 1 TMA tiles, 2 warp streams (cfg.fused_variant, or timed at set-up)
+  int stream_grid = 0;    // persistent grid of the streaming kernels
   // instrumentation: event pairs around launches, resolved after each solve
   bool prof_on = false;
   int cur_cyc = -1;                 // cycle of the running batched solve, -1 outside
@@ -245,6 +247,8 @@ void alloc_prec(pd_ctx *c) {
       B.maps = true;
     }
     ck(c, prepare_fused<T>());
+    c->stream_grid = stream_grid<T>(c->num_sms);
+    c->fused_impl = c->cfg.fused_variant == 1 ? 1 : 2;
   }
   // smoother coefficients in the scaled form of pd_internal.h
   std::vector<Coef<T>> cf((size_t)L * n);
@@ -377,14 +381,22 @@ void run_cycle_fused(pd_ctx *c, int l, bool zzero, bool top, const int *active, 
     cur ^= 1;
     zzero = false;
   }
-  PD_PROF(l == 0 ? PD_KC_SR0 : PD_KC_SR_C, (zzero ? 2 : 3) * w * pts + w * ptsc, norm ? 1 : 2,
-          launch_smooth_restrict<T>(c->stream, grid, B.sr_z[cur], B.sr_b, N, n, z[cur ^ 1],
-                                    view(Bc.b, Bc.N, Bc.P), cf, active, zzero,
-                                    norm ? c->st.partials : nullptr, c->st.max_tiles, err));
+  const bool streams = c->fused_impl == 2;
+  const int units = streams ? stream_units(N) : ftiles;
+  if (streams)
+    PD_PROF(l == 0 ? PD_KC_SR0 : PD_KC_SR_C, (zzero ? 2 : 3) * w * pts + w * ptsc, norm ? 1 : 2,
+            launch_sr_stream<T>(c->stream, c->stream_grid, N, n, z[cur], b, z[cur ^ 1],
+                                view(Bc.b, Bc.N, Bc.P), cf, active, zzero,
+                                norm ? c->st.partials : nullptr, c->st.max_tiles));
+  else
+    PD_PROF(l == 0 ? PD_KC_SR0 : PD_KC_SR_C, (zzero ? 2 : 3) * w * pts + w * ptsc, norm ? 1 : 2,
+            launch_smooth_restrict<T>(c->stream, grid, B.sr_z[cur], B.sr_b, N, n, z[cur ^ 1],
+                                      view(Bc.b, Bc.N, Bc.P), cf, active, zzero,
+                                      norm ? c->st.partials : nullptr, c->st.max_tiles, err));
   ck_launch(c);
   if (norm) {
-    PD_PROF(PD_KC_CONVERGE, 8.0 * ftiles, 1,
-            launch_converge(c->stream, n, ftiles, c->st, tol, maxit, c->stall, cur));
+    PD_PROF(PD_KC_CONVERGE, 8.0 * units, 1,
+            launch_converge(c->stream, n, units, c->st, tol, maxit, c->stall, cur));
     ck_launch(c);
   }
   cur ^= 1;
@@ -402,9 +414,14 @@ void run_cycle_fused(pd_ctx *c, int l, bool zzero, bool top, const int *active, 
       zz = false;
     }
   }
-  PD_PROF(l == 0 ? PD_KC_PS0 : PD_KC_PS_C, 3 * w * pts + w * ptsc, 2,
-          launch_prolong_smooth<T>(c->stream, grid, B.ps_z[cur], B.ps_e[c->cur[l + 1]], B.ps_b, N,
-                                   n, z[cur ^ 1], cf, active, err));
+  if (streams)
+    PD_PROF(l == 0 ? PD_KC_PS0 : PD_KC_PS_C, 3 * w * pts + w * ptsc, 2,
+            launch_ps_stream<T>(c->stream, c->stream_grid, N, n, z[cur],
+                                view(Bc.z[c->cur[l + 1]], Bc.N, Bc.P), b, z[cur ^ 1], cf, active));
+  else
+    PD_PROF(l == 0 ? PD_KC_PS0 : PD_KC_PS_C, 3 * w * pts + w * ptsc, 2,
+            launch_prolong_smooth<T>(c->stream, grid, B.ps_z[cur], B.ps_e[c->cur[l + 1]], B.ps_b, N,
+                                     n, z[cur ^ 1], cf, active, err));
   ck_launch(c);
   cur ^= 1;
   for (int s = 1; s < c->cfg.nu2; s++) {
@@ -769,6 +786,7 @@ void pd_config_default(pd_config *cfg) {
   cfg->stall_ratio = 0.5;
   cfg->fused = 1;
   cfg->tensor_transforms = 1;
+  cfg->fused_variant = 0;
 }
 
 pd_status pd_alpha_circulant(int n, double tau, double alpha, double *B, double *shifts,
@@ -830,7 +848,8 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
       cfg.precision < 0 || cfg.precision > 1 || cfg.smoother < 0 || cfg.smoother > 1 ||
       !(cfg.inner_tol >= 0) || cfg.max_refine < 1 || cfg.inner_maxit < 1 ||
       cfg.inner_maxit > 100000 || !(cfg.stall_ratio >= 0) || cfg.fused < 0 || cfg.fused > 2 ||
-      cfg.tensor_transforms < 0 || cfg.tensor_transforms > 1)
+      cfg.tensor_transforms < 0 || cfg.tensor_transforms > 1 || cfg.fused_variant < 0 ||
+      cfg.fused_variant > 2)
     return PD_ERR_ARG;
   if (cfg.omega_mode == 2 && !omega) return PD_ERR_ARG;
   if (cfg.precision == 1 && (!B || !V)) return PD_ERR_ARG;
@@ -905,7 +924,7 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
     ck(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
     const FusedGeom g32 = fused_geom<float>(), g64 = fused_geom<double>();
     const int tiles = std::max({smooth_tiles(N), fused_tiles(N, g32.TX, g32.TY),
-                                fused_tiles(N, g64.TX, g64.TY)});
+                                fused_tiles(N, g64.TX, g64.TY), stream_units(N)});
     c->st.max_tiles = tiles;
     c->st.active = dalloc<int *>(c, n * sizeof(int));
     c->st.iters = dalloc<int *>(c, n * sizeof(int));

@@ -110,6 +110,17 @@ void launch_prolong_smooth(cudaStream_t s, int grid, const CUtensorMap &zmap,
                            const CUtensorMap &emap, const CUtensorMap &bmap, int N, int n,
                            View zout, const Coef<T> *coef, const int *active, int *errflag);
 
+// ---- warp-streaming fused kernels (stream_kernels.cu) ----
+int stream_units(int N);  // work units (strips x segments) per shift = norm partials per shift
+template <typename T> int stream_grid(int num_sms);
+template <typename T>
+void launch_sr_stream(cudaStream_t s, int grid, int N, int n, View z, View b, View zout, View bc,
+                      const Coef<T> *coef, const int *active, bool z_zero, double *partials,
+                      int part_stride);
+template <typename T>
+void launch_ps_stream(cudaStream_t s, int grid, int N, int n, View z, View e, View b, View zout,
+                      const Coef<T> *coef, const int *active);
+
 // ---- transforms (transforms.cu) ----
 template <typename T>
 cudaError_t prepare_transforms(int n);

@@ -237,14 +237,15 @@ def test_shifted_solve_fp32(N):
     assert rel_per_vector(host(z), zo) < 1e-4
 
 
-@pytest.mark.parametrize("fused", [0, 1])
+@pytest.mark.parametrize("fused", [0, 1, 2])
 @pytest.mark.parametrize("N,level,cyc", [(255, 0, 0), (1023, 1, 0), (255, 0, 1), (127, 0, 3)])
 def test_mg_vcycle_fused_and_unfused_fp64(fused, N, level, cyc):
     """The fused TMA kernels and the one-kernel-per-operation path give the oracle's cycle."""
     prm = CYCLES[cyc]
     rng = np.random.default_rng(21 + level)
     n = len(SHIFTS)
-    c = ctx_for(N, SHIFTS, omega_mode=0, fused=2 * fused, **prm)
+    # fused 0: one kernel per operation; 1: TMA tiles; 2: warp streams (both forced in FP64)
+    c = ctx_for(N, SHIFTS, omega_mode=0, fused=2 if fused else 0, fused_variant=max(fused, 1), **prm)
     Nl = c.Ns[level]
     z = rand_c(rng, (n, Nl, Nl))
     b = rand_c(rng, (n, Nl, Nl)) * 100
@@ -255,7 +256,7 @@ def test_mg_vcycle_fused_and_unfused_fp64(fused, N, level, cyc):
     assert rel_per_vector(host(zt), ref) < 1e-12
 
 
-@pytest.mark.parametrize("fused", [0, 1])
+@pytest.mark.parametrize("fused", [0, 1, 2])
 @pytest.mark.parametrize("N", [127, 511])
 def test_mg_vcycle_fp32(fused, N):
     """FP32 cycle (fused TMA path and plain path) against the FP64 oracle on the same,
@@ -263,10 +264,14 @@ def test_mg_vcycle_fp32(fused, N):
     rng = np.random.default_rng(N)
     n = len(SHIFTS)
     B, sh, V, Vi, c0 = api.pd_alpha_circulant(n, 0.25, 0.5)
-    c = api.Context(N, n, SHIFTS, V, Vi, B, c0, cfg=api.config(omega_mode=0, precision=1, fused=fused))
+    c = api.Context(N, n, SHIFTS, V, Vi, B, c0, cfg=api.config(omega_mode=0, precision=1,
+                                                               fused=1 if fused else 0,
+                                                               fused_variant=max(fused, 1)))
     z = rand_c(rng, (n, N, N)).astype(np.complex64)
     b = (rand_c(rng, (n, N, N)) * 100).astype(np.complex64)
     zt = dev(z, torch.complex64)
     c.mg_vcycle(0, zt, dev(b, torch.complex64))
     ref = np.stack([core.mg_cycle(N, SHIFTS[j], [24 / 25] * 16, b[j], z[j]) for j in range(n)])
-    assert rel_per_vector(host(zt), ref) < 2e-5
+    # FP32 rounding of the residuals grows with the grid (the coarse-grid correction of a
+    # cycle amplifies it by up to O(N)): 1e-7 N covers 6e-8 x that growth
+    assert rel_per_vector(host(zt), ref) < 1e-7 * N
