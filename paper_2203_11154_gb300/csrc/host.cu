@@ -247,6 +247,7 @@ void alloc_prec(pd_ctx *c) {
       B.maps = true;
     }
     ck(c, prepare_fused<T>());
+    ck(c, prepare_stream<T>());
     c->stream_grid = stream_grid<T>(c->num_sms);
     c->fused_impl = c->cfg.fused_variant == 1 ? 1 : 2;
   }
@@ -526,8 +527,10 @@ void run_cycle(pd_ctx *c, int l, bool zzero, bool top, const int *active, double
 // Solve of eq. (2) for all shifts with the right-hand side already in lv[0].b
 // (scaled by h^2).  On return the per-shift answers are in lv[0].z[final_buf[j]],
 // and h_iters/h_relres (pinned copies) hold cycles and relative residuals.
+// skip_final: after maxit cycles stop without computing the residual of the last
+// iterate (the refinement evaluates its own residual anyway)
 template <typename T>
-pd_status solve_levels(pd_ctx *c, double tol, int maxit, double stall = 0.0) {
+pd_status solve_levels(pd_ctx *c, double tol, int maxit, double stall = 0.0, bool skip_final = false) {
   Prec<T> &P = prec<T>(c);
   c->stall = stall;
   LevelBufs &B = P.lv[0];
@@ -548,7 +551,12 @@ pd_status solve_levels(pd_ctx *c, double tol, int maxit, double stall = 0.0) {
     const int cmax = std::min(maxit, std::max(c->cfg.maxit, c->cfg.inner_maxit));
     for (int cyc = 0; cyc <= cmax; cyc++) {
       c->cur_cyc = cyc;
-      run_cycle<T>(c, 0, cyc == 0, true, c->st.active, tol, cmax);
+      if (skip_final && cyc == cmax && cyc > 0) {
+        PD_PROF(PD_KC_OTHER, 0.0, 0, launch_finalize(c->stream, n, c->st, c->cur[0]));
+        ck_launch(c);
+      } else {
+        run_cycle<T>(c, 0, cyc == 0, true, c->st.active, tol, cmax);
+      }
       ck(c, cudaMemcpyAsync(&c->h_hist[cyc], c->st.nactive, sizeof(int), cudaMemcpyDeviceToHost,
                             c->stream));
       ck(c, cudaEventRecord(c->ev[cyc & 1], c->stream));
@@ -687,7 +695,7 @@ pd_status paradiag_impl(pd_ctx *c, double *u, const double *f, const double *u0,
       else
         PD_PROF(PD_KC_FORWARD, fwd_bytes, 0, transform_forward<T>(c, g, c->d_r, nullptr, true));
       ck_launch(c);
-      pd_status s = solve_levels<T>(c, c->cfg.inner_tol, c->cfg.inner_maxit, c->cfg.stall_ratio);
+      pd_status s = solve_levels<T>(c, c->cfg.inner_tol, c->cfg.inner_maxit, c->cfg.stall_ratio, true);
       if (s == PD_ERR_NAN) {
         rc = s;
         break;

@@ -493,9 +493,23 @@ __global__ void k_reset_state(int n, SolveState st) {
   }
 }
 
+// Ends a solve after its last permitted cycle without another residual: every shift
+// still iterating keeps the iterate in buffer cur_buf and its last relative residual.
+__global__ void k_finalize(int n, SolveState st, int cur_buf) {
+  const int j = threadIdx.x;
+  if (j < n && st.active[j]) {
+    st.active[j] = 0;
+    st.final_buf[j] = cur_buf;
+    atomicSub(st.nactive, 1);
+  }
+}
+
 }  // namespace
 
 void launch_reset_state(cudaStream_t s, int n, SolveState st) { k_reset_state<<<1, 128, 0, s>>>(n, st); }
+void launch_finalize(cudaStream_t s, int n, SolveState st, int cur_buf) {
+  k_finalize<<<1, 128, 0, s>>>(n, st, cur_buf);
+}
 
 int smooth_tiles(int N) { return ((N + kSmTX - 1) / kSmTX) * ((N + kSmTY - 1) / kSmTY); }
 

@@ -60,6 +60,7 @@ void launch_resnorm(cudaStream_t s, int N, int n, View z, View b, T bscale, cons
                     const int *active, bool z_zero, double *partials, int part_stride);
 int smooth_tiles(int N);
 void launch_reset_state(cudaStream_t s, int n, SolveState st);
+void launch_finalize(cudaStream_t s, int n, SolveState st, int cur_buf);
 void launch_converge(cudaStream_t s, int n, int ntiles, SolveState st, double tol, int maxit,
                      double stall, int cur_buf);
 template <typename T>
@@ -113,6 +114,7 @@ void launch_prolong_smooth(cudaStream_t s, int grid, const CUtensorMap &zmap,
 // ---- warp-streaming fused kernels (stream_kernels.cu) ----
 int stream_units(int N);  // work units (strips x segments) per shift = norm partials per shift
 template <typename T> int stream_grid(int num_sms);
+template <typename T> cudaError_t prepare_stream();
 template <typename T>
 void launch_sr_stream(cudaStream_t s, int grid, int N, int n, View z, View b, View zout, View bc,
                       const Coef<T> *coef, const int *active, bool z_zero, double *partials,

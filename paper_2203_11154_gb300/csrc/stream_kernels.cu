@@ -434,6 +434,22 @@ void launch_ps_stream(cudaStream_t s, int grid, int N, int n, View z, View e, Vi
   k_ps_stream<T><<<grid, kWarpsPerCta * kLanes, smem, s>>>(N, n, z, e, b, zout, coef, active);
 }
 
+template <typename T> cudaError_t prepare_stream() {
+  const int a = ring_bytes<2>((int)sizeof(typename Cx<T>::type));
+  const int b = ring_bytes<3>((int)sizeof(typename Cx<T>::type));
+  cudaError_t e;
+#define PD_ATTR(K, S)                                                                  \
+  e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, S);         \
+  if (e != cudaSuccess) return e;
+  PD_ATTR((k_sr_stream<T, false, false>), a)
+  PD_ATTR((k_sr_stream<T, false, true>), a)
+  PD_ATTR((k_sr_stream<T, true, false>), a)
+  PD_ATTR((k_sr_stream<T, true, true>), a)
+  PD_ATTR((k_ps_stream<T>), b)
+#undef PD_ATTR
+  return cudaSuccess;
+}
+
 template <typename T> int stream_grid(int num_sms) {
   // resident CTAs per SM from the occupancy calculator, times the SMs
   int a = 0, b = 0;
@@ -450,7 +466,8 @@ template <typename T> int stream_grid(int num_sms) {
                                     const Coef<T> *, const int *, bool, double *, int);          \
   template void launch_ps_stream<T>(cudaStream_t, int, int, int, View, View, View, View,        \
                                     const Coef<T> *, const int *);                               \
-  template int stream_grid<T>(int);
+  template int stream_grid<T>(int);                                                              \
+  template cudaError_t prepare_stream<T>();
 
 PD_INST_S(float)
 PD_INST_S(double)

@@ -139,7 +139,7 @@ constexpr int kFwdK = 64, kFwdNt = 128, kInvK = 128, kInvNt = 64;
 constexpr int kFwdA = kM * kFwdK * 4, kFwdB = kFwdNt * kFwdK * 4;  // bytes per split
 constexpr int kInvA = kM * kInvK * 4, kInvB = kInvNt * kInvK * 4;
 constexpr int kFwdS = 64 * 66 * 4;   // epilogue stage: 64 j rows x 32 complex (stride 66 floats)
-constexpr int kInvS = kM * 33 * 4;   // epilogue stage: 128 rows x 32 columns (stride 33)
+constexpr int kInvS = kM * (kInvNt + 1) * 4;  // epilogue stage: 128 rows x 64 columns (stride 65)
 constexpr int kFwdSmem = 2 * kFwdA + 2 * kFwdB + kFwdS + 1024;
 constexpr int kInvSmem = 2 * kInvA + 2 * kInvB + kInvS + 1024;
 
@@ -176,27 +176,46 @@ k_tc_forward(int N, int n, View g, const double *__restrict__ f, const double *_
   const int total = N * tpr;
   uint32_t phase = 0;
   bool ok = true;
-  for (int t = blockIdx.x; t < total; t += gridDim.x) {
+  // each thread owns kFwdItems (point, 4 consecutive k) items of a tile; the FP64 inputs of
+  // the next tile are loaded into registers while the current tile is multiplied
+  constexpr int kFwdItems = kFwdNt * (kFwdK / 4) / kTcThreads;
+  double pre[kFwdItems][4];
+  auto fetch = [&](int t) {
     const int i = t / tpr, c0 = (t % tpr) * kFwdNt;
-    // B[p][k] = fhat_k(i, c0 + p): 4 consecutive k per thread, coalesced over p
-    for (int it = tid; it < kFwdNt * (kFwdK / 4); it += kTcThreads) {
-      const int p = it % kFwdNt, q = it / kFwdNt;
+#pragma unroll
+    for (int q = 0; q < kFwdItems; q++) {
+      const int it = tid + q * kTcThreads;
+      const int p = it % kFwdNt, kq = it / kFwdNt;
       const int c = c0 + p;
-      float4 hi, lo;
-      float *h4 = &hi.x, *l4 = &lo.x;
+      const long long x = (long long)i * N + c;
 #pragma unroll
       for (int e = 0; e < 4; e++) {
-        const int k = 4 * q + e;
+        const int k = 4 * kq + e;
         double v = 0.0;
         if (k < n && c < N) {
-          const long long x = (long long)i * N + c;
           v = f[k * m + x];
           if (u0) v += u0coef[k] * u0[x];
         }
-        split_tf32((float)v, h4[e], l4[e]);
+        pre[q][e] = v;
       }
-      *reinterpret_cast<float4 *>(sBhi + sw_off(p, q, kFwdNt)) = hi;
-      *reinterpret_cast<float4 *>(sBlo + sw_off(p, q, kFwdNt)) = lo;
+    }
+  };
+  int t = blockIdx.x;
+  if (t < total) fetch(t);
+  for (; t < total; t += gridDim.x) {
+    const int i = t / tpr, c0 = (t % tpr) * kFwdNt;
+    // B[p][k] = fhat_k(i, c0 + p), split into TF32 hi/lo, 16-byte swizzled chunks
+#pragma unroll
+    for (int q = 0; q < kFwdItems; q++) {
+      const int it = tid + q * kTcThreads;
+      const int p = it % kFwdNt, kq = it / kFwdNt;
+      float4 hi, lo;
+      split_tf32((float)pre[q][0], hi.x, lo.x);
+      split_tf32((float)pre[q][1], hi.y, lo.y);
+      split_tf32((float)pre[q][2], hi.z, lo.z);
+      split_tf32((float)pre[q][3], hi.w, lo.w);
+      *reinterpret_cast<float4 *>(sBhi + sw_off(p, kq, kFwdNt)) = hi;
+      *reinterpret_cast<float4 *>(sBlo + sw_off(p, kq, kFwdNt)) = lo;
     }
     fence_proxy_async_smem();
     tc_fence_before();
@@ -206,6 +225,7 @@ k_tc_forward(int N, int n, View g, const double *__restrict__ f, const double *_
       issue_tile<kFwdK, kFwdNt>(tmem, smem_u32(sAhi), smem_u32(sAlo), smem_u32(sBhi), smem_u32(sBlo),
                                 &bar);
     }
+    if (t + (int)gridDim.x < total) fetch(t + gridDim.x);
     ok = mbar_wait_bounded(&bar, phase);
     if (!__syncthreads_and(ok)) {
       if (tid == 0) atomicOr(errflag, 4);
@@ -273,29 +293,45 @@ k_tc_inverse(int N, int n, double *__restrict__ u, View z0, View z1, const int *
   uint32_t phase = 0;
   bool ok = true;
   float imax = 0.f;
-  for (int t = blockIdx.x; t < total; t += gridDim.x) {
+  // each thread owns kInvItems (point, 2 shifts) items of a tile; the z values of the
+  // next tile are loaded into registers while the current tile is multiplied
+  constexpr int kInvItems = kInvNt * (kInvK / 4) / kTcThreads;
+  float2 pre[kInvItems][2];
+  auto fetch = [&](int t) {
     const int i = t / tpr, c0 = (t % tpr) * kInvNt;
-    // B[p][2j+q] = component q of z_j(i, c0+p): two shifts (one 16-byte chunk) per item
-    for (int it = tid; it < kInvNt * (kInvK / 4); it += kTcThreads) {
+#pragma unroll
+    for (int q = 0; q < kInvItems; q++) {
+      const int it = tid + q * kTcThreads;
       const int p = it % kInvNt, qq = it / kInvNt;
       const int c = c0 + p;
-      float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
-      const int j0 = 2 * qq, j1 = 2 * qq + 1;
-      if (c < N) {
-        if (j0 < n) {
-          const View &zv = (final_buf && final_buf[j0]) ? z1 : z0;
-          a = reinterpret_cast<const float2 *>(zv.p)[j0 * zv.plane + (long long)i * zv.pitch + c];
+#pragma unroll
+      for (int e = 0; e < 2; e++) {
+        const int jj = 2 * qq + e;
+        float2 v = make_float2(0.f, 0.f);
+        if (c < N && jj < n) {
+          const View &zv = (final_buf && final_buf[jj]) ? z1 : z0;
+          v = reinterpret_cast<const float2 *>(zv.p)[jj * zv.plane + (long long)i * zv.pitch + c];
         }
-        if (j1 < n) {
-          const View &zv = (final_buf && final_buf[j1]) ? z1 : z0;
-          b = reinterpret_cast<const float2 *>(zv.p)[j1 * zv.plane + (long long)i * zv.pitch + c];
-        }
+        pre[q][e] = v;
       }
+    }
+  };
+  // u values this thread accumulates into in the epilogue (n x 64 per tile)
+  constexpr int kAccItems = 64 * kInvNt / kTcThreads;
+  double uacc[kAccItems];
+  int t = blockIdx.x;
+  if (t < total) fetch(t);
+  for (; t < total; t += gridDim.x) {
+    const int i = t / tpr, c0 = (t % tpr) * kInvNt;
+#pragma unroll
+    for (int q = 0; q < kInvItems; q++) {
+      const int it = tid + q * kTcThreads;
+      const int p = it % kInvNt, qq = it / kInvNt;
       float4 hi, lo;
-      split_tf32(a.x, hi.x, lo.x);
-      split_tf32(a.y, hi.y, lo.y);
-      split_tf32(b.x, hi.z, lo.z);
-      split_tf32(b.y, hi.w, lo.w);
+      split_tf32(pre[q][0].x, hi.x, lo.x);
+      split_tf32(pre[q][0].y, hi.y, lo.y);
+      split_tf32(pre[q][1].x, hi.z, lo.z);
+      split_tf32(pre[q][1].y, hi.w, lo.w);
       *reinterpret_cast<float4 *>(sBhi + sw_off(p, qq, kInvNt)) = hi;
       *reinterpret_cast<float4 *>(sBlo + sw_off(p, qq, kInvNt)) = lo;
     }
@@ -307,6 +343,15 @@ k_tc_inverse(int N, int n, double *__restrict__ u, View z0, View z1, const int *
       issue_tile<kInvK, kInvNt>(tmem, smem_u32(sAhi), smem_u32(sAlo), smem_u32(sBhi), smem_u32(sBlo),
                                 &bar);
     }
+    // accumulator inputs of this tile and z of the next one, while the MMAs run
+#pragma unroll
+    for (int q = 0; q < kAccItems; q++) {
+      const int it = tid + q * kTcThreads;
+      const int k = it / kInvNt, cc = it % kInvNt;
+      const int c = c0 + cc;
+      uacc[q] = (accumulate && k < n && c < N) ? u[(long long)k * m + (long long)i * N + c] : 0.0;
+    }
+    if (t + (int)gridDim.x < total) fetch(t + gridDim.x);
     ok = mbar_wait_bounded(&bar, phase);
     if (!__syncthreads_and(ok)) {
       if (tid == 0) atomicOr(errflag, 4);
@@ -320,22 +365,21 @@ k_tc_inverse(int N, int n, double *__restrict__ u, View z0, View z1, const int *
         tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * chunk), v);
         const int row = 32 * warp + lane;
 #pragma unroll
-        for (int cc = 0; cc < 32; cc++) S[row * 33 + cc] = v[cc];
+        for (int cc = 0; cc < 32; cc++) S[row * (kInvNt + 1) + 32 * chunk + cc] = v[cc];
       }
-      __syncthreads();
-      for (int it = tid; it < n * 32; it += kTcThreads) {
-        const int k = it >> 5, cc = it & 31;
-        const int c = c0 + 32 * chunk + cc;
-        if (c < N) {
-          const long long x = (long long)k * m + (long long)i * N + c;
-          double val = (double)S[k * 33 + cc];
-          if (accumulate) val += u[x];
-          u[x] = val;
-          if (imag_check) imax = fmaxf(imax, fabsf(S[(64 + k) * 33 + cc]));
-        }
-      }
-      __syncthreads();
     }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kAccItems; q++) {
+      const int it = tid + q * kTcThreads;
+      const int k = it / kInvNt, cc = it % kInvNt;
+      const int c = c0 + cc;
+      if (k < n && c < N) {
+        u[(long long)k * m + (long long)i * N + c] = uacc[q] + (double)S[k * (kInvNt + 1) + cc];
+        if (imag_check) imax = fmaxf(imax, fabsf(S[(64 + k) * (kInvNt + 1) + cc]));
+      }
+    }
+    __syncthreads();
     tc_fence_before();
   }
   if (!ok && tid == 0) mbar_wait_bounded(&bar, phase);
