@@ -29,6 +29,8 @@ struct LevelBufs {
   CUtensorMap sr_z[2], sr_b;          // smooth+restrict: z and bt of this level
   CUtensorMap ps_z[2], ps_e[2], ps_b; // prolong+smooth: z of this level, z of the next, bt
   bool maps = false;
+  int variant = 2;  // fused implementation of this level: 1 TMA tiles, 2 warp streams
+  int seg = 128;    // rows per warp-stream segment
 };
 
 template <typename T> struct Prec {
@@ -67,14 +69,17 @@ struct pd_ctx {
   double *d_u0coef = nullptr;
   int *d_Bptr = nullptr, *d_Bcol = nullptr;
   double *d_Bval = nullptr;
-  double *d_r = nullptr;       // refinement residual [n][N][N]
+  double *d_r = nullptr;       // refinement residual [n][N][N] (general B)
+  float *d_r32 = nullptr;      // refinement residual in FP32 (bidiagonal B)
+  bool bidiag = false;         // B has nonzeros only at (k,k) and (k,k-1 mod n)
+  double *d_bd = nullptr, *d_bs = nullptr;
+  double fnorm = -1.0;         // ||fhat|| of the running refinement
   double *d_part = nullptr;    // all-at-once residual partial sums
   double *h_part = nullptr;    // pinned copy
   unsigned long long *d_imag = nullptr;
   double *d_stage_f = nullptr, *d_stage_u = nullptr, *d_stage_u0 = nullptr;
   long long launches = 0;
   int num_sms = 0;
-  int fused_impl = 2;     // 1 TMA tiles, 2 warp streams (cfg.fused_variant, or timed at set-up)
   int stream_grid = 0;    // persistent grid of the streaming kernels
   // instrumentation: event pairs around launches, resolved after each solve
   bool prof_on = false;
@@ -217,6 +222,75 @@ template <> Prec<float> &prec<float>(pd_ctx *c) { return c->p32; }
 
 double hl(const pd_ctx *c, int l) { return 1.0 / (c->Ns[l] + 1); }
 
+// Set-up autotuner of the fused kernels: on each global-memory level, times the
+// smoothing+restriction and interpolation+smoothing pair of every candidate (TMA tiles;
+// warp streams with 16, 32, 64 or 128 rows per segment) on the context's own (zeroed)
+// buffers, all shifts active, and keeps the fastest; cfg.fused_variant 1 or 2 restricts
+// the candidates to one implementation.
+template <typename T>
+void autotune_fused(pd_ctx *c) {
+  Prec<T> &P = prec<T>(c);
+  const int n = c->n;
+  const FusedGeom g = fused_geom<T>();
+  const int segs[4] = {16, 32, 64, 128};
+  cudaEvent_t e0, e1;
+  ck(c, cudaEventCreate(&e0));
+  ck(c, cudaEventCreate(&e1));
+  int *dummy_err = c->st.flags;
+  for (int l = 0; l < c->L - 1; l++) {
+    LevelBufs &B = P.lv[l], &Bc = P.lv[l + 1];
+    if (!B.maps) continue;
+    const size_t bytes = (size_t)n * B.N * B.P * sizeof(typename Cx<T>::type);
+    const size_t bytesc = (size_t)n * Bc.N * Bc.P * sizeof(typename Cx<T>::type);
+    for (int q = 0; q < 2; q++) {
+      ck(c, cudaMemsetAsync(B.z[q], 0, bytes, c->stream));
+      ck(c, cudaMemsetAsync(Bc.z[q], 0, bytesc, c->stream));
+    }
+    ck(c, cudaMemsetAsync(B.b, 0, bytes, c->stream));
+    const View b = view(B.b, B.N, B.P), z0 = view(B.z[0], B.N, B.P), z1 = view(B.z[1], B.N, B.P);
+    const View bc = view(Bc.b, Bc.N, Bc.P), ec = view(Bc.z[0], Bc.N, Bc.P);
+    const Coef<T> *cf = P.coef + (size_t)l * n;
+    const int grid = std::max(1, std::min(c->num_sms, n * fused_tiles(B.N, g.TX, g.TY)));
+    float best = 1e30f;
+    int bv = 2, bs = 128;
+    for (int cand = 0; cand < 5; cand++) {
+      const int variant = cand == 0 ? 1 : 2, seg = cand == 0 ? 0 : segs[cand - 1];
+      if (c->cfg.fused_variant != 0 && c->cfg.fused_variant != variant) continue;
+      if (variant == 2 && seg > 2 * B.N) continue;
+      float tmin = 1e30f;
+      for (int rep = 0; rep < 3; rep++) {
+        ck(c, cudaEventRecord(e0, c->stream));
+        if (variant == 1) {
+          launch_smooth_restrict<T>(c->stream, grid, B.sr_z[0], B.sr_b, B.N, n, z1, bc, cf, nullptr,
+                                    false, nullptr, 0, dummy_err);
+          launch_prolong_smooth<T>(c->stream, grid, B.ps_z[1], B.ps_e[0], B.ps_b, B.N, n, z0, cf,
+                                   nullptr, dummy_err);
+        } else {
+          launch_sr_stream<T>(c->stream, c->stream_grid, B.N, n, seg, z0, b, z1, bc, cf, nullptr,
+                              false, nullptr, 0);
+          launch_ps_stream<T>(c->stream, c->stream_grid, B.N, n, seg, z1, ec, b, z0, cf, nullptr);
+        }
+        ck(c, cudaEventRecord(e1, c->stream));
+        ck(c, cudaEventSynchronize(e1));
+        ck(c, cudaGetLastError());
+        float ms = 0.f;
+        ck(c, cudaEventElapsedTime(&ms, e0, e1));
+        tmin = std::min(tmin, ms);
+      }
+      c->launches += 6;
+      if (tmin < best) {
+        best = tmin;
+        bv = variant;
+        bs = seg;
+      }
+    }
+    B.variant = bv;
+    B.seg = bs > 0 ? bs : 128;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+}
+
 template <typename T>
 void alloc_prec(pd_ctx *c) {
   using C = typename Cx<T>::type;
@@ -249,7 +323,6 @@ void alloc_prec(pd_ctx *c) {
     ck(c, prepare_fused<T>());
     ck(c, prepare_stream<T>());
     c->stream_grid = stream_grid<T>(c->num_sms);
-    c->fused_impl = c->cfg.fused_variant == 1 ? 1 : 2;
   }
   // smoother coefficients in the scaled form of pd_internal.h
   std::vector<Coef<T>> cf((size_t)L * n);
@@ -344,6 +417,7 @@ void alloc_prec(pd_ctx *c) {
   // can use (coarse launches never exceed kCoarseSmemLimit; transforms need n <= 128)
   ck(c, prepare_coarse<T>(kCoarseSmemLimit));
   ck(c, prepare_transforms<T>(kMaxShifts));
+  if (P.lv.size() > 0 && P.lv[0].maps) autotune_fused<T>(c);
 }
 
 template <typename T>
@@ -382,11 +456,11 @@ void run_cycle_fused(pd_ctx *c, int l, bool zzero, bool top, const int *active, 
     cur ^= 1;
     zzero = false;
   }
-  const bool streams = c->fused_impl == 2;
-  const int units = streams ? stream_units(N) : ftiles;
+  const bool streams = B.variant == 2;
+  const int units = streams ? stream_units(N, B.seg) : ftiles;
   if (streams)
     PD_PROF(l == 0 ? PD_KC_SR0 : PD_KC_SR_C, (zzero ? 2 : 3) * w * pts + w * ptsc, norm ? 1 : 2,
-            launch_sr_stream<T>(c->stream, c->stream_grid, N, n, z[cur], b, z[cur ^ 1],
+            launch_sr_stream<T>(c->stream, c->stream_grid, N, n, B.seg, z[cur], b, z[cur ^ 1],
                                 view(Bc.b, Bc.N, Bc.P), cf, active, zzero,
                                 norm ? c->st.partials : nullptr, c->st.max_tiles));
   else
@@ -417,7 +491,7 @@ void run_cycle_fused(pd_ctx *c, int l, bool zzero, bool top, const int *active, 
   }
   if (streams)
     PD_PROF(l == 0 ? PD_KC_PS0 : PD_KC_PS_C, 3 * w * pts + w * ptsc, 2,
-            launch_ps_stream<T>(c->stream, c->stream_grid, N, n, z[cur],
+            launch_ps_stream<T>(c->stream, c->stream_grid, N, n, B.seg, z[cur],
                                 view(Bc.z[c->cur[l + 1]], Bc.N, Bc.P), b, z[cur ^ 1], cf, active));
   else
     PD_PROF(l == 0 ? PD_KC_PS0 : PD_KC_PS_C, 3 * w * pts + w * ptsc, 2,
@@ -585,12 +659,21 @@ pd_status solve_levels(pd_ctx *c, double tol, int maxit, double stall = 0.0, boo
 }
 
 // ||fhat - A u|| and ||fhat|| from the per-CTA partial sums (fixed order)
+// r (FP64, may be NULL) or r32 (FP32) = fhat - A u and the norms; with a bidiagonal B
+// and known_fn >= 0 the ||fhat|| sums are skipped and known_fn returned
 void allatonce_norms(pd_ctx *c, double *r, const double *u, const double *f, const double *u0,
-                     double *rn, double *fn) {
+                     double *rn, double *fn, float *r32 = nullptr, double known_fn = -1.0) {
   const double m = (double)c->N * c->N;
-  PD_PROF(PD_KC_RESIDUAL, (r ? 24.0 : 16.0) * m + (u0 ? 8.0 * m / c->n : 0.0), 0,
-          launch_allatonce_residual(c->stream, c->N, c->n, r, u, f, u0, c->d_u0coef, c->d_Bptr,
-                                    c->d_Bcol, c->d_Bval, c->d_part));
+  const bool want_f = known_fn < 0.0;
+  if (c->bidiag)
+    PD_PROF(PD_KC_RESIDUAL,
+            (r ? 24.0 : r32 ? 20.0 : 16.0) * m + (u0 ? 8.0 * m / c->n : 0.0), 0,
+            launch_residual_bidiag(c->stream, c->N, c->n, r, r32, u, f, u0, c->d_u0coef, c->d_bd,
+                                   c->d_bs, want_f, c->d_part));
+  else
+    PD_PROF(PD_KC_RESIDUAL, (r ? 24.0 : 16.0) * m + (u0 ? 8.0 * m / c->n : 0.0), 0,
+            launch_allatonce_residual(c->stream, c->N, c->n, r, u, f, u0, c->d_u0coef, c->d_Bptr,
+                                      c->d_Bcol, c->d_Bval, c->d_part));
   ck_launch(c);
   const int nb = allatonce_blocks();
   ck(c, cudaMemcpyAsync(c->h_part, c->d_part, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost,
@@ -602,21 +685,23 @@ void allatonce_norms(pd_ctx *c, double *r, const double *u, const double *f, con
     b += c->h_part[2 * k + 1];
   }
   *rn = std::sqrt(a);
-  *fn = std::sqrt(b);
+  *fn = (c->bidiag && !want_f) ? known_fn : std::sqrt(b);
   prof_resolve(c);
 }
 
-// forward transform into view g (scaled: the level-0 h^2 scaling; else unscaled)
+// forward transform into view g (scaled: the level-0 h^2 scaling; else unscaled);
+// f is FP64, or FP32 when f32 (the refinement residual)
 template <typename T>
-void transform_forward(pd_ctx *c, View g, const double *f, const double *u0, bool scaled) {
+void transform_forward(pd_ctx *c, View g, const void *f, const double *u0, bool scaled,
+                       bool f32 = false) {
   Prec<T> &P = prec<T>(c);
   const double h = hl(c, 0);
   if (P.tc) {
-    launch_tc_forward(c->stream, c->num_sms, c->N, c->n, g, f, u0, c->d_u0coef,
+    launch_tc_forward(c->stream, c->num_sms, c->N, c->n, g, f, f32, u0, c->d_u0coef,
                       scaled ? P.tc_fwd_hi : P.tc_fwd1_hi, scaled ? P.tc_fwd_lo : P.tc_fwd1_lo,
                       c->st.flags);
   } else {
-    launch_transform_forward<T>(c->stream, c->N, c->n, g, f, u0, c->d_u0coef, P.Wf,
+    launch_transform_forward<T>(c->stream, c->N, c->n, g, f, f32, u0, c->d_u0coef, P.Wf,
                                 scaled ? h * h : 1.0);
   }
 }
@@ -692,6 +777,9 @@ pd_status paradiag_impl(pd_ctx *c, double *u, const double *f, const double *u0,
       if (step == 0)
         PD_PROF(PD_KC_FORWARD, fwd_bytes + (u0 ? fwd_u0 : 0.0), 0,
                 transform_forward<T>(c, g, f, u0, true));
+      else if (c->bidiag)
+        PD_PROF(PD_KC_FORWARD, fwd_bytes - 4.0 * m, 0,
+                transform_forward<T>(c, g, c->d_r32, nullptr, true, true));
       else
         PD_PROF(PD_KC_FORWARD, fwd_bytes, 0, transform_forward<T>(c, g, c->d_r, nullptr, true));
       ck_launch(c);
@@ -705,7 +793,12 @@ pd_status paradiag_impl(pd_ctx *c, double *u, const double *f, const double *u0,
               transform_inverse<T>(c, u, z0, z1, c->st.final_buf, step > 0, imag));
       ck_launch(c);
       double rn, fn;
-      allatonce_norms(c, c->d_r, u, f, u0, &rn, &fn);
+      if (c->bidiag) {
+        allatonce_norms(c, nullptr, u, f, u0, &rn, &fn, c->d_r32, step == 0 ? -1.0 : c->fnorm);
+        c->fnorm = fn;
+      } else {
+        allatonce_norms(c, c->d_r, u, f, u0, &rn, &fn);
+      }
       steps = step + 1;
       relres = fn > 0 ? rn / fn : 0.0;
       if (!std::isfinite(relres)) {
@@ -932,7 +1025,7 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
     ck(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
     const FusedGeom g32 = fused_geom<float>(), g64 = fused_geom<double>();
     const int tiles = std::max({smooth_tiles(N), fused_tiles(N, g32.TX, g32.TY),
-                                fused_tiles(N, g64.TX, g64.TY), stream_units(N)});
+                                fused_tiles(N, g64.TX, g64.TY), stream_units(N, 16)});
     c->st.max_tiles = tiles;
     c->st.active = dalloc<int *>(c, n * sizeof(int));
     c->st.iters = dalloc<int *>(c, n * sizeof(int));
@@ -947,6 +1040,22 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
     c->d_part = dalloc<double *>(c, 2 * allatonce_blocks() * sizeof(double));
     c->d_imag = dalloc<unsigned long long *>(c, sizeof(unsigned long long));
     if (B) {
+      bool bid = true;
+      std::vector<double> bd(n), bs(n);
+      for (int k = 0; k < n; k++) {
+        const int kp = (k + n - 1) % n;
+        bd[k] = B[(size_t)k * n + k];
+        bs[k] = n > 1 ? B[(size_t)k * n + kp] : 0.0;
+        for (int l = 0; l < n; l++)
+          if (B[(size_t)k * n + l] != 0.0 && l != k && l != kp) bid = false;
+      }
+      if (n > 1 && bid) {
+        c->bidiag = true;
+        c->d_bd = dalloc<double *>(c, n * sizeof(double));
+        c->d_bs = dalloc<double *>(c, n * sizeof(double));
+        ck(c, cudaMemcpy(c->d_bd, bd.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+        ck(c, cudaMemcpy(c->d_bs, bs.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+      }
       std::vector<int> ptr(n + 1, 0), col;
       std::vector<double> val;
       for (int k = 0; k < n; k++) {
@@ -970,7 +1079,8 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
       alloc_prec<double>(c);
     } else {
       alloc_prec<float>(c);
-      c->d_r = dalloc<double *>(c, (size_t)n * N * N * sizeof(double));
+      if (c->bidiag) c->d_r32 = dalloc<float *>(c, (size_t)n * N * N * sizeof(float));
+      else c->d_r = dalloc<double *>(c, (size_t)n * N * N * sizeof(double));
     }
     ck(c, cudaDeviceSynchronize());
   } catch (const CudaFail &) {

@@ -112,23 +112,24 @@ void launch_prolong_smooth(cudaStream_t s, int grid, const CUtensorMap &zmap,
                            View zout, const Coef<T> *coef, const int *active, int *errflag);
 
 // ---- warp-streaming fused kernels (stream_kernels.cu) ----
-int stream_units(int N);  // work units (strips x segments) per shift = norm partials per shift
+// work units (strips x segments of `seg` rows) per shift = norm partials per shift
+int stream_units(int N, int seg);
 template <typename T> int stream_grid(int num_sms);
 template <typename T> cudaError_t prepare_stream();
 template <typename T>
-void launch_sr_stream(cudaStream_t s, int grid, int N, int n, View z, View b, View zout, View bc,
-                      const Coef<T> *coef, const int *active, bool z_zero, double *partials,
+void launch_sr_stream(cudaStream_t s, int grid, int N, int n, int seg, View z, View b, View zout,
+                      View bc, const Coef<T> *coef, const int *active, bool z_zero, double *partials,
                       int part_stride);
 template <typename T>
-void launch_ps_stream(cudaStream_t s, int grid, int N, int n, View z, View e, View b, View zout,
-                      const Coef<T> *coef, const int *active);
+void launch_ps_stream(cudaStream_t s, int grid, int N, int n, int seg, View z, View e, View b,
+                      View zout, const Coef<T> *coef, const int *active);
 
 // ---- transforms (transforms.cu) ----
 template <typename T>
 cudaError_t prepare_transforms(int n);
 // g (view, working type) = scale * W fhat, fhat_k = f_k + u0coef[k] u0 (f, u0 double)
 template <typename T>
-void launch_transform_forward(cudaStream_t s, int N, int n, View g, const double *f,
+void launch_transform_forward(cudaStream_t s, int N, int n, View g, const void *f, bool f32,
                               const double *u0, const double *u0coef,
                               const typename Cx<T>::type *W, double scale);
 // u (double, [n][N][N]) = or += Re(W z); z_j read from z1 where final_buf[j] != 0
@@ -145,12 +146,19 @@ void launch_allatonce_residual(cudaStream_t s, int N, int n, double *r, const do
                                const int *Bptr, const int *Bcol, const double *Bval,
                                double *part);
 
+// r = fhat - (B kron I + I kron A) u for B with nonzeros only at (k,k) (bd) and
+// (k, k-1 mod n) (bs); r written as FP64 (r64) or FP32 (r32); part as above, the fhat
+// sums only when want_f
+void launch_residual_bidiag(cudaStream_t s, int N, int n, double *r64, float *r32, const double *u,
+                            const double *f, const double *u0, const double *u0coef,
+                            const double *bd, const double *bs, bool want_f, double *part);
+
 // ---- tensor-core transforms (tc_transforms.cu), FP32 working type, n <= 64 ----
 bool tc_transforms_supported(int N, int n);
 cudaError_t prepare_tc_transforms();
 void tc_build_operands(int n, const double *Vinv, const double *V, double scale, float *fwd_hi,
                        float *fwd_lo, float *inv_hi, float *inv_lo);
-void launch_tc_forward(cudaStream_t s, int grid, int N, int n, View g, const double *f,
+void launch_tc_forward(cudaStream_t s, int grid, int N, int n, View g, const void *f, bool f32,
                        const double *u0, const double *u0coef, const float *Ahi, const float *Alo,
                        int *errflag);
 void launch_tc_inverse(cudaStream_t s, int grid, int N, int n, double *u, View z0, View z1,

@@ -8,7 +8,8 @@
 //   with rt(z) = bt - (4 + eta) z + (sum of the 4 neighbours of z), bt = h^2 b.
 //
 // Each warp owns a strip of 64 grid columns (2 per lane; the 56 middle ones are its
-// output, 4 on each side are recomputed halo) and streams down a segment of rows.
+// output, 4 on each side are recomputed halo) and streams down a segment of `seg` rows
+// (even; chosen per level by the set-up autotuner).
 // Horizontal neighbours come from the adjacent lanes by shuffles, vertical ones from
 // short register windows of the previous rows, so every input value is read from
 // memory once per strip and nothing waits at a CTA barrier.  Rows are prefetched
@@ -27,7 +28,6 @@ namespace {
 
 constexpr int kLanes = 32;
 constexpr int kStripOut = 56;     // output columns per warp strip
-constexpr int kSegRows = 128;     // output rows per segment
 constexpr int kDepth = 4;         // rows prefetched ahead
 constexpr int kWarpsPerCta = 8;
 
@@ -89,14 +89,15 @@ template <typename C> __device__ __forceinline__ Pair<C> read_pair(const C *s) {
 
 template <typename T, bool ZZERO, bool NORM>
 __global__ void __launch_bounds__(kWarpsPerCta * kLanes)
-k_sr_stream(int N, int n, View z, View b, View zout, View bc, const Coef<T> *__restrict__ coef,
-            const int *__restrict__ active, double *__restrict__ partials, int part_stride) {
+k_sr_stream(int N, int n, int seg, View z, View b, View zout, View bc,
+            const Coef<T> *__restrict__ coef, const int *__restrict__ active,
+            double *__restrict__ partials, int part_stride) {
   using C = typename Cx<T>::type;
   extern __shared__ __align__(16) unsigned char ring_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   // ring: kDepth slots x (z row, bt row) x 32 lanes x 2 complex
   C *ring = reinterpret_cast<C *>(ring_raw) + (size_t)wib * kDepth * 2 * kLanes * 2;
-  const int nsx = (N + kStripOut - 1) / kStripOut, nsy = (N + kSegRows - 1) / kSegRows;
+  const int nsx = (N + kStripOut - 1) / kStripOut, nsy = (N + seg - 1) / seg;
   const int total = n * nsx * nsy;
   const int Nc = (N - 1) / 2;
   const int gw = blockIdx.x * kWarpsPerCta + wib, nw = gridDim.x * kWarpsPerCta;
@@ -104,7 +105,7 @@ k_sr_stream(int N, int n, View z, View b, View zout, View bc, const Coef<T> *__r
     const int sx = u % nsx, sy = (u / nsx) % nsy, j = u / (nsx * nsy);
     if (active && !active[j]) continue;
     const Coef<T> cf = coef[j];
-    const int x0 = sx * kStripOut, y0 = sy * kSegRows, y1 = min(y0 + kSegRows, N);
+    const int x0 = sx * kStripOut, y0 = sy * seg, y1 = min(y0 + seg, N);
     const int xend = min(x0 + kStripOut, N);
     const int a = x0 - 4 + 2 * lane;  // this lane's columns a, a+1
     const bool cin0 = a >= 0 && a < N, cin1 = a + 1 >= 0 && a + 1 < N;
@@ -261,14 +262,14 @@ k_sr_stream(int N, int n, View z, View b, View zout, View bc, const Coef<T> *__r
 
 template <typename T>
 __global__ void __launch_bounds__(kWarpsPerCta * kLanes)
-k_ps_stream(int N, int n, View z, View e, View b, View zout, const Coef<T> *__restrict__ coef,
-            const int *__restrict__ active) {
+k_ps_stream(int N, int n, int seg, View z, View e, View b, View zout,
+            const Coef<T> *__restrict__ coef, const int *__restrict__ active) {
   using C = typename Cx<T>::type;
   extern __shared__ __align__(16) unsigned char ring_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   // ring: kDepth slots x (z' row, bt row, coarse row) x 32 lanes x 2 complex
   C *ring = reinterpret_cast<C *>(ring_raw) + (size_t)wib * kDepth * 3 * kLanes * 2;
-  const int nsx = (N + kStripOut - 1) / kStripOut, nsy = (N + kSegRows - 1) / kSegRows;
+  const int nsx = (N + kStripOut - 1) / kStripOut, nsy = (N + seg - 1) / seg;
   const int total = n * nsx * nsy;
   const int Nc = (N - 1) / 2;
   const int gw = blockIdx.x * kWarpsPerCta + wib, nw = gridDim.x * kWarpsPerCta;
@@ -276,7 +277,7 @@ k_ps_stream(int N, int n, View z, View e, View b, View zout, const Coef<T> *__re
     const int sx = u % nsx, sy = (u / nsx) % nsy, j = u / (nsx * nsy);
     if (active && !active[j]) continue;
     const Coef<T> cf = coef[j];
-    const int x0 = sx * kStripOut, y0 = sy * kSegRows, y1 = min(y0 + kSegRows, N);
+    const int x0 = sx * kStripOut, y0 = sy * seg, y1 = min(y0 + seg, N);
     const int xend = min(x0 + kStripOut, N);
     const int a = x0 - 4 + 2 * lane;
     const int J = a >> 1;  // coarse column of the odd fine column a+1
@@ -404,34 +405,34 @@ template <int ROWS> constexpr int ring_bytes(int elem) { return kWarpsPerCta * k
 
 }  // namespace
 
-int stream_units(int N) {
-  return ((N + kStripOut - 1) / kStripOut) * ((N + kSegRows - 1) / kSegRows);
+int stream_units(int N, int seg) {
+  return ((N + kStripOut - 1) / kStripOut) * ((N + seg - 1) / seg);
 }
 
 template <typename T>
-void launch_sr_stream(cudaStream_t s, int grid, int N, int n, View z, View b, View zout, View bc,
-                      const Coef<T> *coef, const int *active, bool z_zero, double *partials,
+void launch_sr_stream(cudaStream_t s, int grid, int N, int n, int seg, View z, View b, View zout,
+                      View bc, const Coef<T> *coef, const int *active, bool z_zero, double *partials,
                       int part_stride) {
   const int smem = ring_bytes<2>((int)sizeof(typename Cx<T>::type));
   const int th = kWarpsPerCta * kLanes;
   if (z_zero) {
     if (partials)
-      k_sr_stream<T, true, true><<<grid, th, smem, s>>>(N, n, z, b, zout, bc, coef, active, partials, part_stride);
+      k_sr_stream<T, true, true><<<grid, th, smem, s>>>(N, n, seg, z, b, zout, bc, coef, active, partials, part_stride);
     else
-      k_sr_stream<T, true, false><<<grid, th, smem, s>>>(N, n, z, b, zout, bc, coef, active, partials, part_stride);
+      k_sr_stream<T, true, false><<<grid, th, smem, s>>>(N, n, seg, z, b, zout, bc, coef, active, partials, part_stride);
   } else {
     if (partials)
-      k_sr_stream<T, false, true><<<grid, th, smem, s>>>(N, n, z, b, zout, bc, coef, active, partials, part_stride);
+      k_sr_stream<T, false, true><<<grid, th, smem, s>>>(N, n, seg, z, b, zout, bc, coef, active, partials, part_stride);
     else
-      k_sr_stream<T, false, false><<<grid, th, smem, s>>>(N, n, z, b, zout, bc, coef, active, partials, part_stride);
+      k_sr_stream<T, false, false><<<grid, th, smem, s>>>(N, n, seg, z, b, zout, bc, coef, active, partials, part_stride);
   }
 }
 
 template <typename T>
-void launch_ps_stream(cudaStream_t s, int grid, int N, int n, View z, View e, View b, View zout,
-                      const Coef<T> *coef, const int *active) {
+void launch_ps_stream(cudaStream_t s, int grid, int N, int n, int seg, View z, View e, View b,
+                      View zout, const Coef<T> *coef, const int *active) {
   const int smem = ring_bytes<3>((int)sizeof(typename Cx<T>::type));
-  k_ps_stream<T><<<grid, kWarpsPerCta * kLanes, smem, s>>>(N, n, z, e, b, zout, coef, active);
+  k_ps_stream<T><<<grid, kWarpsPerCta * kLanes, smem, s>>>(N, n, seg, z, e, b, zout, coef, active);
 }
 
 template <typename T> cudaError_t prepare_stream() {
@@ -462,9 +463,9 @@ template <typename T> int stream_grid(int num_sms) {
 }
 
 #define PD_INST_S(T)                                                                             \
-  template void launch_sr_stream<T>(cudaStream_t, int, int, int, View, View, View, View,        \
+  template void launch_sr_stream<T>(cudaStream_t, int, int, int, int, View, View, View, View,   \
                                     const Coef<T> *, const int *, bool, double *, int);          \
-  template void launch_ps_stream<T>(cudaStream_t, int, int, int, View, View, View, View,        \
+  template void launch_ps_stream<T>(cudaStream_t, int, int, int, int, View, View, View, View,   \
                                     const Coef<T> *, const int *);                               \
   template int stream_grid<T>(int);                                                              \
   template cudaError_t prepare_stream<T>();

@@ -6,7 +6,7 @@
 // FP32-compensated product the refinement needs because V can be ill-conditioned.
 //
 //   forward:  K = 64 (k < n),  rows 2j / 2j+1 of A = Re / Im of h^2 V^{-1}[j][k],
-//             B[k][p] = fhat_k at point p (FP64 input, rounded to FP32 then split);
+//             B[k][p] = fhat_k at point p (FP64 or FP32 input, rounded to FP32 then split);
 //             g_j(p) = (D[2j][p], D[2j+1][p]).
 //   inverse:  K = 128 (2j + re/im), row k of A = (Re V[k][j], -Im V[k][j]) and row 64 + k =
 //             (Im V[k][j], Re V[k][j]), B[2j+q][p] = component q of z_j(p);
@@ -149,8 +149,9 @@ __device__ __forceinline__ unsigned char *align1024(unsigned char *p) {
 
 // g_j(p) = h^2 sum_k V^{-1}[j][k] fhat_k(p), fhat_k = f_k + u0coef[k] u0, for the points
 // p = (i, c0..c0+127) of grid row i; written into the h^2-scaled level-0 RHS view.
+template <typename InT>
 __global__ void __launch_bounds__(kTcThreads, 1)
-k_tc_forward(int N, int n, View g, const double *__restrict__ f, const double *__restrict__ u0,
+k_tc_forward(int N, int n, View g, const InT *__restrict__ f, const double *__restrict__ u0,
              const double *__restrict__ u0coef, const float *__restrict__ Ahi,
              const float *__restrict__ Alo, int *__restrict__ errflag) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -193,7 +194,7 @@ k_tc_forward(int N, int n, View g, const double *__restrict__ f, const double *_
         const int k = 4 * kq + e;
         double v = 0.0;
         if (k < n && c < N) {
-          v = f[k * m + x];
+          v = (double)f[k * m + x];
           if (u0) v += u0coef[k] * u0[x];
         }
         pre[q][e] = v;
@@ -402,7 +403,9 @@ k_tc_inverse(int N, int n, double *__restrict__ u, View z0, View z1, const int *
 bool tc_transforms_supported(int N, int n) { return n <= 64 && N >= 127; }
 
 cudaError_t prepare_tc_transforms() {
-  cudaError_t e = cudaFuncSetAttribute(k_tc_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_tc_forward<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_tc_forward<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmem);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_tc_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, kInvSmem);
 }
@@ -441,10 +444,15 @@ void tc_build_operands(int n, const double *Vinv, const double *V, double scale,
     }
 }
 
-void launch_tc_forward(cudaStream_t s, int grid, int N, int n, View g, const double *f,
+void launch_tc_forward(cudaStream_t s, int grid, int N, int n, View g, const void *f, bool f32,
                        const double *u0, const double *u0coef, const float *Ahi, const float *Alo,
                        int *errflag) {
-  k_tc_forward<<<grid, kTcThreads, kFwdSmem, s>>>(N, n, g, f, u0, u0coef, Ahi, Alo, errflag);
+  if (f32)
+    k_tc_forward<float><<<grid, kTcThreads, kFwdSmem, s>>>(N, n, g, static_cast<const float *>(f), u0,
+                                                           u0coef, Ahi, Alo, errflag);
+  else
+    k_tc_forward<double><<<grid, kTcThreads, kFwdSmem, s>>>(N, n, g, static_cast<const double *>(f), u0,
+                                                            u0coef, Ahi, Alo, errflag);
 }
 
 void launch_tc_inverse(cudaStream_t s, int grid, int N, int n, double *u, View z0, View z1,

@@ -22,9 +22,9 @@ __device__ __forceinline__ void stv(const View &v, int j, long long i, long long
 }
 
 // g_j = scale * sum_k W[j][k] fhat_k, fhat_k = f_k + u0coef[k] u0 (real input).
-template <typename T>
+template <typename T, typename InT>
 __global__ void __launch_bounds__(kThreads)
-k_transform_forward(int N, int n, View g, const double *__restrict__ f,
+k_transform_forward(int N, int n, View g, const InT *__restrict__ f,
                     const double *__restrict__ u0, const double *__restrict__ u0coef,
                     const typename Cx<T>::type *__restrict__ W, T scale) {
   using C = typename Cx<T>::type;
@@ -37,7 +37,7 @@ k_transform_forward(int N, int n, View g, const double *__restrict__ f,
     const long long x = x0 + p;
     double v = 0.0;
     if (x < m) {
-      v = f[k * m + x];
+      v = (double)f[k * m + x];
       if (u0) v += u0coef[k] * u0[x];
     }
     xs[t] = (T)v;
@@ -172,27 +172,112 @@ k_allatonce_residual(int N, int n, double *__restrict__ r, const double *__restr
   }
 }
 
+// Residual of eq. (1) for a B with nonzeros only at (k, k) and (k, k-1 mod n) (backward
+// Euler, its alpha-circulant variant):
+//   r_k = fhat_k - (bd_k u_k + bs_k u_{k-1 mod n}) - (1/h^2)(4 u_k - sum of 4 neighbours)
+// with 8 FP64 operations per point (GB300's FP64 rate bounds this kernel).  One CTA
+// sweeps whole grid rows (k, i); per-CTA sums of r^2 (and of fhat^2 when WANT_F) go to
+// part[2b], part[2b+1] over a fixed grid, so the sums are reproducible.
+template <typename OutT, bool WANT_F>
+__global__ void __launch_bounds__(kResThreads)
+k_residual_bidiag(int N, int n, OutT *__restrict__ r, const double *__restrict__ u,
+                  const double *__restrict__ f, const double *__restrict__ u0,
+                  const double *__restrict__ u0coef, const double *__restrict__ bd,
+                  const double *__restrict__ bs, double ih2, double *__restrict__ part) {
+  __shared__ double red[2][kResThreads / 32];
+  const long long m = (long long)N * N;
+  double ar = 0.0, af = 0.0;
+  for (int row = blockIdx.x; row < n * N; row += gridDim.x) {
+    const int k = row / N, i = row - k * N;
+    const int kp = k == 0 ? n - 1 : k - 1;
+    const double dk = bd[k], sk = bs[k], ck = u0 ? u0coef[k] : 0.0;
+    const double *uk = u + (long long)k * m + (long long)i * N;
+    const double *up = u + (long long)kp * m + (long long)i * N;
+    const double *fk = f + (long long)k * m + (long long)i * N;
+    const double *u0r = u0 ? u0 + (long long)i * N : nullptr;
+    for (int c = threadIdx.x; c < N; c += kResThreads) {
+      double fh = fk[c];
+      if (ck != 0.0) fh = fma(ck, u0r[c], fh);
+      const double uc = uk[c];
+      double nb = 0.0;
+      if (i > 0) nb += uk[c - N];
+      if (i < N - 1) nb += uk[c + N];
+      if (c > 0) nb += uk[c - 1];
+      if (c < N - 1) nb += uk[c + 1];
+      const double lap = fma(4.0, uc, -nb);
+      const double bu = fma(sk, up[c], dk * uc);
+      const double rv = fma(-ih2, lap, fh - bu);
+      if (r) r[(long long)k * m + (long long)i * N + c] = (OutT)rv;
+      ar = fma(rv, rv, ar);
+      if (WANT_F) af = fma(fh, fh, af);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ar += __shfl_down_sync(0xffffffffu, ar, o);
+    if (WANT_F) af += __shfl_down_sync(0xffffffffu, af, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = ar;
+    red[1][threadIdx.x >> 5] = af;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int w = 0; w < kResThreads / 32; w++) {
+      s0 += red[0][w];
+      s1 += red[1][w];
+    }
+    part[2 * blockIdx.x] = s0;
+    part[2 * blockIdx.x + 1] = s1;
+  }
+}
+
 }  // namespace
+
+void launch_residual_bidiag(cudaStream_t s, int N, int n, double *r64, float *r32, const double *u,
+                            const double *f, const double *u0, const double *u0coef,
+                            const double *bd, const double *bs, bool want_f, double *part) {
+  const double h = 1.0 / (N + 1), ih2 = 1.0 / (h * h);
+  const int g = allatonce_blocks();
+  if (r32) {
+    if (want_f)
+      k_residual_bidiag<float, true><<<g, kResThreads, 0, s>>>(N, n, r32, u, f, u0, u0coef, bd, bs, ih2, part);
+    else
+      k_residual_bidiag<float, false><<<g, kResThreads, 0, s>>>(N, n, r32, u, f, u0, u0coef, bd, bs, ih2, part);
+  } else {
+    if (want_f)
+      k_residual_bidiag<double, true><<<g, kResThreads, 0, s>>>(N, n, r64, u, f, u0, u0coef, bd, bs, ih2, part);
+    else
+      k_residual_bidiag<double, false><<<g, kResThreads, 0, s>>>(N, n, r64, u, f, u0, u0coef, bd, bs, ih2, part);
+  }
+}
 
 template <typename T>
 cudaError_t prepare_transforms(int n) {
   using C = typename Cx<T>::type;
-  cudaError_t e = cudaFuncSetAttribute(k_transform_forward<T>,
+  cudaError_t e = cudaFuncSetAttribute(k_transform_forward<T, double>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(n * kPts * sizeof(T)));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_transform_forward<T, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(n * kPts * sizeof(T)));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_transform_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)(n * kPts * sizeof(C)));
 }
 
 template <typename T>
-void launch_transform_forward(cudaStream_t s, int N, int n, View g, const double *f,
+void launch_transform_forward(cudaStream_t s, int N, int n, View g, const void *f, bool f32,
                               const double *u0, const double *u0coef,
                               const typename Cx<T>::type *W, double scale) {
   const long long m = (long long)N * N;
   const unsigned blocks = (unsigned)((m + kPts - 1) / kPts);
-  k_transform_forward<T><<<blocks, kThreads, n * kPts * sizeof(T), s>>>(N, n, g, f, u0, u0coef, W,
-                                                                        (T)scale);
+  if (f32)
+    k_transform_forward<T, float><<<blocks, kThreads, n * kPts * sizeof(T), s>>>(
+        N, n, g, static_cast<const float *>(f), u0, u0coef, W, (T)scale);
+  else
+    k_transform_forward<T, double><<<blocks, kThreads, n * kPts * sizeof(T), s>>>(
+        N, n, g, static_cast<const double *>(f), u0, u0coef, W, (T)scale);
 }
 
 template <typename T>
@@ -220,10 +305,10 @@ void launch_allatonce_residual(cudaStream_t s, int N, int n, double *r, const do
 
 template cudaError_t prepare_transforms<double>(int);
 template cudaError_t prepare_transforms<float>(int);
-template void launch_transform_forward<double>(cudaStream_t, int, int, View, const double *,
+template void launch_transform_forward<double>(cudaStream_t, int, int, View, const void *, bool,
                                                const double *, const double *, const double2 *,
                                                double);
-template void launch_transform_forward<float>(cudaStream_t, int, int, View, const double *,
+template void launch_transform_forward<float>(cudaStream_t, int, int, View, const void *, bool,
                                               const double *, const double *, const float2 *,
                                               double);
 template void launch_transform_inverse<double>(cudaStream_t, int, int, double *, View, View,
