@@ -73,11 +73,13 @@ typedef struct {
     int fused_variant; /* implementation of the fused kernels: 0 = chosen at set-up by timing
                           both on the context's own levels, 1 = TMA-staged shared-memory
                           tiles, 2 = warp-streaming strips (cp.async ring, shuffles) */
+    double kappa;      /* diffusion coefficient scaling A in eq. (1): (B kron I + kappa I kron A);
+                          the shifted systems become (kappa A + lam_j I) z = b (default 1) */
 } pd_config;
 
 /* Fills cfg with V(1,1), coarsest 3, maxit 100, tol 1e-10, omega_mode 1, FP64,
  * Vanka, inner_tol 1e-6, max_refine 12, imag_check 1, inner_maxit 3, stall_ratio 0.5,
- * fused 1, tensor_transforms 1, fused_variant 0. */
+ * fused 1, tensor_transforms 1, fused_variant 0, kappa 1. */
 void pd_config_default(pd_config *cfg);
 
 /*
@@ -117,6 +119,15 @@ pd_status paradiag_setup(pd_ctx **ctx, int N, double h, int n, const double *h_s
                          const double *h_V, const double *h_Vinv, const double *h_B,
                          const double *h_u0_coef, const double *h_omega,
                          const pd_config *cfg, void *stream);
+
+/*
+ * Context of the adjoint step (used to differentiate a solve): the transpose of eq. (1),
+ * (B^T kron I_h + kappa I_t kron A) w = g, with B^T = V^{-H} conj(D) V^H, i.e. the shifted
+ * systems (kappa A + conj(lam_j) I) of the same multigrid, transforms V^H and V^{-H}, B^T
+ * for the refinement residual, no initial-value term, the forward context's options,
+ * relaxation table and stream.  Errors: PD_ERR_STATE without V, as paradiag_setup.
+ */
+pd_status pd_adjoint_setup(const pd_ctx *ctx, pd_ctx **adj);
 
 /* Number of grid levels (finest N down to the coarsest) and the relaxation
  * parameter table [n][levels] the context uses (host copy). */
@@ -214,6 +225,21 @@ pd_status pd_transform_forward(pd_ctx *ctx, void *d_g, const double *d_f, const 
 pd_status pd_transform_inverse(pd_ctx *ctx, double *d_u, const void *d_z, int accumulate);
 pd_status pd_allatonce_residual(pd_ctx *ctx, double *d_r, const double *d_u, const double *d_f,
                                 const double *d_u0, double *h_norms);
+
+/*
+ * Gradient reduction of the adjoint (differentiation with respect to a coefficient
+ * kappa scaling A in eq. (1)): *h_out = sum_k <d_w_k, A d_u_k>, A the five-point
+ * operator of the context's grid (Sec. 1), in FP64 with a fixed summation order.
+ * d_w, d_u: [n][N][N] double, device.  Synchronises.
+ */
+pd_status pd_laplacian_dot(pd_ctx *ctx, const double *d_w, const double *d_u, double *h_out);
+
+/*
+ * Gradient with respect to the initial value: fhat_k = f_k + u0_coef[k] u0, so
+ * d_gu0 = sum_k u0_coef[k] d_w_k for the adjoint solution d_w (the forward context's
+ * u0_coef).  d_w: [n][N][N] double, d_gu0: [N][N] double, device.  Asynchronous.
+ */
+pd_status pd_initial_value_gradient(pd_ctx *ctx, const double *d_w, double *d_gu0);
 
 /*
  * Allocation-free residual check for the alpha-circulant backward-Euler system (the

@@ -30,11 +30,14 @@ KERNEL_CLASSES = ["smooth0", "restrict0", "prolong0", "smooth_c", "restrict_c", 
 STATUS = {0: "PD_OK", 1: "PD_ERR_ARG", 2: "PD_ERR_CUDA", 3: "PD_ERR_NOMEM", 4: "PD_ERR_NOCONV",
           5: "PD_ERR_NAN", 6: "PD_ERR_SING", 7: "PD_ERR_STATE"}
 
-EXPORTS = ["pd_config_default", "pd_alpha_circulant", "paradiag_setup", "pd_num_levels",
+EXPORTS = ["pd_config_default", "pd_alpha_circulant", "paradiag_setup", "pd_adjoint_setup",
+           "pd_num_levels",
            "pd_get_omega", "mg_vcycle", "shifted_solve_batched", "paradiag_solve",
            "paradiag_solve_host", "pd_smooth", "pd_residual_restrict", "pd_prolong_add",
            "pd_coarse_solve", "pd_transform_forward", "pd_transform_inverse",
-           "pd_allatonce_residual", "pd_allatonce_residual_static", "pd_profile_enable", "pd_profile_read", "pd_synchronize", "pd_launch_count", "paradiag_destroy",
+           "pd_allatonce_residual", "pd_allatonce_residual_static", "pd_laplacian_dot",
+           "pd_initial_value_gradient",
+           "pd_profile_enable", "pd_profile_read", "pd_synchronize", "pd_launch_count", "paradiag_destroy",
            "pd_status_str", "pd_last_error"]
 
 
@@ -51,7 +54,8 @@ class pd_config(C.Structure):
                 ("omega_mode", C.c_int), ("precision", C.c_int), ("smoother", C.c_int),
                 ("inner_tol", C.c_double), ("max_refine", C.c_int), ("imag_check", C.c_int),
                 ("inner_maxit", C.c_int), ("stall_ratio", C.c_double), ("fused", C.c_int),
-                ("tensor_transforms", C.c_int), ("fused_variant", C.c_int)]
+                ("tensor_transforms", C.c_int), ("fused_variant", C.c_int),
+                ("kappa", C.c_double)]
 
 
 _P = C.c_void_p
@@ -75,6 +79,7 @@ def lib(path=None):
             "pd_alpha_circulant": (_I, [_I, _D, _D, _P, _P, _P, _P, _P]),
             "paradiag_setup": (_I, [C.POINTER(_P), _I, _D, _I, _P, _P, _P, _P, _P, _P,
                                     C.POINTER(pd_config), _P]),
+            "pd_adjoint_setup": (_I, [_P, C.POINTER(_P)]),
             "pd_num_levels": (_I, [_P]),
             "pd_get_omega": (_I, [_P, _P]),
             "mg_vcycle": (_I, [_P, _I, _P, _P]),
@@ -89,6 +94,8 @@ def lib(path=None):
             "pd_transform_inverse": (_I, [_P, _P, _P, _I]),
             "pd_allatonce_residual": (_I, [_P, _P, _P, _P, _P, _P]),
             "pd_allatonce_residual_static": (_I, [_I, _I, _D, _D, _P, _P, _P, _P, _P, _P]),
+            "pd_laplacian_dot": (_I, [_P, _P, _P, _P]),
+            "pd_initial_value_gradient": (_I, [_P, _P, _P]),
             "pd_profile_enable": (_I, [_P, _I]),
             "pd_profile_read": (_I, [_P, _I, _P, _P, _P]),
             "pd_synchronize": (_I, [_P]),
@@ -205,6 +212,16 @@ class Context:
     def synchronize(self):
         _check(lib().pd_synchronize(self.h), "pd_synchronize", self.h)
 
+    def adjoint(self):
+        """Context of the transposed step (pd_adjoint_setup)."""
+        a = Context.__new__(Context)
+        h = C.c_void_p()
+        _check(lib().pd_adjoint_setup(self.h, C.byref(h)), "pd_adjoint_setup", self.h)
+        a.h = h
+        a.N, a.n, a.cfg, a.stream, a._keep = self.N, self.n, self.cfg, self.stream, []
+        a.levels, a.Ns, a.ctype = self.levels, list(self.Ns), self.ctype
+        return a
+
     def launch_count(self):
         return int(lib().pd_launch_count(self.h))
 
@@ -318,6 +335,22 @@ class Context:
         m = self.n * self.N * self.N
         _check(lib().pd_transform_inverse(self.h, _dptr(u, torch.float64, m), self._grid(z),
                                           int(bool(accumulate))), "pd_transform_inverse", self.h)
+
+    def pd_laplacian_dot(self, w, u):
+        """sum_k <w_k, A u_k> (FP64)."""
+        import torch
+        m = self.n * self.N * self.N
+        out = C.c_double()
+        _check(lib().pd_laplacian_dot(self.h, _dptr(w, torch.float64, m), _dptr(u, torch.float64, m),
+                                      C.byref(out)), "pd_laplacian_dot", self.h)
+        return out.value
+
+    def pd_initial_value_gradient(self, w, gu0):
+        import torch
+        m = self.n * self.N * self.N
+        _check(lib().pd_initial_value_gradient(self.h, _dptr(w, torch.float64, m),
+                                               _dptr(gu0, torch.float64, self.N * self.N)),
+               "pd_initial_value_gradient", self.h)
 
     def pd_allatonce_residual(self, r, u, f, u0=None):
         import torch

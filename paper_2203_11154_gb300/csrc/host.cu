@@ -71,7 +71,8 @@ struct pd_ctx {
   double *d_Bval = nullptr;
   double *d_r = nullptr;       // refinement residual [n][N][N] (general B)
   float *d_r32 = nullptr;      // refinement residual in FP32 (bidiagonal B)
-  bool bidiag = false;         // B has nonzeros only at (k,k) and (k,k-1 mod n)
+  bool bidiag = false;         // B has nonzeros only at (k,k) and (k,k+boff mod n)
+  int boff = -1;
   double *d_bd = nullptr, *d_bs = nullptr;
   double fnorm = -1.0;         // ||fhat|| of the running refinement
   double *d_part = nullptr;    // all-at-once residual partial sums
@@ -80,6 +81,7 @@ struct pd_ctx {
   double *d_stage_f = nullptr, *d_stage_u = nullptr, *d_stage_u0 = nullptr;
   long long launches = 0;
   int num_sms = 0;
+  double kappa = 1.0;     // A is scaled by kappa in eq. (1); the multigrid sees lam / kappa
   int stream_grid = 0;    // persistent grid of the streaming kernels
   // instrumentation: event pairs around launches, resolved after each solve
   bool prof_on = false;
@@ -221,6 +223,8 @@ template <> Prec<double> &prec<double>(pd_ctx *c) { return c->p64; }
 template <> Prec<float> &prec<float>(pd_ctx *c) { return c->p32; }
 
 double hl(const pd_ctx *c, int l) { return 1.0 / (c->Ns[l] + 1); }
+// scale of a right-hand side of level l in the kernels' form: h_l^2 / kappa
+double rs(const pd_ctx *c, int l) { return hl(c, l) * hl(c, l) / c->kappa; }
 
 // Set-up autotuner of the fused kernels: on each global-memory level, times the
 // smoothing+restriction and interpolation+smoothing pair of every candidate (TMA tiles;
@@ -329,7 +333,8 @@ void alloc_prec(pd_ctx *c) {
   for (int l = 0; l < L; l++) {
     const double h = hl(c, l);
     for (int j = 0; j < n; j++) {
-      const std::complex<double> lam(c->shifts[2 * j], c->shifts[2 * j + 1]);
+      const std::complex<double> lam =
+          std::complex<double>(c->shifts[2 * j], c->shifts[2 * j + 1]) / c->kappa;
       const std::complex<double> eta = lam * h * h, d = 4.0 + eta;
       const double w = c->omega[(size_t)j * L + l];
       double abc[6];
@@ -357,7 +362,8 @@ void alloc_prec(pd_ctx *c) {
   const double h = hl(c, L - 1);
   std::vector<C> inv((size_t)n * m * m);
   for (int j = 0; j < n; j++) {
-    const std::complex<double> lam(c->shifts[2 * j], c->shifts[2 * j + 1]);
+    const std::complex<double> lam =
+        std::complex<double>(c->shifts[2 * j], c->shifts[2 * j + 1]) / c->kappa;
     const std::complex<double> d = 4.0 + lam * h * h;
     std::vector<double> A((size_t)2 * m * m, 0.0);
     for (int i = 0; i < Nc; i++)
@@ -396,7 +402,8 @@ void alloc_prec(pd_ctx *c) {
     const size_t fa = 128 * 64, ia = 128 * 128;
     std::vector<float> fh(fa), fl(fa), ih(ia), il(ia), f1h(fa), f1l(fa), ih2(ia), il2(ia);
     const double h0 = hl(c, 0);
-    tc_build_operands(n, c->Vinv.data(), c->V.data(), h0 * h0, fh.data(), fl.data(), ih.data(), il.data());
+    tc_build_operands(n, c->Vinv.data(), c->V.data(), h0 * h0 / c->kappa, fh.data(), fl.data(), ih.data(),
+                      il.data());
     tc_build_operands(n, c->Vinv.data(), c->V.data(), 1.0, f1h.data(), f1l.data(), ih2.data(), il2.data());
     P.tc_fwd_hi = dalloc<float *>(c, fa * 4);
     P.tc_fwd_lo = dalloc<float *>(c, fa * 4);
@@ -668,12 +675,12 @@ void allatonce_norms(pd_ctx *c, double *r, const double *u, const double *f, con
   if (c->bidiag)
     PD_PROF(PD_KC_RESIDUAL,
             (r ? 24.0 : r32 ? 20.0 : 16.0) * m + (u0 ? 8.0 * m / c->n : 0.0), 0,
-            launch_residual_bidiag(c->stream, c->N, c->n, r, r32, u, f, u0, c->d_u0coef, c->d_bd,
-                                   c->d_bs, want_f, c->d_part));
+            launch_residual_bidiag(c->stream, c->N, c->n, c->boff, c->kappa, r, r32, u, f, u0,
+                                   c->d_u0coef, c->d_bd, c->d_bs, want_f, c->d_part));
   else
     PD_PROF(PD_KC_RESIDUAL, (r ? 24.0 : 16.0) * m + (u0 ? 8.0 * m / c->n : 0.0), 0,
-            launch_allatonce_residual(c->stream, c->N, c->n, r, u, f, u0, c->d_u0coef, c->d_Bptr,
-                                      c->d_Bcol, c->d_Bval, c->d_part));
+            launch_allatonce_residual(c->stream, c->N, c->n, c->kappa, r, u, f, u0, c->d_u0coef,
+                                      c->d_Bptr, c->d_Bcol, c->d_Bval, c->d_part));
   ck_launch(c);
   const int nb = allatonce_blocks();
   ck(c, cudaMemcpyAsync(c->h_part, c->d_part, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost,
@@ -702,7 +709,7 @@ void transform_forward(pd_ctx *c, View g, const void *f, const double *u0, bool 
                       c->st.flags);
   } else {
     launch_transform_forward<T>(c->stream, c->N, c->n, g, f, f32, u0, c->d_u0coef, P.Wf,
-                                scaled ? h * h : 1.0);
+                                scaled ? h * h / c->kappa : 1.0);
   }
 }
 
@@ -888,6 +895,7 @@ void pd_config_default(pd_config *cfg) {
   cfg->fused = 1;
   cfg->tensor_transforms = 1;
   cfg->fused_variant = 0;
+  cfg->kappa = 1.0;
 }
 
 pd_status pd_alpha_circulant(int n, double tau, double alpha, double *B, double *shifts,
@@ -950,7 +958,7 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
       !(cfg.inner_tol >= 0) || cfg.max_refine < 1 || cfg.inner_maxit < 1 ||
       cfg.inner_maxit > 100000 || !(cfg.stall_ratio >= 0) || cfg.fused < 0 || cfg.fused > 2 ||
       cfg.tensor_transforms < 0 || cfg.tensor_transforms > 1 || cfg.fused_variant < 0 ||
-      cfg.fused_variant > 2)
+      cfg.fused_variant > 2 || !(cfg.kappa > 0) || !std::isfinite(cfg.kappa))
     return PD_ERR_ARG;
   if (cfg.omega_mode == 2 && !omega) return PD_ERR_ARG;
   if (cfg.precision == 1 && (!B || !V)) return PD_ERR_ARG;
@@ -961,6 +969,7 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
   c->N = N;
   c->n = n;
   c->cfg = cfg;
+  c->kappa = cfg.kappa;
   int Nl = N;
   c->Ns.push_back(Nl);
   while (Nl > cfg.coarsest_n) {
@@ -991,7 +1000,8 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
       else if (cfg.omega_mode == 0) w = cfg.smoother == 1 ? 0.8 : 24.0 / 25.0;
       else {
         const double hh = 1.0 / (c->Ns[l] + 1);
-        w = lfa_omega_opt(shifts[2 * j] * hh * hh, shifts[2 * j + 1] * hh * hh, cfg.smoother);
+        w = lfa_omega_opt(shifts[2 * j] * hh * hh / cfg.kappa, shifts[2 * j + 1] * hh * hh / cfg.kappa,
+                          cfg.smoother);
       }
       c->omega[(size_t)j * c->L + l] = w;
     }
@@ -1040,17 +1050,22 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
     c->d_part = dalloc<double *>(c, 2 * allatonce_blocks() * sizeof(double));
     c->d_imag = dalloc<unsigned long long *>(c, sizeof(unsigned long long));
     if (B) {
-      bool bid = true;
       std::vector<double> bd(n), bs(n);
-      for (int k = 0; k < n; k++) {
-        const int kp = (k + n - 1) % n;
-        bd[k] = B[(size_t)k * n + k];
-        bs[k] = n > 1 ? B[(size_t)k * n + kp] : 0.0;
-        for (int l = 0; l < n; l++)
-          if (B[(size_t)k * n + l] != 0.0 && l != k && l != kp) bid = false;
+      for (int off = -1; off <= 1 && !c->bidiag; off += 2) {
+        bool bid = n > 1;
+        for (int k = 0; k < n; k++) {
+          const int kp = (k + off + n) % n;
+          bd[k] = B[(size_t)k * n + k];
+          bs[k] = n > 1 ? B[(size_t)k * n + kp] : 0.0;
+          for (int l = 0; l < n; l++)
+            if (B[(size_t)k * n + l] != 0.0 && l != k && l != kp) bid = false;
+        }
+        if (bid && n > 2) {
+          c->bidiag = true;
+          c->boff = off;
+        }
       }
-      if (n > 1 && bid) {
-        c->bidiag = true;
+      if (c->bidiag) {
         c->d_bd = dalloc<double *>(c, n * sizeof(double));
         c->d_bs = dalloc<double *>(c, n * sizeof(double));
         ck(c, cudaMemcpy(c->d_bd, bd.data(), n * sizeof(double), cudaMemcpyHostToDevice));
@@ -1097,6 +1112,35 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
   return PD_OK;
 }
 
+pd_status pd_adjoint_setup(const pd_ctx *c, pd_ctx **out) {
+  if (!c || !out) return PD_ERR_ARG;
+  if (!c->have_V) return PD_ERR_STATE;
+  const int n = c->n;
+  std::vector<double> sh(2 * n), Va(2 * (size_t)n * n), Via(2 * (size_t)n * n), Bt;
+  for (int j = 0; j < n; j++) {
+    sh[2 * j] = c->shifts[2 * j];
+    sh[2 * j + 1] = -c->shifts[2 * j + 1];
+  }
+  // V_adj = (V^{-1})^H, V_adj^{-1} = V^H
+  for (int k = 0; k < n; k++)
+    for (int j = 0; j < n; j++) {
+      const size_t e = (size_t)k * n + j, t = (size_t)j * n + k;
+      Va[2 * e] = c->Vinv[2 * t];
+      Va[2 * e + 1] = -c->Vinv[2 * t + 1];
+      Via[2 * e] = c->V[2 * t];
+      Via[2 * e + 1] = -c->V[2 * t + 1];
+    }
+  if (c->have_B) {
+    Bt.resize((size_t)n * n);
+    for (int k = 0; k < n; k++)
+      for (int l = 0; l < n; l++) Bt[(size_t)k * n + l] = c->B[(size_t)l * n + k];
+  }
+  pd_config cfg = c->cfg;
+  cfg.omega_mode = 2;  // conj(lam) has the same LFA optimum; reuse the forward table
+  return paradiag_setup(out, c->N, 1.0 / (c->N + 1), n, sh.data(), Va.data(), Via.data(),
+                        c->have_B ? Bt.data() : nullptr, nullptr, c->omega.data(), &cfg, c->stream);
+}
+
 int pd_num_levels(const pd_ctx *c) { return c ? c->L : 0; }
 
 pd_status pd_get_omega(const pd_ctx *c, double *h_omega) {
@@ -1112,7 +1156,7 @@ pd_status mg_vcycle(pd_ctx *c, int level, void *z, const void *b) {
     const double h = hl(c, level);
     if (c->cfg.precision == 0) {
       LevelBufs &B = c->p64.lv[level];
-      launch_copy_scale<double>(c->stream, N, n, view(B.b, N, B.P), uview(b, N), h * h);
+      launch_copy_scale<double>(c->stream, N, n, view(B.b, N, B.P), uview(b, N), rs(c, level));
       launch_copy_scale<double>(c->stream, N, n, view(B.z[0], N, B.P), uview(z, N), 1.0);
       ck_launch(c, 2);
       c->cur[level] = 0;
@@ -1120,7 +1164,7 @@ pd_status mg_vcycle(pd_ctx *c, int level, void *z, const void *b) {
       launch_copy_scale<double>(c->stream, N, n, uview(z, N), view(B.z[c->cur[level]], N, B.P), 1.0);
     } else {
       LevelBufs &B = c->p32.lv[level];
-      launch_copy_scale<float>(c->stream, N, n, view(B.b, N, B.P), uview(b, N), (float)(h * h));
+      launch_copy_scale<float>(c->stream, N, n, view(B.b, N, B.P), uview(b, N), (float)rs(c, level));
       launch_copy_scale<float>(c->stream, N, n, view(B.z[0], N, B.P), uview(z, N), 1.0f);
       ck_launch(c, 2);
       c->cur[level] = 0;
@@ -1140,14 +1184,14 @@ pd_status shifted_solve_batched(pd_ctx *c, void *z, const void *b, int *h_iters,
     pd_status rc;
     if (c->cfg.precision == 0) {
       LevelBufs &B = c->p64.lv[0];
-      launch_copy_scale<double>(c->stream, N, n, view(B.b, N, B.P), uview(b, N), h * h);
+      launch_copy_scale<double>(c->stream, N, n, view(B.b, N, B.P), uview(b, N), rs(c, 0));
       ck_launch(c);
       rc = solve_levels<double>(c, c->cfg.tol, c->cfg.maxit);
       launch_gather_final<double>(c->stream, N, n, uview(z, N), view(B.z[0], N, B.P),
                                   view(B.z[1], N, B.P), c->st.final_buf);
     } else {
       LevelBufs &B = c->p32.lv[0];
-      launch_copy_scale<float>(c->stream, N, n, view(B.b, N, B.P), uview(b, N), (float)(h * h));
+      launch_copy_scale<float>(c->stream, N, n, view(B.b, N, B.P), uview(b, N), (float)rs(c, 0));
       ck_launch(c);
       rc = solve_levels<float>(c, c->cfg.tol, c->cfg.maxit);
       launch_gather_final<float>(c->stream, N, n, uview(z, N), view(B.z[0], N, B.P),
@@ -1203,11 +1247,11 @@ pd_status pd_smooth(pd_ctx *c, int level, void *zout, const void *zin, const voi
     const double h = hl(c, level);
     const bool jac = c->cfg.smoother == 1;
     if (c->cfg.precision == 0)
-      launch_smooth<double>(c->stream, N, n, uview(zin, N), uview(zout, N), uview(b, N), h * h,
+      launch_smooth<double>(c->stream, N, n, uview(zin, N), uview(zout, N), uview(b, N), rs(c, level),
                             c->p64.coef + (size_t)level * n, nullptr, false, jac, nullptr, 0);
     else
       launch_smooth<float>(c->stream, N, n, uview(zin, N), uview(zout, N), uview(b, N),
-                           (float)(h * h), c->p32.coef + (size_t)level * n, nullptr, false, jac,
+                           (float)rs(c, level), c->p32.coef + (size_t)level * n, nullptr, false, jac,
                            nullptr, 0);
     ck_launch(c);
     return PD_OK;
@@ -1220,12 +1264,12 @@ pd_status pd_residual_restrict(pd_ctx *c, int level, void *bc, const void *z, co
     const int N = c->Ns[level], Nc = c->Ns[level + 1], n = c->n;
     const double h = hl(c, level), hc = hl(c, level + 1);
     if (c->cfg.precision == 0)
-      launch_residual_restrict<double>(c->stream, N, n, uview(z, N), uview(b, N), h * h,
-                                       uview(bc, Nc), 1.0 / (hc * hc),
+      launch_residual_restrict<double>(c->stream, N, n, uview(z, N), uview(b, N), rs(c, level),
+                                       uview(bc, Nc), c->kappa / (hc * hc),
                                        c->p64.coef + (size_t)level * n, nullptr, false);
     else
-      launch_residual_restrict<float>(c->stream, N, n, uview(z, N), uview(b, N), (float)(h * h),
-                                      uview(bc, Nc), (float)(1.0 / (hc * hc)),
+      launch_residual_restrict<float>(c->stream, N, n, uview(z, N), uview(b, N), (float)rs(c, level),
+                                      uview(bc, Nc), (float)(c->kappa / (hc * hc)),
                                       c->p32.coef + (size_t)level * n, nullptr, false);
     ck_launch(c);
     return PD_OK;
@@ -1251,10 +1295,10 @@ pd_status pd_coarse_solve(pd_ctx *c, void *z, const void *b) {
     const int l = c->L - 1, N = c->Ns[l], n = c->n;
     const double h = hl(c, l);
     if (c->cfg.precision == 0)
-      launch_coarse<double>(c->stream, c->plan, l, n, uview(b, N), h * h, uview(z, N), c->p64.coef,
+      launch_coarse<double>(c->stream, c->plan, l, n, uview(b, N), rs(c, l), uview(z, N), c->p64.coef,
                             c->p64.cinv, nullptr, 1, 0, 0, 0.0, 0, c->st);
     else
-      launch_coarse<float>(c->stream, c->plan, l, n, uview(b, N), (float)(h * h), uview(z, N),
+      launch_coarse<float>(c->stream, c->plan, l, n, uview(b, N), (float)rs(c, l), uview(z, N),
                            c->p32.coef, c->p32.cinv, nullptr, 1, 0, 0, 0.0, 0, c->st);
     ck_launch(c);
     return PD_OK;
@@ -1301,6 +1345,34 @@ pd_status pd_allatonce_residual(pd_ctx *c, double *r, const double *u, const dou
       h_norms[0] = rn;
       h_norms[1] = fn;
     }
+    return PD_OK;
+  })
+}
+
+pd_status pd_laplacian_dot(pd_ctx *c, const double *w, const double *u, double *h_out) {
+  if (!c || !w || !u || !h_out) return PD_ERR_ARG;
+  PD_TRY(c, {
+    PD_PROF(PD_KC_OTHER, 16.0 * c->N * c->N, 0,
+            launch_laplacian_dot(c->stream, c->N, c->n, w, u, c->d_part));
+    ck_launch(c);
+    const int nb = allatonce_blocks();
+    ck(c, cudaMemcpyAsync(c->h_part, c->d_part, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream));
+    ck(c, cudaStreamSynchronize(c->stream));
+    double acc = 0.0;
+    for (int k = 0; k < nb; k++) acc += c->h_part[2 * k];
+    *h_out = acc;
+    prof_resolve(c);
+    return PD_OK;
+  })
+}
+
+pd_status pd_initial_value_gradient(pd_ctx *c, const double *w, double *gu0) {
+  if (!c || !w || !gu0) return PD_ERR_ARG;
+  PD_TRY(c, {
+    PD_PROF(PD_KC_OTHER, 16.0 * c->N * c->N, 0,
+            launch_initial_value_gradient(c->stream, c->N, c->n, w, c->d_u0coef, gu0));
+    ck_launch(c);
     return PD_OK;
   })
 }

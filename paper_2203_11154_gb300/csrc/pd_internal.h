@@ -141,17 +141,25 @@ void launch_transform_inverse(cudaStream_t s, int N, int n, double *u, View z0, 
 // r = fhat - (B kron I + I kron A) u in FP64 (r may be NULL); part[2b], part[2b+1] =
 // per-CTA sums of r^2 and fhat^2 over allatonce_blocks() CTAs
 int allatonce_blocks();
-void launch_allatonce_residual(cudaStream_t s, int N, int n, double *r, const double *u,
+void launch_allatonce_residual(cudaStream_t s, int N, int n, double kappa, double *r, const double *u,
                                const double *f, const double *u0, const double *u0coef,
                                const int *Bptr, const int *Bcol, const double *Bval,
                                double *part);
 
-// r = fhat - (B kron I + I kron A) u for B with nonzeros only at (k,k) (bd) and
-// (k, k-1 mod n) (bs); r written as FP64 (r64) or FP32 (r32); part as above, the fhat
-// sums only when want_f
-void launch_residual_bidiag(cudaStream_t s, int N, int n, double *r64, float *r32, const double *u,
-                            const double *f, const double *u0, const double *u0coef,
-                            const double *bd, const double *bs, bool want_f, double *part);
+// r = fhat - (B kron I + kappa I kron A) u for B with nonzeros only at (k,k) (bd) and
+// (k, k+off mod n) (bs), off = -1 or +1; r written as FP64 (r64) or FP32 (r32), or not at
+// all; part as above, the fhat sums only when want_f
+void launch_residual_bidiag(cudaStream_t s, int N, int n, int off, double kappa, double *r64,
+                            float *r32, const double *u, const double *f, const double *u0,
+                            const double *u0coef, const double *bd, const double *bs, bool want_f,
+                            double *part);
+
+// gu0 = sum_k u0coef[k] w_k
+void launch_initial_value_gradient(cudaStream_t s, int N, int n, const double *w,
+                                   const double *u0coef, double *gu0);
+// part[2b] = per-CTA sums of w . (A u) over allatonce_blocks() CTAs (FP64)
+void launch_laplacian_dot(cudaStream_t s, int N, int n, const double *w, const double *u,
+                          double *part);
 
 // ---- tensor-core transforms (tc_transforms.cu), FP32 working type, n <= 64 ----
 bool tc_transforms_supported(int N, int n);

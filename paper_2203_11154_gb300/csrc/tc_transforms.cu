@@ -180,7 +180,9 @@ k_tc_forward(int N, int n, View g, const InT *__restrict__ f, const double *__re
   // each thread owns kFwdItems (point, 4 consecutive k) items of a tile; the FP64 inputs of
   // the next tile are loaded into registers while the current tile is multiplied
   constexpr int kFwdItems = kFwdNt * (kFwdK / 4) / kTcThreads;
-  double pre[kFwdItems][4];
+  // held in FP32 (the operand precision); FP64 arithmetic only for the initial-value
+  // term of the rows where it is nonzero (GB300's FP64 rate is 1/58 of FP32)
+  float pre[kFwdItems][4];
   auto fetch = [&](int t) {
     const int i = t / tpr, c0 = (t % tpr) * kFwdNt;
 #pragma unroll
@@ -192,10 +194,11 @@ k_tc_forward(int N, int n, View g, const InT *__restrict__ f, const double *__re
 #pragma unroll
       for (int e = 0; e < 4; e++) {
         const int k = 4 * kq + e;
-        double v = 0.0;
+        float v = 0.f;
         if (k < n && c < N) {
-          v = (double)f[k * m + x];
-          if (u0) v += u0coef[k] * u0[x];
+          const double ck = u0 ? u0coef[k] : 0.0;
+          if (ck != 0.0) v = (float)((double)f[k * m + x] + ck * u0[x]);
+          else v = (float)f[k * m + x];
         }
         pre[q][e] = v;
       }
@@ -211,10 +214,10 @@ k_tc_forward(int N, int n, View g, const InT *__restrict__ f, const double *__re
       const int it = tid + q * kTcThreads;
       const int p = it % kFwdNt, kq = it / kFwdNt;
       float4 hi, lo;
-      split_tf32((float)pre[q][0], hi.x, lo.x);
-      split_tf32((float)pre[q][1], hi.y, lo.y);
-      split_tf32((float)pre[q][2], hi.z, lo.z);
-      split_tf32((float)pre[q][3], hi.w, lo.w);
+      split_tf32(pre[q][0], hi.x, lo.x);
+      split_tf32(pre[q][1], hi.y, lo.y);
+      split_tf32(pre[q][2], hi.z, lo.z);
+      split_tf32(pre[q][3], hi.w, lo.w);
       *reinterpret_cast<float4 *>(sBhi + sw_off(p, kq, kFwdNt)) = hi;
       *reinterpret_cast<float4 *>(sBlo + sw_off(p, kq, kFwdNt)) = lo;
     }

@@ -6,6 +6,8 @@
 #include "cplx.cuh"
 #include "pd_internal.h"
 
+#include <algorithm>
+
 namespace pd {
 
 namespace {
@@ -121,7 +123,7 @@ k_transform_inverse(int N, int n, double *__restrict__ u, View z0, View z1,
 
 constexpr int kResThreads = 256;
 
-// r_k = fhat_k - sum_l B[k][l] u_l - A u_k (eq. (1)), A = (1/h^2) 5-point, FP64.
+// r_k = fhat_k - sum_l B[k][l] u_l - kappa A u_k (eq. (1)), A = (1/h^2) 5-point, FP64.
 // part[2b], part[2b+1]: this CTA's sums of r^2 and fhat^2 (fixed grid, fixed order).
 __global__ void __launch_bounds__(kResThreads)
 k_allatonce_residual(int N, int n, double *__restrict__ r, const double *__restrict__ u,
@@ -172,15 +174,15 @@ k_allatonce_residual(int N, int n, double *__restrict__ r, const double *__restr
   }
 }
 
-// Residual of eq. (1) for a B with nonzeros only at (k, k) and (k, k-1 mod n) (backward
-// Euler, its alpha-circulant variant):
-//   r_k = fhat_k - (bd_k u_k + bs_k u_{k-1 mod n}) - (1/h^2)(4 u_k - sum of 4 neighbours)
-// with 8 FP64 operations per point (GB300's FP64 rate bounds this kernel).  One CTA
+// Residual of eq. (1) for a B with nonzeros only at (k, k) and (k, k+off mod n), off = -1
+// (backward Euler, its alpha-circulant variant) or +1 (their transposes, the adjoint):
+//   r_k = fhat_k - (bd_k u_k + bs_k u_{k+off mod n}) - (kappa/h^2)(4 u_k - sum of 4 neighbours)
+// with 6 FP64 operations per point (GB300's FP64 rate bounds this kernel).  One CTA
 // sweeps whole grid rows (k, i); per-CTA sums of r^2 (and of fhat^2 when WANT_F) go to
 // part[2b], part[2b+1] over a fixed grid, so the sums are reproducible.
 template <typename OutT, bool WANT_F>
 __global__ void __launch_bounds__(kResThreads)
-k_residual_bidiag(int N, int n, OutT *__restrict__ r, const double *__restrict__ u,
+k_residual_bidiag(int N, int n, int off, OutT *__restrict__ r, const double *__restrict__ u,
                   const double *__restrict__ f, const double *__restrict__ u0,
                   const double *__restrict__ u0coef, const double *__restrict__ bd,
                   const double *__restrict__ bs, double ih2, double *__restrict__ part) {
@@ -189,28 +191,35 @@ k_residual_bidiag(int N, int n, OutT *__restrict__ r, const double *__restrict__
   double ar = 0.0, af = 0.0;
   for (int row = blockIdx.x; row < n * N; row += gridDim.x) {
     const int k = row / N, i = row - k * N;
-    const int kp = k == 0 ? n - 1 : k - 1;
-    const double dk = bd[k], sk = bs[k], ck = u0 ? u0coef[k] : 0.0;
+    const int kp = (k + off + n) % n;
+    // r = fhat - (bd + 4 kappa/h^2) u - bs u_prev + (kappa/h^2)(sum of neighbours):
+    // 3 additions and 3 FMAs in FP64 per point; with an FP32 output (the refinement's
+    // residual, whose norm only decides when to stop) |r|^2 of a row is summed in FP32
+    // and added to the FP64 total per row, else in FP64
+    const double c1 = bd[k] + 4.0 * ih2, sk = bs[k], ck = u0 ? u0coef[k] : 0.0;
     const double *uk = u + (long long)k * m + (long long)i * N;
     const double *up = u + (long long)kp * m + (long long)i * N;
     const double *fk = f + (long long)k * m + (long long)i * N;
     const double *u0r = u0 ? u0 + (long long)i * N : nullptr;
+    float arow = 0.f;
+    double arow64 = 0.0;
     for (int c = threadIdx.x; c < N; c += kResThreads) {
       double fh = fk[c];
       if (ck != 0.0) fh = fma(ck, u0r[c], fh);
-      const double uc = uk[c];
-      double nb = 0.0;
+      double nb = (c > 0 ? uk[c - 1] : 0.0) + (c < N - 1 ? uk[c + 1] : 0.0);
       if (i > 0) nb += uk[c - N];
       if (i < N - 1) nb += uk[c + N];
-      if (c > 0) nb += uk[c - 1];
-      if (c < N - 1) nb += uk[c + 1];
-      const double lap = fma(4.0, uc, -nb);
-      const double bu = fma(sk, up[c], dk * uc);
-      const double rv = fma(-ih2, lap, fh - bu);
+      const double rv = fma(ih2, nb, fma(-sk, up[c], fma(-c1, uk[c], fh)));
       if (r) r[(long long)k * m + (long long)i * N + c] = (OutT)rv;
-      ar = fma(rv, rv, ar);
+      if (sizeof(OutT) == 4) {
+        const float rf = (float)rv;
+        arow = fmaf(rf, rf, arow);
+      } else {
+        arow64 = fma(rv, rv, arow64);
+      }
       if (WANT_F) af = fma(fh, fh, af);
     }
+    ar += (double)arow + arow64;
   }
   for (int o = 16; o > 0; o >>= 1) {
     ar += __shfl_down_sync(0xffffffffu, ar, o);
@@ -232,23 +241,80 @@ k_residual_bidiag(int N, int n, OutT *__restrict__ r, const double *__restrict__
   }
 }
 
+// sum over k, x of w_k(x) (A u_k)(x), A = (1/h^2) 5-point, FP64, per-CTA partials
+__global__ void __launch_bounds__(kResThreads)
+k_laplacian_dot(int N, int n, const double *__restrict__ w, const double *__restrict__ u,
+                double ih2, double *__restrict__ part) {
+  __shared__ double red[kResThreads / 32];
+  const long long m = (long long)N * N;
+  double acc = 0.0;
+  for (int row = blockIdx.x; row < n * N; row += gridDim.x) {
+    const int k = row / N, i = row - k * N;
+    const double *uk = u + (long long)k * m + (long long)i * N;
+    const double *wk = w + (long long)k * m + (long long)i * N;
+    for (int c = threadIdx.x; c < N; c += kResThreads) {
+      double nb = 0.0;
+      if (i > 0) nb += uk[c - N];
+      if (i < N - 1) nb += uk[c + N];
+      if (c > 0) nb += uk[c - 1];
+      if (c < N - 1) nb += uk[c + 1];
+      acc = fma(wk[c], ih2 * fma(4.0, uk[c], -nb), acc);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0;
+    for (int q = 0; q < kResThreads / 32; q++) s0 += red[q];
+    part[2 * blockIdx.x] = s0;
+    part[2 * blockIdx.x + 1] = 0.0;
+  }
+}
+
+// gu0 = sum_k u0coef[k] w_k (FP64): the gradient with respect to the initial value
+__global__ void k_initial_value_gradient(long long m, int n, const double *__restrict__ w,
+                                         const double *__restrict__ u0coef, double *__restrict__ gu0) {
+  for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < m;
+       x += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < n; k++)
+      if (u0coef[k] != 0.0) s = fma(u0coef[k], w[(long long)k * m + x], s);
+    gu0[x] = s;
+  }
+}
+
 }  // namespace
 
-void launch_residual_bidiag(cudaStream_t s, int N, int n, double *r64, float *r32, const double *u,
-                            const double *f, const double *u0, const double *u0coef,
-                            const double *bd, const double *bs, bool want_f, double *part) {
-  const double h = 1.0 / (N + 1), ih2 = 1.0 / (h * h);
+void launch_initial_value_gradient(cudaStream_t s, int N, int n, const double *w,
+                                   const double *u0coef, double *gu0) {
+  const long long m = (long long)N * N;
+  k_initial_value_gradient<<<(unsigned)std::min<long long>((m + 255) / 256, 4096), 256, 0, s>>>(
+      m, n, w, u0coef, gu0);
+}
+
+void launch_laplacian_dot(cudaStream_t s, int N, int n, const double *w, const double *u,
+                          double *part) {
+  const double h = 1.0 / (N + 1);
+  k_laplacian_dot<<<allatonce_blocks(), kResThreads, 0, s>>>(N, n, w, u, 1.0 / (h * h), part);
+}
+
+void launch_residual_bidiag(cudaStream_t s, int N, int n, int off, double kappa, double *r64,
+                            float *r32, const double *u, const double *f, const double *u0,
+                            const double *u0coef, const double *bd, const double *bs, bool want_f,
+                            double *part) {
+  const double h = 1.0 / (N + 1), ih2 = kappa / (h * h);
   const int g = allatonce_blocks();
   if (r32) {
     if (want_f)
-      k_residual_bidiag<float, true><<<g, kResThreads, 0, s>>>(N, n, r32, u, f, u0, u0coef, bd, bs, ih2, part);
+      k_residual_bidiag<float, true><<<g, kResThreads, 0, s>>>(N, n, off, r32, u, f, u0, u0coef, bd, bs, ih2, part);
     else
-      k_residual_bidiag<float, false><<<g, kResThreads, 0, s>>>(N, n, r32, u, f, u0, u0coef, bd, bs, ih2, part);
+      k_residual_bidiag<float, false><<<g, kResThreads, 0, s>>>(N, n, off, r32, u, f, u0, u0coef, bd, bs, ih2, part);
   } else {
     if (want_f)
-      k_residual_bidiag<double, true><<<g, kResThreads, 0, s>>>(N, n, r64, u, f, u0, u0coef, bd, bs, ih2, part);
+      k_residual_bidiag<double, true><<<g, kResThreads, 0, s>>>(N, n, off, r64, u, f, u0, u0coef, bd, bs, ih2, part);
     else
-      k_residual_bidiag<double, false><<<g, kResThreads, 0, s>>>(N, n, r64, u, f, u0, u0coef, bd, bs, ih2, part);
+      k_residual_bidiag<double, false><<<g, kResThreads, 0, s>>>(N, n, off, r64, u, f, u0, u0coef, bd, bs, ih2, part);
   }
 }
 
@@ -294,13 +360,13 @@ void launch_transform_inverse(cudaStream_t s, int N, int n, double *u, View z0, 
 
 int allatonce_blocks() { return 4 * 152; }
 
-void launch_allatonce_residual(cudaStream_t s, int N, int n, double *r, const double *u,
+void launch_allatonce_residual(cudaStream_t s, int N, int n, double kappa, double *r, const double *u,
                                const double *f, const double *u0, const double *u0coef,
                                const int *Bptr, const int *Bcol, const double *Bval,
                                double *part) {
   const double h = 1.0 / (N + 1);
   k_allatonce_residual<<<allatonce_blocks(), kResThreads, 0, s>>>(
-      N, n, r, u, f, u0, u0coef, Bptr, Bcol, Bval, 1.0 / (h * h), part);
+      N, n, r, u, f, u0, u0coef, Bptr, Bcol, Bval, kappa / (h * h), part);
 }
 
 template cudaError_t prepare_transforms<double>(int);

@@ -16,7 +16,10 @@ Workloads (unit square, homogeneous Dirichlet, N x N interior, h = 1/(N+1)):
                  n in {16,32,32,64,64,64,128,128}; shifts lam = r e^{i phi},
                  log10 r ~ U(0,4), phi ~ U(-pi/2+0.05, pi/2-0.05); complex U(-1,1)
                  right-hand sides, seed 2, instance by instance (r, phi, Re b, Im b).
-Smaller variants of the same recipes (`scaled`) serve the parity tests.
+  adjoint-1023   as paradiag-1023 (seed 1 for f), plus a target u_target = sum of 8
+                 modes A_q sin(k_q pi x) sin(l_q pi y), k_q, l_q ~ U{1..8}, A_q ~ N(0,1),
+                 seed 3 (drawn k, then l, then A).
+Smaller variants of the same recipes serve the parity tests.
 """
 import numpy as np
 
@@ -24,6 +27,8 @@ WORKLOADS = {
     "shifted-63": dict(kind="shifted", N=63, n=16, tau=1.0 / 16, alpha=1e-2, seed=0),
     "paradiag-1023": dict(kind="paradiag", N=1023, n=64, tau=1.0 / 64, alpha=1e-3, seed=1),
     "paradiag-2047": dict(kind="paradiag", N=2047, n=128, tau=1.0 / 128, alpha=1e-3, seed=1),
+    "adjoint-1023": dict(kind="adjoint", N=1023, n=64, tau=1.0 / 64, alpha=1e-3, seed=1,
+                         target_seed=3),
     "uneven-8": dict(kind="uneven", Ns=(127, 255, 255, 511, 511, 1023, 1023, 2047),
                      ns=(16, 32, 32, 64, 64, 64, 128, 128), seed=2),
 }
@@ -79,4 +84,17 @@ def uneven_problem(Ns=(127, 255, 255, 511, 511, 1023, 1023, 2047),
         lam = random_shifts(rng, n)
         b = complex_rhs(rng, n, N)
         out.append((N, lam, b))
+    return out
+
+
+def sine_modes_target(N, seed=3, modes=8):
+    """u_target = sum_q A_q sin(k_q pi x) sin(l_q pi y) at the interior nodes."""
+    rng = np.random.default_rng(seed)
+    k = rng.integers(1, 9, size=modes)
+    l = rng.integers(1, 9, size=modes)
+    A = rng.standard_normal(modes)
+    x, y = grid_coords(N)
+    out = np.zeros((N, N))
+    for q in range(modes):
+        out += A[q] * np.sin(k[q] * np.pi * x) * np.sin(l[q] * np.pi * y)
     return out
