@@ -75,11 +75,17 @@ typedef struct {
                           tiles, 2 = warp-streaming strips (cp.async ring, shuffles) */
     double kappa;      /* diffusion coefficient scaling A in eq. (1): (B kron I + kappa I kron A);
                           the shifted systems become (kappa A + lam_j I) z = b (default 1) */
+    int outer_maxit;   /* precision 0: FP64 correction steps on eq. (1) after the first solve,
+                          u += P^{-1}(fhat - (B kron I + kappa I kron A) u), until the relative
+                          residual of eq. (1) is <= tol (0 = the single solve).  When B is not
+                          the matrix whose shifts and V were given (e.g. sequential backward
+                          Euler with the alpha-circulant shifts), this is the ParaDIAG-II
+                          outer iteration; the precision-1 refinement does the same. */
 } pd_config;
 
 /* Fills cfg with V(1,1), coarsest 3, maxit 100, tol 1e-10, omega_mode 1, FP64,
  * Vanka, inner_tol 1e-6, max_refine 12, imag_check 1, inner_maxit 3, stall_ratio 0.5,
- * fused 1, tensor_transforms 1, fused_variant 0, kappa 1. */
+ * fused 1, tensor_transforms 1, fused_variant 0, kappa 1, outer_maxit 0. */
 void pd_config_default(pd_config *cfg);
 
 /*

@@ -288,6 +288,28 @@ def allatonce_residual(N, n, tau, alpha, u, fhat, want_r=False):
     return (rn, fn.value, r) if want_r else (rn, fn.value)
 
 
+def sequential_backward_euler(N, n, tau, f, u0, kappa=1.0):
+    """The system ParaDIAG-II converges to: eq. (1) with alpha = 0, i.e. backward Euler
+    stepped in sequence, (I / tau + kappa A) u_k = f_k + u_{k-1} / tau, u_0 the initial
+    value, A the five-point Laplacian with h = 1/(N+1) (eq. (1), Sec. 1).  Each step is a
+    sparse LU solve (SuperLU through scipy)."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+    f = _rvec(f, (n, N, N))
+    u0 = _rvec(u0, (N, N))
+    h = 1.0 / (N + 1)
+    T = sp.diags([-np.ones(N - 1), 2.0 * np.ones(N), -np.ones(N - 1)], [-1, 0, 1])
+    I = sp.identity(N)
+    A = (sp.kron(I, T) + sp.kron(T, I)) / (h * h)
+    lu = spl.splu((sp.identity(N * N) / tau + kappa * A).tocsc())
+    u = np.empty_like(f)
+    prev = u0.ravel()
+    for k in range(n):
+        prev = lu.solve(f[k].ravel() + prev / tau)
+        u[k] = prev.reshape(N, N)
+    return u
+
+
 def set_threads(k):
     """Sets the number of OpenMP threads of the batched oracle routines."""
     lib().or_set_threads(int(k))

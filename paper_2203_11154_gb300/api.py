@@ -55,7 +55,7 @@ class pd_config(C.Structure):
                 ("inner_tol", C.c_double), ("max_refine", C.c_int), ("imag_check", C.c_int),
                 ("inner_maxit", C.c_int), ("stall_ratio", C.c_double), ("fused", C.c_int),
                 ("tensor_transforms", C.c_int), ("fused_variant", C.c_int),
-                ("kappa", C.c_double)]
+                ("kappa", C.c_double), ("outer_maxit", C.c_int)]
 
 
 _P = C.c_void_p
@@ -372,3 +372,29 @@ def alpha_circulant_context(N, n, tau, alpha, **cfg_fields):
     """Context for the backward-Euler alpha-circulant ParaDIAG step on an N x N grid."""
     B, sh, V, Vi, c0 = pd_alpha_circulant(n, tau, alpha)
     return Context(N, n, sh, V, Vi, B, c0, None, config(**cfg_fields))
+
+
+def paradiag2_context(N, n, tau, alpha, **cfg_fields):
+    """ParaDIAG-II for sequential backward Euler: the residual of eq. (1) uses the lower-
+    bidiagonal B_0 = (1/tau)(I - C_0) (no corner), the solves use the shifts and V of the
+    alpha-circulant B_alpha, so each correction step contracts the error by about
+    alpha / (1 - alpha).  Precision 1 refines with it by construction; precision 0 needs
+    outer_maxit > 0 (set to 20 here unless given)."""
+    B, sh, V, Vi, c0 = pd_alpha_circulant(n, tau, alpha)
+    B = B.copy()
+    if n > 1:
+        B[0, n - 1] = 0.0
+    cfg_fields.setdefault("outer_maxit", 20 if cfg_fields.get("precision", 0) == 0 else 0)
+    return Context(N, n, sh, V, Vi, B, c0, None, config(**cfg_fields))
+
+
+def dense_B_context(B, N, u0_coef=None, **cfg_fields):
+    """Context for eq. (1) with a general diagonalisable time matrix B (n x n real), e.g.
+    the boundary-value-method B of Example 1 (eq. (9)) or the quasi-BVM B of Example 2
+    (eq. (10)).  The eigendecomposition B = V D V^{-1} is set-up work on the host (numpy's
+    LAPACK eig); the library receives the shifts, V and V^{-1} like any other."""
+    B = np.ascontiguousarray(np.asarray(B, dtype=np.float64))
+    n = B.shape[0]
+    lam, V = np.linalg.eig(B)
+    Vinv = np.linalg.inv(V)
+    return Context(N, n, lam, V, Vinv, B, u0_coef, None, config(**cfg_fields))

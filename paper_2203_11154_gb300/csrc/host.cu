@@ -730,6 +730,7 @@ void check_wait_flags(pd_ctx *c) {
   ck(c, cudaStreamSynchronize(c->stream));
   if (c->h_pinned[2] & 6) {
     c->err = "a bounded wait ran out in a TMA or tensor-core kernel";
+    cudaMemsetAsync(c->st.flags, 0, sizeof(int), c->stream);  // report each timeout once
     throw CudaFail{cudaErrorLaunchTimeout};
   }
 }
@@ -771,9 +772,35 @@ pd_status paradiag_impl(pd_ctx *c, double *u, const double *f, const double *u0,
             transform_inverse<T>(c, u, z0, z1, c->st.final_buf, false, imag));
     ck_launch(c);
     if (c->have_B) {
+      const int outer = c->cfg.outer_maxit;
       double rn, fn;
-      allatonce_norms(c, nullptr, u, f, u0, &rn, &fn);
-      st_local[PD_STAT_RELRES_ALLATONCE] = fn > 0 ? rn / fn : 0.0;
+      allatonce_norms(c, outer > 0 ? c->d_r : nullptr, u, f, u0, &rn, &fn);
+      double relres = fn > 0 ? rn / fn : 0.0;
+      int steps = 1;
+      // FP64 corrections: d = (V kron I)(D kron I + kappa I kron A)^{-1}(V^{-1} kron I) r
+      for (int s = 0; s < outer && rc == PD_OK && relres > c->cfg.tol; s++) {
+        PD_PROF(PD_KC_FORWARD, fwd_bytes, 0, transform_forward<T>(c, g, c->d_r, nullptr, true));
+        ck_launch(c);
+        rc = solve_levels<T>(c, c->cfg.tol, c->cfg.maxit);
+        if (rc == PD_ERR_NAN) break;
+        if (rc == PD_ERR_NOCONV) rc = PD_OK;  // the outer residual decides
+        accumulate_iters();
+        PD_PROF(PD_KC_INVERSE, (w + 16.0) * m, 0,
+                transform_inverse<T>(c, u, z0, z1, c->st.final_buf, true, imag));
+        ck_launch(c);
+        allatonce_norms(c, c->d_r, u, f, u0, &rn, &fn);
+        const double prev = relres;
+        relres = fn > 0 ? rn / fn : 0.0;
+        steps++;
+        if (!std::isfinite(relres)) {
+          rc = PD_ERR_NAN;
+          break;
+        }
+        if (relres > 0.9 * prev) break;  // no longer contracts
+      }
+      st_local[PD_STAT_RELRES_ALLATONCE] = relres;
+      st_local[PD_STAT_REFINE_STEPS] = outer > 0 ? steps : 0;
+      if (outer > 0 && rc == PD_OK && !(relres <= c->cfg.tol)) rc = PD_ERR_NOCONV;
     }
   } else {
     // FP64 iterative refinement on eq. (1) around FP32 ParaDIAG steps.  Step 1 transforms
@@ -896,6 +923,7 @@ void pd_config_default(pd_config *cfg) {
   cfg->tensor_transforms = 1;
   cfg->fused_variant = 0;
   cfg->kappa = 1.0;
+  cfg->outer_maxit = 0;
 }
 
 pd_status pd_alpha_circulant(int n, double tau, double alpha, double *B, double *shifts,
@@ -958,8 +986,10 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
       !(cfg.inner_tol >= 0) || cfg.max_refine < 1 || cfg.inner_maxit < 1 ||
       cfg.inner_maxit > 100000 || !(cfg.stall_ratio >= 0) || cfg.fused < 0 || cfg.fused > 2 ||
       cfg.tensor_transforms < 0 || cfg.tensor_transforms > 1 || cfg.fused_variant < 0 ||
-      cfg.fused_variant > 2 || !(cfg.kappa > 0) || !std::isfinite(cfg.kappa))
+      cfg.fused_variant > 2 || !(cfg.kappa > 0) || !std::isfinite(cfg.kappa) ||
+      cfg.outer_maxit < 0 || cfg.outer_maxit > 1000)
     return PD_ERR_ARG;
+  if (cfg.precision == 0 && cfg.outer_maxit > 0 && (!B || !V)) return PD_ERR_ARG;
   if (cfg.omega_mode == 2 && !omega) return PD_ERR_ARG;
   if (cfg.precision == 1 && (!B || !V)) return PD_ERR_ARG;
   for (int k = 0; k < 2 * n; k++)
@@ -1042,6 +1072,8 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
     c->st.final_buf = dalloc<int *>(c, n * sizeof(int));
     c->st.nactive = dalloc<int *>(c, 2 * sizeof(int));
     c->st.flags = c->st.nactive + 1;
+    // the wait flags are read after standalone component calls that never reset the state
+    ck(c, cudaMemset(c->st.nactive, 0, 2 * sizeof(int)));
     c->st.bn2 = dalloc<double *>(c, n * sizeof(double));
     c->st.relres = dalloc<double *>(c, n * sizeof(double));
     c->st.partials = dalloc<double *>(c, (size_t)n * tiles * sizeof(double));
@@ -1049,6 +1081,7 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
     ck(c, cudaMemcpy(c->d_u0coef, c->u0coef.data(), n * sizeof(double), cudaMemcpyHostToDevice));
     c->d_part = dalloc<double *>(c, 2 * allatonce_blocks() * sizeof(double));
     c->d_imag = dalloc<unsigned long long *>(c, sizeof(unsigned long long));
+    ck(c, cudaMemset(c->d_imag, 0, sizeof(unsigned long long)));
     if (B) {
       std::vector<double> bd(n), bs(n);
       for (int off = -1; off <= 1 && !c->bidiag; off += 2) {
@@ -1092,6 +1125,7 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
     }
     if (cfg.precision == 0) {
       alloc_prec<double>(c);
+      if (cfg.outer_maxit > 0) c->d_r = dalloc<double *>(c, (size_t)n * N * N * sizeof(double));
     } else {
       alloc_prec<float>(c);
       if (c->bidiag) c->d_r32 = dalloc<float *>(c, (size_t)n * N * N * sizeof(float));

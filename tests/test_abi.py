@@ -36,6 +36,7 @@ def test_config_defaults():
     c = api.config()
     assert (c.cycle_gamma, c.nu1, c.nu2, c.coarsest_n, c.maxit) == (1, 1, 1, 3, 100)
     assert c.tol == 1e-10 and c.omega_mode == 1 and c.precision == 0 and c.smoother == 0
+    assert c.kappa == 1.0 and c.outer_maxit == 0 and c.max_refine == 12 and c.inner_maxit == 3
 
 
 def test_alpha_circulant_matches_oracle():
@@ -67,6 +68,10 @@ def test_setup_rejects_bad_arguments_before_touching_the_gpu():
     bad = api.config(coarsest_n=5)
     assert L.paradiag_setup(C.byref(h), 7, 1 / 8, 4, p, None, None, None, None, None, C.byref(bad), None) == 1
     bad = api.config(precision=1)  # needs B and V
+    assert L.paradiag_setup(C.byref(h), 7, 1 / 8, 4, p, None, None, None, None, None, C.byref(bad), None) == 1
+    bad = api.config(outer_maxit=3)  # FP64 corrections need B and V
+    assert L.paradiag_setup(C.byref(h), 7, 1 / 8, 4, p, None, None, None, None, None, C.byref(bad), None) == 1
+    bad = api.config(outer_maxit=-1)
     assert L.paradiag_setup(C.byref(h), 7, 1 / 8, 4, p, None, None, None, None, None, C.byref(bad), None) == 1
     nan = np.array([np.nan] * 8)
     assert L.paradiag_setup(C.byref(h), 7, 1 / 8, 4, nan.ctypes.data_as(C.c_void_p), None, None, None,

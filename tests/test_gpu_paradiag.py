@@ -54,6 +54,23 @@ def residual_error_bound(N, n, alpha, rr1, rr2, fnorm):
     return alpha ** (-(n - 1) / n) / mu * (rr1 + rr2) * fnorm
 
 
+def residual_rounding(N, n, tau, alpha, u, fhat):
+    """8 eps || |fhat| + |B| |u| + |A| |u| ||: a bound on the difference between two FP64
+    evaluations of ||fhat - (B kron I + I kron A) u|| in different operation orders, which
+    dominates once the residual reaches the FP64 floor."""
+    h = 1.0 / (N + 1)
+    a = np.abs(u)
+    nb = np.zeros_like(a)
+    nb[:, 1:, :] += a[:, :-1, :]
+    nb[:, :-1, :] += a[:, 1:, :]
+    nb[:, :, 1:] += a[:, :, :-1]
+    nb[:, :, :-1] += a[:, :, 1:]
+    prev = np.roll(a, 1, axis=0)
+    prev[0] *= alpha
+    t = np.abs(fhat) + (a + prev) / tau + (4 * a + nb) / h ** 2
+    return 8 * np.finfo(float).eps * np.linalg.norm(t)
+
+
 def oracle_paradiag(N, n, tau, alpha, f, u0, omega_mode="lfa", tol=1e-10):
     lam, V, Vinv = core.alpha_circulant(n, tau, alpha)
     om = lfa.omega_table(lam, N, mode=omega_mode)
@@ -110,7 +127,8 @@ def test_paradiag_fp64(N, n, alpha):
     assert weighted_rel_err(uh, uo, alpha) < 1e-12
     rn, fn = core.allatonce_residual(N, n, tau, alpha, uh, fhat)
     rno, _ = core.allatonce_residual(N, n, tau, alpha, uo, fhat)
-    assert abs(out["relres_allatonce"] - rn / fn) <= 1e-3 * rn / fn
+    noise = residual_rounding(N, n, tau, alpha, uh, fhat) / fn
+    assert abs(out["relres_allatonce"] - rn / fn) <= 1e-3 * rn / fn + noise
     assert np.linalg.norm(uh - uo) <= residual_error_bound(N, n, alpha, rn / fn, rno / fn, fn)
     assert out["imag_max"] < 1e-10 * np.max(np.abs(uo)) / alpha
 
@@ -127,7 +145,8 @@ def test_paradiag_precision_form(N, n, alpha):
     fhat = core.assemble_rhs(N, n, tau, f, u0)
     rn, fn = core.allatonce_residual(N, n, tau, alpha, uh, fhat)
     assert rn / fn <= 1e-10 and out["relres_allatonce"] <= 1e-10
-    assert abs(out["relres_allatonce"] - rn / fn) <= 1e-3 * rn / fn
+    noise = residual_rounding(N, n, tau, alpha, uh, fhat) / fn
+    assert abs(out["relres_allatonce"] - rn / fn) <= 1e-3 * rn / fn + noise
     assert 1 <= out["refine_steps"] <= 8
     uo, _, _, _ = oracle_paradiag(N, n, tau, alpha, f, u0, tol=1e-12)
     rno, _ = core.allatonce_residual(N, n, tau, alpha, uo, fhat)

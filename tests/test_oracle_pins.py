@@ -390,3 +390,51 @@ def test_mg_cycle_levels_and_w_cycle():
     zw = core.mg_cycle(N, lam, om, b, np.zeros((N, N)), core.mg_params(2, 1, 1, 3))
     ev, ew = np.linalg.norm(zv - ref), np.linalg.norm(zw - ref)
     assert ew <= ev * 1.001 and ev < 0.2 * np.linalg.norm(ref)
+
+
+def test_sequential_backward_euler_is_alpha_zero_kronecker_solve():
+    """alpha = 0 in eq. (1) is backward Euler stepped in sequence: the oracle's time stepping
+    equals the dense Kronecker solve with the lower-bidiagonal B_0, and for a spatial
+    eigenmode it equals the scalar recursion u_k = u_{k-1} / (1 + tau mu)."""
+    N, n, tau = 7, 4, 0.25
+    rng = np.random.default_rng(12)
+    f = rng.uniform(-1, 1, (n, N, N))
+    u0 = rng.uniform(-1, 1, (N, N))
+    u = core.sequential_backward_euler(N, n, tau, f, u0)
+    fhat = core.assemble_rhs(N, n, tau, f, u0)
+    ref = np.linalg.solve(kron_system(N, n, tau, 0.0), fhat.ravel()).reshape(n, N, N)
+    assert np.linalg.norm(u - ref) <= 1e-12 * np.linalg.norm(ref)
+    h = 1.0 / (N + 1)
+    t = h * np.arange(1, N + 1)
+    y, x = np.meshgrid(t, t, indexing="ij")
+    mode = np.sin(2 * np.pi * x) * np.sin(np.pi * y)
+    mu = (4 / h ** 2) * (np.sin(np.pi * h) ** 2 + np.sin(np.pi * h / 2) ** 2)
+    u = core.sequential_backward_euler(N, n, tau, np.zeros((n, N, N)), mode, kappa=0.5)
+    for k in range(n):
+        assert np.allclose(u[k], mode / (1 + 0.5 * tau * mu) ** (k + 1), rtol=1e-12, atol=1e-14)
+
+
+def test_paradiag2_iteration_contracts_by_alpha():
+    """ParaDIAG-II: u <- u + P_alpha^{-1}(fhat - A_0 u) with the alpha-circulant step as
+    P_alpha converges to the sequential solution, each step reducing the error by at least
+    alpha / (1 - alpha) (for diffusion far more: the wrapped-around error is damped by the
+    propagator over the whole window)."""
+    N, n, tau, alpha = 7, 8, 1.0 / 8, 0.05
+    rng = np.random.default_rng(13)
+    f = rng.uniform(-1, 1, (n, N, N))
+    u0 = rng.uniform(-1, 1, (N, N))
+    useq = core.sequential_backward_euler(N, n, tau, f, u0)
+    fhat = core.assemble_rhs(N, n, tau, f, u0)
+    lam, V, Vinv = core.alpha_circulant(n, tau, alpha)
+    om = lfa.omega_table(lam, N, mode="fixed")
+    A0 = kron_system(N, n, tau, 0.0)
+    u = np.zeros_like(fhat)
+    errs = []
+    for _ in range(6):
+        r = fhat - (A0 @ u.ravel()).reshape(n, N, N)
+        d, _, _, _ = core.paradiag_solve(N, lam, V, Vinv, om, r, tol=1e-14, maxit=100)
+        u = u + d
+        errs.append(np.linalg.norm(u - useq) / np.linalg.norm(useq))
+    bound = alpha / (1 - alpha)
+    assert errs[0] <= bound and errs[1] <= bound * errs[0]
+    assert errs[3] <= 1e-13
