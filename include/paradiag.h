@@ -81,11 +81,20 @@ typedef struct {
                           the matrix whose shifts and V were given (e.g. sequential backward
                           Euler with the alpha-circulant shifts), this is the ParaDIAG-II
                           outer iteration; the precision-1 refinement does the same. */
+    int cuda_graphs;   /* 1: each multigrid cycle is captured once into a CUDA graph (per
+                          kind of cycle and tolerance) and replayed, when the context's
+                          stream is not the legacy default stream and profiling is off;
+                          0: every kernel launched one by one (default 1) */
+    int fx_residual;   /* precision 1 with a bidiagonal B: the refinement residual of eq. (1)
+                          without FP64 instructions (stencil difference exact in 64-bit fixed
+                          point per 16 x 128 tile, the other terms in float-float; more
+                          accurate than the FP64 formula); 0: FP64 (default 1) */
 } pd_config;
 
 /* Fills cfg with V(1,1), coarsest 3, maxit 100, tol 1e-10, omega_mode 1, FP64,
  * Vanka, inner_tol 1e-6, max_refine 12, imag_check 1, inner_maxit 3, stall_ratio 0.5,
- * fused 1, tensor_transforms 1, fused_variant 0, kappa 1, outer_maxit 0. */
+ * fused 1, tensor_transforms 1, fused_variant 0, kappa 1, outer_maxit 0, cuda_graphs 1,
+ * fx_residual 1. */
 void pd_config_default(pd_config *cfg);
 
 /*
@@ -161,6 +170,44 @@ pd_status mg_vcycle(pd_ctx *ctx, int level, void *d_z, const void *d_b);
 pd_status shifted_solve_batched(pd_ctx *ctx, void *d_z, const void *d_b, int *h_iters,
                                 double *h_relres);
 
+/*
+ * The shifted systems of eq. (2), (kappa A + lam_j I) z_j = b_j, to the FP64 relative
+ * residual cfg.tol per shift, with FP64 complex d_z, d_b [n][N][N] for either precision.
+ * Precision 0: as shifted_solve_batched.  Precision 1: FP64 iterative refinement per shift
+ * around the FP32 multigrid: r_j = b_j - L_j z_j in FP64, at most inner_maxit FP32 cycles
+ * (stall_ratio as in paradiag_solve) for the correction, z_j += d_j in FP64; a shift stops
+ * once its FP64 relative residual is <= tol, after max_refine corrections, or when a
+ * correction reduces it by less than 10 %.  h_iters: FP32 cycles summed over corrections;
+ * h_relres: the last FP64 relative residual.  Synchronises.  Errors: PD_ERR_NOCONV if a
+ * shift missed tol, PD_ERR_NAN, PD_ERR_CUDA.
+ */
+pd_status shifted_solve_refined(pd_ctx *ctx, void *d_z, const void *d_b, int *h_iters,
+                                double *h_relres);
+
+/*
+ * A batch of independent shifted-system problems of uneven sizes (several PDE instances,
+ * each with its own grid N_i = 2^k - 1 and n_i shifts): one context per instance with the
+ * common cfg (omega_mode 0 or 1; no V, B or tables), each on a stream of its own that the
+ * batch creates, so that the instances' kernels overlap on the GPU.  pd_batch_solve
+ * advances all instances together, one multigrid cycle of every unfinished instance per
+ * round (each a replayed CUDA graph when cfg.cuda_graphs), with the solve of
+ * shifted_solve_refined per instance; it is ordered after the work queued on `stream`
+ * before the call, and work queued on `stream` after it waits for it.
+ *   h_N, h_n: count sizes; h_shifts[i]: n_i complex shifts (host, copied).
+ *   d_z[i], d_b[i]: FP64 complex [n_i][N_i][N_i] device arrays of instance i.
+ *   h_iters, h_relres (may be NULL): sum n_i entries, instance by instance.
+ * The paper has no multi-instance form: this batches the independent solves of eq. (2).
+ * Errors: PD_ERR_ARG (count outside 1..64, a bad instance), the instance's setup or solve
+ * error (the first in instance order; pd_batch_last_error gives its text).
+ */
+typedef struct pd_batch pd_batch;
+pd_status pd_batch_setup(pd_batch **batch, int count, const int *h_N, const int *h_n,
+                         const double *const *h_shifts, const pd_config *cfg, void *stream);
+pd_status pd_batch_solve(pd_batch *batch, void *const *d_z, const void *const *d_b, int *h_iters,
+                         double *h_relres);
+pd_status pd_batch_destroy(pd_batch *batch);
+const char *pd_batch_last_error(const pd_batch *batch);
+
 /* Indices of the values paradiag_solve writes to h_stats (PD_STATS_LEN doubles). */
 enum {
     PD_STAT_RELRES_ALLATONCE = 0, /* ||fhat - (B kron I + I kron A) u|| / ||fhat||, or -1 without B */
@@ -231,6 +278,16 @@ pd_status pd_transform_forward(pd_ctx *ctx, void *d_g, const double *d_f, const 
 pd_status pd_transform_inverse(pd_ctx *ctx, double *d_u, const void *d_z, int accumulate);
 pd_status pd_allatonce_residual(pd_ctx *ctx, double *d_r, const double *d_u, const double *d_f,
                                 const double *d_u0, double *h_norms);
+
+/*
+ * The refinement's residual of eq. (1) as it is handed to the FP32 forward transform:
+ * d_r32 [n][N][N] float = fhat - (B kron I_h + kappa I_t kron A) d_u rounded to FP32,
+ * h_norms[0] = ||r||_2 (of the FP32 values), h_norms[1] = ||fhat||_2.  With a bidiagonal B
+ * and cfg.fx_residual, computed without FP64 arithmetic (see fx_residual); else with the
+ * FP64 formula.  Needs precision 1 and B (else PD_ERR_STATE).  Synchronises.
+ */
+pd_status pd_allatonce_residual32(pd_ctx *ctx, float *d_r32, const double *d_u, const double *d_f,
+                                  const double *d_u0, double *h_norms);
 
 /*
  * Gradient reduction of the adjoint (differentiation with respect to a coefficient

@@ -64,6 +64,7 @@ def lib():
             "or_paradiag_solve": (_I, [C.POINTER(MGParams), _I, _I, _P, _P, _P, _P, _I, _I,
                                        _D, _P, _P, _P, _P, _P]),
             "or_allatonce_residual": (_D, [_I, _I, _D, _D, _P, _P, _P, _P]),
+            "or_allatonce_residual_ld": (_D, [_I, _I, _D, _D, _P, _P, _P]),
             "or_set_threads": (None, [_I]),
             "or_max_threads": (_I, []),
         }
@@ -286,6 +287,16 @@ def allatonce_residual(N, n, tau, alpha, u, fhat, want_r=False):
     rn = lib().or_allatonce_residual(N, n, float(tau), float(alpha), _ptr(u), _ptr(fhat),
                                      _ptr(r) if want_r else None, C.byref(fn))
     return (rn, fn.value, r) if want_r else (rn, fn.value)
+
+
+def allatonce_residual_ld(N, n, tau, alpha, u, fhat):
+    """(||r||_2, r) of eq. (1) with the alpha-circulant B, evaluated in long double and
+    rounded to double at the end (a reference below the FP64 rounding of the formula)."""
+    u = _rvec(u, (n, N, N))
+    fhat = _rvec(fhat, (n, N, N))
+    r = np.empty_like(u)
+    rn = lib().or_allatonce_residual_ld(N, n, float(tau), float(alpha), _ptr(u), _ptr(fhat), _ptr(r))
+    return rn, r
 
 
 def sequential_backward_euler(N, n, tau, f, u0, kappa=1.0):

@@ -425,6 +425,38 @@ double or_allatonce_residual(int N, int n, double tau, double alpha, const doubl
     return sqrt(rs);
 }
 
+/* The same residual of eq. (1) (alpha-circulant backward Euler, unscaled A) evaluated in
+ * long double (64-bit significand on x86-64, 113-bit on AArch64 Linux), each term formed
+ * separately: a reference for residual kernels whose error lies below the FP64 rounding
+ * of the formula.  r (may be NULL) receives the residual rounded to double. */
+double or_allatonce_residual_ld(int N, int n, double tau, double alpha, const double *u,
+                                const double *fhat, double *r)
+{
+    size_t m = (size_t)N * N;
+    long double h = 1.0L / (N + 1), ih2 = 1.0L / (h * h);
+    double rs = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : rs)
+    for (int k = 0; k < n; k++) {
+        const double *uk = u + (size_t)k * m;
+        const double *up = (k == 0) ? u + (size_t)(n - 1) * m : u + (size_t)(k - 1) * m;
+        long double cprev = (k == 0) ? (long double)alpha : 1.0L;
+        for (int i = 0; i < N; i++)
+            for (int j = 0; j < N; j++) {
+                size_t p = (size_t)i * N + j;
+                long double c = uk[p];
+                long double nb = (long double)(i > 0 ? uk[p - N] : 0.0) + (long double)(i < N - 1 ? uk[p + N] : 0.0)
+                                 + (long double)(j > 0 ? uk[p - 1] : 0.0) + (long double)(j < N - 1 ? uk[p + 1] : 0.0);
+                long double Au = ih2 * (4.0L * c - nb);
+                long double Bu = (c - cprev * (long double)up[p]) / (long double)tau;
+                long double rv = (long double)fhat[(size_t)k * m + p] - Bu - Au;
+                if (r)
+                    r[(size_t)k * m + p] = (double)rv;
+                rs += (double)(rv * rv);
+            }
+    }
+    return sqrt(rs);
+}
+
 /* OpenMP thread count used by the batched routines (reported with CPU timings). */
 void or_set_threads(int k)
 {

@@ -38,7 +38,8 @@ EXPORTS = ["pd_config_default", "pd_alpha_circulant", "paradiag_setup", "pd_adjo
            "pd_allatonce_residual", "pd_allatonce_residual_static", "pd_laplacian_dot",
            "pd_initial_value_gradient",
            "pd_profile_enable", "pd_profile_read", "pd_synchronize", "pd_launch_count", "paradiag_destroy",
-           "pd_status_str", "pd_last_error"]
+           "pd_status_str", "pd_last_error", "shifted_solve_refined", "pd_allatonce_residual32", "pd_batch_setup",
+           "pd_batch_solve", "pd_batch_destroy", "pd_batch_last_error"]
 
 
 class PDError(RuntimeError):
@@ -55,7 +56,8 @@ class pd_config(C.Structure):
                 ("inner_tol", C.c_double), ("max_refine", C.c_int), ("imag_check", C.c_int),
                 ("inner_maxit", C.c_int), ("stall_ratio", C.c_double), ("fused", C.c_int),
                 ("tensor_transforms", C.c_int), ("fused_variant", C.c_int),
-                ("kappa", C.c_double), ("outer_maxit", C.c_int)]
+                ("kappa", C.c_double), ("outer_maxit", C.c_int), ("cuda_graphs", C.c_int),
+                ("fx_residual", C.c_int)]
 
 
 _P = C.c_void_p
@@ -103,6 +105,12 @@ def lib(path=None):
             "paradiag_destroy": (_I, [_P]),
             "pd_status_str": (C.c_char_p, [_I]),
             "pd_last_error": (C.c_char_p, [_P]),
+            "shifted_solve_refined": (_I, [_P, _P, _P, _P, _P]),
+            "pd_allatonce_residual32": (_I, [_P, _P, _P, _P, _P, _P]),
+            "pd_batch_setup": (_I, [C.POINTER(_P), _I, _P, _P, _P, C.POINTER(pd_config), _P]),
+            "pd_batch_solve": (_I, [_P, _P, _P, _P, _P]),
+            "pd_batch_destroy": (_I, [_P]),
+            "pd_batch_last_error": (C.c_char_p, [_P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -264,6 +272,18 @@ class Context:
             _check(code, "shifted_solve_batched", self.h)
         return it, rr
 
+    def shifted_solve_refined(self, z, b, raise_on_noconv=True):
+        """z, b: complex128 [n][N][N] device tensors (FP64 answer for either precision)."""
+        import torch
+        it = np.zeros(self.n, np.int32)
+        rr = np.zeros(self.n)
+        m = self.n * self.N * self.N
+        code = lib().shifted_solve_refined(self.h, _dptr(z, torch.complex128, m),
+                                           _dptr(b, torch.complex128, m), _hptr(it), _hptr(rr))
+        if code != 0 and not (code == 4 and not raise_on_noconv):
+            _check(code, "shifted_solve_refined", self.h)
+        return it, rr
+
     def _solve_out(self, code, it, rr, stats, where, raise_on_noconv):
         if code != 0 and not (code == 4 and not raise_on_noconv):
             _check(code, where, self.h)
@@ -362,6 +382,17 @@ class Context:
                "pd_allatonce_residual", self.h)
         return norms[0], norms[1]
 
+    def pd_allatonce_residual32(self, r32, u, f, u0=None):
+        """r32: float32 [n][N][N] device tensor; returns (||r||, ||fhat||)."""
+        import torch
+        m = self.n * self.N * self.N
+        norms = np.zeros(2)
+        _check(lib().pd_allatonce_residual32(self.h, _dptr(r32, torch.float32, m),
+                                             _dptr(u, torch.float64, m), _dptr(f, torch.float64, m),
+                                             _dptr(u0, torch.float64, self.N * self.N), _hptr(norms)),
+               "pd_allatonce_residual32", self.h)
+        return norms[0], norms[1]
+
 
 def paradiag_setup(N, n, shifts, V=None, Vinv=None, B=None, u0_coef=None, omega=None, cfg=None,
                    stream=None):
@@ -398,3 +429,63 @@ def dense_B_context(B, N, u0_coef=None, **cfg_fields):
     lam, V = np.linalg.eig(B)
     Vinv = np.linalg.inv(V)
     return Context(N, n, lam, V, Vinv, B, u0_coef, None, config(**cfg_fields))
+
+
+class Batch:
+    """pd_batch: independent shifted-system problems of uneven sizes solved together
+    (instance i: N_i x N_i grid, shifts[i] of length n_i)."""
+
+    def __init__(self, Ns, shifts, cfg=None, stream=None):
+        import torch
+        self.Ns = [int(N) for N in Ns]
+        self.shifts = [np.ascontiguousarray(np.asarray(s, dtype=np.complex128).ravel()) for s in shifts]
+        self.ns = [s.size for s in self.shifts]
+        k = len(self.Ns)
+        if len(self.shifts) != k:
+            raise ValueError("one shift array per instance")
+        self.cfg = cfg if cfg is not None else config()
+        Narr = (C.c_int * k)(*self.Ns)
+        narr = (C.c_int * k)(*self.ns)
+        sarr = (C.c_void_p * k)(*[s.ctypes.data for s in self.shifts])
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        h = C.c_void_p()
+        code = lib().pd_batch_setup(C.byref(h), k, C.cast(Narr, C.c_void_p), C.cast(narr, C.c_void_p),
+                                    C.cast(sarr, C.c_void_p), C.byref(self.cfg), C.c_void_p(stream))
+        if code != 0:
+            raise PDError(code, "pd_batch_setup", "")
+        self.h = h
+
+    def solve(self, zs, bs, raise_on_noconv=True):
+        """zs, bs: lists of complex128 [n_i][N_i][N_i] device tensors.  Returns per-instance
+        (iters, relres) lists."""
+        import torch
+        k = len(self.Ns)
+        zp = (C.c_void_p * k)(*[_dptr(z, torch.complex128, n * N * N).value
+                                for z, n, N in zip(zs, self.ns, self.Ns)])
+        bp = (C.c_void_p * k)(*[_dptr(b, torch.complex128, n * N * N).value
+                                for b, n, N in zip(bs, self.ns, self.Ns)])
+        tot = sum(self.ns)
+        it = np.zeros(tot, np.int32)
+        rr = np.zeros(tot)
+        code = lib().pd_batch_solve(self.h, C.cast(zp, C.c_void_p), C.cast(bp, C.c_void_p),
+                                    _hptr(it), _hptr(rr))
+        if code != 0 and not (code == 4 and not raise_on_noconv):
+            detail = lib().pd_batch_last_error(self.h).decode(errors="replace")
+            raise PDError(code, "pd_batch_solve", detail)
+        out, o = [], 0
+        for n in self.ns:
+            out.append((it[o:o + n].copy(), rr[o:o + n].copy()))
+            o += n
+        return out
+
+    def destroy(self):
+        if getattr(self, "h", None):
+            lib().pd_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

@@ -97,6 +97,20 @@ struct pd_ctx {
   std::vector<ProfRec> prof_pending;
   double prof_ms[PD_KC_COUNT] = {0}, prof_bytes[PD_KC_COUNT] = {0};
   long long prof_n[PD_KC_COUNT] = {0};
+  // FP64 refinement of the shifted systems (shifted_solve_refined, batches)
+  int *d_frozen = nullptr, *h_frozen = nullptr;  // [n] shift done: zero RHS, no update
+  double2 *d_c1 = nullptr;                       // [n] lam_j + 4 kappa / h^2
+  double *d_srpart = nullptr, *h_srpart = nullptr;  // [2][n][blocks] residual partial sums
+  // CUDA graphs of whole cycles, keyed by everything a cycle's launches depend on
+  struct CycleGraph {
+    int prec, zzero, cur0, cmax;
+    double tol, stall;
+    cudaGraphExec_t exec;
+    int cur_after[kMaxLevels];
+    long long launches;
+  };
+  std::vector<CycleGraph> graphs;
+  bool graphs_ok = true;  // cleared when a capture fails: launches go one by one
   std::string err;
   std::vector<void *> allocs;
 };
@@ -225,6 +239,9 @@ template <> Prec<float> &prec<float>(pd_ctx *c) { return c->p32; }
 double hl(const pd_ctx *c, int l) { return 1.0 / (c->Ns[l] + 1); }
 // scale of a right-hand side of level l in the kernels' form: h_l^2 / kappa
 double rs(const pd_ctx *c, int l) { return hl(c, l) * hl(c, l) / c->kappa; }
+
+// partial sums of the all-at-once residual kernels (the larger of the two grids)
+int part_blocks(const pd_ctx *c) { return std::max(allatonce_blocks(), residual_fx_blocks(c->num_sms)); }
 
 // Set-up autotuner of the fused kernels: on each global-memory level, times the
 // smoothing+restriction and interpolation+smoothing pair of every candidate (TMA tiles;
@@ -605,13 +622,70 @@ void run_cycle(pd_ctx *c, int l, bool zzero, bool top, const int *active, double
   }
 }
 
-// Solve of eq. (2) for all shifts with the right-hand side already in lv[0].b
-// (scaled by h^2).  On return the per-shift answers are in lv[0].z[final_buf[j]],
-// and h_iters/h_relres (pinned copies) hold cycles and relative residuals.
-// skip_final: after maxit cycles stop without computing the residual of the last
-// iterate (the refinement evaluates its own residual anyway)
+// One cycle of level 0 as a CUDA graph: captured the first time its key is seen, then
+// replayed; the host-side ping-pong state a captured cycle leaves is restored on every
+// replay.  Returns false (nothing launched) where graphs do not apply or a capture fails.
 template <typename T>
-pd_status solve_levels(pd_ctx *c, double tol, int maxit, double stall = 0.0, bool skip_final = false) {
+bool cycle_graph(pd_ctx *c, bool zzero, double tol, int cmax) {
+  if (!c->cfg.cuda_graphs || c->prof_on || !c->graphs_ok || c->stream == nullptr) return false;
+  const int prec_id = sizeof(T) == sizeof(double) ? 0 : 1;
+  for (const auto &g : c->graphs)
+    if (g.prec == prec_id && g.zzero == (int)zzero && g.cur0 == c->cur[0] && g.cmax == cmax &&
+        g.tol == tol && g.stall == c->stall) {
+      ck(c, cudaGraphLaunch(g.exec, c->stream));
+      std::memcpy(c->cur, g.cur_after, sizeof(c->cur));
+      c->launches += g.launches;
+      return true;
+    }
+  if (c->graphs.size() >= 32) return false;
+  pd_ctx::CycleGraph g{};
+  g.prec = prec_id;
+  g.zzero = zzero;
+  g.cur0 = c->cur[0];
+  g.cmax = cmax;
+  g.tol = tol;
+  g.stall = c->stall;
+  int cur_before[kMaxLevels];
+  std::memcpy(cur_before, c->cur, sizeof(c->cur));
+  const long long l0 = c->launches;
+  auto give_up = [&](cudaGraph_t gr) {
+    if (gr) cudaGraphDestroy(gr);
+    cudaGetLastError();
+    std::memcpy(c->cur, cur_before, sizeof(c->cur));
+    c->launches = l0;
+    c->graphs_ok = false;
+    return false;
+  };
+  if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return give_up(nullptr);
+  cudaGraph_t graph = nullptr;
+  try {
+    run_cycle<T>(c, 0, zzero, true, c->st.active, tol, cmax);
+  } catch (const CudaFail &) {
+    cudaStreamEndCapture(c->stream, &graph);
+    return give_up(graph);
+  }
+  if (cudaStreamEndCapture(c->stream, &graph) != cudaSuccess || !graph) return give_up(graph);
+  if (cudaGraphInstantiate(&g.exec, graph, 0) != cudaSuccess) return give_up(graph);
+  cudaGraphDestroy(graph);
+  std::memcpy(g.cur_after, c->cur, sizeof(c->cur));
+  g.launches = c->launches - l0;
+  c->graphs.push_back(g);
+  ck(c, cudaGraphLaunch(g.exec, c->stream));
+  return true;
+}
+
+// Solve of eq. (2) for all shifts with the right-hand side already in lv[0].b
+// (scaled by h^2), in three parts so that several contexts can advance together:
+// solve_begin resets the state (returns the cycle limit, or -1 when the coarse kernel
+// solved the whole problem), solve_cycle queues cycle `cyc` and the copy of its active
+// count, solve_poll waits for the count of the cycle before (false once it left no shift
+// active), solve_end collects the answers.  On return the per-shift answers are in
+// lv[0].z[final_buf[j]], and h_iters/h_relres (pinned copies) hold cycles and relative
+// residuals.  skip_final: after the last permitted cycle stop without computing the
+// residual of the last iterate (the refinement evaluates its own residual anyway).
+template <typename T>
+int solve_begin(pd_ctx *c, double tol, int maxit, double stall) {
   Prec<T> &P = prec<T>(c);
   c->stall = stall;
   LevelBufs &B = P.lv[0];
@@ -625,28 +699,37 @@ pd_status solve_levels(pd_ctx *c, double tol, int maxit, double stall = 0.0, boo
                              view(B.z[0], B.N, B.P), P.coef, P.cinv, nullptr, 0, 0, 1, tol, maxit,
                              c->st));
     ck_launch(c);
-  } else {
-    ck(c, cudaMemsetAsync(B.z[0], 0, (size_t)n * B.N * B.P * sizeof(typename Cx<T>::type),
-                          c->stream));
-    c->cur[0] = 0;
-    const int cmax = std::min(maxit, std::max(c->cfg.maxit, c->cfg.inner_maxit));
-    for (int cyc = 0; cyc <= cmax; cyc++) {
-      c->cur_cyc = cyc;
-      if (skip_final && cyc == cmax && cyc > 0) {
-        PD_PROF(PD_KC_OTHER, 0.0, 0, launch_finalize(c->stream, n, c->st, c->cur[0]));
-        ck_launch(c);
-      } else {
-        run_cycle<T>(c, 0, cyc == 0, true, c->st.active, tol, cmax);
-      }
-      ck(c, cudaMemcpyAsync(&c->h_hist[cyc], c->st.nactive, sizeof(int), cudaMemcpyDeviceToHost,
-                            c->stream));
-      ck(c, cudaEventRecord(c->ev[cyc & 1], c->stream));
-      if (cyc >= 1) {
-        ck(c, cudaEventSynchronize(c->ev[(cyc - 1) & 1]));
-        if (c->h_hist[cyc - 1] == 0) break;
-      }
-    }
+    return -1;
   }
+  ck(c, cudaMemsetAsync(B.z[0], 0, (size_t)n * B.N * B.P * sizeof(typename Cx<T>::type),
+                        c->stream));
+  c->cur[0] = 0;
+  return std::min(maxit, std::max(c->cfg.maxit, c->cfg.inner_maxit));
+}
+
+template <typename T>
+void solve_cycle(pd_ctx *c, int cyc, int cmax, double tol, bool skip_final) {
+  c->cur_cyc = cyc;
+  if (skip_final && cyc == cmax && cyc > 0) {
+    PD_PROF(PD_KC_OTHER, 0.0, 0, launch_finalize(c->stream, c->n, c->st, c->cur[0]));
+    ck_launch(c);
+  } else if (!cycle_graph<T>(c, cyc == 0, tol, cmax)) {
+    run_cycle<T>(c, 0, cyc == 0, true, c->st.active, tol, cmax);
+  }
+  ck(c, cudaMemcpyAsync(&c->h_hist[cyc], c->st.nactive, sizeof(int), cudaMemcpyDeviceToHost,
+                        c->stream));
+  ck(c, cudaEventRecord(c->ev[cyc & 1], c->stream));
+}
+
+bool solve_poll(pd_ctx *c, int cyc) {
+  if (cyc < 1) return true;
+  ck(c, cudaEventSynchronize(c->ev[(cyc - 1) & 1]));
+  return c->h_hist[cyc - 1] != 0;
+}
+
+template <typename T>
+pd_status solve_end(pd_ctx *c, double tol) {
+  const int n = c->n;
   ck(c, cudaMemcpyAsync(c->h_iters, c->st.iters, n * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   ck(c, cudaMemcpyAsync(c->h_relres, c->st.relres, n * sizeof(double), cudaMemcpyDeviceToHost,
                         c->stream));
@@ -665,6 +748,168 @@ pd_status solve_levels(pd_ctx *c, double tol, int maxit, double stall = 0.0, boo
   return PD_OK;
 }
 
+template <typename T>
+pd_status solve_levels(pd_ctx *c, double tol, int maxit, double stall = 0.0, bool skip_final = false) {
+  const int cmax = solve_begin<T>(c, tol, maxit, stall);
+  for (int cyc = 0; cyc <= cmax; cyc++) {
+    solve_cycle<T>(c, cyc, cmax, tol, skip_final);
+    if (!solve_poll(c, cyc)) break;
+  }
+  return solve_end<T>(c, tol);
+}
+
+// Several contexts solved together: every round queues one cycle of each context still
+// iterating (each on its own stream), then waits for the counts of the round before.
+// inner: the refinement's inner solve (inner_tol, inner_maxit, stall_ratio, no final
+// residual) instead of the plain one (tol, maxit).
+template <typename T>
+void lockstep_solve(const std::vector<pd_ctx *> &cs, bool inner, std::vector<pd_status> &rc) {
+  const size_t k = cs.size();
+  std::vector<int> cmax(k);
+  std::vector<char> live(k), sent(k);
+  auto tol_of = [&](pd_ctx *c) { return inner ? c->cfg.inner_tol : c->cfg.tol; };
+  for (size_t i = 0; i < k; i++) {
+    pd_ctx *c = cs[i];
+    cmax[i] = solve_begin<T>(c, tol_of(c), inner ? c->cfg.inner_maxit : c->cfg.maxit,
+                             inner ? c->cfg.stall_ratio : 0.0);
+    live[i] = cmax[i] >= 0;
+  }
+  for (int cyc = 0;; cyc++) {
+    bool any = false;
+    for (size_t i = 0; i < k; i++) {
+      sent[i] = live[i] && cyc <= cmax[i];
+      if (sent[i]) {
+        solve_cycle<T>(cs[i], cyc, cmax[i], tol_of(cs[i]), inner);
+        any = true;
+      } else {
+        live[i] = 0;
+      }
+    }
+    if (!any) break;
+    for (size_t i = 0; i < k; i++)
+      if (sent[i] && !solve_poll(cs[i], cyc)) live[i] = 0;
+  }
+  rc.assign(k, PD_OK);
+  for (size_t i = 0; i < k; i++) rc[i] = solve_end<T>(cs[i], tol_of(cs[i]));
+}
+
+// ---- FP64 refinement of the shifted systems around the FP32 multigrid ----
+struct RefRun {
+  pd_ctx *c = nullptr;
+  double2 *z = nullptr;
+  const double2 *b = nullptr;
+  std::vector<double> bn, prev, relres;
+  std::vector<int> it_sum;
+  int evals = 0;  // residual evaluations done (the first one is ||b||)
+  bool done = false;
+  pd_status rc = PD_OK;
+};
+
+// queues r = b - L z (z = 0 on the first evaluation) into the FP32 level-0 RHS, its
+// per-shift partial norms and their copy to the host
+void refine_eval_launch(RefRun &r) {
+  pd_ctx *c = r.c;
+  LevelBufs &B = c->p32.lv[0];
+  const int N = c->N, n = c->n, gx = shift_residual_blocks(N, n);
+  const bool first = r.evals == 0;
+  const double h = hl(c, 0);
+  const double w = 8.0, m = (double)N * N;
+  PD_PROF(PD_KC_RESIDUAL, (first ? 16.0 + w : 32.0 + w) * m, 0,
+          launch_shift_residual(c->stream, N, n, first ? nullptr : r.z, r.b, c->d_c1,
+                                c->kappa / (h * h), (float)rs(c, 0), view(B.b, N, B.P),
+                                first ? nullptr : c->d_frozen, first, c->d_srpart));
+  ck_launch(c);
+  ck(c, cudaMemcpyAsync(c->h_srpart, c->d_srpart, (first ? 2 : 1) * (size_t)n * gx * sizeof(double),
+                        cudaMemcpyDeviceToHost, c->stream));
+  ck(c, cudaEventRecord(c->ev[0], c->stream));
+}
+
+// after the evaluation: relative residuals; shifts that converged, stopped contracting or
+// used up max_refine corrections are frozen (their next RHS is zero and they get no
+// update).  Sets r.done when no shift needs another correction.
+void refine_eval_finish(RefRun &r) {
+  pd_ctx *c = r.c;
+  const int N = c->N, n = c->n, gx = shift_residual_blocks(N, n);
+  ck(c, cudaEventSynchronize(c->ev[0]));
+  prof_resolve(c);
+  const bool first = r.evals == 0;
+  if (first) {
+    r.bn.assign(n, 0.0);
+    r.prev.assign(n, 0.0);
+    r.relres.assign(n, 1.0);
+    r.it_sum.assign(n, 0);
+    for (int j = 0; j < n; j++) c->h_frozen[j] = 0;
+  }
+  bool any = false;
+  for (int j = 0; j < n; j++) {
+    if (c->h_frozen[j]) continue;
+    double s = 0.0, sb = 0.0;
+    for (int x = 0; x < gx; x++) s += c->h_srpart[(size_t)j * gx + x];
+    if (first) {
+      for (int x = 0; x < gx; x++) sb += c->h_srpart[(size_t)(n + j) * gx + x];
+      r.bn[j] = std::sqrt(sb);
+    }
+    const double rr = r.bn[j] > 0.0 ? std::sqrt(s) / r.bn[j] : 0.0;
+    r.relres[j] = rr;
+    if (!std::isfinite(rr)) {
+      r.rc = PD_ERR_NAN;
+      c->h_frozen[j] = 1;
+      continue;
+    }
+    const bool stuck = r.evals >= 2 && rr > 0.9 * r.prev[j];
+    if (rr <= c->cfg.tol || stuck || r.evals >= c->cfg.max_refine) c->h_frozen[j] = 1;
+    else any = true;
+    r.prev[j] = rr;
+  }
+  r.evals++;
+  ck(c, cudaMemcpyAsync(c->d_frozen, c->h_frozen, n * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  r.done = !any || r.rc != PD_OK;
+}
+
+// shifted_solve_refined for a set of runs (one per context), advanced together
+void refine_runs(std::vector<RefRun> &runs) {
+  for (auto &r : runs) refine_eval_launch(r);
+  for (auto &r : runs) refine_eval_finish(r);
+  for (;;) {
+    std::vector<pd_ctx *> act;
+    std::vector<RefRun *> ar;
+    for (auto &r : runs)
+      if (!r.done) {
+        act.push_back(r.c);
+        ar.push_back(&r);
+      }
+    if (act.empty()) break;
+    std::vector<pd_status> rc;
+    lockstep_solve<float>(act, true, rc);
+    for (size_t i = 0; i < ar.size(); i++) {
+      RefRun &r = *ar[i];
+      pd_ctx *c = r.c;
+      if (rc[i] == PD_ERR_NAN) {
+        r.rc = PD_ERR_NAN;
+        r.done = true;
+        continue;
+      }
+      for (int j = 0; j < c->n; j++) r.it_sum[j] += c->h_iters[j];
+      LevelBufs &B = c->p32.lv[0];
+      const int N = c->N;
+      // the first update writes every shift (z = d; d = 0 for a zero right-hand side)
+      PD_PROF(PD_KC_OTHER, 24.0 * N * N, 0,
+              launch_shift_update(c->stream, N, c->n, r.z, view(B.z[0], N, B.P),
+                                  view(B.z[1], N, B.P), c->st.final_buf,
+                                  r.evals > 1 ? c->d_frozen : nullptr, r.evals > 1));
+      ck_launch(c);
+      refine_eval_launch(r);
+    }
+    for (RefRun *r : ar)
+      if (!r->done) refine_eval_finish(*r);
+  }
+  for (auto &r : runs) {
+    if (r.rc != PD_OK) continue;
+    for (int j = 0; j < r.c->n; j++)
+      if (!(r.relres[j] <= r.c->cfg.tol)) r.rc = PD_ERR_NOCONV;
+  }
+}
+
 // ||fhat - A u|| and ||fhat|| from the per-CTA partial sums (fixed order)
 // r (FP64, may be NULL) or r32 (FP32) = fhat - A u and the norms; with a bidiagonal B
 // and known_fn >= 0 the ||fhat|| sums are skipped and known_fn returned
@@ -672,7 +917,13 @@ void allatonce_norms(pd_ctx *c, double *r, const double *u, const double *f, con
                      double *rn, double *fn, float *r32 = nullptr, double known_fn = -1.0) {
   const double m = (double)c->N * c->N;
   const bool want_f = known_fn < 0.0;
-  if (c->bidiag)
+  int nb = allatonce_blocks();
+  if (c->bidiag && r32 && !r && c->cfg.fx_residual) {
+    nb = residual_fx_blocks(c->num_sms);
+    PD_PROF(PD_KC_RESIDUAL, 20.0 * m + (u0 ? 8.0 * m / c->n : 0.0), 0,
+            launch_residual_fx(c->stream, nb, c->N, c->n, c->boff, c->kappa, r32, u, f, u0,
+                               c->d_u0coef, c->d_bd, c->d_bs, want_f, c->d_part));
+  } else if (c->bidiag)
     PD_PROF(PD_KC_RESIDUAL,
             (r ? 24.0 : r32 ? 20.0 : 16.0) * m + (u0 ? 8.0 * m / c->n : 0.0), 0,
             launch_residual_bidiag(c->stream, c->N, c->n, c->boff, c->kappa, r, r32, u, f, u0,
@@ -682,7 +933,6 @@ void allatonce_norms(pd_ctx *c, double *r, const double *u, const double *f, con
             launch_allatonce_residual(c->stream, c->N, c->n, c->kappa, r, u, f, u0, c->d_u0coef,
                                       c->d_Bptr, c->d_Bcol, c->d_Bval, c->d_part));
   ck_launch(c);
-  const int nb = allatonce_blocks();
   ck(c, cudaMemcpyAsync(c->h_part, c->d_part, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost,
                         c->stream));
   ck(c, cudaStreamSynchronize(c->stream));
@@ -892,6 +1142,9 @@ void free_ctx(pd_ctx *c) {
   if (c->h_relres) cudaFreeHost(c->h_relres);
   if (c->h_part) cudaFreeHost(c->h_part);
   if (c->h_hist) cudaFreeHost(c->h_hist);
+  if (c->h_frozen) cudaFreeHost(c->h_frozen);
+  if (c->h_srpart) cudaFreeHost(c->h_srpart);
+  for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
   for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
   for (int k = 0; k < 2; k++)
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);
@@ -924,6 +1177,8 @@ void pd_config_default(pd_config *cfg) {
   cfg->fused_variant = 0;
   cfg->kappa = 1.0;
   cfg->outer_maxit = 0;
+  cfg->cuda_graphs = 1;
+  cfg->fx_residual = 1;
 }
 
 pd_status pd_alpha_circulant(int n, double tau, double alpha, double *B, double *shifts,
@@ -987,11 +1242,14 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
       cfg.inner_maxit > 100000 || !(cfg.stall_ratio >= 0) || cfg.fused < 0 || cfg.fused > 2 ||
       cfg.tensor_transforms < 0 || cfg.tensor_transforms > 1 || cfg.fused_variant < 0 ||
       cfg.fused_variant > 2 || !(cfg.kappa > 0) || !std::isfinite(cfg.kappa) ||
-      cfg.outer_maxit < 0 || cfg.outer_maxit > 1000)
+      cfg.outer_maxit < 0 || cfg.outer_maxit > 1000 || cfg.cuda_graphs < 0 || cfg.cuda_graphs > 1 ||
+      cfg.fx_residual < 0 || cfg.fx_residual > 1)
     return PD_ERR_ARG;
   if (cfg.precision == 0 && cfg.outer_maxit > 0 && (!B || !V)) return PD_ERR_ARG;
   if (cfg.omega_mode == 2 && !omega) return PD_ERR_ARG;
-  if (cfg.precision == 1 && (!B || !V)) return PD_ERR_ARG;
+  // precision 1 needs B (the refinement residual of eq. (1)) with V, or neither (shifted
+  // solves only)
+  if (cfg.precision == 1 && (B == nullptr) != (V == nullptr)) return PD_ERR_ARG;
   for (int k = 0; k < 2 * n; k++)
     if (!std::isfinite(shifts[k])) return PD_ERR_ARG;
   pd_ctx *c = new (std::nothrow) pd_ctx();
@@ -1057,12 +1315,28 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
     ck(c, cudaMallocHost(&c->h_pinned, 4 * sizeof(int)));
     ck(c, cudaMallocHost(&c->h_iters, n * sizeof(int)));
     ck(c, cudaMallocHost(&c->h_relres, n * sizeof(double)));
-    ck(c, cudaMallocHost(&c->h_part, 2 * allatonce_blocks() * sizeof(double)));
+    {
+      int dev = 0;
+      ck(c, cudaGetDevice(&dev));
+      ck(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    ck(c, cudaMallocHost(&c->h_part, 2 * part_blocks(c) * sizeof(double)));
     ck(c, cudaMallocHost(&c->h_hist, (std::max(cfg.maxit, cfg.inner_maxit) + 2) * sizeof(int)));
+    {
+      const int gx = shift_residual_blocks(N, n);
+      ck(c, cudaMallocHost(&c->h_frozen, n * sizeof(int)));
+      ck(c, cudaMallocHost(&c->h_srpart, 2 * (size_t)n * gx * sizeof(double)));
+      c->d_frozen = dalloc<int *>(c, n * sizeof(int));
+      c->d_srpart = dalloc<double *>(c, 2 * (size_t)n * gx * sizeof(double));
+      c->d_c1 = dalloc<double2 *>(c, n * sizeof(double2));
+      std::vector<double2> c1(n);
+      const double hh = 1.0 / (N + 1);
+      for (int j = 0; j < n; j++)
+        c1[j] = make_double2(shifts[2 * j] + 4.0 * cfg.kappa / (hh * hh), shifts[2 * j + 1]);
+      ck(c, cudaMemcpy(c->d_c1, c1.data(), n * sizeof(double2), cudaMemcpyHostToDevice));
+      ck(c, cudaMemset(c->d_frozen, 0, n * sizeof(int)));
+    }
     // solve state
-    int dev = 0;
-    ck(c, cudaGetDevice(&dev));
-    ck(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
     const FusedGeom g32 = fused_geom<float>(), g64 = fused_geom<double>();
     const int tiles = std::max({smooth_tiles(N), fused_tiles(N, g32.TX, g32.TY),
                                 fused_tiles(N, g64.TX, g64.TY), stream_units(N, 16)});
@@ -1079,7 +1353,7 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
     c->st.partials = dalloc<double *>(c, (size_t)n * tiles * sizeof(double));
     c->d_u0coef = dalloc<double *>(c, n * sizeof(double));
     ck(c, cudaMemcpy(c->d_u0coef, c->u0coef.data(), n * sizeof(double), cudaMemcpyHostToDevice));
-    c->d_part = dalloc<double *>(c, 2 * allatonce_blocks() * sizeof(double));
+    c->d_part = dalloc<double *>(c, 2 * part_blocks(c) * sizeof(double));
     c->d_imag = dalloc<unsigned long long *>(c, sizeof(unsigned long long));
     ck(c, cudaMemset(c->d_imag, 0, sizeof(unsigned long long)));
     if (B) {
@@ -1128,8 +1402,10 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
       if (cfg.outer_maxit > 0) c->d_r = dalloc<double *>(c, (size_t)n * N * N * sizeof(double));
     } else {
       alloc_prec<float>(c);
-      if (c->bidiag) c->d_r32 = dalloc<float *>(c, (size_t)n * N * N * sizeof(float));
-      else c->d_r = dalloc<double *>(c, (size_t)n * N * N * sizeof(double));
+      if (c->have_B) {
+        if (c->bidiag) c->d_r32 = dalloc<float *>(c, (size_t)n * N * N * sizeof(float));
+        else c->d_r = dalloc<double *>(c, (size_t)n * N * N * sizeof(double));
+      }
     }
     ck(c, cudaDeviceSynchronize());
   } catch (const CudaFail &) {
@@ -1471,5 +1747,204 @@ const char *pd_status_str(pd_status s) {
 }
 
 const char *pd_last_error(const pd_ctx *c) { return c ? c->err.c_str() : ""; }
+
+pd_status pd_allatonce_residual32(pd_ctx *c, float *r32, const double *u, const double *f,
+                                  const double *u0, double *h_norms) {
+  if (!c || !r32 || !u || !f) return PD_ERR_ARG;
+  if (!c->have_B || c->cfg.precision != 1) return PD_ERR_STATE;
+  PD_TRY(c, {
+    double rn, fn;
+    if (c->bidiag) {
+      allatonce_norms(c, nullptr, u, f, u0, &rn, &fn, r32, -1.0);
+    } else {
+      // general B: the FP64 residual, then rounded
+      allatonce_norms(c, c->d_r, u, f, u0, &rn, &fn);
+      launch_round_to_float(c->stream, (long long)c->n * c->N * c->N, c->d_r, r32);
+      ck_launch(c);
+      ck(c, cudaStreamSynchronize(c->stream));
+    }
+    if (h_norms) {
+      h_norms[0] = rn;
+      h_norms[1] = fn;
+    }
+    return PD_OK;
+  })
+}
+
+pd_status shifted_solve_refined(pd_ctx *c, void *z, const void *b, int *h_iters, double *h_relres) {
+  if (!c || !z || !b) return PD_ERR_ARG;
+  if (c->cfg.precision == 0) return shifted_solve_batched(c, z, b, h_iters, h_relres);
+  PD_TRY(c, {
+    std::vector<RefRun> runs(1);
+    runs[0].c = c;
+    runs[0].z = static_cast<double2 *>(z);
+    runs[0].b = static_cast<const double2 *>(b);
+    refine_runs(runs);
+    ck(c, cudaStreamSynchronize(c->stream));
+    check_wait_flags(c);
+    for (int j = 0; j < c->n; j++) {
+      if (h_iters) h_iters[j] = runs[0].it_sum.empty() ? 0 : runs[0].it_sum[j];
+      if (h_relres) h_relres[j] = runs[0].relres.empty() ? 0.0 : runs[0].relres[j];
+    }
+    return runs[0].rc;
+  })
+}
+
+}  // extern "C"
+
+struct pd_batch {
+  std::vector<pd_ctx *> ctx;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> done;
+  cudaEvent_t fork = nullptr;
+  cudaStream_t user = nullptr;
+  std::string err;
+};
+
+namespace {
+
+void free_batch(pd_batch *bt) {
+  for (cudaStream_t s : bt->streams)
+    if (s) cudaStreamSynchronize(s);
+  for (pd_ctx *c : bt->ctx) free_ctx(c);
+  for (cudaEvent_t e : bt->done)
+    if (e) cudaEventDestroy(e);
+  if (bt->fork) cudaEventDestroy(bt->fork);
+  for (cudaStream_t s : bt->streams)
+    if (s) cudaStreamDestroy(s);
+  delete bt;
+}
+
+}  // namespace
+
+extern "C" {
+
+pd_status pd_batch_setup(pd_batch **out, int count, const int *h_N, const int *h_n,
+                         const double *const *h_shifts, const pd_config *cfg_in, void *stream) {
+  if (!out) return PD_ERR_ARG;
+  *out = nullptr;
+  if (count < 1 || count > 64 || !h_N || !h_n || !h_shifts) return PD_ERR_ARG;
+  pd_config cfg;
+  if (cfg_in) cfg = *cfg_in;
+  else pd_config_default(&cfg);
+  if (cfg.omega_mode == 2) return PD_ERR_ARG;
+  for (int i = 0; i < count; i++)
+    if (!is_pow2m1(h_N[i]) || h_n[i] < 1 || h_n[i] > kMaxShifts || !h_shifts[i]) return PD_ERR_ARG;
+  pd_batch *bt = new (std::nothrow) pd_batch();
+  if (!bt) return PD_ERR_NOMEM;
+  bt->user = (cudaStream_t)stream;
+  bt->streams.assign(count, nullptr);
+  bt->done.assign(count, nullptr);
+  auto fail = [&](pd_status st) {
+    free_batch(bt);
+    return st;
+  };
+  if (cudaEventCreateWithFlags(&bt->fork, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(PD_ERR_CUDA);
+  }
+  for (int i = 0; i < count; i++) {
+    if (cudaStreamCreateWithFlags(&bt->streams[i], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&bt->done[i], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(PD_ERR_CUDA);
+    }
+    pd_ctx *c = nullptr;
+    const pd_status st = paradiag_setup(&c, h_N[i], 1.0 / (h_N[i] + 1), h_n[i], h_shifts[i], nullptr,
+                                        nullptr, nullptr, nullptr, nullptr, &cfg, bt->streams[i]);
+    if (st != PD_OK) return fail(st);
+    bt->ctx.push_back(c);
+  }
+  *out = bt;
+  return PD_OK;
+}
+
+pd_status pd_batch_solve(pd_batch *bt, void *const *d_z, const void *const *d_b, int *h_iters,
+                         double *h_relres) {
+  if (!bt || !d_z || !d_b) return PD_ERR_ARG;
+  const size_t k = bt->ctx.size();
+  for (size_t i = 0; i < k; i++)
+    if (!d_z[i] || !d_b[i]) return PD_ERR_ARG;
+  pd_ctx *c0 = bt->ctx[0];
+  pd_ctx *c = c0;  // context whose error text a failure reports
+  try {
+    ck(c0, cudaEventRecord(bt->fork, bt->user));
+    for (size_t i = 0; i < k; i++) ck(bt->ctx[i], cudaStreamWaitEvent(bt->streams[i], bt->fork, 0));
+    std::vector<pd_status> rc(k, PD_OK);
+    std::vector<std::vector<int>> its(k);
+    std::vector<std::vector<double>> rel(k);
+    if (c0->cfg.precision == 0) {
+      for (size_t i = 0; i < k; i++) {
+        c = bt->ctx[i];
+        LevelBufs &B = c->p64.lv[0];
+        launch_copy_scale<double>(c->stream, c->N, c->n, view(B.b, c->N, B.P), uview(d_b[i], c->N),
+                                  rs(c, 0));
+        ck_launch(c);
+      }
+      c = c0;
+      lockstep_solve<double>(bt->ctx, false, rc);
+      for (size_t i = 0; i < k; i++) {
+        c = bt->ctx[i];
+        LevelBufs &B = c->p64.lv[0];
+        launch_gather_final<double>(c->stream, c->N, c->n, uview(d_z[i], c->N),
+                                    view(B.z[0], c->N, B.P), view(B.z[1], c->N, B.P),
+                                    c->st.final_buf);
+        ck_launch(c);
+        its[i].assign(c->h_iters, c->h_iters + c->n);
+        rel[i].assign(c->h_relres, c->h_relres + c->n);
+      }
+    } else {
+      std::vector<RefRun> runs(k);
+      for (size_t i = 0; i < k; i++) {
+        runs[i].c = bt->ctx[i];
+        runs[i].z = static_cast<double2 *>(d_z[i]);
+        runs[i].b = static_cast<const double2 *>(d_b[i]);
+      }
+      refine_runs(runs);
+      for (size_t i = 0; i < k; i++) {
+        rc[i] = runs[i].rc;
+        its[i] = runs[i].it_sum;
+        rel[i] = runs[i].relres;
+      }
+    }
+    for (size_t i = 0; i < k; i++) {
+      c = bt->ctx[i];
+      ck(c, cudaEventRecord(bt->done[i], bt->streams[i]));
+      ck(c, cudaStreamWaitEvent(bt->user, bt->done[i], 0));
+      check_wait_flags(c);
+    }
+    size_t o = 0;
+    pd_status out = PD_OK;
+    for (size_t i = 0; i < k; i++) {
+      const int n = bt->ctx[i]->n;
+      for (int j = 0; j < n; j++, o++) {
+        if (h_iters) h_iters[o] = its[i].empty() ? 0 : its[i][j];
+        if (h_relres) h_relres[o] = rel[i].empty() ? 0.0 : rel[i][j];
+      }
+      if (out == PD_OK && rc[i] != PD_OK) {
+        out = rc[i];
+        bt->err = "instance " + std::to_string(i) + ": " + pd_status_str(rc[i]);
+      }
+    }
+    return out;
+  } catch (const CudaFail &) {
+    bt->err = c->err;
+    return PD_ERR_CUDA;
+  } catch (const std::bad_alloc &) {
+    bt->err = "out of memory";
+    return PD_ERR_NOMEM;
+  } catch (pd_status st) {
+    bt->err = pd_status_str(st);
+    return st;
+  }
+}
+
+pd_status pd_batch_destroy(pd_batch *bt) {
+  if (!bt) return PD_ERR_ARG;
+  free_batch(bt);
+  return PD_OK;
+}
+
+const char *pd_batch_last_error(const pd_batch *bt) { return bt ? bt->err.c_str() : ""; }
 
 }  // extern "C"

@@ -69,6 +69,21 @@ void launch_residual_restrict(cudaStream_t s, int Nf, int n, View z, View b, T b
 template <typename T>
 void launch_prolong_add(cudaStream_t s, int Nf, int n, View z, View ec, const int *active);
 
+// ---- residual of eq. (1) without FP64 arithmetic (residual_fx.cu) ----
+int residual_fx_blocks(int num_sms);
+void launch_residual_fx(cudaStream_t s, int blocks, int N, int n, int off, double kappa, float *r,
+                        const double *u, const double *f, const double *u0, const double *u0coef,
+                        const double *bd, const double *bs, bool want_f, double *part);
+
+// ---- FP64 refinement of the shifted systems (shift_refine.cu) ----
+int shift_residual_blocks(int N, int n);
+void launch_round_to_float(cudaStream_t s, long long count, const double *x, float *y);
+void launch_shift_residual(cudaStream_t s, int N, int n, const double2 *z, const double2 *b,
+                           const double2 *c1, double off, float oscale, View out,
+                           const int *frozen, bool want_b, double *part);
+void launch_shift_update(cudaStream_t s, int N, int n, double2 *z, View z0, View z1,
+                         const int *final_buf, const int *frozen, bool accumulate);
+
 struct CoarsePlan {
   int lc;                   // first level handled inside one CTA per shift
   int L;                    // total levels

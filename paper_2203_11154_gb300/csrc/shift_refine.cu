@@ -1,0 +1,137 @@
+// FP64 refinement of the shifted systems of eq. (2) around the FP32 multigrid: the FP64
+// residual of each system, handed to the FP32 levels as the next right-hand side, and the
+// FP64 update of the solution with the FP32 correction.
+//
+//   r_j = b_j - (lam_j I + kappa A) z_j,  A the five-point Laplacian (1/h^2)[4, -1 x 4]
+//
+// written per point as r = b - c1 z + off * (sum of the 4 neighbours of z), c1 = lam_j +
+// 4 kappa/h^2 and off = kappa/h^2, in FP64 complex; the FP32 copy handed to the multigrid
+// is scaled by h^2/kappa, the scaling of the level-0 right-hand side.
+#include "cplx.cuh"
+#include "pd_internal.h"
+
+namespace pd {
+namespace {
+
+constexpr int kSrThreads = 256;
+
+// grid (gx, n): CTA x of shift j strides over the grid rows of shift j.  part[j][x] gets
+// the CTA's sum of |r|^2 (and of |b|^2 in part[n + j][x] when want_b); frozen shifts
+// (already converged) get a zero right-hand side and no sums.
+__global__ void __launch_bounds__(kSrThreads)
+k_shift_residual(int N, const double2 *__restrict__ z, const double2 *__restrict__ b,
+                 const double2 *__restrict__ c1, double off, float oscale, View out,
+                 const int *__restrict__ frozen, int want_b, double *__restrict__ part) {
+  __shared__ double red[2][kSrThreads / 32];
+  const int j = blockIdx.y;
+  const long long m = (long long)N * N;
+  const bool fz = frozen && frozen[j];
+  const double2 cj = c1[j];
+  float2 *o = reinterpret_cast<float2 *>(out.p) + (long long)j * out.plane;
+  double ar = 0.0, ab = 0.0;
+  for (int i = blockIdx.x; i < N; i += gridDim.x) {
+    const double2 *br = b + j * m + (long long)i * N;
+    const double2 *zr = z ? z + j * m + (long long)i * N : nullptr;
+    float rowr = 0.f, rowb = 0.f;
+    for (int c = threadIdx.x; c < N; c += kSrThreads) {
+      if (fz) {
+        o[(long long)i * out.pitch + c] = make_float2(0.f, 0.f);
+        continue;
+      }
+      const double2 bv = br[c];
+      double2 r = bv;
+      if (zr) {
+        double2 nb = make_double2(0.0, 0.0);
+        if (c > 0) nb = cadd(nb, zr[c - 1]);
+        if (c < N - 1) nb = cadd(nb, zr[c + 1]);
+        if (i > 0) nb = cadd(nb, zr[c - N]);
+        if (i < N - 1) nb = cadd(nb, zr[c + N]);
+        const double2 zv = zr[c];
+        // r = b - c1 z + off nb
+        r.x = fma(off, nb.x, fma(-cj.x, zv.x, fma(cj.y, zv.y, bv.x)));
+        r.y = fma(off, nb.y, fma(-cj.x, zv.y, fma(-cj.y, zv.x, bv.y)));
+      }
+      const float2 rf = make_float2((float)r.x, (float)r.y);
+      rowr = fmaf(rf.x, rf.x, fmaf(rf.y, rf.y, rowr));
+      if (want_b) {
+        const float2 bf = make_float2((float)bv.x, (float)bv.y);
+        rowb = fmaf(bf.x, bf.x, fmaf(bf.y, bf.y, rowb));
+      }
+      o[(long long)i * out.pitch + c] = make_float2(rf.x * oscale, rf.y * oscale);
+    }
+    ar += (double)rowr;
+    ab += (double)rowb;
+  }
+  for (int s = 16; s > 0; s >>= 1) {
+    ar += __shfl_down_sync(0xffffffffu, ar, s);
+    ab += __shfl_down_sync(0xffffffffu, ab, s);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = ar;
+    red[1][threadIdx.x >> 5] = ab;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int w = 0; w < kSrThreads / 32; w++) {
+      s0 += red[0][w];
+      s1 += red[1][w];
+    }
+    part[(long long)j * gridDim.x + blockIdx.x] = s0;
+    if (want_b) part[(long long)(gridDim.y + j) * gridDim.x + blockIdx.x] = s1;
+  }
+}
+
+// z_j (+)= d_j for the shifts that are not frozen; d_j is the FP32 answer of the multigrid
+// in z0 or z1 (final_buf[j])
+__global__ void k_shift_update(int N, double2 *__restrict__ z, View z0, View z1,
+                               const int *__restrict__ final_buf, const int *__restrict__ frozen,
+                               int accumulate) {
+  const int j = blockIdx.z;
+  if (frozen && frozen[j]) return;
+  const int i = blockIdx.y * 8 + threadIdx.y, c = blockIdx.x * 32 + threadIdx.x;
+  if (i >= N || c >= N) return;
+  const View &src = final_buf[j] ? z1 : z0;
+  const float2 d =
+      reinterpret_cast<const float2 *>(src.p)[(long long)j * src.plane + (long long)i * src.pitch + c];
+  double2 &dst = z[(long long)j * N * N + (long long)i * N + c];
+  if (accumulate) {
+    dst.x += (double)d.x;
+    dst.y += (double)d.y;
+  } else {
+    dst = make_double2((double)d.x, (double)d.y);
+  }
+}
+
+__global__ void k_round_to_float(long long count, const double *__restrict__ x, float *__restrict__ y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+
+}  // namespace
+
+void launch_round_to_float(cudaStream_t s, long long count, const double *x, float *y) {
+  k_round_to_float<<<4 * 152, 256, 0, s>>>(count, x, y);
+}
+
+int shift_residual_blocks(int N, int n) {
+  const int want = (4 * 152 + n - 1) / n;
+  return want < 1 ? 1 : (want > N ? N : want);
+}
+
+void launch_shift_residual(cudaStream_t s, int N, int n, const double2 *z, const double2 *b,
+                           const double2 *c1, double off, float oscale, View out,
+                           const int *frozen, bool want_b, double *part) {
+  dim3 grid(shift_residual_blocks(N, n), n);
+  k_shift_residual<<<grid, kSrThreads, 0, s>>>(N, z, b, c1, off, oscale, out, frozen,
+                                               want_b ? 1 : 0, part);
+}
+
+void launch_shift_update(cudaStream_t s, int N, int n, double2 *z, View z0, View z1,
+                         const int *final_buf, const int *frozen, bool accumulate) {
+  dim3 grid((N + 31) / 32, (N + 7) / 8, n);
+  k_shift_update<<<grid, dim3(32, 8), 0, s>>>(N, z, z0, z1, final_buf, frozen, accumulate ? 1 : 0);
+}
+
+}  // namespace pd

@@ -67,7 +67,11 @@ def test_setup_rejects_bad_arguments_before_touching_the_gpu():
     assert L.paradiag_setup(C.byref(h), 7, 1 / 8, 4, p, None, None, None, None, None, C.byref(bad), None) == 1
     bad = api.config(coarsest_n=5)
     assert L.paradiag_setup(C.byref(h), 7, 1 / 8, 4, p, None, None, None, None, None, C.byref(bad), None) == 1
-    bad = api.config(precision=1)  # needs B and V
+    bad = api.config(precision=1)  # B for the refinement of eq. (1) needs V as well
+    Bm = np.eye(4)
+    assert L.paradiag_setup(C.byref(h), 7, 1 / 8, 4, p, None, None, Bm.ctypes.data_as(C.c_void_p), None,
+                            None, C.byref(bad), None) == 1
+    bad = api.config(cuda_graphs=2)
     assert L.paradiag_setup(C.byref(h), 7, 1 / 8, 4, p, None, None, None, None, None, C.byref(bad), None) == 1
     bad = api.config(outer_maxit=3)  # FP64 corrections need B and V
     assert L.paradiag_setup(C.byref(h), 7, 1 / 8, 4, p, None, None, None, None, None, C.byref(bad), None) == 1
@@ -77,6 +81,27 @@ def test_setup_rejects_bad_arguments_before_touching_the_gpu():
     assert L.paradiag_setup(C.byref(h), 7, 1 / 8, 4, nan.ctypes.data_as(C.c_void_p), None, None, None,
                             None, None, C.byref(cfg), None) == 1
     assert h.value is None
+
+
+def test_batch_setup_rejects_bad_arguments_before_touching_the_gpu():
+    L = api.lib()
+    h = C.c_void_p()
+    sh = np.array([1.0, 0.5, 2.0, -0.5])
+    Ns = (C.c_int * 2)(7, 8)
+    ns = (C.c_int * 2)(2, 2)
+    sp = (C.c_void_p * 2)(sh.ctypes.data, sh.ctypes.data)
+    cfg = api.config()
+    args = (C.cast(ns, C.c_void_p), C.cast(sp, C.c_void_p), C.byref(cfg), None)
+    assert L.pd_batch_setup(C.byref(h), 2, C.cast(Ns, C.c_void_p), *args) == 1  # N = 8
+    assert L.pd_batch_setup(C.byref(h), 0, C.cast(Ns, C.c_void_p), *args) == 1
+    assert L.pd_batch_setup(C.byref(h), 65, C.cast(Ns, C.c_void_p), *args) == 1
+    bad = api.config(omega_mode=2)
+    Ns[1] = 15
+    assert L.pd_batch_setup(C.byref(h), 2, C.cast(Ns, C.c_void_p), C.cast(ns, C.c_void_p),
+                            C.cast(sp, C.c_void_p), C.byref(bad), None) == 1
+    assert h.value is None
+    assert L.pd_batch_destroy(None) == 1
+    assert L.pd_batch_last_error(None) == b""
 
 
 def test_status_strings():

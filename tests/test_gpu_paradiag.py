@@ -200,3 +200,61 @@ def test_transforms_fp32_tensor_cores(tc, N, n):
     g_w = (alpha ** (np.arange(n) / n))[:, None, None]
     err = np.linalg.norm(g_w * (host(u) - ref)) / np.linalg.norm(g_w * ref)
     assert err < 2e-6
+
+
+def converged_iterate(N, n, tau, alpha, fhat, steps=3):
+    """u with ||fhat - A u|| / ||fhat|| near the FP64 floor: oracle ParaDIAG steps refined
+    with the oracle's own residual."""
+    lam, V, Vinv = core.alpha_circulant(n, tau, alpha)
+    om = lfa.omega_table(lam, N, mode="lfa")
+    u = np.zeros_like(fhat)
+    for _ in range(steps):
+        _, _, r = core.allatonce_residual(N, n, tau, alpha, u, fhat, want_r=True)
+        d, _, _, _ = core.paradiag_solve(N, lam, V, Vinv, om, r, tol=1e-12)
+        u += d
+    return u
+
+
+@pytest.mark.parametrize("fx", [1, 0])
+@pytest.mark.parametrize("N,n,alpha", [(127, 8, 1e-3), (255, 16, 1e-2), (63, 5, 0.3)])
+def test_refinement_residual32(fx, N, n, alpha):
+    """The FP32 residual the refinement hands to the forward transform, element by element
+    against the oracle's long-double residual, on a random and on a converged u.  Without
+    FP64 arithmetic (fx = 1) the error bound is the FP32 rounding of r plus 2^-43 of the
+    terms and the fixed-point truncation ih2 2^-54 max|u_k| — far below the FP64 rounding of
+    the formula (4 eps of ih2 (4|u| + sum|nb|)), which bounds fx = 0."""
+    tau = 1.0 / n
+    h = 1.0 / (N + 1)
+    ih2 = 1.0 / h ** 2
+    f, u0 = inputs.paradiag_problem(N, n, seed=7)
+    fhat = core.assemble_rhs(N, n, tau, f, u0)
+    c = api.alpha_circulant_context(N, n, tau, alpha, precision=1, fx_residual=fx)
+    rng = np.random.default_rng(N + n)
+    for u in (rng.standard_normal((n, N, N)), converged_iterate(N, n, tau, alpha, fhat)):
+        r32 = torch.empty(n, N, N, dtype=torch.float32, device="cuda")
+        rn, fn = c.pd_allatonce_residual32(r32, dev(u), dev(f), dev(u0))
+        r = host(r32).astype(np.float64)
+        rn_ld, r_ld = core.allatonce_residual_ld(N, n, tau, alpha, u, fhat)
+        a = np.abs(u)
+        nb = np.zeros_like(u)
+        nb[:, 1:, :] += u[:, :-1, :]
+        nb[:, :-1, :] += u[:, 1:, :]
+        nb[:, :, 1:] += u[:, :, :-1]
+        nb[:, :, :-1] += u[:, :, 1:]
+        anb = np.zeros_like(a)
+        anb[:, 1:, :] += a[:, :-1, :]
+        anb[:, :-1, :] += a[:, 1:, :]
+        anb[:, :, 1:] += a[:, :, :-1]
+        anb[:, :, :-1] += a[:, :, 1:]
+        prev = np.roll(a, 1, axis=0)
+        prev[0] *= alpha
+        if fx:
+            T = np.abs(fhat) + (a + prev) / tau + ih2 * np.abs(4 * u - nb)
+            umax = np.max(a.reshape(n, -1), axis=1)[:, None, None]
+            tol = 2.0 ** -24 * np.abs(r_ld) + 2.0 ** -43 * T + ih2 * 2.0 ** -54 * umax
+        else:
+            T = np.abs(fhat) + (a + prev) / tau + ih2 * (4 * a + anb)
+            tol = 2.0 ** -24 * np.abs(r_ld) + 4 * np.finfo(float).eps * T
+        assert np.all(np.abs(r - r_ld) <= tol)
+        assert abs(rn - rn_ld) <= 1e-5 * rn_ld + np.linalg.norm(tol)
+        assert fn == pytest.approx(np.linalg.norm(fhat), rel=1e-5)

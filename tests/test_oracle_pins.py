@@ -438,3 +438,36 @@ def test_paradiag2_iteration_contracts_by_alpha():
     bound = alpha / (1 - alpha)
     assert errs[0] <= bound and errs[1] <= bound * errs[0]
     assert errs[3] <= 1e-13
+
+
+def test_extended_precision_residual():
+    """The long-double residual of eq. (1): equal to the FP64 one up to the FP64 rounding of
+    the formula, and exact where every term is exactly representable (dyadic data on a grid
+    with h = 1/8), checked against integer arithmetic."""
+    N, n, tau, alpha = 7, 4, 0.25, 0.5
+    rng = np.random.default_rng(14)
+    u = rng.integers(-64, 64, (n, N, N)) / 8.0
+    fhat = rng.integers(-64, 64, (n, N, N)) / 4.0
+    rn, r = core.allatonce_residual_ld(N, n, tau, alpha, u, fhat)
+    # exact: fhat - (u_k - c u_{k-1})/tau - 64 (4 u_k - nb), all integers / 8
+    U = (u * 8).astype(np.int64)
+    Fh = (fhat * 8).astype(np.int64)
+    ex = np.zeros_like(U)
+    for k in range(n):
+        prev = U[k - 1] if k > 0 else U[n - 1]
+        c = 1 if k > 0 else 0  # alpha = 1/2 handled below
+        nb = np.zeros((N, N), np.int64)
+        nb[1:, :] += U[k, :-1, :]
+        nb[:-1, :] += U[k, 1:, :]
+        nb[:, 1:] += U[k, :, :-1]
+        nb[:, :-1] += U[k, :, 1:]
+        Bu = 4 * (2 * U[k] - (2 * prev if c else prev))  # (u - c prev)/tau, times 2 for alpha
+        ex[k] = 2 * Fh[k] - Bu - 2 * 64 * (4 * U[k] - nb)
+    assert np.array_equal(r * 16, ex.astype(float))
+    assert rn == pytest.approx(np.linalg.norm(ex / 16.0), rel=1e-14)
+    # random data: agrees with the FP64 residual to its rounding
+    u = rng.standard_normal((n, N, N))
+    fhat = rng.standard_normal((n, N, N))
+    rn_ld, r_ld = core.allatonce_residual_ld(N, n, tau, alpha, u, fhat)
+    rn64, _, r64 = core.allatonce_residual(N, n, tau, alpha, u, fhat, want_r=True)
+    assert np.max(np.abs(r_ld - r64)) <= 1e-13 * np.max(np.abs(r64))
