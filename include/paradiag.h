@@ -89,12 +89,16 @@ typedef struct {
                           without FP64 instructions (stencil difference exact in 64-bit fixed
                           point per 16 x 128 tile, the other terms in float-float; more
                           accurate than the FP64 formula); 0: FP64 (default 1) */
+    int fft_transforms; /* 1: when V and V^{-1} given at set-up are those of the alpha-
+                          circulant B (pd_alpha_circulant, to 1e-12) and n is a power of two
+                          <= 128, the time transforms run as Gamma-weighted FFTs (both
+                          precisions); 0: dense products (default 1) */
 } pd_config;
 
 /* Fills cfg with V(1,1), coarsest 3, maxit 100, tol 1e-10, omega_mode 1, FP64,
  * Vanka, inner_tol 1e-6, max_refine 12, imag_check 1, inner_maxit 3, stall_ratio 0.5,
  * fused 1, tensor_transforms 1, fused_variant 0, kappa 1, outer_maxit 0, cuda_graphs 1,
- * fx_residual 1. */
+ * fx_residual 1, fft_transforms 1. */
 void pd_config_default(pd_config *cfg);
 
 /*

@@ -57,7 +57,7 @@ class pd_config(C.Structure):
                 ("inner_maxit", C.c_int), ("stall_ratio", C.c_double), ("fused", C.c_int),
                 ("tensor_transforms", C.c_int), ("fused_variant", C.c_int),
                 ("kappa", C.c_double), ("outer_maxit", C.c_int), ("cuda_graphs", C.c_int),
-                ("fx_residual", C.c_int)]
+                ("fx_residual", C.c_int), ("fft_transforms", C.c_int)]
 
 
 _P = C.c_void_p

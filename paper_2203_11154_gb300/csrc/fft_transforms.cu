@@ -1,0 +1,314 @@
+// Time transforms of eq. (1) for the alpha-circulant backward-Euler B by FFT.
+//
+// With B = (1/tau)(I - C_alpha) the eigenvector matrices are scaled Fourier matrices:
+//   V^{-1}[j][k] = alpha^{k/n} e^{+2 pi i j k / n} / n,   V[k][j] = alpha^{-k/n} e^{-2 pi i k j / n},
+// so at every grid point
+//   forward:  g_j = s/n sum_k e^{+2 pi i j k / n} (alpha^{k/n} fhat_k)       (s = h^2/kappa or 1)
+//   inverse:  u_k (+)= alpha^{-k/n} Re sum_j e^{-2 pi i k j / n} z_j
+// are a weighted DFT of length n, O(n log n) per point instead of the O(n^2) dense product.
+//
+// One thread per grid point.  n = N1 N2 (both powers of two): the four-step decomposition
+//   X[k1 + N1 k2] = sum_{j2} w_n^{j2 k1} [sum_{j1} x[N2 j1 + j2] w_{N1}^{j1 k1}] w_{N2}^{j2 k2}
+// with the small DFTs as unrolled radix-2 butterflies in registers and the n values of the
+// thread's point in its own column of shared memory ([n][P], conflict-free, no barrier:
+// no thread reads another thread's column).  Loads and stores of the n time slices are
+// coalesced across the threads of a warp (consecutive grid points).
+#include "cplx.cuh"
+#include "pd_internal.h"
+
+namespace pd {
+namespace {
+
+// grid points (threads) per CTA: up to 128, with the CTA's columns within 96 KB of shared
+// memory (a multiple of 32)
+template <typename T, int n> __host__ __device__ constexpr int fft_points() {
+  return (98304 / (n * (int)sizeof(typename Cx<T>::type))) >= 128
+             ? 128
+             : ((98304 / (n * (int)sizeof(typename Cx<T>::type))) / 32) * 32;
+}
+
+__host__ __device__ constexpr int bitrev(int i, int bits) {
+  int r = 0;
+  for (int b = 0; b < bits; b++) r |= ((i >> b) & 1) << (bits - 1 - b);
+  return r;
+}
+__host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x >> 1); }
+
+// in-place DFT of length R (power of two) of v in registers: v_out[k] = sum_j v[j] w^{jk},
+// w = tw[step] (tw[t] = w_n^t, n = R * step), radix-2 decimation in time
+template <typename C, int R>
+__device__ __forceinline__ void dft_small(C (&v)[R], const C *__restrict__ tw, int step) {
+  constexpr int bits = ilog2(R);
+#pragma unroll
+  for (int i = 0; i < R; i++) {
+    const int r = bitrev(i, bits);
+    if (r > i) {
+      const C t = v[i];
+      v[i] = v[r];
+      v[r] = t;
+    }
+  }
+#pragma unroll
+  for (int m = 2; m <= R; m <<= 1) {
+#pragma unroll
+    for (int k = 0; k < R; k += m) {
+#pragma unroll
+      for (int j = 0; j < m / 2; j++) {
+        C t = v[k + j + m / 2];
+        if (j != 0) t = cmul(tw[j * (R / m) * step], t);
+        v[k + j + m / 2] = csub(v[k + j], t);
+        v[k + j] = cadd(v[k + j], t);
+      }
+    }
+  }
+}
+
+// the two passes of the four-step DFT on the thread's column col[e * P]
+template <typename C, int N1, int N2, int P>
+__device__ __forceinline__ void fft_column(C *col, const C *__restrict__ tw) {
+  constexpr int n = N1 * N2;
+  // pass 1: for each j2, DFT over j1 of x[N2 j1 + j2], times w_n^{j2 k1}
+  for (int j2 = 0; j2 < N2; j2++) {
+    C v[N1];
+#pragma unroll
+    for (int j1 = 0; j1 < N1; j1++) v[j1] = col[(N2 * j1 + j2) * P];
+    dft_small<C, N1>(v, tw, N2);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; k1++) {
+      const C t = (k1 == 0 || j2 == 0) ? v[k1] : cmul(tw[(j2 * k1) % n], v[k1]);
+      col[(N2 * k1 + j2) * P] = t;
+    }
+  }
+  // pass 2: for each k1, DFT over j2; X[k1 + N1 k2] ends in slot N2 k1 + k2
+  for (int k1 = 0; k1 < N1; k1++) {
+    C v[N2];
+#pragma unroll
+    for (int j2 = 0; j2 < N2; j2++) v[j2] = col[(N2 * k1 + j2) * P];
+    dft_small<C, N2>(v, tw, N1);
+#pragma unroll
+    for (int k2 = 0; k2 < N2; k2++) col[(N2 * k1 + k2) * P] = v[k2];
+  }
+}
+
+// exact FP32 -> FP64 by bit operations (the conversion instruction issues on the FP64
+// pipe); zero and subnormal inputs give 0, Inf/NaN give NaN
+__device__ __forceinline__ double f32_to_f64(float v) {
+  const unsigned b = __float_as_uint(v);
+  const unsigned e = (b >> 23) & 0xFFu;
+  if (e == 0) return 0.0;
+  if (e == 0xFFu) return __longlong_as_double(0x7FF8000000000000ll);
+  const unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b >> 3) & 0xFFFFFu);
+  return __hiloint2double((int)hi, (int)(b << 29));
+}
+__device__ __forceinline__ double to_f64(float v) { return f32_to_f64(v); }
+__device__ __forceinline__ double to_f64(double v) { return v; }
+
+template <typename T, typename InT> __device__ __forceinline__ T load_in(const InT *p) { return (T)*p; }
+
+// g_j(point) = wk-weighted DFT (+ exponent) of fhat; wk[k] = s alpha^{k/n} / n
+template <typename T, int N1, int N2, typename InT>
+__global__ void __launch_bounds__(fft_points<T, N1 * N2>())
+k_fft_forward(int N, View g, const InT *__restrict__ f, const double *__restrict__ u0,
+              const double *__restrict__ u0coef, const T *__restrict__ wk,
+              const typename Cx<T>::type *__restrict__ tw) {
+  using C = typename Cx<T>::type;
+  constexpr int n = N1 * N2, P = fft_points<T, n>();
+  extern __shared__ __align__(16) unsigned char fft_raw[];
+  C *col = reinterpret_cast<C *>(fft_raw) + threadIdx.x;
+  const long long m = (long long)N * N;
+  for (long long base = (long long)blockIdx.x * P; base < m; base += (long long)gridDim.x * P) {
+    const long long x = base + threadIdx.x;
+    const bool ok = x < m;
+    const double u0x = (ok && u0) ? u0[x] : 0.0;
+    // batches of kBatch loads in flight per thread (the CTA holds few threads: its columns
+    // fill shared memory), then into the column
+    constexpr int kBatch = n < 16 ? n : 16;
+#pragma unroll 1
+    for (int k0 = 0; k0 < n; k0 += kBatch) {
+      InT in[kBatch];
+#pragma unroll
+      for (int q = 0; q < kBatch; q++) in[q] = ok ? f[(long long)(k0 + q) * m + x] : (InT)0;
+#pragma unroll
+      for (int q = 0; q < kBatch; q++) {
+        const int k = k0 + q;
+        // the initial-value term (FP64) only on the time steps whose coefficient is nonzero
+        // (tested on the bits: no FP64 comparison per point)
+        const double ck = u0 ? u0coef[k] : 0.0;
+        T v;
+        if (u0 && (__double_as_longlong(ck) << 1) != 0) v = (T)(to_f64(in[q]) + ck * u0x);
+        else v = (T)in[q];
+        col[k * P] = cx<C>(v * wk[k], (T)0);
+      }
+    }
+    fft_column<C, N1, N2, P>(col, tw);
+    if (ok) {
+      const int i = (int)(x / N), c = (int)(x - (long long)i * N);
+      C *gp = reinterpret_cast<C *>(g.p) + (long long)i * g.pitch + c;
+#pragma unroll 4
+      for (int s = 0; s < n; s++) {
+        const int k1 = s / N2, k2 = s % N2;
+        gp[(long long)(k1 + N1 * k2) * g.plane] = col[s * P];
+      }
+    }
+  }
+}
+
+// u_k(point) (+)= wk[k] Re(DFT (- exponent) of z)_k, wk[k] = alpha^{-k/n}; z_j from z1 where
+// final_buf[j] is set, else z0; imag_check: atomic max of |wk[k] Im(.)_k| (bits of a double)
+template <typename T, int N1, int N2>
+__global__ void __launch_bounds__(fft_points<T, N1 * N2>())
+k_fft_inverse(int N, double *__restrict__ u, View z0, View z1, const int *__restrict__ final_buf,
+              const T *__restrict__ wk, const typename Cx<T>::type *__restrict__ tw, int accumulate,
+              int imag_check, unsigned long long *imag_bits) {
+  using C = typename Cx<T>::type;
+  constexpr int n = N1 * N2, P = fft_points<T, n>();
+  extern __shared__ __align__(16) unsigned char fft_raw[];
+  __shared__ float red[P / 32];
+  C *col = reinterpret_cast<C *>(fft_raw) + threadIdx.x;
+  const long long m = (long long)N * N;
+  float imax = 0.f;
+  for (long long base = (long long)blockIdx.x * P; base < m; base += (long long)gridDim.x * P) {
+    const long long x = base + threadIdx.x;
+    const bool ok = x < m;
+    const int i = (int)(x / N), c = (int)(x - (long long)i * N);
+    constexpr int kBatch = n < 16 ? n : 16;
+#pragma unroll 1
+    for (int j0 = 0; j0 < n; j0 += kBatch) {
+      C in[kBatch];
+#pragma unroll
+      for (int q = 0; q < kBatch; q++) {
+        const int j = j0 + q;
+        const View &zv = (final_buf && final_buf[j]) ? z1 : z0;
+        in[q] = ok ? reinterpret_cast<const C *>(zv.p)[(long long)j * zv.plane + (long long)i * zv.pitch + c]
+                   : czero<C>();
+      }
+#pragma unroll
+      for (int q = 0; q < kBatch; q++) col[(j0 + q) * P] = in[q];
+    }
+    fft_column<C, N1, N2, P>(col, tw);
+    if (ok) {
+#pragma unroll 1
+      for (int s0 = 0; s0 < n; s0 += kBatch) {
+        double uo[kBatch];
+        if (accumulate) {
+#pragma unroll
+          for (int q = 0; q < kBatch; q++) {
+            const int s = s0 + q, k = s / N2 + N1 * (s % N2);
+            uo[q] = u[(long long)k * m + x];
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < kBatch; q++) {
+          const int s = s0 + q, k = s / N2 + N1 * (s % N2);
+          const C v = col[s * P];
+          const T re = v.x * wk[k];
+          u[(long long)k * m + x] = accumulate ? uo[q] + to_f64(re) : to_f64(re);
+          if (imag_check) imax = fmaxf(imax, fabsf((float)(v.y * wk[k])));
+        }
+      }
+    }
+  }
+  if (imag_check) {
+    for (int o = 16; o > 0; o >>= 1) imax = fmaxf(imax, __shfl_down_sync(0xffffffffu, imax, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = imax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float mx = 0.f;
+      for (int w = 0; w < P / 32; w++) mx = fmaxf(mx, red[w]);
+      atomicMax(imag_bits, (unsigned long long)__double_as_longlong((double)mx));
+    }
+  }
+}
+
+template <typename T, int n> size_t fft_smem() {
+  return (size_t)n * fft_points<T, n>() * sizeof(typename Cx<T>::type);
+}
+
+int fft_grid(int N, int points, int num_sms) {
+  const long long m = (long long)N * N;
+  const long long ctas = (m + points - 1) / points;
+  const long long cap = 8LL * num_sms;
+  return (int)(ctas < cap ? ctas : cap);
+}
+
+template <typename T, int N1, int N2>
+cudaError_t prepare_one() {
+  const int bytes = (int)fft_smem<T, N1 * N2>();
+  cudaError_t e = cudaFuncSetAttribute(k_fft_forward<T, N1, N2, double>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_fft_forward<T, N1, N2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_fft_inverse<T, N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              bytes);
+}
+
+// the factorisations n = N1 N2 used for n = 2..128
+#define PD_FFT_SIZES(X) X(2, 1) X(2, 2) X(4, 2) X(4, 4) X(8, 4) X(8, 8) X(16, 8)
+
+}  // namespace
+
+bool fft_transforms_supported(int n) { return n >= 2 && n <= 128 && (n & (n - 1)) == 0; }
+
+template <typename T>
+cudaError_t prepare_fft_transforms() {
+  cudaError_t e = cudaSuccess;
+#define PD_FFT_PREP(A, B)                      \
+  if (e == cudaSuccess) e = prepare_one<T, A, B>();
+  PD_FFT_SIZES(PD_FFT_PREP)
+#undef PD_FFT_PREP
+  return e;
+}
+
+template <typename T>
+void launch_fft_forward(cudaStream_t s, int num_sms, int N, int n, View g, const void *f, bool f32,
+                        const double *u0, const double *u0coef, const T *wk,
+                        const typename Cx<T>::type *tw) {
+#define PD_FFT_FWD(A, B)                                                                          \
+  if (n == A * B) {                                                                               \
+    constexpr int P = fft_points<T, A * B>();                                                      \
+    const int grid = fft_grid(N, P, num_sms);                                                     \
+    const size_t smem = fft_smem<T, A * B>();                                                     \
+    if (f32)                                                                                      \
+      k_fft_forward<T, A, B, float><<<grid, P, smem, s>>>(N, g, static_cast<const float *>(f),     \
+                                                          u0, u0coef, wk, tw);                    \
+    else                                                                                          \
+      k_fft_forward<T, A, B, double><<<grid, P, smem, s>>>(N, g, static_cast<const double *>(f),   \
+                                                           u0, u0coef, wk, tw);                   \
+    return;                                                                                       \
+  }
+  PD_FFT_SIZES(PD_FFT_FWD)
+#undef PD_FFT_FWD
+}
+
+template <typename T>
+void launch_fft_inverse(cudaStream_t s, int num_sms, int N, int n, double *u, View z0, View z1,
+                        const int *final_buf, const T *wk, const typename Cx<T>::type *tw,
+                        bool accumulate, bool imag_check, unsigned long long *imag_bits) {
+#define PD_FFT_INV(A, B)                                                                       \
+  if (n == A * B) {                                                                            \
+    constexpr int P = fft_points<T, A * B>();                                                   \
+    const int grid = fft_grid(N, P, num_sms);                                                  \
+    const size_t smem = fft_smem<T, A * B>();                                                  \
+    k_fft_inverse<T, A, B><<<grid, P, smem, s>>>(N, u, z0, z1, final_buf, wk, tw,              \
+                                                 accumulate ? 1 : 0, imag_check ? 1 : 0,       \
+                                                 imag_bits);                                   \
+    return;                                                                                    \
+  }
+  PD_FFT_SIZES(PD_FFT_INV)
+#undef PD_FFT_INV
+}
+
+#define PD_FFT_INST(T)                                                                            \
+  template cudaError_t prepare_fft_transforms<T>();                                               \
+  template void launch_fft_forward<T>(cudaStream_t, int, int, int, View, const void *, bool,     \
+                                      const double *, const double *, const T *,                  \
+                                      const typename Cx<T>::type *);                              \
+  template void launch_fft_inverse<T>(cudaStream_t, int, int, int, double *, View, View,         \
+                                      const int *, const T *, const typename Cx<T>::type *, bool, \
+                                      bool, unsigned long long *);
+PD_FFT_INST(double)
+PD_FFT_INST(float)
+
+}  // namespace pd

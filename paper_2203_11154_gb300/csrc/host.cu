@@ -44,6 +44,11 @@ template <typename T> struct Prec {
   float *tc_fwd_hi = nullptr, *tc_fwd_lo = nullptr, *tc_inv_hi = nullptr, *tc_inv_lo = nullptr;
   float *tc_fwd1_hi = nullptr, *tc_fwd1_lo = nullptr;
   bool tc = false;
+  // FFT route for an alpha-circulant V: weights alpha^{k/n} h^2/(kappa n), alpha^{k/n}/n
+  // (unscaled) and alpha^{-k/n}; twiddles e^{+-2 pi i t/n}
+  T *fft_wf = nullptr, *fft_wf1 = nullptr, *fft_wi = nullptr;
+  C *fft_twf = nullptr, *fft_twi = nullptr;
+  bool fft = false;
 };
 
 }  // namespace
@@ -312,6 +317,33 @@ void autotune_fused(pd_ctx *c) {
   cudaEventDestroy(e1);
 }
 
+// True when the context's V and V^{-1} are those of the alpha-circulant backward-Euler B
+// (pd_alpha_circulant) for some alpha in (0, 1], to 1e-12 relative: the FFT route applies.
+bool alpha_circulant_alpha(const pd_ctx *c, double *alpha_out) {
+  const int n = c->n;
+  if (n < 2) return false;
+  const double v10 = c->V[2 * (size_t)n];  // V[1][0] = alpha^{-1/n}
+  if (!(v10 >= 1.0) || c->V[2 * (size_t)n + 1] != 0.0) return false;
+  const double alpha = std::pow(v10, -(double)n);
+  if (!(alpha > 0.0 && alpha <= 1.0)) return false;
+  double vmax = 0.0, imax = 0.0, dv = 0.0, di = 0.0;
+  for (int k = 0; k < n; k++)
+    for (int j = 0; j < n; j++) {
+      const size_t e = (size_t)k * n + j;
+      const double ang = 2.0 * M_PI * (double)((long long)k * j % n) / n;
+      const std::complex<double> v = std::pow(alpha, -(double)k / n) * std::polar(1.0, -ang);
+      const std::complex<double> w = std::polar(1.0, ang) * std::pow(alpha, (double)j / n) / (double)n;
+      const std::complex<double> gv(c->V[2 * e], c->V[2 * e + 1]), gw(c->Vinv[2 * e], c->Vinv[2 * e + 1]);
+      vmax = std::max(vmax, std::abs(v));
+      imax = std::max(imax, std::abs(w));
+      dv = std::max(dv, std::abs(gv - v));
+      di = std::max(di, std::abs(gw - w));
+    }
+  if (!(dv <= 1e-12 * vmax && di <= 1e-12 * imax)) return false;
+  *alpha_out = alpha;
+  return true;
+}
+
 template <typename T>
 void alloc_prec(pd_ctx *c) {
   using C = typename Cx<T>::type;
@@ -414,7 +446,37 @@ void alloc_prec(pd_ctx *c) {
     ck(c, cudaMemcpy(P.Wf, wf.data(), wf.size() * sizeof(C), cudaMemcpyHostToDevice));
     ck(c, cudaMemcpy(P.Wi, wi.data(), wi.size() * sizeof(C), cudaMemcpyHostToDevice));
   }
-  if (sizeof(T) == sizeof(float) && c->have_V && c->cfg.tensor_transforms &&
+  double alpha_fft = 0.0;
+  if (c->have_V && c->cfg.fft_transforms && fft_transforms_supported(n) &&
+      alpha_circulant_alpha(c, &alpha_fft)) {
+    std::vector<T> wf(n), wf1(n), wi(n);
+    std::vector<C> twf(n), twi(n);
+    const double h0 = hl(c, 0);
+    for (int k = 0; k < n; k++) {
+      const double a = std::pow(alpha_fft, (double)k / n);
+      wf[k] = (T)(a * h0 * h0 / (c->kappa * n));
+      wf1[k] = (T)(a / n);
+      wi[k] = (T)(1.0 / a);
+      const std::complex<double> e = std::polar(1.0, 2.0 * M_PI * k / n);
+      twf[k].x = (T)e.real();
+      twf[k].y = (T)e.imag();
+      twi[k].x = (T)e.real();
+      twi[k].y = (T)-e.imag();
+    }
+    P.fft_wf = dalloc<T *>(c, n * sizeof(T));
+    P.fft_wf1 = dalloc<T *>(c, n * sizeof(T));
+    P.fft_wi = dalloc<T *>(c, n * sizeof(T));
+    P.fft_twf = dalloc<C *>(c, n * sizeof(C));
+    P.fft_twi = dalloc<C *>(c, n * sizeof(C));
+    ck(c, cudaMemcpy(P.fft_wf, wf.data(), n * sizeof(T), cudaMemcpyHostToDevice));
+    ck(c, cudaMemcpy(P.fft_wf1, wf1.data(), n * sizeof(T), cudaMemcpyHostToDevice));
+    ck(c, cudaMemcpy(P.fft_wi, wi.data(), n * sizeof(T), cudaMemcpyHostToDevice));
+    ck(c, cudaMemcpy(P.fft_twf, twf.data(), n * sizeof(C), cudaMemcpyHostToDevice));
+    ck(c, cudaMemcpy(P.fft_twi, twi.data(), n * sizeof(C), cudaMemcpyHostToDevice));
+    ck(c, prepare_fft_transforms<T>());
+    P.fft = true;
+  }
+  if (!P.fft && sizeof(T) == sizeof(float) && c->have_V && c->cfg.tensor_transforms &&
       tc_transforms_supported(c->N, n)) {
     const size_t fa = 128 * 64, ia = 128 * 128;
     std::vector<float> fh(fa), fl(fa), ih(ia), il(ia), f1h(fa), f1l(fa), ih2(ia), il2(ia);
@@ -953,7 +1015,10 @@ void transform_forward(pd_ctx *c, View g, const void *f, const double *u0, bool 
                        bool f32 = false) {
   Prec<T> &P = prec<T>(c);
   const double h = hl(c, 0);
-  if (P.tc) {
+  if (P.fft) {
+    launch_fft_forward<T>(c->stream, c->num_sms, c->N, c->n, g, f, f32, u0, c->d_u0coef,
+                          scaled ? P.fft_wf : P.fft_wf1, P.fft_twf);
+  } else if (P.tc) {
     launch_tc_forward(c->stream, c->num_sms, c->N, c->n, g, f, f32, u0, c->d_u0coef,
                       scaled ? P.tc_fwd_hi : P.tc_fwd1_hi, scaled ? P.tc_fwd_lo : P.tc_fwd1_lo,
                       c->st.flags);
@@ -967,7 +1032,10 @@ template <typename T>
 void transform_inverse(pd_ctx *c, double *u, View z0, View z1, const int *final_buf, bool acc,
                        bool imag) {
   Prec<T> &P = prec<T>(c);
-  if (P.tc)
+  if (P.fft)
+    launch_fft_inverse<T>(c->stream, c->num_sms, c->N, c->n, u, z0, z1, final_buf, P.fft_wi,
+                          P.fft_twi, acc, imag, c->d_imag);
+  else if (P.tc)
     launch_tc_inverse(c->stream, c->num_sms, c->N, c->n, u, z0, z1, final_buf, P.tc_inv_hi,
                       P.tc_inv_lo, acc, imag, c->d_imag, c->st.flags);
   else
@@ -1179,6 +1247,7 @@ void pd_config_default(pd_config *cfg) {
   cfg->outer_maxit = 0;
   cfg->cuda_graphs = 1;
   cfg->fx_residual = 1;
+  cfg->fft_transforms = 1;
 }
 
 pd_status pd_alpha_circulant(int n, double tau, double alpha, double *B, double *shifts,
@@ -1243,7 +1312,8 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
       cfg.tensor_transforms < 0 || cfg.tensor_transforms > 1 || cfg.fused_variant < 0 ||
       cfg.fused_variant > 2 || !(cfg.kappa > 0) || !std::isfinite(cfg.kappa) ||
       cfg.outer_maxit < 0 || cfg.outer_maxit > 1000 || cfg.cuda_graphs < 0 || cfg.cuda_graphs > 1 ||
-      cfg.fx_residual < 0 || cfg.fx_residual > 1)
+      cfg.fx_residual < 0 || cfg.fx_residual > 1 || cfg.fft_transforms < 0 ||
+      cfg.fft_transforms > 1)
     return PD_ERR_ARG;
   if (cfg.precision == 0 && cfg.outer_maxit > 0 && (!B || !V)) return PD_ERR_ARG;
   if (cfg.omega_mode == 2 && !omega) return PD_ERR_ARG;

@@ -69,6 +69,18 @@ void launch_residual_restrict(cudaStream_t s, int Nf, int n, View z, View b, T b
 template <typename T>
 void launch_prolong_add(cudaStream_t s, int Nf, int n, View z, View ec, const int *active);
 
+// ---- time transforms by FFT for the alpha-circulant B (fft_transforms.cu) ----
+bool fft_transforms_supported(int n);
+template <typename T> cudaError_t prepare_fft_transforms();
+template <typename T>
+void launch_fft_forward(cudaStream_t s, int num_sms, int N, int n, View g, const void *f, bool f32,
+                        const double *u0, const double *u0coef, const T *wk,
+                        const typename Cx<T>::type *tw);
+template <typename T>
+void launch_fft_inverse(cudaStream_t s, int num_sms, int N, int n, double *u, View z0, View z1,
+                        const int *final_buf, const T *wk, const typename Cx<T>::type *tw,
+                        bool accumulate, bool imag_check, unsigned long long *imag_bits);
+
 // ---- residual of eq. (1) without FP64 arithmetic (residual_fx.cu) ----
 int residual_fx_blocks(int num_sms);
 void launch_residual_fx(cudaStream_t s, int blocks, int N, int n, int off, double kappa, float *r,

@@ -65,8 +65,15 @@ __device__ __forceinline__ float scale_down(float x, int s) {
 }
 __device__ __forceinline__ DF df_scale_down(DF x, int s) { return {scale_down(x.hi, s), scale_down(x.lo, s)}; }
 
-// FP64 bits -> float-float: |x| >= 2^-100 kept (hi truncated to 24 bits, lo the rest),
-// smaller values are 0; Inf/NaN give NaN
+// Integer -> FP32 without a conversion instruction (conversions issue on GB300's slow
+// FP64 pipe): for 0 <= x < 2^23, the FP32 number with x in the mantissa of 2^23 is
+// 2^23 + x exactly; subtracting 2^23 leaves x.
+__device__ __forceinline__ float u23_to_float(unsigned x) {
+  return __fsub_rn(__uint_as_float(0x4B000000u | x), 8388608.f);
+}
+
+// FP64 bits -> float-float: |x| >= 2^-100 kept (hi truncated to 24 bits, lo the rest,
+// rounded to 24 bits), smaller values are 0; Inf/NaN give NaN
 __device__ __forceinline__ DF split_bits(uint32_t hw, uint32_t lw) {
   const int e = (int)((hw >> 20) & 0x7FFu);
   if (e == 0x7FF || e > 1023 + 127) return {__int_as_float(0x7FC00000), 0.f};
@@ -76,7 +83,9 @@ __device__ __forceinline__ DF split_bits(uint32_t hw, uint32_t lw) {
   // remaining 29 bits, weight 2^(e - 1075), e - 1075 in [-152, 52]
   const int ex = e - 1075;
   const int a = ex >> 1;
-  float lo = __fmul_rn(__fmul_rn(__uint2float_rn(lw & 0x1FFFFFFFu), pow2f(a)), pow2f(ex - a));
+  const unsigned rem = lw & 0x1FFFFFFFu;  // 29 bits = 23 high + 6 low
+  const float remf = __fmaf_rn(u23_to_float(rem >> 6), 64.f, u23_to_float(rem & 63u));
+  float lo = __fmul_rn(__fmul_rn(remf, pow2f(a)), pow2f(ex - a));
   if (sign) lo = -lo;
   return {hi, lo};
 }
@@ -98,16 +107,29 @@ __device__ __forceinline__ long long to_fixed(uint32_t hw, uint32_t lw, int S) {
   return (hw & 0x80000000u) ? -sv : sv;
 }
 
-// exact 64-bit integer -> float-float (hi = rounded to 24 bits, lo = rounded remainder)
+// 64-bit integer |v| < 2^62 -> float-float, about 2^-47 relative.  64-bit integer <-> float
+// conversions run on the FP64 pipe, so v is cut into three 21-bit chunks that FP32 holds
+// exactly, v = t2 2^42 + t1 2^21 + t0 (t2 signed), and summed error-free.
 __device__ __forceinline__ DF df_from_ll(long long v) {
-  const float hi = __ll2float_rn(v);
-  const long long rest = v - __float2ll_rz(hi);
-  return {hi, __ll2float_rn(rest)};
+  const unsigned lo32 = (unsigned)v, hi32 = (unsigned)((unsigned long long)v >> 32);
+  const int t2 = (int)hi32 >> 10;
+  const unsigned t1 = __funnelshift_r(lo32, hi32, 21) & 0x1FFFFFu;
+  const unsigned t0 = lo32 & 0x1FFFFFu;
+  // t2 in [-2^20, 2^20): offset by 2^20 into [0, 2^21)
+  const float f2 = __fsub_rn(u23_to_float((unsigned)(t2 + (1 << 20))), 1048576.f);
+  DF s = two_sum(__fmul_rn(f2, 4398046511104.f),                 // 2^42
+                 __fmul_rn(u23_to_float(t1), 2097152.f));         // 2^21
+  s.lo = __fadd_rn(s.lo, u23_to_float(t0));
+  return fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ DF df_shfl_down(DF a, int o) {
+  return {__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o)};
 }
 
 // grid-stride over tiles (x tile, y tile, k); part[2 * blockIdx.x] = sum |r|^2 (FP32 per
 // tile), part[2 * blockIdx.x + 1] = sum |fhat|^2 when want_f
-__global__ void __launch_bounds__(kFxThreads)
+__global__ void __launch_bounds__(kFxThreads, 4)
 k_residual_fx(int N, int n, int off, float *__restrict__ r, const double *__restrict__ u,
               const double *__restrict__ f, const double *__restrict__ u0,
               const double *__restrict__ u0coef, const double *__restrict__ bd,
@@ -119,7 +141,8 @@ k_residual_fx(int N, int n, int off, float *__restrict__ r, const double *__rest
   const int tx = (N + kFxCols - 1) / kFxCols, ty = (N + kFxRows - 1) / kFxRows;
   const long long tiles = (long long)tx * ty * n;
   const DF ihd = split(ih2);  // kappa / h^2
-  double ar = 0.0, af = 0.0;
+  // per-thread sums of the per-tile FP32 sums in float-float (no FP64 arithmetic)
+  DF ar = {0.f, 0.f}, af = {0.f, 0.f};
   for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
     const int k = (int)(t / ((long long)tx * ty));
     const int rem = (int)(t - (long long)k * tx * ty);
@@ -188,28 +211,29 @@ k_residual_fx(int N, int n, int off, float *__restrict__ r, const double *__rest
         }
       }
     }
-    ar += (double)rowr;
-    af += (double)rowf;
+    ar = df_add(ar, DF{rowr, 0.f});
+    af = df_add(af, DF{rowf, 0.f});
     __syncthreads();  // the shared tile is reused by the next tile
   }
+  // CTA sums: float-float over the warps, one conversion to FP64 per CTA
   for (int o = 16; o > 0; o >>= 1) {
-    ar += __shfl_down_sync(0xffffffffu, ar, o);
-    af += __shfl_down_sync(0xffffffffu, af, o);
+    ar = df_add(ar, df_shfl_down(ar, o));
+    af = df_add(af, df_shfl_down(af, o));
   }
-  __shared__ double redd[2][kFxThreads / 32];
+  __shared__ DF redf[2][kFxThreads / 32];
   if (lane == 0) {
-    redd[0][warp] = ar;
-    redd[1][warp] = af;
+    redf[0][warp] = ar;
+    redf[1][warp] = af;
   }
   __syncthreads();
   if (tid == 0) {
-    double s0 = 0.0, s1 = 0.0;
+    DF s0 = {0.f, 0.f}, s1 = {0.f, 0.f};
     for (int w = 0; w < kFxThreads / 32; w++) {
-      s0 += redd[0][w];
-      s1 += redd[1][w];
+      s0 = df_add(s0, redf[0][w]);
+      s1 = df_add(s1, redf[1][w]);
     }
-    part[2 * blockIdx.x] = s0;
-    part[2 * blockIdx.x + 1] = s1;
+    part[2 * blockIdx.x] = (double)s0.hi + (double)s0.lo;
+    part[2 * blockIdx.x + 1] = (double)s1.hi + (double)s1.lo;
   }
 }
 

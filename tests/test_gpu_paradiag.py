@@ -79,10 +79,14 @@ def oracle_paradiag(N, n, tau, alpha, f, u0, omega_mode="lfa", tol=1e-10):
     return u, fhat, iters, relres
 
 
-@pytest.mark.parametrize("N,n,alpha", [(15, 4, 1e-2), (63, 16, 1e-3), (127, 8, 1e-3)])
-def test_transforms_fp64(N, n, alpha):
+@pytest.mark.parametrize("fft", [1, 0])
+@pytest.mark.parametrize("N,n,alpha", [(15, 4, 1e-2), (63, 16, 1e-3), (127, 8, 1e-3), (31, 128, 1e-3),
+                                       (31, 2, 0.5)])
+def test_transforms_fp64(N, n, alpha, fft):
+    """FP64 time transforms, the Gamma-weighted FFTs of the alpha-circulant V (fft = 1) and
+    the dense products (fft = 0), against the oracle's dense products."""
     rng = np.random.default_rng(N)
-    c = api.alpha_circulant_context(N, n, 1.0 / n, alpha)
+    c = api.alpha_circulant_context(N, n, 1.0 / n, alpha, fft_transforms=fft)
     lam, V, Vinv = core.alpha_circulant(n, 1.0 / n, alpha)
     f = rng.uniform(-1, 1, (n, N, N))
     u0 = inputs.sine_initial_value(N)
@@ -176,15 +180,16 @@ def test_paradiag_without_V_is_a_state_error():
     assert e.value.status == "PD_ERR_STATE"
 
 
-@pytest.mark.parametrize("tc", [1, 0])
-@pytest.mark.parametrize("N,n", [(127, 16), (255, 64), (255, 5)])
-def test_transforms_fp32_tensor_cores(tc, N, n):
-    """FP32 context: TF32x3 tcgen05 transforms (tc=1) and FP32 CUDA-core products (tc=0)
-    against the FP64 oracle: relative error per shift vector of a few 1e-7 (TF32x3
-    keeps about 21 bits per product; fhat is rounded to FP32 first)."""
+@pytest.mark.parametrize("path", ["fft", "tc", "cuda_cores"])
+@pytest.mark.parametrize("N,n", [(127, 16), (255, 64), (255, 5), (127, 128)])
+def test_transforms_fp32(path, N, n):
+    """FP32 context: Gamma-weighted FFTs (path fft), TF32x3 tcgen05 products (tc) and FP32
+    CUDA-core products against the FP64 oracle: relative error per shift vector of a few
+    1e-7 (TF32x3 keeps about 21 bits per product; fhat is rounded to FP32 first)."""
     alpha = 1e-3
     rng = np.random.default_rng(N + n)
-    c = api.alpha_circulant_context(N, n, 1.0 / n, alpha, precision=1, tensor_transforms=tc)
+    c = api.alpha_circulant_context(N, n, 1.0 / n, alpha, precision=1,
+                                    tensor_transforms=int(path == "tc"), fft_transforms=int(path == "fft"))
     lam, V, Vinv = core.alpha_circulant(n, 1.0 / n, alpha)
     f = rng.uniform(-1, 1, (n, N, N))
     u0 = inputs.sine_initial_value(N)
