@@ -96,7 +96,7 @@ typedef struct {
 } pd_config;
 
 /* Fills cfg with V(1,1), coarsest 3, maxit 100, tol 1e-10, omega_mode 1, FP64,
- * Vanka, inner_tol 1e-6, max_refine 12, imag_check 1, inner_maxit 3, stall_ratio 0.5,
+ * Vanka, inner_tol 1e-6, max_refine 12, imag_check 1, inner_maxit 2, stall_ratio 0.5,
  * fused 1, tensor_transforms 1, fused_variant 0, kappa 1, outer_maxit 0, cuda_graphs 1,
  * fx_residual 1, fft_transforms 1. */
 void pd_config_default(pd_config *cfg);

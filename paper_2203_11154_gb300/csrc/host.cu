@@ -1238,7 +1238,7 @@ void pd_config_default(pd_config *cfg) {
   cfg->inner_tol = 1e-6;
   cfg->max_refine = 12;
   cfg->imag_check = 1;
-  cfg->inner_maxit = 3;
+  cfg->inner_maxit = 2;
   cfg->stall_ratio = 0.5;
   cfg->fused = 1;
   cfg->tensor_transforms = 1;

@@ -36,7 +36,7 @@ def test_config_defaults():
     c = api.config()
     assert (c.cycle_gamma, c.nu1, c.nu2, c.coarsest_n, c.maxit) == (1, 1, 1, 3, 100)
     assert c.tol == 1e-10 and c.omega_mode == 1 and c.precision == 0 and c.smoother == 0
-    assert c.kappa == 1.0 and c.outer_maxit == 0 and c.max_refine == 12 and c.inner_maxit == 3
+    assert c.kappa == 1.0 and c.outer_maxit == 0 and c.max_refine == 12 and c.inner_maxit == 2
 
 
 def test_alpha_circulant_matches_oracle():
