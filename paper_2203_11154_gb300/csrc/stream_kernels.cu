@@ -67,17 +67,24 @@ template <typename C> __device__ __forceinline__ C sel(bool keep, C x) {
 
 // copies the lane's two complex values of row `row`, columns a, a+1, of shift plane
 // `base` into shared memory; zeros outside the grid (rows, or a pair wholly outside)
-template <typename C>
+// IN: the caller guarantees row and both columns inside the grid (no predicates)
+template <typename C, bool IN = false>
 __device__ __forceinline__ void load_pair(uint32_t dst, const C *base, long long pitch, int N, int row,
                                           int a) {
-  const bool ok = (unsigned)row < (unsigned)N && a >= 0 && a < N;
+  const bool ok = IN || ((unsigned)row < (unsigned)N && a >= 0 && a < N);
   const C *src = base + (ok ? (long long)row * pitch + a : 0);
   if (sizeof(C) == 8) {
     cp_async16(dst, src, ok ? 16 : 0);  // a+1 may be the padding column: masked on use
   } else {
     cp_async16(dst, src, ok ? 16 : 0);
-    cp_async16(dst + 16, src + 1, (ok && a + 1 < N) ? 16 : 0);
+    cp_async16(dst + 16, src + 1, (IN || (ok && a + 1 < N)) ? 16 : 0);
   }
+}
+
+// A unit (strip x segment of one shift) whose loaded rows and columns, coarse rows and
+// columns included, all lie inside the grid: its boundary tests fold away.
+__device__ __forceinline__ bool interior_unit(int N, int x0, int y0, int y1) {
+  return x0 >= 4 && x0 + 61 <= N && y0 >= 4 && y1 + 4 <= N;
 }
 
 template <typename C> __device__ __forceinline__ Pair<C> read_pair(const C *s) {
@@ -85,6 +92,170 @@ template <typename C> __device__ __forceinline__ Pair<C> read_pair(const C *s) {
   p.v[0] = s[0];
   p.v[1] = s[1];
   return p;
+}
+
+// one unit of k_sr_stream (see above); IN: interior_unit
+template <typename T, bool ZZERO, bool NORM, bool IN>
+__device__ __forceinline__ void sr_unit(int N, int seg, int u, int nsx, int nsy, int Nc, int lane,
+                                        typename Cx<T>::type *ring, const View &z, const View &b,
+                                        const View &zout, const View &bc,
+                                        const Coef<T> *__restrict__ coef,
+                                        double *__restrict__ partials, int part_stride) {
+  using C = typename Cx<T>::type;
+  const int sx = u % nsx, sy = (u / nsx) % nsy, j = u / (nsx * nsy);
+  const Coef<T> cf = coef[j];
+  const int x0 = sx * kStripOut, y0 = sy * seg, y1 = min(y0 + seg, N);
+  const int xend = min(x0 + kStripOut, N);
+  const int a = x0 - 4 + 2 * lane;  // this lane's columns a, a+1
+  const bool cin0 = IN || (a >= 0 && a < N), cin1 = IN || (a + 1 >= 0 && a + 1 < N);
+  const bool out0 = a >= x0 && a < xend, out1 = a + 1 >= x0 && a + 1 < xend;
+  const C *zb = reinterpret_cast<const C *>(z.p) + (long long)j * z.plane;
+  const C *bb = reinterpret_cast<const C *>(b.p) + (long long)j * b.plane;
+  C *zo = reinterpret_cast<C *>(zout.p) + (long long)j * zout.plane;
+  C *bco = reinterpret_cast<C *>(bc.p) + (long long)j * bc.plane;
+  const int L = y1 - y0 + 7;  // rows y0-3 .. y1+3
+  auto slot_z = [&](int s) { return ring + ((s % kDepth) * 2 + 0) * kLanes * 2 + lane * 2; };
+  auto slot_b = [&](int s) { return ring + ((s % kDepth) * 2 + 1) * kLanes * 2 + lane * 2; };
+  auto issue = [&](int s) {
+    if (s < L) {
+      const int row = y0 - 3 + s;
+      if (!ZZERO) load_pair<C, IN>(smem_u32(slot_z(s)), zb, z.pitch, N, row, a);
+      load_pair<C, IN>(smem_u32(slot_b(s)), bb, b.pitch, N, row, a);
+    }
+    cp_commit();
+  };
+#pragma unroll
+  for (int s = 0; s < kDepth; s++) issue(s);
+  // register windows (rows relative to the row i being loaded)
+  C zm2[2], zm1[2], bm1[2], bm2[2], bm3[2];
+  C rm3[4], rm2[4], rm1[4], zpm4[4], zpm3[4], zpm2[4], rpm5[3], rpm4[3], rpm3[3];
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    rm3[q] = rm2[q] = rm1[q] = zpm4[q] = zpm3[q] = zpm2[q] = czero<C>();
+    if (q < 3) rpm5[q] = rpm4[q] = rpm3[q] = czero<C>();
+    if (q < 2) zm2[q] = zm1[q] = bm1[q] = bm2[q] = bm3[q] = czero<C>();
+  }
+  T acc = 0;
+  for (int s = 0; s < L; s++) {
+    const int i = y0 - 3 + s;
+    cp_wait<kDepth - 1>();
+    C zi[2], bi[2];
+    {
+      const Pair<C> pb = read_pair(slot_b(s));
+      bi[0] = pb.v[0];
+      bi[1] = sel(cin1, pb.v[1]);
+      if (ZZERO) {
+        zi[0] = zi[1] = czero<C>();
+      } else {
+        const Pair<C> pz = read_pair(slot_z(s));
+        zi[0] = pz.v[0];
+        zi[1] = sel(cin1, pz.v[1]);
+      }
+    }
+    issue(s + kDepth);
+    // rt of z on row i-1
+    const bool r_in = IN || (unsigned)(i - 1) < (unsigned)N;
+    C rn[4];
+    {
+      const C zL = shfl_up1(zm1[1]), zR = shfl_dn1(zm1[0]);
+      C r0 = bm1[0], r1 = bm1[1];
+      if (!ZZERO) {
+        r0 = csub(cadd(r0, cadd(cadd(zm2[0], zi[0]), cadd(zL, zm1[1]))), cmul(cf.d, zm1[0]));
+        r1 = csub(cadd(r1, cadd(cadd(zm2[1], zi[1]), cadd(zm1[0], zR))), cmul(cf.d, zm1[1]));
+      }
+      r0 = sel(r_in && cin0, r0);
+      r1 = sel(r_in && cin1, r1);
+      if (NORM && i - 1 >= y0 && i - 1 < y1) {
+        if (out0) acc += r0.x * r0.x + r0.y * r0.y;
+        if (out1) acc += r1.x * r1.x + r1.y * r1.y;
+      }
+      rn[0] = shfl_up1(r1);
+      rn[1] = r0;
+      rn[2] = r1;
+      rn[3] = shfl_dn1(r0);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      rm3[q] = rm2[q];
+      rm2[q] = rm1[q];
+      rm1[q] = rn[q];
+    }
+    // z' = z + omega M rt on row i-2
+    const bool p_in = IN || (unsigned)(i - 2) < (unsigned)N;
+    C zp[2];
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+      const C e = cadd(cadd(rm3[k + 1], rm1[k + 1]), cadd(rm2[k], rm2[k + 2]));
+      const C co = cadd(cadd(rm3[k], rm3[k + 2]), cadd(rm1[k], rm1[k + 2]));
+      C upd = cmul(cf.ca, rm2[k + 1]);
+      upd = cfma(cf.cb, e, upd);
+      upd = cfma(cf.cc, co, upd);
+      zp[k] = sel(p_in && (k ? cin1 : cin0), ZZERO ? upd : cadd(zm2[k], upd));
+    }
+    if (i - 2 >= y0 && i - 2 < y1) {
+      C *dst = zo + (long long)(i - 2) * zout.pitch + a;
+      if (out0) dst[0] = zp[0];
+      if (out1) dst[1] = zp[1];
+    }
+    {
+      const C l = shfl_up1(zp[1]), r = shfl_dn1(zp[0]);
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        zpm4[q] = zpm3[q];
+        zpm3[q] = zpm2[q];
+      }
+      zpm2[0] = l;
+      zpm2[1] = zp[0];
+      zpm2[2] = zp[1];
+      zpm2[3] = r;
+    }
+    // rt of z' on row i-3
+    const bool q_in = IN || (unsigned)(i - 3) < (unsigned)N;
+    C rp[2];
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+      const C nb = cadd(cadd(zpm4[k + 1], zpm2[k + 1]), cadd(zpm3[k], zpm3[k + 2]));
+      rp[k] = sel(q_in && (k ? cin1 : cin0), csub(cadd(bm3[k], nb), cmul(cf.d, zpm3[k + 1])));
+    }
+    {
+      const C r = shfl_dn1(rp[0]);
+#pragma unroll
+      for (int q = 0; q < 3; q++) {
+        rpm5[q] = rpm4[q];
+        rpm4[q] = rpm3[q];
+      }
+      rpm3[0] = rp[0];
+      rpm3[1] = rp[1];
+      rpm3[2] = r;
+    }
+    // full weighting around the coarse point (I, J) at fine (i-4, a+1)
+    const int cr = i - 4;
+    if ((cr & 1) && cr >= y0 && cr < y1 && out1) {
+      const int I = (cr - 1) >> 1, J = a >> 1;
+      if (IN || (I < Nc && J < Nc)) {
+        const C e = cadd(cadd(rpm5[1], rpm3[1]), cadd(rpm4[0], rpm4[2]));
+        const C co = cadd(cadd(rpm5[0], rpm5[2]), cadd(rpm3[0], rpm3[2]));
+        const C sum = cadd(cadd(cscale(rpm4[1], (T)4), cscale(e, (T)2)), co);
+        bco[(long long)I * bc.pitch + J] = cscale(sum, (T)0.25);
+      }
+    }
+    zm2[0] = zm1[0];
+    zm2[1] = zm1[1];
+    zm1[0] = zi[0];
+    zm1[1] = zi[1];
+    bm3[0] = bm2[0];
+    bm3[1] = bm2[1];
+    bm2[0] = bm1[0];
+    bm2[1] = bm1[1];
+    bm1[0] = bi[0];
+    bm1[1] = bi[1];
+  }
+  cp_wait<0>();
+  if (NORM) {
+    double s = (double)acc;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) partials[(long long)j * part_stride + sy * nsx + sx] = s;
+  }
 }
 
 template <typename T, bool ZZERO, bool NORM>
@@ -104,160 +275,146 @@ k_sr_stream(int N, int n, int seg, View z, View b, View zout, View bc,
   for (int u = gw; u < total; u += nw) {
     const int sx = u % nsx, sy = (u / nsx) % nsy, j = u / (nsx * nsy);
     if (active && !active[j]) continue;
-    const Coef<T> cf = coef[j];
     const int x0 = sx * kStripOut, y0 = sy * seg, y1 = min(y0 + seg, N);
-    const int xend = min(x0 + kStripOut, N);
-    const int a = x0 - 4 + 2 * lane;  // this lane's columns a, a+1
-    const bool cin0 = a >= 0 && a < N, cin1 = a + 1 >= 0 && a + 1 < N;
-    const bool out0 = a >= x0 && a < xend, out1 = a + 1 >= x0 && a + 1 < xend;
-    const C *zb = reinterpret_cast<const C *>(z.p) + (long long)j * z.plane;
-    const C *bb = reinterpret_cast<const C *>(b.p) + (long long)j * b.plane;
-    C *zo = reinterpret_cast<C *>(zout.p) + (long long)j * zout.plane;
-    C *bco = reinterpret_cast<C *>(bc.p) + (long long)j * bc.plane;
-    const int L = y1 - y0 + 7;  // rows y0-3 .. y1+3
-    auto slot_z = [&](int s) { return ring + ((s % kDepth) * 2 + 0) * kLanes * 2 + lane * 2; };
-    auto slot_b = [&](int s) { return ring + ((s % kDepth) * 2 + 1) * kLanes * 2 + lane * 2; };
-    auto issue = [&](int s) {
-      if (s < L) {
-        const int row = y0 - 3 + s;
-        if (!ZZERO) load_pair<C>(smem_u32(slot_z(s)), zb, z.pitch, N, row, a);
-        load_pair<C>(smem_u32(slot_b(s)), bb, b.pitch, N, row, a);
-      }
-      cp_commit();
-    };
+    if (interior_unit(N, x0, y0, y1))
+      sr_unit<T, ZZERO, NORM, true>(N, seg, u, nsx, nsy, Nc, lane, ring, z, b, zout, bc, coef,
+                                    partials, part_stride);
+    else
+      sr_unit<T, ZZERO, NORM, false>(N, seg, u, nsx, nsy, Nc, lane, ring, z, b, zout, bc, coef,
+                                     partials, part_stride);
+  }
+}
+
+// one unit of k_ps_stream (see above); IN: interior_unit
+template <typename T, bool IN>
+__device__ __forceinline__ void ps_unit(int N, int seg, int u, int nsx, int nsy, int Nc, int lane,
+                                        typename Cx<T>::type *ring, const View &z, const View &e,
+                                        const View &b, const View &zout,
+                                        const Coef<T> *__restrict__ coef) {
+  using C = typename Cx<T>::type;
+  const int sx = u % nsx, sy = (u / nsx) % nsy, j = u / (nsx * nsy);
+  const Coef<T> cf = coef[j];
+  const int x0 = sx * kStripOut, y0 = sy * seg, y1 = min(y0 + seg, N);
+  const int xend = min(x0 + kStripOut, N);
+  const int a = x0 - 4 + 2 * lane;
+  const int J = a >> 1;  // coarse column of the odd fine column a+1
+  const bool cin0 = IN || (a >= 0 && a < N), cin1 = IN || (a + 1 >= 0 && a + 1 < N);
+  const bool out0 = a >= x0 && a < xend, out1 = a + 1 >= x0 && a + 1 < xend;
+  const C *zb = reinterpret_cast<const C *>(z.p) + (long long)j * z.plane;
+  const C *eb = reinterpret_cast<const C *>(e.p) + (long long)j * e.plane;
+  const C *bb = reinterpret_cast<const C *>(b.p) + (long long)j * b.plane;
+  C *zo = reinterpret_cast<C *>(zout.p) + (long long)j * zout.plane;
+  const int L = y1 - y0 + 4;  // rows y0-2 .. y1+1
+  auto slot = [&](int s, int k) { return ring + ((s % kDepth) * 3 + k) * kLanes * 2 + lane * 2; };
+  // coarse row m (complex at column J) into the slot's third row; zero outside
+  auto load_coarse = [&](uint32_t dst, int m) {
+    const bool ok = IN || ((unsigned)m < (unsigned)Nc && (unsigned)J < (unsigned)Nc);
+    const C *src = eb + (ok ? (long long)m * e.pitch + J : 0);
+    if (sizeof(C) == 8) cp_async8(dst, src, ok ? 8 : 0);
+    else cp_async16(dst, src, ok ? 16 : 0);
+  };
+  auto issue = [&](int s) {
+    if (s < L) {
+      const int row = y0 - 2 + s;
+      load_pair<C, IN>(smem_u32(slot(s, 0)), zb, z.pitch, N, row, a);
+      load_pair<C, IN>(smem_u32(slot(s, 1)), bb, b.pitch, N, row, a);
+      if (!(row & 1)) load_coarse(smem_u32(slot(s, 2)), row >> 1);  // coarse row m at fine 2m
+    }
+    cp_commit();
+  };
+  // coarse row y0/2 - 2: the first fine row y0 - 2 (even) shifts it into eprev and
+  // loads row y0/2 - 1 into ecur
+  C eprev = czero<C>(), ecur;
+  {
+    const int m = y0 / 2 - 2;
+    const bool ok = IN || ((unsigned)m < (unsigned)Nc && (unsigned)J < (unsigned)Nc);
+    ecur = ok ? eb[(long long)m * e.pitch + J] : czero<C>();
+  }
 #pragma unroll
-    for (int s = 0; s < kDepth; s++) issue(s);
-    // register windows (rows relative to the row i being loaded)
-    C zm2[2], zm1[2], bm1[2], bm2[2], bm3[2];
-    C rm3[4], rm2[4], rm1[4], zpm4[4], zpm3[4], zpm2[4], rpm5[3], rpm4[3], rpm3[3];
+  for (int s = 0; s < kDepth; s++) issue(s);
+  C zz1[4], zz0[4], bm1[2], rm3[4], rm2[4], rm1[4];  // z'' rows i-1 (zz1), i-2 (zz0)
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    zz1[q] = zz0[q] = rm3[q] = rm2[q] = rm1[q] = czero<C>();
+    if (q < 2) bm1[q] = czero<C>();
+  }
+  for (int s = 0; s < L; s++) {
+    const int i = y0 - 2 + s;
+    cp_wait<kDepth - 1>();
+    C zi[2], bi[2];
+    {
+      const Pair<C> pz = read_pair(slot(s, 0));
+      const Pair<C> pb = read_pair(slot(s, 1));
+      zi[0] = pz.v[0];
+      zi[1] = sel(cin1, pz.v[1]);
+      bi[0] = pb.v[0];
+      bi[1] = sel(cin1, pb.v[1]);
+      if (!(i & 1)) {
+        eprev = ecur;
+        ecur = *slot(s, 2);
+      }
+    }
+    issue(s + kDepth);
+    // z'' = z' + P e_c on row i: odd rows sit on coarse row (i-1)/2 = ecur, even rows
+    // between eprev (i/2 - 1) and ecur (i/2); odd columns on coarse column J, even
+    // columns between J-1 (from the left lane) and J
+    const bool i_in = IN || (unsigned)i < (unsigned)N;
+    C zn[4];
+    {
+      const C ev = (i & 1) ? ecur : cscale(cadd(eprev, ecur), (T)0.5);
+      const C evl = shfl_up1(ev);
+      const C p0 = cscale(cadd(evl, ev), (T)0.5), p1 = ev;
+      const C z0 = sel(i_in && cin0, cadd(zi[0], p0));
+      const C z1 = sel(i_in && cin1, cadd(zi[1], p1));
+      zn[0] = shfl_up1(z1);
+      zn[1] = z0;
+      zn[2] = z1;
+      zn[3] = shfl_dn1(z0);
+    }
+    // rt of z'' on row i-1
+    const bool r_in = IN || (unsigned)(i - 1) < (unsigned)N;
+    C rn[4];
+    {
+      C r0 = csub(cadd(bm1[0], cadd(cadd(zz0[1], zn[1]), cadd(zz1[0], zz1[2]))), cmul(cf.d, zz1[1]));
+      C r1 = csub(cadd(bm1[1], cadd(cadd(zz0[2], zn[2]), cadd(zz1[1], zz1[3]))), cmul(cf.d, zz1[2]));
+      r0 = sel(r_in && cin0, r0);
+      r1 = sel(r_in && cin1, r1);
+      rn[0] = shfl_up1(r1);
+      rn[1] = r0;
+      rn[2] = r1;
+      rn[3] = shfl_dn1(r0);
+    }
 #pragma unroll
     for (int q = 0; q < 4; q++) {
-      rm3[q] = rm2[q] = rm1[q] = zpm4[q] = zpm3[q] = zpm2[q] = czero<C>();
-      if (q < 3) rpm5[q] = rpm4[q] = rpm3[q] = czero<C>();
-      if (q < 2) zm2[q] = zm1[q] = bm1[q] = bm2[q] = bm3[q] = czero<C>();
+      rm3[q] = rm2[q];
+      rm2[q] = rm1[q];
+      rm1[q] = rn[q];
     }
-    T acc = 0;
-    for (int s = 0; s < L; s++) {
-      const int i = y0 - 3 + s;
-      cp_wait<kDepth - 1>();
-      C zi[2], bi[2];
-      {
-        const Pair<C> pb = read_pair(slot_b(s));
-        bi[0] = pb.v[0];
-        bi[1] = sel(cin1, pb.v[1]);
-        if (ZZERO) {
-          zi[0] = zi[1] = czero<C>();
-        } else {
-          const Pair<C> pz = read_pair(slot_z(s));
-          zi[0] = pz.v[0];
-          zi[1] = sel(cin1, pz.v[1]);
-        }
-      }
-      issue(s + kDepth);
-      // rt of z on row i-1
-      const bool r_in = (unsigned)(i - 1) < (unsigned)N;
-      C rn[4];
-      {
-        const C zL = shfl_up1(zm1[1]), zR = shfl_dn1(zm1[0]);
-        C r0 = bm1[0], r1 = bm1[1];
-        if (!ZZERO) {
-          r0 = csub(cadd(r0, cadd(cadd(zm2[0], zi[0]), cadd(zL, zm1[1]))), cmul(cf.d, zm1[0]));
-          r1 = csub(cadd(r1, cadd(cadd(zm2[1], zi[1]), cadd(zm1[0], zR))), cmul(cf.d, zm1[1]));
-        }
-        r0 = sel(r_in && cin0, r0);
-        r1 = sel(r_in && cin1, r1);
-        if (NORM && i - 1 >= y0 && i - 1 < y1) {
-          if (out0) acc += r0.x * r0.x + r0.y * r0.y;
-          if (out1) acc += r1.x * r1.x + r1.y * r1.y;
-        }
-        rn[0] = shfl_up1(r1);
-        rn[1] = r0;
-        rn[2] = r1;
-        rn[3] = shfl_dn1(r0);
-      }
-#pragma unroll
-      for (int q = 0; q < 4; q++) {
-        rm3[q] = rm2[q];
-        rm2[q] = rm1[q];
-        rm1[q] = rn[q];
-      }
-      // z' = z + omega M rt on row i-2
-      const bool p_in = (unsigned)(i - 2) < (unsigned)N;
-      C zp[2];
+    // z''' = z'' + omega M rt on row i-2 (z''(i-2) is zz0 before the shift below)
+    if (i - 2 >= y0 && i - 2 < y1) {
+      C out[2];
 #pragma unroll
       for (int k = 0; k < 2; k++) {
-        const C e = cadd(cadd(rm3[k + 1], rm1[k + 1]), cadd(rm2[k], rm2[k + 2]));
+        const C e2 = cadd(cadd(rm3[k + 1], rm1[k + 1]), cadd(rm2[k], rm2[k + 2]));
         const C co = cadd(cadd(rm3[k], rm3[k + 2]), cadd(rm1[k], rm1[k + 2]));
         C upd = cmul(cf.ca, rm2[k + 1]);
-        upd = cfma(cf.cb, e, upd);
+        upd = cfma(cf.cb, e2, upd);
         upd = cfma(cf.cc, co, upd);
-        zp[k] = sel(p_in && (k ? cin1 : cin0), ZZERO ? upd : cadd(zm2[k], upd));
+        out[k] = cadd(zz0[k + 1], upd);
       }
-      if (i - 2 >= y0 && i - 2 < y1) {
-        C *dst = zo + (long long)(i - 2) * zout.pitch + a;
-        if (out0) dst[0] = zp[0];
-        if (out1) dst[1] = zp[1];
-      }
-      {
-        const C l = shfl_up1(zp[1]), r = shfl_dn1(zp[0]);
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-          zpm4[q] = zpm3[q];
-          zpm3[q] = zpm2[q];
-        }
-        zpm2[0] = l;
-        zpm2[1] = zp[0];
-        zpm2[2] = zp[1];
-        zpm2[3] = r;
-      }
-      // rt of z' on row i-3
-      const bool q_in = (unsigned)(i - 3) < (unsigned)N;
-      C rp[2];
-#pragma unroll
-      for (int k = 0; k < 2; k++) {
-        const C nb = cadd(cadd(zpm4[k + 1], zpm2[k + 1]), cadd(zpm3[k], zpm3[k + 2]));
-        rp[k] = sel(q_in && (k ? cin1 : cin0), csub(cadd(bm3[k], nb), cmul(cf.d, zpm3[k + 1])));
-      }
-      {
-        const C r = shfl_dn1(rp[0]);
-#pragma unroll
-        for (int q = 0; q < 3; q++) {
-          rpm5[q] = rpm4[q];
-          rpm4[q] = rpm3[q];
-        }
-        rpm3[0] = rp[0];
-        rpm3[1] = rp[1];
-        rpm3[2] = r;
-      }
-      // full weighting around the coarse point (I, J) at fine (i-4, a+1)
-      const int cr = i - 4;
-      if ((cr & 1) && cr >= y0 && cr < y1 && out1) {
-        const int I = (cr - 1) >> 1, J = a >> 1;
-        if (I < Nc && J < Nc) {
-          const C e = cadd(cadd(rpm5[1], rpm3[1]), cadd(rpm4[0], rpm4[2]));
-          const C co = cadd(cadd(rpm5[0], rpm5[2]), cadd(rpm3[0], rpm3[2]));
-          const C sum = cadd(cadd(cscale(rpm4[1], (T)4), cscale(e, (T)2)), co);
-          bco[(long long)I * bc.pitch + J] = cscale(sum, (T)0.25);
-        }
-      }
-      zm2[0] = zm1[0];
-      zm2[1] = zm1[1];
-      zm1[0] = zi[0];
-      zm1[1] = zi[1];
-      bm3[0] = bm2[0];
-      bm3[1] = bm2[1];
-      bm2[0] = bm1[0];
-      bm2[1] = bm1[1];
-      bm1[0] = bi[0];
-      bm1[1] = bi[1];
+      C *dst = zo + (long long)(i - 2) * zout.pitch + a;
+      if (out0) dst[0] = out[0];
+      if (out1) dst[1] = out[1];
     }
-    cp_wait<0>();
-    if (NORM) {
-      double s = (double)acc;
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-      if (lane == 0) partials[(long long)j * part_stride + sy * nsx + sx] = s;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      zz0[q] = zz1[q];
+      zz1[q] = zn[q];
     }
+    bm1[0] = bi[0];
+    bm1[1] = bi[1];
   }
+  cp_wait<0>();
 }
 
 template <typename T>
@@ -276,128 +433,11 @@ k_ps_stream(int N, int n, int seg, View z, View e, View b, View zout,
   for (int u = gw; u < total; u += nw) {
     const int sx = u % nsx, sy = (u / nsx) % nsy, j = u / (nsx * nsy);
     if (active && !active[j]) continue;
-    const Coef<T> cf = coef[j];
     const int x0 = sx * kStripOut, y0 = sy * seg, y1 = min(y0 + seg, N);
-    const int xend = min(x0 + kStripOut, N);
-    const int a = x0 - 4 + 2 * lane;
-    const int J = a >> 1;  // coarse column of the odd fine column a+1
-    const bool cin0 = a >= 0 && a < N, cin1 = a + 1 >= 0 && a + 1 < N;
-    const bool out0 = a >= x0 && a < xend, out1 = a + 1 >= x0 && a + 1 < xend;
-    const C *zb = reinterpret_cast<const C *>(z.p) + (long long)j * z.plane;
-    const C *eb = reinterpret_cast<const C *>(e.p) + (long long)j * e.plane;
-    const C *bb = reinterpret_cast<const C *>(b.p) + (long long)j * b.plane;
-    C *zo = reinterpret_cast<C *>(zout.p) + (long long)j * zout.plane;
-    const int L = y1 - y0 + 4;  // rows y0-2 .. y1+1
-    auto slot = [&](int s, int k) { return ring + ((s % kDepth) * 3 + k) * kLanes * 2 + lane * 2; };
-    // coarse row m (complex at column J) into the slot's third row; zero outside
-    auto load_coarse = [&](uint32_t dst, int m) {
-      const bool ok = (unsigned)m < (unsigned)Nc && (unsigned)J < (unsigned)Nc;
-      const C *src = eb + (ok ? (long long)m * e.pitch + J : 0);
-      if (sizeof(C) == 8) cp_async8(dst, src, ok ? 8 : 0);
-      else cp_async16(dst, src, ok ? 16 : 0);
-    };
-    auto issue = [&](int s) {
-      if (s < L) {
-        const int row = y0 - 2 + s;
-        load_pair<C>(smem_u32(slot(s, 0)), zb, z.pitch, N, row, a);
-        load_pair<C>(smem_u32(slot(s, 1)), bb, b.pitch, N, row, a);
-        if (!(row & 1)) load_coarse(smem_u32(slot(s, 2)), row >> 1);  // coarse row m at fine 2m
-      }
-      cp_commit();
-    };
-    // coarse row y0/2 - 2: the first fine row y0 - 2 (even) shifts it into eprev and
-    // loads row y0/2 - 1 into ecur
-    C eprev = czero<C>(), ecur;
-    {
-      const int m = y0 / 2 - 2;
-      const bool ok = (unsigned)m < (unsigned)Nc && (unsigned)J < (unsigned)Nc;
-      ecur = ok ? eb[(long long)m * e.pitch + J] : czero<C>();
-    }
-#pragma unroll
-    for (int s = 0; s < kDepth; s++) issue(s);
-    C zz1[4], zz0[4], bm1[2], rm3[4], rm2[4], rm1[4];  // z'' rows i-1 (zz1), i-2 (zz0)
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      zz1[q] = zz0[q] = rm3[q] = rm2[q] = rm1[q] = czero<C>();
-      if (q < 2) bm1[q] = czero<C>();
-    }
-    for (int s = 0; s < L; s++) {
-      const int i = y0 - 2 + s;
-      cp_wait<kDepth - 1>();
-      C zi[2], bi[2];
-      {
-        const Pair<C> pz = read_pair(slot(s, 0));
-        const Pair<C> pb = read_pair(slot(s, 1));
-        zi[0] = pz.v[0];
-        zi[1] = sel(cin1, pz.v[1]);
-        bi[0] = pb.v[0];
-        bi[1] = sel(cin1, pb.v[1]);
-        if (!(i & 1)) {
-          eprev = ecur;
-          ecur = *slot(s, 2);
-        }
-      }
-      issue(s + kDepth);
-      // z'' = z' + P e_c on row i: odd rows sit on coarse row (i-1)/2 = ecur, even rows
-      // between eprev (i/2 - 1) and ecur (i/2); odd columns on coarse column J, even
-      // columns between J-1 (from the left lane) and J
-      const bool i_in = (unsigned)i < (unsigned)N;
-      C zn[4];
-      {
-        const C ev = (i & 1) ? ecur : cscale(cadd(eprev, ecur), (T)0.5);
-        const C evl = shfl_up1(ev);
-        const C p0 = cscale(cadd(evl, ev), (T)0.5), p1 = ev;
-        const C z0 = sel(i_in && cin0, cadd(zi[0], p0));
-        const C z1 = sel(i_in && cin1, cadd(zi[1], p1));
-        zn[0] = shfl_up1(z1);
-        zn[1] = z0;
-        zn[2] = z1;
-        zn[3] = shfl_dn1(z0);
-      }
-      // rt of z'' on row i-1
-      const bool r_in = (unsigned)(i - 1) < (unsigned)N;
-      C rn[4];
-      {
-        C r0 = csub(cadd(bm1[0], cadd(cadd(zz0[1], zn[1]), cadd(zz1[0], zz1[2]))), cmul(cf.d, zz1[1]));
-        C r1 = csub(cadd(bm1[1], cadd(cadd(zz0[2], zn[2]), cadd(zz1[1], zz1[3]))), cmul(cf.d, zz1[2]));
-        r0 = sel(r_in && cin0, r0);
-        r1 = sel(r_in && cin1, r1);
-        rn[0] = shfl_up1(r1);
-        rn[1] = r0;
-        rn[2] = r1;
-        rn[3] = shfl_dn1(r0);
-      }
-#pragma unroll
-      for (int q = 0; q < 4; q++) {
-        rm3[q] = rm2[q];
-        rm2[q] = rm1[q];
-        rm1[q] = rn[q];
-      }
-      // z''' = z'' + omega M rt on row i-2 (z''(i-2) is zz0 before the shift below)
-      if (i - 2 >= y0 && i - 2 < y1) {
-        C out[2];
-#pragma unroll
-        for (int k = 0; k < 2; k++) {
-          const C e2 = cadd(cadd(rm3[k + 1], rm1[k + 1]), cadd(rm2[k], rm2[k + 2]));
-          const C co = cadd(cadd(rm3[k], rm3[k + 2]), cadd(rm1[k], rm1[k + 2]));
-          C upd = cmul(cf.ca, rm2[k + 1]);
-          upd = cfma(cf.cb, e2, upd);
-          upd = cfma(cf.cc, co, upd);
-          out[k] = cadd(zz0[k + 1], upd);
-        }
-        C *dst = zo + (long long)(i - 2) * zout.pitch + a;
-        if (out0) dst[0] = out[0];
-        if (out1) dst[1] = out[1];
-      }
-#pragma unroll
-      for (int q = 0; q < 4; q++) {
-        zz0[q] = zz1[q];
-        zz1[q] = zn[q];
-      }
-      bm1[0] = bi[0];
-      bm1[1] = bi[1];
-    }
-    cp_wait<0>();
+    if (interior_unit(N, x0, y0, y1))
+      ps_unit<T, true>(N, seg, u, nsx, nsy, Nc, lane, ring, z, e, b, zout, coef);
+    else
+      ps_unit<T, false>(N, seg, u, nsx, nsy, Nc, lane, ring, z, e, b, zout, coef);
   }
 }
 
