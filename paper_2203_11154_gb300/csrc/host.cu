@@ -76,6 +76,7 @@ struct pd_ctx {
   double *d_Bval = nullptr;
   double *d_r = nullptr;       // refinement residual [n][N][N] (general B)
   float *d_r32 = nullptr;      // refinement residual in FP32 (bidiagonal B)
+  float2 *d_fcache = nullptr;  // fhat in float-float, written by a solve's first residual
   bool bidiag = false;         // B has nonzeros only at (k,k) and (k,k+boff mod n)
   int boff = -1;
   double *d_bd = nullptr, *d_bs = nullptr;
@@ -975,16 +976,21 @@ void refine_runs(std::vector<RefRun> &runs) {
 // ||fhat - A u|| and ||fhat|| from the per-CTA partial sums (fixed order)
 // r (FP64, may be NULL) or r32 (FP32) = fhat - A u and the norms; with a bidiagonal B
 // and known_fn >= 0 the ||fhat|| sums are skipped and known_fn returned
+// fcache: 0 none, 1 write fhat (float-float) into the context's cache, 2 read it from there
 void allatonce_norms(pd_ctx *c, double *r, const double *u, const double *f, const double *u0,
-                     double *rn, double *fn, float *r32 = nullptr, double known_fn = -1.0) {
+                     double *rn, double *fn, float *r32 = nullptr, double known_fn = -1.0,
+                     int fcache = 0) {
   const double m = (double)c->N * c->N;
   const bool want_f = known_fn < 0.0;
   int nb = allatonce_blocks();
   if (c->bidiag && r32 && !r && c->cfg.fx_residual) {
     nb = residual_fx_blocks(c->num_sms);
-    PD_PROF(PD_KC_RESIDUAL, 20.0 * m + (u0 ? 8.0 * m / c->n : 0.0), 0,
+    const bool use = fcache && c->d_fcache;
+    PD_PROF(PD_KC_RESIDUAL, 20.0 * m + (u0 && !(use && fcache == 2) ? 8.0 * m / c->n : 0.0), 0,
             launch_residual_fx(c->stream, nb, c->N, c->n, c->boff, c->kappa, r32, u, f, u0,
-                               c->d_u0coef, c->d_bd, c->d_bs, want_f, c->d_part));
+                               c->d_u0coef, c->d_bd, c->d_bs, want_f, c->d_part,
+                               use && fcache == 2 ? c->d_fcache : nullptr,
+                               use && fcache == 1 ? c->d_fcache : nullptr));
   } else if (c->bidiag)
     PD_PROF(PD_KC_RESIDUAL,
             (r ? 24.0 : r32 ? 20.0 : 16.0) * m + (u0 ? 8.0 * m / c->n : 0.0), 0,
@@ -1146,7 +1152,8 @@ pd_status paradiag_impl(pd_ctx *c, double *u, const double *f, const double *u0,
       ck_launch(c);
       double rn, fn;
       if (c->bidiag) {
-        allatonce_norms(c, nullptr, u, f, u0, &rn, &fn, c->d_r32, step == 0 ? -1.0 : c->fnorm);
+        allatonce_norms(c, nullptr, u, f, u0, &rn, &fn, c->d_r32, step == 0 ? -1.0 : c->fnorm,
+                        step == 0 ? 1 : 2);
         c->fnorm = fn;
       } else {
         allatonce_norms(c, c->d_r, u, f, u0, &rn, &fn);
@@ -1474,6 +1481,8 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
       alloc_prec<float>(c);
       if (c->have_B) {
         if (c->bidiag) c->d_r32 = dalloc<float *>(c, (size_t)n * N * N * sizeof(float));
+        if (c->bidiag && cfg.fx_residual)
+          c->d_fcache = dalloc<float2 *>(c, (size_t)n * N * N * sizeof(float2));
         else c->d_r = dalloc<double *>(c, (size_t)n * N * N * sizeof(double));
       }
     }

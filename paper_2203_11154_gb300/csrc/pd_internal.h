@@ -85,7 +85,8 @@ void launch_fft_inverse(cudaStream_t s, int num_sms, int N, int n, double *u, Vi
 int residual_fx_blocks(int num_sms);
 void launch_residual_fx(cudaStream_t s, int blocks, int N, int n, int off, double kappa, float *r,
                         const double *u, const double *f, const double *u0, const double *u0coef,
-                        const double *bd, const double *bs, bool want_f, double *part);
+                        const double *bd, const double *bs, bool want_f, double *part,
+                        const float2 *fc_in, float2 *fc_out);
 
 // ---- FP64 refinement of the shifted systems (shift_refine.cu) ----
 int shift_residual_blocks(int N, int n);

@@ -133,7 +133,8 @@ __global__ void __launch_bounds__(kFxThreads, 4)
 k_residual_fx(int N, int n, int off, float *__restrict__ r, const double *__restrict__ u,
               const double *__restrict__ f, const double *__restrict__ u0,
               const double *__restrict__ u0coef, const double *__restrict__ bd,
-              const double *__restrict__ bs, double ih2, int want_f, double *__restrict__ part) {
+              const double *__restrict__ bs, double ih2, int want_f, double *__restrict__ part,
+              const float2 *__restrict__ fc_in, float2 *__restrict__ fc_out) {
   __shared__ long long sfx[kFxHR * kFxHC];
   __shared__ unsigned red_e[kFxThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -195,8 +196,17 @@ k_residual_fx(int N, int n, int off, float *__restrict__ r, const double *__rest
         const long long uc = sfx[q];
         const long long t1 = 4 * uc - (sfx[q - 1] + sfx[q + 1] + sfx[q - kFxHC] + sfx[q + kFxHC]);
         const long long x = (long long)i * N + c;
-        DF acc = split(f[(long long)k * m + x]);
-        if (has_u0) acc = df_add(acc, df_mul(ck, split(u0[x])));
+        // fhat in float-float: from the cache of an earlier residual of the same solve, or
+        // from f and u0 (and then cached when asked)
+        DF acc;
+        if (fc_in) {
+          const float2 q = fc_in[(long long)k * m + x];
+          acc = {q.x, q.y};
+        } else {
+          acc = split(f[(long long)k * m + x]);
+          if (has_u0) acc = df_add(acc, df_mul(ck, split(u0[x])));
+          if (fc_out) fc_out[(long long)k * m + x] = make_float2(acc.hi, acc.lo);
+        }
         DF fh = acc;
         acc = df_add(acc, df_neg(df_mul(cb, df_from_ll(uc))));
         acc = df_add(acc, df_neg(df_mul(bsk, split(u[(long long)kp * m + x]))));
@@ -243,10 +253,11 @@ int residual_fx_blocks(int num_sms) { return 8 * num_sms; }
 
 void launch_residual_fx(cudaStream_t s, int blocks, int N, int n, int off, double kappa, float *r,
                         const double *u, const double *f, const double *u0, const double *u0coef,
-                        const double *bd, const double *bs, bool want_f, double *part) {
+                        const double *bd, const double *bs, bool want_f, double *part,
+                        const float2 *fc_in, float2 *fc_out) {
   const double h = 1.0 / (N + 1);
   k_residual_fx<<<blocks, kFxThreads, 0, s>>>(N, n, off, r, u, f, u0, u0coef, bd, bs,
-                                              kappa / (h * h), want_f ? 1 : 0, part);
+                                              kappa / (h * h), want_f ? 1 : 0, part, fc_in, fc_out);
 }
 
 }  // namespace pd
