@@ -128,6 +128,30 @@ def oracle_sample(workload, threads):
     return n / step, t_tr + t_mg, desc
 
 
+def rank_seed(workload, rank):
+    """Each rank solves its own problem: the workload's input recipe with seed + rank
+    (weak scaling; no collective on the data path)."""
+    from paper_2203_11154_gb300 import inputs
+    return inputs.WORKLOADS[workload]["seed"] + rank
+
+
+def max_over_ranks(x, world, device):
+    """The step time of the job: the maximum over ranks (all_reduce MAX)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(n, steps, world, ms):
+    """Shifted solves of all ranks per second: n systems per step on each of `world` ranks,
+    over the slowest rank's time for `steps` steps."""
+    return n * steps * world / (ms / 1e3)
+
+
 def bench_config(workload):
     """The workload description both arms print."""
     from paper_2203_11154_gb300 import inputs
@@ -201,16 +225,12 @@ def main():
         if world > 1:
             dist.barrier()
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def rank_max(x):
+        return max_over_ranks(x, world, "cuda")
 
     w = inputs.WORKLOADS[args.workload]
     N, n, tau, alpha = w["N"], w["n"], w["tau"], w["alpha"]
-    f, u0 = inputs.paradiag_problem(N, n, seed=w["seed"] + rank)
+    f, u0 = inputs.paradiag_problem(N, n, seed=rank_seed(args.workload, rank))
     fd = torch.from_numpy(f).cuda()
     u0d = torch.from_numpy(u0).cuda()
     u = torch.empty_like(fd)
@@ -238,7 +258,7 @@ def main():
         torch.cuda.synchronize()
         barrier()
         ck = clocks.stop() if clocks else None
-        ms = max_over_ranks(e0.elapsed_time(e1))
+        ms = rank_max(e0.elapsed_time(e1))
         prof = ctx.profile_read() if profile else None
         if profile:
             ctx.profile_enable(False)
@@ -248,7 +268,7 @@ def main():
     ctx = api.alpha_circulant_context(N, n, tau, alpha, precision=1, imag_check=0)
     clocks = Clocks(local)
     ms_ir, out_ir, _, launches, ck = timed(ctx, args.steps, args.warmup, clocks=clocks)
-    value = n * args.steps * world / (ms_ir / 1e3)
+    value = job_throughput(n, args.steps, world, ms_ir)
     # per-kernel durations: CUDA events around every launch, in a second pass of the same
     # K steps (kept out of the timed pass above, whose step time they would inflate)
     ms_prof, _, prof, _, _ = timed(ctx, args.steps, 0, profile=True)
@@ -271,8 +291,8 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        ms_e2e = max_over_ranks(e0.elapsed_time(e1))
-        e2e = {"value": n * args.steps * world / (ms_e2e / 1e3), "unit": "solves/s",
+        ms_e2e = rank_max(e0.elapsed_time(e1))
+        e2e = {"value": job_throughput(n, args.steps, world, ms_e2e), "unit": "solves/s",
                "h2d_bytes_per_step": int(fh.numel() * 8 + u0h.numel() * 8),
                "d2h_bytes_per_step": int(uh.numel() * 8), "ms_per_step": ms_e2e / args.steps}
         del fh, u0h, uh
@@ -283,7 +303,7 @@ def main():
     k64 = args.fp64_steps or args.steps
     ms64, out64, _, _, _ = timed(ctx64, k64, args.warmup)
     ctx64.destroy()
-    value64 = n * k64 * world / (ms64 / 1e3)
+    value64 = job_throughput(n, k64, world, ms64)
 
     # roofline of the dominant kernel class (its own launch times, live in the timed region)
     peak, peak_src = measured_peaks()

@@ -63,24 +63,28 @@ __device__ __forceinline__ void dft_small(C (&v)[R], const C *__restrict__ tw, i
   }
 }
 
-// the two passes of the four-step DFT on the thread's column col[e * P]
-template <typename C, int N1, int N2, int P>
-__device__ __forceinline__ void fft_column(C *col, const C *__restrict__ tw) {
+// the two passes of the four-step DFT on the point's column col[e * P], shared by the TP
+// threads of the point (thread t takes every TP-th small DFT of each pass); the CTA
+// synchronises before and between the passes
+template <typename C, int N1, int N2, int P, int TP>
+__device__ __forceinline__ void fft_column(C *col, const C *__restrict__ tw, int t) {
   constexpr int n = N1 * N2;
+  __syncthreads();
   // pass 1: for each j2, DFT over j1 of x[N2 j1 + j2], times w_n^{j2 k1}
-  for (int j2 = 0; j2 < N2; j2++) {
+  for (int j2 = t; j2 < N2; j2 += TP) {
     C v[N1];
 #pragma unroll
     for (int j1 = 0; j1 < N1; j1++) v[j1] = col[(N2 * j1 + j2) * P];
     dft_small<C, N1>(v, tw, N2);
 #pragma unroll
     for (int k1 = 0; k1 < N1; k1++) {
-      const C t = (k1 == 0 || j2 == 0) ? v[k1] : cmul(tw[(j2 * k1) % n], v[k1]);
-      col[(N2 * k1 + j2) * P] = t;
+      const C x = (k1 == 0 || j2 == 0) ? v[k1] : cmul(tw[(j2 * k1) % n], v[k1]);
+      col[(N2 * k1 + j2) * P] = x;
     }
   }
+  __syncthreads();
   // pass 2: for each k1, DFT over j2; X[k1 + N1 k2] ends in slot N2 k1 + k2
-  for (int k1 = 0; k1 < N1; k1++) {
+  for (int k1 = t; k1 < N1; k1 += TP) {
     C v[N2];
 #pragma unroll
     for (int j2 = 0; j2 < N2; j2++) v[j2] = col[(N2 * k1 + j2) * P];
@@ -88,6 +92,18 @@ __device__ __forceinline__ void fft_column(C *col, const C *__restrict__ tw) {
 #pragma unroll
     for (int k2 = 0; k2 < N2; k2++) col[(N2 * k1 + k2) * P] = v[k2];
   }
+  __syncthreads();
+}
+
+// threads per grid point: two where both passes have at least two small DFTs
+template <int N1, int N2> __host__ __device__ constexpr int fft_tp() { return (N1 >= 2 && N2 >= 2) ? 2 : 1; }
+// CTAs per SM that the shared memory allows (at most 3), for the register budget
+template <typename T, int n> __host__ __device__ constexpr int fft_min_blocks() {
+  return (229376 / (n * fft_points<T, n>() * (int)sizeof(typename Cx<T>::type))) >= 3
+             ? 3
+             : ((229376 / (n * fft_points<T, n>() * (int)sizeof(typename Cx<T>::type))) < 1
+                    ? 1
+                    : 229376 / (n * fft_points<T, n>() * (int)sizeof(typename Cx<T>::type)));
 }
 
 // exact FP32 -> FP64 by bit operations (the conversion instruction issues on the FP64
@@ -105,32 +121,35 @@ __device__ __forceinline__ double to_f64(double v) { return v; }
 
 template <typename T, typename InT> __device__ __forceinline__ T load_in(const InT *p) { return (T)*p; }
 
-// g_j(point) = wk-weighted DFT (+ exponent) of fhat; wk[k] = s alpha^{k/n} / n
+// g_j(point) = wk-weighted DFT (+ exponent) of fhat; wk[k] = s alpha^{k/n} / n.  Thread
+// (t, p) of the CTA (p = threadIdx.x % P) serves point p: its loads and stores are the time
+// slices t, t + TP, ..., so a warp touches 32 consecutive points of one slice.
 template <typename T, int N1, int N2, typename InT>
-__global__ void __launch_bounds__(fft_points<T, N1 * N2>())
+__global__ void __launch_bounds__(fft_points<T, N1 * N2>() * fft_tp<N1, N2>(), fft_min_blocks<T, N1 * N2>())
 k_fft_forward(int N, View g, const InT *__restrict__ f, const double *__restrict__ u0,
               const double *__restrict__ u0coef, const T *__restrict__ wk,
               const typename Cx<T>::type *__restrict__ tw) {
   using C = typename Cx<T>::type;
-  constexpr int n = N1 * N2, P = fft_points<T, n>();
+  constexpr int n = N1 * N2, P = fft_points<T, n>(), TP = fft_tp<N1, N2>();
   extern __shared__ __align__(16) unsigned char fft_raw[];
-  C *col = reinterpret_cast<C *>(fft_raw) + threadIdx.x;
+  const int p = threadIdx.x % P, t = threadIdx.x / P;
+  C *col = reinterpret_cast<C *>(fft_raw) + p;
   const long long m = (long long)N * N;
+  constexpr int kPer = n / TP;                         // slices per thread
+  constexpr int kBatch = kPer < 16 ? kPer : 16;        // loads in flight per thread
   for (long long base = (long long)blockIdx.x * P; base < m; base += (long long)gridDim.x * P) {
-    const long long x = base + threadIdx.x;
+    const long long x = base + p;
     const bool ok = x < m;
     const double u0x = (ok && u0) ? u0[x] : 0.0;
-    // batches of kBatch loads in flight per thread (the CTA holds few threads: its columns
-    // fill shared memory), then into the column
-    constexpr int kBatch = n < 16 ? n : 16;
 #pragma unroll 1
-    for (int k0 = 0; k0 < n; k0 += kBatch) {
+    for (int q0 = 0; q0 < kPer; q0 += kBatch) {
       InT in[kBatch];
 #pragma unroll
-      for (int q = 0; q < kBatch; q++) in[q] = ok ? f[(long long)(k0 + q) * m + x] : (InT)0;
+      for (int q = 0; q < kBatch; q++)
+        in[q] = ok ? f[(long long)(TP * (q0 + q) + t) * m + x] : (InT)0;
 #pragma unroll
       for (int q = 0; q < kBatch; q++) {
-        const int k = k0 + q;
+        const int k = TP * (q0 + q) + t;
         // the initial-value term (FP64) only on the time steps whose coefficient is nonzero
         // (tested on the bits: no FP64 comparison per point)
         const double ck = u0 ? u0coef[k] : 0.0;
@@ -140,66 +159,69 @@ k_fft_forward(int N, View g, const InT *__restrict__ f, const double *__restrict
         col[k * P] = cx<C>(v * wk[k], (T)0);
       }
     }
-    fft_column<C, N1, N2, P>(col, tw);
+    fft_column<C, N1, N2, P, TP>(col, tw, t);
     if (ok) {
       const int i = (int)(x / N), c = (int)(x - (long long)i * N);
       C *gp = reinterpret_cast<C *>(g.p) + (long long)i * g.pitch + c;
 #pragma unroll 4
-      for (int s = 0; s < n; s++) {
+      for (int s = t; s < n; s += TP) {
         const int k1 = s / N2, k2 = s % N2;
         gp[(long long)(k1 + N1 * k2) * g.plane] = col[s * P];
       }
     }
+    __syncthreads();  // the columns are refilled by the next points
   }
 }
 
 // u_k(point) (+)= wk[k] Re(DFT (- exponent) of z)_k, wk[k] = alpha^{-k/n}; z_j from z1 where
 // final_buf[j] is set, else z0; imag_check: atomic max of |wk[k] Im(.)_k| (bits of a double)
 template <typename T, int N1, int N2>
-__global__ void __launch_bounds__(fft_points<T, N1 * N2>())
+__global__ void __launch_bounds__(fft_points<T, N1 * N2>() * fft_tp<N1, N2>(), fft_min_blocks<T, N1 * N2>())
 k_fft_inverse(int N, double *__restrict__ u, View z0, View z1, const int *__restrict__ final_buf,
               const T *__restrict__ wk, const typename Cx<T>::type *__restrict__ tw, int accumulate,
               int imag_check, unsigned long long *imag_bits) {
   using C = typename Cx<T>::type;
-  constexpr int n = N1 * N2, P = fft_points<T, n>();
+  constexpr int n = N1 * N2, P = fft_points<T, n>(), TP = fft_tp<N1, N2>();
   extern __shared__ __align__(16) unsigned char fft_raw[];
-  __shared__ float red[P / 32];
-  C *col = reinterpret_cast<C *>(fft_raw) + threadIdx.x;
+  __shared__ float red[P * TP / 32];
+  const int p = threadIdx.x % P, t = threadIdx.x / P;
+  C *col = reinterpret_cast<C *>(fft_raw) + p;
   const long long m = (long long)N * N;
+  constexpr int kPer = n / TP;
+  constexpr int kBatch = kPer < 16 ? kPer : 16;
   float imax = 0.f;
   for (long long base = (long long)blockIdx.x * P; base < m; base += (long long)gridDim.x * P) {
-    const long long x = base + threadIdx.x;
+    const long long x = base + p;
     const bool ok = x < m;
     const int i = (int)(x / N), c = (int)(x - (long long)i * N);
-    constexpr int kBatch = n < 16 ? n : 16;
 #pragma unroll 1
-    for (int j0 = 0; j0 < n; j0 += kBatch) {
+    for (int q0 = 0; q0 < kPer; q0 += kBatch) {
       C in[kBatch];
 #pragma unroll
       for (int q = 0; q < kBatch; q++) {
-        const int j = j0 + q;
+        const int j = TP * (q0 + q) + t;
         const View &zv = (final_buf && final_buf[j]) ? z1 : z0;
         in[q] = ok ? reinterpret_cast<const C *>(zv.p)[(long long)j * zv.plane + (long long)i * zv.pitch + c]
                    : czero<C>();
       }
 #pragma unroll
-      for (int q = 0; q < kBatch; q++) col[(j0 + q) * P] = in[q];
+      for (int q = 0; q < kBatch; q++) col[(TP * (q0 + q) + t) * P] = in[q];
     }
-    fft_column<C, N1, N2, P>(col, tw);
+    fft_column<C, N1, N2, P, TP>(col, tw, t);
     if (ok) {
 #pragma unroll 1
-      for (int s0 = 0; s0 < n; s0 += kBatch) {
+      for (int q0 = 0; q0 < kPer; q0 += kBatch) {
         double uo[kBatch];
         if (accumulate) {
 #pragma unroll
           for (int q = 0; q < kBatch; q++) {
-            const int s = s0 + q, k = s / N2 + N1 * (s % N2);
+            const int s = TP * (q0 + q) + t, k = s / N2 + N1 * (s % N2);
             uo[q] = u[(long long)k * m + x];
           }
         }
 #pragma unroll
         for (int q = 0; q < kBatch; q++) {
-          const int s = s0 + q, k = s / N2 + N1 * (s % N2);
+          const int s = TP * (q0 + q) + t, k = s / N2 + N1 * (s % N2);
           const C v = col[s * P];
           const T re = v.x * wk[k];
           u[(long long)k * m + x] = accumulate ? uo[q] + to_f64(re) : to_f64(re);
@@ -207,6 +229,7 @@ k_fft_inverse(int N, double *__restrict__ u, View z0, View z1, const int *__rest
         }
       }
     }
+    __syncthreads();  // the columns are refilled by the next points
   }
   if (imag_check) {
     for (int o = 16; o > 0; o >>= 1) imax = fmaxf(imax, __shfl_down_sync(0xffffffffu, imax, o));
@@ -214,7 +237,7 @@ k_fft_inverse(int N, double *__restrict__ u, View z0, View z1, const int *__rest
     __syncthreads();
     if (threadIdx.x == 0) {
       float mx = 0.f;
-      for (int w = 0; w < P / 32; w++) mx = fmaxf(mx, red[w]);
+      for (int w = 0; w < P * TP / 32; w++) mx = fmaxf(mx, red[w]);
       atomicMax(imag_bits, (unsigned long long)__double_as_longlong((double)mx));
     }
   }
@@ -267,15 +290,15 @@ void launch_fft_forward(cudaStream_t s, int num_sms, int N, int n, View g, const
                         const typename Cx<T>::type *tw) {
 #define PD_FFT_FWD(A, B)                                                                          \
   if (n == A * B) {                                                                               \
-    constexpr int P = fft_points<T, A * B>();                                                      \
+    constexpr int P = fft_points<T, A * B>(), TH = P * fft_tp<A, B>();                           \
     const int grid = fft_grid(N, P, num_sms);                                                     \
     const size_t smem = fft_smem<T, A * B>();                                                     \
     if (f32)                                                                                      \
-      k_fft_forward<T, A, B, float><<<grid, P, smem, s>>>(N, g, static_cast<const float *>(f),     \
-                                                          u0, u0coef, wk, tw);                    \
-    else                                                                                          \
-      k_fft_forward<T, A, B, double><<<grid, P, smem, s>>>(N, g, static_cast<const double *>(f),   \
+      k_fft_forward<T, A, B, float><<<grid, TH, smem, s>>>(N, g, static_cast<const float *>(f),    \
                                                            u0, u0coef, wk, tw);                   \
+    else                                                                                          \
+      k_fft_forward<T, A, B, double><<<grid, TH, smem, s>>>(N, g, static_cast<const double *>(f),  \
+                                                            u0, u0coef, wk, tw);                  \
     return;                                                                                       \
   }
   PD_FFT_SIZES(PD_FFT_FWD)
@@ -288,10 +311,10 @@ void launch_fft_inverse(cudaStream_t s, int num_sms, int N, int n, double *u, Vi
                         bool accumulate, bool imag_check, unsigned long long *imag_bits) {
 #define PD_FFT_INV(A, B)                                                                       \
   if (n == A * B) {                                                                            \
-    constexpr int P = fft_points<T, A * B>();                                                   \
+    constexpr int P = fft_points<T, A * B>(), TH = P * fft_tp<A, B>();                        \
     const int grid = fft_grid(N, P, num_sms);                                                  \
     const size_t smem = fft_smem<T, A * B>();                                                  \
-    k_fft_inverse<T, A, B><<<grid, P, smem, s>>>(N, u, z0, z1, final_buf, wk, tw,              \
+    k_fft_inverse<T, A, B><<<grid, TH, smem, s>>>(N, u, z0, z1, final_buf, wk, tw,             \
                                                  accumulate ? 1 : 0, imag_check ? 1 : 0,       \
                                                  imag_bits);                                   \
     return;                                                                                    \
