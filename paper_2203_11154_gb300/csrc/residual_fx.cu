@@ -25,7 +25,7 @@
 namespace pd {
 namespace {
 
-constexpr int kFxRows = 16, kFxCols = 128, kFxThreads = 256;
+constexpr int kFxRows = 32, kFxCols = 128, kFxThreads = 256;
 constexpr int kFxHR = kFxRows + 2, kFxHC = kFxCols + 2;  // halo tile
 
 struct DF {
