@@ -136,6 +136,7 @@ __device__ __forceinline__ void sr_unit(int N, int seg, int u, int nsx, int nsy,
     if (q < 2) zm2[q] = zm1[q] = bm1[q] = bm2[q] = bm3[q] = czero<C>();
   }
   T acc = 0;
+#pragma unroll 3
   for (int s = 0; s < L; s++) {
     const int i = y0 - 3 + s;
     cp_wait<kDepth - 1>();
@@ -259,7 +260,7 @@ __device__ __forceinline__ void sr_unit(int N, int seg, int u, int nsx, int nsy,
 }
 
 template <typename T, bool ZZERO, bool NORM>
-__global__ void __launch_bounds__(kWarpsPerCta * kLanes)
+__global__ void __launch_bounds__(kWarpsPerCta * kLanes, sizeof(T) == 4 ? 2 : 1)
 k_sr_stream(int N, int n, int seg, View z, View b, View zout, View bc,
             const Coef<T> *__restrict__ coef, const int *__restrict__ active,
             double *__restrict__ partials, int part_stride) {
@@ -338,6 +339,7 @@ __device__ __forceinline__ void ps_unit(int N, int seg, int u, int nsx, int nsy,
     zz1[q] = zz0[q] = rm3[q] = rm2[q] = rm1[q] = czero<C>();
     if (q < 2) bm1[q] = czero<C>();
   }
+#pragma unroll 3
   for (int s = 0; s < L; s++) {
     const int i = y0 - 2 + s;
     cp_wait<kDepth - 1>();
@@ -418,7 +420,7 @@ __device__ __forceinline__ void ps_unit(int N, int seg, int u, int nsx, int nsy,
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kWarpsPerCta * kLanes)
+__global__ void __launch_bounds__(kWarpsPerCta * kLanes, sizeof(T) == 4 ? 2 : 1)
 k_ps_stream(int N, int n, int seg, View z, View e, View b, View zout,
             const Coef<T> *__restrict__ coef, const int *__restrict__ active) {
   using C = typename Cx<T>::type;
