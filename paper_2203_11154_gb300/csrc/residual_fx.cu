@@ -94,15 +94,14 @@ __device__ __forceinline__ DF split(double x) {
   return split_bits((uint32_t)__double2hiint(x), (uint32_t)__double2loint(x));
 }
 
-// FP64 bits -> fixed point with 2^-S units (S from the tile's largest exponent, see above)
+// FP64 bits -> fixed point with 2^-S units (S = 1081 - e_max from the tile's largest
+// biased exponent e_max, see above): m 2^(e-1075) 2^S = (m << 6) >> (e_max - e), one
+// branch-free right shift (m < 2^53, so m << 6 < 2^59 loses nothing); truncated below a unit
 __device__ __forceinline__ long long to_fixed(uint32_t hw, uint32_t lw, int S) {
   const int e = (int)((hw >> 20) & 0x7FFu);
-  if (e == 0) return 0;
   const unsigned long long m = ((unsigned long long)((hw & 0xFFFFFu) | 0x100000u) << 32) | lw;
-  const int sh = e - 1075 + S;  // <= 6
-  unsigned long long v;
-  if (sh >= 0) v = m << sh;
-  else v = sh > -64 ? (m >> (-sh)) : 0ull;
+  const int rs = 1081 - S - e;  // >= 0
+  const unsigned long long v = (e == 0 || rs >= 64) ? 0ull : ((m << 6) >> rs);
   const long long sv = (long long)v;
   return (hw & 0x80000000u) ? -sv : sv;
 }

@@ -76,3 +76,55 @@ def test_paradiag_2047_residual():
         acc += float(np.sum(t * t))
     noise = 8 * np.finfo(float).eps * np.sqrt(acc) / fn
     assert abs(out["relres_allatonce"] - rn / fn) <= 1e-3 * rn / fn + noise
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_adjoint_1023_against_finite_differences(precision):
+    """The differentiation workload at full size (1023^2, n = 64, the 8-mode target): the
+    adjoint gradients in f and u0 along random directions against central differences of
+    the GPU forward solve (exact for the quadratic loss up to the solves' error), in kappa
+    against Richardson-extrapolated differences; spec bar 1e-6 relative."""
+    from paper_2203_11154_gb300 import adjoint
+    w = inputs.WORKLOADS["adjoint-1023"]
+    N, n, tau, alpha = w["N"], w["n"], w["tau"], w["alpha"]
+    f, u0 = inputs.paradiag_problem(N, n, seed=w["seed"])
+    target = inputs.sine_modes_target(N, seed=w["target_seed"])
+    if precision == 1:
+        step = adjoint.HeatStep(N, n, tau, alpha, precision=1, tol=1e-11, max_refine=30)
+    else:  # FP64 corrections bring eq. (1) itself to the tolerance (the FP64 residual's
+        # own rounding is near 1e-11 at N = 1023)
+        step = adjoint.HeatStep(N, n, tau, alpha, precision=0, tol=1e-10, outer_maxit=6)
+    tt = torch.from_numpy(target).cuda()
+
+    def loss(fd, u0d, kd):
+        u = step(fd, u0d, kd)
+        return 0.5 * torch.sum((u[-1] - tt) ** 2)
+
+    fd = torch.from_numpy(f).cuda().requires_grad_(True)
+    u0d = torch.from_numpy(u0).cuda().requires_grad_(True)
+    kd = torch.tensor(1.0, dtype=torch.float64, device="cuda", requires_grad=True)
+    J = loss(fd, u0d, kd)
+    J.backward()
+    gf, gu0, gk = fd.grad.detach(), u0d.grad.detach(), float(kd.grad)
+    rng = np.random.default_rng(5)
+    df = torch.from_numpy(rng.standard_normal(f.shape)).cuda()
+    # u0 along the computed gradient: over the unit horizon diffusion damps every initial
+    # mode by at least e^{-2 pi^2} ~ 3e-9, so J depends on u0 only weakly; J is quadratic,
+    # central differences are exact for any step, and a step of 1e6 along the unit
+    # gradient direction moves J far above its rounding
+    du0 = gu0 / torch.linalg.vector_norm(gu0)
+    f0, u00 = torch.from_numpy(f).cuda(), torch.from_numpy(u0).cuda()
+    one = torch.tensor(1.0, dtype=torch.float64, device="cuda")
+    with torch.no_grad():
+        eps = 0.5
+        fd_f = float(loss(f0 + eps * df, u00, one) - loss(f0 - eps * df, u00, one)) / (2 * eps)
+        e0 = 1e6
+        fd_u0 = float(loss(f0, u00 + e0 * du0, one) - loss(f0, u00 - e0 * du0, one)) / (2 * e0)
+
+        def dk(e):
+            return float(loss(f0, u00, one + e) - loss(f0, u00, one - e)) / (2 * e)
+
+        fd_k = (4 * dk(5e-4) - dk(1e-3)) / 3
+    assert abs(fd_f - float(torch.sum(gf * df))) <= 1e-6 * abs(fd_f)
+    assert abs(fd_u0 - float(torch.sum(gu0 * du0))) <= 1e-6 * abs(fd_u0)
+    assert abs(fd_k - gk) <= 1e-6 * abs(fd_k)
