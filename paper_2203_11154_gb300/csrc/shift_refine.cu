@@ -15,6 +15,27 @@ namespace {
 
 constexpr int kSrThreads = 256;
 
+// FP32 <-> FP64 by bit operations (the conversion instructions issue on GB300's slow FP64
+// pipe).  to_f64 is exact (zero and subnormal inputs give 0, Inf/NaN give NaN); to_f32
+// truncates to 24 significant bits (relative error below 2^-23, ample for a right-hand
+// side of the FP32 multigrid), flushing |x| < 2^-126 to 0 and overflowing to NaN.
+__device__ __forceinline__ double to_f64(float v) {
+  const unsigned b = __float_as_uint(v);
+  const unsigned e = (b >> 23) & 0xFFu;
+  if (e == 0) return 0.0;
+  if (e == 0xFFu) return __longlong_as_double(0x7FF8000000000000ll);
+  return __hiloint2double((int)((b & 0x80000000u) | ((e + 896u) << 20) | ((b >> 3) & 0xFFFFFu)),
+                          (int)(b << 29));
+}
+__device__ __forceinline__ float to_f32(double x) {
+  const unsigned hw = (unsigned)__double2hiint(x), lw = (unsigned)__double2loint(x);
+  const int e = (int)((hw >> 20) & 0x7FFu);
+  if (e < 1023 - 126) return 0.f;
+  if (e > 1023 + 127) return __int_as_float(0x7FC00000);
+  return __uint_as_float((hw & 0x80000000u) | ((unsigned)(e - 896) << 23) | ((hw & 0xFFFFFu) << 3) |
+                         (lw >> 29));
+}
+
 // grid (gx, n): CTA x of shift j strides over the grid rows of shift j.  part[j][x] gets
 // the CTA's sum of |r|^2 (and of |b|^2 in part[n + j][x] when want_b); frozen shifts
 // (already converged) get a zero right-hand side and no sums.
@@ -51,10 +72,10 @@ k_shift_residual(int N, const double2 *__restrict__ z, const double2 *__restrict
         r.x = fma(off, nb.x, fma(-cj.x, zv.x, fma(cj.y, zv.y, bv.x)));
         r.y = fma(off, nb.y, fma(-cj.x, zv.y, fma(-cj.y, zv.x, bv.y)));
       }
-      const float2 rf = make_float2((float)r.x, (float)r.y);
+      const float2 rf = make_float2(to_f32(r.x), to_f32(r.y));
       rowr = fmaf(rf.x, rf.x, fmaf(rf.y, rf.y, rowr));
       if (want_b) {
-        const float2 bf = make_float2((float)bv.x, (float)bv.y);
+        const float2 bf = make_float2(to_f32(bv.x), to_f32(bv.y));
         rowb = fmaf(bf.x, bf.x, fmaf(bf.y, bf.y, rowb));
       }
       o[(long long)i * out.pitch + c] = make_float2(rf.x * oscale, rf.y * oscale);
@@ -96,10 +117,10 @@ __global__ void k_shift_update(int N, double2 *__restrict__ z, View z0, View z1,
       reinterpret_cast<const float2 *>(src.p)[(long long)j * src.plane + (long long)i * src.pitch + c];
   double2 &dst = z[(long long)j * N * N + (long long)i * N + c];
   if (accumulate) {
-    dst.x += (double)d.x;
-    dst.y += (double)d.y;
+    dst.x += to_f64(d.x);
+    dst.y += to_f64(d.y);
   } else {
-    dst = make_double2((double)d.x, (double)d.y);
+    dst = make_double2(to_f64(d.x), to_f64(d.y));
   }
 }
 
