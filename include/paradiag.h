@@ -252,6 +252,19 @@ pd_status paradiag_solve_host(pd_ctx *ctx, double *h_u, const double *h_f, const
                               int *h_iters, double *h_relres, double *h_stats);
 
 /*
+ * count independent steps of eq. (1) with host buffers, pipelined: the host-to-device copy
+ * of step k+1's f and u0 and the device-to-host copy of step k-1's u run on a copy stream
+ * that the context creates (once) while step k is solved on the context's stream, through
+ * two device staging sets (2 x (f, u, u0)).  h_u[k], h_f[k]: [n][N][N] double host arrays
+ * (pinned for full speed); h_u0 NULL or h_u0[k] NULL for no initial-value term.  h_iters,
+ * h_relres: count x n entries; h_stats: count x PD_STATS_LEN (each may be NULL).
+ * Synchronises.  Returns the first non-OK status of the steps (PD_ERR_CUDA at once).
+ */
+pd_status paradiag_solve_host_batch(pd_ctx *ctx, int count, double *const *h_u,
+                                    const double *const *h_f, const double *const *h_u0,
+                                    int *h_iters, double *h_relres, double *h_stats);
+
+/*
  * Component entry points (one kernel each, all shifts of one level, asynchronous),
  * exposed so that each kernel can be checked against the oracle on its own.  Grid
  * arrays are [n][N_l][N_l] complex of the working type unless stated otherwise.

@@ -38,7 +38,8 @@ EXPORTS = ["pd_config_default", "pd_alpha_circulant", "paradiag_setup", "pd_adjo
            "pd_allatonce_residual", "pd_allatonce_residual_static", "pd_laplacian_dot",
            "pd_initial_value_gradient",
            "pd_profile_enable", "pd_profile_read", "pd_synchronize", "pd_launch_count", "paradiag_destroy",
-           "pd_status_str", "pd_last_error", "shifted_solve_refined", "pd_allatonce_residual32", "pd_batch_setup",
+           "pd_status_str", "pd_last_error", "shifted_solve_refined", "pd_allatonce_residual32",
+           "paradiag_solve_host_batch", "pd_batch_setup",
            "pd_batch_solve", "pd_batch_destroy", "pd_batch_last_error"]
 
 
@@ -107,6 +108,7 @@ def lib(path=None):
             "pd_last_error": (C.c_char_p, [_P]),
             "shifted_solve_refined": (_I, [_P, _P, _P, _P, _P]),
             "pd_allatonce_residual32": (_I, [_P, _P, _P, _P, _P, _P]),
+            "paradiag_solve_host_batch": (_I, [_P, _I, _P, _P, _P, _P, _P, _P]),
             "pd_batch_setup": (_I, [C.POINTER(_P), _I, _P, _P, _P, C.POINTER(pd_config), _P]),
             "pd_batch_solve": (_I, [_P, _P, _P, _P, _P]),
             "pd_batch_destroy": (_I, [_P]),
@@ -304,19 +306,48 @@ class Context:
                                     _hptr(rr), _hptr(stats))
         return self._solve_out(code, it, rr, stats, "paradiag_solve", raise_on_noconv)
 
+    @staticmethod
+    def _host_ptr(a, numel):
+        if a is None:
+            return None
+        if hasattr(a, "data_ptr"):
+            if a.is_cuda or not a.is_contiguous() or a.numel() != numel:
+                raise ValueError("expected a contiguous host tensor of %d elements" % numel)
+            return C.c_void_p(a.data_ptr())
+        a = np.asarray(a)
+        if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != numel:
+            raise ValueError("expected a contiguous float64 array of %d elements" % numel)
+        return _hptr(a)
+
+    def paradiag_solve_host_batch(self, us, fs, u0s=None, raise_on_noconv=True):
+        """count steps with host buffers, copies pipelined with the solves; us, fs (and u0s)
+        are lists of contiguous float64 host tensors or arrays.  Returns a list of result
+        dicts (as paradiag_solve)."""
+        k = len(fs)
+        if len(us) != k or (u0s is not None and len(u0s) != k):
+            raise ValueError("one u (and u0) per f")
+        m = self.n * self.N * self.N
+        up = (C.c_void_p * k)(*[self._host_ptr(a, m).value for a in us])
+        fp = (C.c_void_p * k)(*[self._host_ptr(a, m).value for a in fs])
+        u0p = None
+        if u0s is not None:
+            u0p = (C.c_void_p * k)(*[(self._host_ptr(a, self.N * self.N).value if a is not None else None)
+                                     for a in u0s])
+        it = np.zeros(k * self.n, np.int32)
+        rr = np.zeros(k * self.n)
+        stats = np.zeros(k * PD_STATS_LEN)
+        code = lib().paradiag_solve_host_batch(self.h, k, C.cast(up, C.c_void_p), C.cast(fp, C.c_void_p),
+                                               C.cast(u0p, C.c_void_p) if u0p is not None else None,
+                                               _hptr(it), _hptr(rr), _hptr(stats))
+        if code != 0 and not (code == 4 and not raise_on_noconv):
+            _check(code, "paradiag_solve_host_batch", self.h)
+        return [self._solve_out(0, it[j * self.n:(j + 1) * self.n], rr[j * self.n:(j + 1) * self.n],
+                                stats[j * PD_STATS_LEN:(j + 1) * PD_STATS_LEN],
+                                "paradiag_solve_host_batch", False) for j in range(k)]
+
     def paradiag_solve_host(self, u, f, u0=None, raise_on_noconv=True):
         """u, f, u0: contiguous float64 host tensors or numpy arrays (pinned is fastest)."""
-        def hp(a, numel):
-            if a is None:
-                return None
-            if hasattr(a, "data_ptr"):
-                if a.is_cuda or not a.is_contiguous() or a.numel() != numel:
-                    raise ValueError("expected a contiguous host tensor of %d elements" % numel)
-                return C.c_void_p(a.data_ptr())
-            a = np.asarray(a)
-            if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != numel:
-                raise ValueError("expected a contiguous float64 array of %d elements" % numel)
-            return _hptr(a)
+        hp = self._host_ptr
         it = np.zeros(self.n, np.int32)
         rr = np.zeros(self.n)
         stats = np.zeros(PD_STATS_LEN)

@@ -85,6 +85,10 @@ struct pd_ctx {
   double *h_part = nullptr;    // pinned copy
   unsigned long long *d_imag = nullptr;
   double *d_stage_f = nullptr, *d_stage_u = nullptr, *d_stage_u0 = nullptr;
+  // pipelined host solves: a copy stream and two staging sets (f, u, u0)
+  cudaStream_t copy_stream = nullptr;
+  double *d_pf[2] = {nullptr, nullptr}, *d_pu[2] = {nullptr, nullptr}, *d_pu0[2] = {nullptr, nullptr};
+  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
   long long launches = 0;
   int num_sms = 0;
   double kappa = 1.0;     // A is scaled by kappa in eq. (1); the multigrid sees lam / kappa
@@ -1224,6 +1228,15 @@ void free_ctx(pd_ctx *c) {
   for (int k = 0; k < 2; k++)
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  if (c->copy_stream) {
+    cudaStreamSynchronize(c->copy_stream);
+    cudaStreamDestroy(c->copy_stream);
+  }
+  for (int q = 0; q < 2; q++) {
+    if (c->ev_in[q]) cudaEventDestroy(c->ev_in[q]);
+    if (c->ev_done[q]) cudaEventDestroy(c->ev_done[q]);
+    if (c->ev_out[q]) cudaEventDestroy(c->ev_out[q]);
+  }
   delete c;
 }
 
@@ -1626,6 +1639,62 @@ pd_status paradiag_solve_host(pd_ctx *c, double *h_u, const double *h_f, const d
     ck(c, cudaMemcpyAsync(h_u, c->d_stage_u, bytes, cudaMemcpyDeviceToHost, c->stream));
     ck(c, cudaStreamSynchronize(c->stream));
     return rc;
+  })
+}
+
+pd_status paradiag_solve_host_batch(pd_ctx *c, int count, double *const *h_u,
+                                    const double *const *h_f, const double *const *h_u0,
+                                    int *h_iters, double *h_relres, double *h_stats) {
+  if (!c || count < 1 || !h_u || !h_f) return PD_ERR_ARG;
+  for (int k = 0; k < count; k++)
+    if (!h_u[k] || !h_f[k]) return PD_ERR_ARG;
+  if (!c->have_V) return PD_ERR_STATE;
+  PD_TRY(c, {
+    const size_t bytes = (size_t)c->n * c->N * c->N * sizeof(double);
+    const size_t b0 = (size_t)c->N * c->N * sizeof(double);
+    if (!c->copy_stream) {
+      ck(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+      for (int q = 0; q < 2; q++) {
+        c->d_pf[q] = dalloc<double *>(c, bytes);
+        c->d_pu[q] = dalloc<double *>(c, bytes);
+        c->d_pu0[q] = dalloc<double *>(c, b0);
+        ck(c, cudaEventCreateWithFlags(&c->ev_in[q], cudaEventDisableTiming));
+        ck(c, cudaEventCreateWithFlags(&c->ev_done[q], cudaEventDisableTiming));
+        ck(c, cudaEventCreateWithFlags(&c->ev_out[q], cudaEventDisableTiming));
+      }
+    }
+    // the copy stream starts after the work queued on the context's stream before the call
+    ck(c, cudaEventRecord(c->ev_done[1], c->stream));
+    ck(c, cudaStreamWaitEvent(c->copy_stream, c->ev_done[1], 0));
+    auto copy_in = [&](int j) {
+      const int q = j & 1;
+      if (j >= 2) ck(c, cudaStreamWaitEvent(c->copy_stream, c->ev_done[q], 0));  // solve j-2 done
+      ck(c, cudaMemcpyAsync(c->d_pf[q], h_f[j], bytes, cudaMemcpyHostToDevice, c->copy_stream));
+      if (h_u0 && h_u0[j])
+        ck(c, cudaMemcpyAsync(c->d_pu0[q], h_u0[j], b0, cudaMemcpyHostToDevice, c->copy_stream));
+      ck(c, cudaEventRecord(c->ev_in[q], c->copy_stream));
+    };
+    copy_in(0);
+    pd_status worst = PD_OK;
+    for (int k = 0; k < count; k++) {
+      const int q = k & 1;
+      if (k + 1 < count) copy_in(k + 1);
+      ck(c, cudaStreamWaitEvent(c->stream, c->ev_in[q], 0));
+      if (k >= 2) ck(c, cudaStreamWaitEvent(c->stream, c->ev_out[q], 0));  // u of k-2 copied out
+      const pd_status rc = paradiag_solve(c, c->d_pu[q], c->d_pf[q],
+                                          (h_u0 && h_u0[k]) ? c->d_pu0[q] : nullptr,
+                                          h_iters ? h_iters + (size_t)k * c->n : nullptr,
+                                          h_relres ? h_relres + (size_t)k * c->n : nullptr,
+                                          h_stats ? h_stats + (size_t)k * PD_STATS_LEN : nullptr);
+      if (rc == PD_ERR_CUDA) return rc;
+      if (worst == PD_OK && rc != PD_OK) worst = rc;
+      ck(c, cudaEventRecord(c->ev_done[q], c->stream));
+      ck(c, cudaStreamWaitEvent(c->copy_stream, c->ev_done[q], 0));
+      ck(c, cudaMemcpyAsync(h_u[k], c->d_pu[q], bytes, cudaMemcpyDeviceToHost, c->copy_stream));
+      ck(c, cudaEventRecord(c->ev_out[q], c->copy_stream));
+    }
+    ck(c, cudaStreamSynchronize(c->copy_stream));
+    return worst;
   })
 }
 

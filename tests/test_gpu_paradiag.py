@@ -263,3 +263,23 @@ def test_refinement_residual32(fx, N, n, alpha):
         assert np.all(np.abs(r - r_ld) <= tol)
         assert abs(rn - rn_ld) <= 1e-5 * rn_ld + np.linalg.norm(tol)
         assert fn == pytest.approx(np.linalg.norm(fhat), rel=1e-5)
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_paradiag_host_batch_pipelined(precision):
+    """paradiag_solve_host_batch: three independent steps with host buffers, copies of the
+    neighbouring steps overlapping each solve, each result identical to paradiag_solve on
+    the same input."""
+    N, n, tau, alpha = 63, 8, 1.0 / 8, 1e-3
+    c = api.alpha_circulant_context(N, n, tau, alpha, precision=precision)
+    probs = [inputs.paradiag_problem(N, n, seed=20 + k) for k in range(3)]
+    fs = [torch.from_numpy(f).pin_memory() for f, _ in probs]
+    u0s = [torch.from_numpy(u0).pin_memory() for _, u0 in probs]
+    us = [torch.empty_like(fs[0]).pin_memory() for _ in range(3)]
+    outs = c.paradiag_solve_host_batch(us, fs, u0s)
+    for (f, u0), uh, out in zip(probs, us, outs):
+        ud = torch.empty(n, N, N, dtype=torch.float64, device="cuda")
+        ref = c.paradiag_solve(ud, dev(f), dev(u0))
+        assert np.array_equal(uh.numpy(), host(ud))
+        assert np.array_equal(out["iters"], ref["iters"])
+        assert out["relres_allatonce"] == ref["relres_allatonce"]
