@@ -95,8 +95,11 @@ __device__ __forceinline__ void fft_column(C *col, const C *__restrict__ tw, int
   __syncthreads();
 }
 
-// threads per grid point: two where both passes have at least two small DFTs
-template <int N1, int N2> __host__ __device__ constexpr int fft_tp() { return (N1 >= 2 && N2 >= 2) ? 2 : 1; }
+// threads per grid point: four for n = 128 (both passes have at least eight small DFTs
+// there), two where both passes have at least two, else one
+template <int N1, int N2> __host__ __device__ constexpr int fft_tp() {
+  return (N1 * N2 >= 128 && N1 >= 4 && N2 >= 4) ? 4 : ((N1 >= 2 && N2 >= 2) ? 2 : 1);
+}
 // CTAs per SM that the shared memory allows (at most 3), for the register budget
 template <typename T, int n> __host__ __device__ constexpr int fft_min_blocks() {
   return (229376 / (n * fft_points<T, n>() * (int)sizeof(typename Cx<T>::type))) >= 3
