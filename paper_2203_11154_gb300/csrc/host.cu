@@ -255,7 +255,7 @@ int part_blocks(const pd_ctx *c) { return std::max(allatonce_blocks(), residual_
 
 // Set-up autotuner of the fused kernels: on each global-memory level, times the
 // smoothing+restriction and interpolation+smoothing pair of every candidate (TMA tiles;
-// warp streams with 8, 16, 32, 64 or 128 rows per segment) on the context's own (zeroed)
+// warp streams with 8, 16, 32, 64, 128 or 256 rows per segment) on the context's own (zeroed)
 // buffers, all shifts active, and keeps the fastest; cfg.fused_variant 1 or 2 restricts
 // the candidates to one implementation.
 template <typename T>
@@ -263,7 +263,7 @@ void autotune_fused(pd_ctx *c) {
   Prec<T> &P = prec<T>(c);
   const int n = c->n;
   const FusedGeom g = fused_geom<T>();
-  const int segs[5] = {8, 16, 32, 64, 128};
+  const int segs[6] = {8, 16, 32, 64, 128, 256};
   cudaEvent_t e0, e1;
   ck(c, cudaEventCreate(&e0));
   ck(c, cudaEventCreate(&e1));
@@ -284,7 +284,7 @@ void autotune_fused(pd_ctx *c) {
     const int grid = std::max(1, std::min(c->num_sms, n * fused_tiles(B.N, g.TX, g.TY)));
     float best = 1e30f;
     int bv = 2, bs = 128;
-    for (int cand = 0; cand < 6; cand++) {
+    for (int cand = 0; cand < 7; cand++) {
       const int variant = cand == 0 ? 1 : 2, seg = cand == 0 ? 0 : segs[cand - 1];
       if (c->cfg.fused_variant != 0 && c->cfg.fused_variant != variant) continue;
       if (variant == 2 && seg > 2 * B.N) continue;
