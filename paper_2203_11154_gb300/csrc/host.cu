@@ -990,7 +990,8 @@ void allatonce_norms(pd_ctx *c, double *r, const double *u, const double *f, con
   if (c->bidiag && r32 && !r && c->cfg.fx_residual) {
     nb = residual_fx_blocks(c->num_sms);
     const bool use = fcache && c->d_fcache;
-    PD_PROF(PD_KC_RESIDUAL, 20.0 * m + (u0 && !(use && fcache == 2) ? 8.0 * m / c->n : 0.0), 0,
+    PD_PROF(PD_KC_RESIDUAL,
+            (use && fcache == 1 ? 28.0 : 20.0) * m + (u0 && !(use && fcache == 2) ? 8.0 * m / c->n : 0.0), 0,
             launch_residual_fx(c->stream, nb, c->N, c->n, c->boff, c->kappa, r32, u, f, u0,
                                c->d_u0coef, c->d_bd, c->d_bs, want_f, c->d_part,
                                use && fcache == 2 ? c->d_fcache : nullptr,
