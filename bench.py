@@ -384,6 +384,13 @@ def main():
                 "traffic": traffic, "alg_bytes_per_launch": tby / tn,
                 "avg_launch_us": 1e3 * tms / tn}
 
+    # the whole solve against the HBM peak: algorithmic bytes of every kernel of a step
+    # (from the profiled pass) over the step time of the timed pass
+    step_bytes = sum(v[2] for v in prof.values()) / args.steps
+    solve_gbs = step_bytes / (ms_ir / args.steps * 1e-3) / 1e9
+    solve_hbm = {"alg_bytes_per_step": step_bytes, "achieved": round(solve_gbs, 1), "peak": peak,
+                 "unit": "GB/s", "frac": round(solve_gbs / peak, 4)}
+
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_ir / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -398,7 +405,7 @@ def main():
                      "cycles_max": out64["cycles_max"]},
             "speedup_vs_fp64": value / value64,
             "clocks": ck, "e2e": e2e, "gpu_launches": launches,
-            "roofline": roofline, "kernels": kernels,
+            "roofline": roofline, "solve_hbm": solve_hbm, "kernels": kernels,
             "kernel_timing": "CUDA events around each launch on the context's stream, in a "
                              "second pass of the same %d steps (%.2f ms/step with the events)"
                              % (args.steps, ms_prof / args.steps)}

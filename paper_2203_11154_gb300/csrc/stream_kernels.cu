@@ -128,11 +128,12 @@ __device__ __forceinline__ void sr_unit(int N, int seg, int u, int nsx, int nsy,
   for (int s = 0; s < kDepth; s++) issue(s);
   // register windows (rows relative to the row i being loaded)
   C zm2[2], zm1[2], bm1[2], bm2[2], bm3[2];
-  C rm3[4], rm2[4], rm1[4], zpm4[4], zpm3[4], zpm2[4], rpm5[3], rpm4[3], rpm3[3];
+  C rm3[4], rm2[4], rm1[4], zpm4[4], zpm3[4], zpm2[4];
+  C va[2];  // vertical 1-2-1 sums of rt(z') of the coarse row being built (own columns)
+  va[0] = va[1] = czero<C>();
 #pragma unroll
   for (int q = 0; q < 4; q++) {
     rm3[q] = rm2[q] = rm1[q] = zpm4[q] = zpm3[q] = zpm2[q] = czero<C>();
-    if (q < 3) rpm5[q] = rpm4[q] = rpm3[q] = czero<C>();
     if (q < 2) zm2[q] = zm1[q] = bm1[q] = bm2[q] = bm3[q] = czero<C>();
   }
   T acc = 0;
@@ -218,27 +219,27 @@ __device__ __forceinline__ void sr_unit(int N, int seg, int u, int nsx, int nsy,
       const C nb = cadd(cadd(zpm4[k + 1], zpm2[k + 1]), cadd(zpm3[k], zpm3[k + 2]));
       rp[k] = sel(q_in && (k ? cin1 : cin0), csub(cadd(bm3[k], nb), cmul(cf.d, zpm3[k + 1])));
     }
-    {
-      const C r = shfl_dn1(rp[0]);
-#pragma unroll
-      for (int q = 0; q < 3; q++) {
-        rpm5[q] = rpm4[q];
-        rpm4[q] = rpm3[q];
+    // full weighting, separable: the vertical 1-2-1 sums per column are accumulated as the
+    // rows of rt(z') arrive (row q = i-3: weight 2 on an odd row, the centre of a coarse
+    // row; an even row closes the sums of the coarse row centred on q-1 and opens the
+    // next), then combined 1-2-1 across the columns a, a+1, a+2 (the last from the right
+    // lane) for the coarse point (I, J) at fine (q-1, a+1)
+    if (!(i & 1)) {
+      va[0] = cadd(va[0], cscale(rp[0], (T)2));
+      va[1] = cadd(va[1], cscale(rp[1], (T)2));
+    } else {
+      va[0] = cadd(va[0], rp[0]);
+      va[1] = cadd(va[1], rp[1]);
+      const C vr = shfl_dn1(va[0]);
+      const int cr = i - 4;
+      if (cr >= y0 && cr < y1 && out1) {
+        const int I = (cr - 1) >> 1, J = a >> 1;
+        if (IN || (I < Nc && J < Nc))
+          bco[(long long)I * bc.pitch + J] =
+              cscale(cadd(cadd(va[0], vr), cscale(va[1], (T)2)), (T)0.25);
       }
-      rpm3[0] = rp[0];
-      rpm3[1] = rp[1];
-      rpm3[2] = r;
-    }
-    // full weighting around the coarse point (I, J) at fine (i-4, a+1)
-    const int cr = i - 4;
-    if ((cr & 1) && cr >= y0 && cr < y1 && out1) {
-      const int I = (cr - 1) >> 1, J = a >> 1;
-      if (IN || (I < Nc && J < Nc)) {
-        const C e = cadd(cadd(rpm5[1], rpm3[1]), cadd(rpm4[0], rpm4[2]));
-        const C co = cadd(cadd(rpm5[0], rpm5[2]), cadd(rpm3[0], rpm3[2]));
-        const C sum = cadd(cadd(cscale(rpm4[1], (T)4), cscale(e, (T)2)), co);
-        bco[(long long)I * bc.pitch + J] = cscale(sum, (T)0.25);
-      }
+      va[0] = rp[0];
+      va[1] = rp[1];
     }
     zm2[0] = zm1[0];
     zm2[1] = zm1[1];

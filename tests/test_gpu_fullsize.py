@@ -82,8 +82,12 @@ def test_paradiag_2047_residual():
 def test_adjoint_1023_against_finite_differences(precision):
     """The differentiation workload at full size (1023^2, n = 64, the 8-mode target): the
     adjoint gradients in f and u0 along random directions against central differences of
-    the GPU forward solve (exact for the quadratic loss up to the solves' error), in kappa
-    against Richardson-extrapolated differences; spec bar 1e-6 relative."""
+    the GPU forward solve (exact for the quadratic loss up to the solves' error), bar 1e-6
+    relative.  In kappa the reference at 1e-6 is the tangent-linear derivative
+    <u_n - target, v_n>, v the forward solve of (B x I + kappa I x A) v = -(I x A) u: at this
+    size J is known only to the solves' floor (relres about 4e-12, the FP64 rounding of u
+    amplified by 8 kappa/h^2 = 8.4e6), which central differences in kappa divide by the step,
+    so they are kept as a check at 1e-5."""
     from paper_2203_11154_gb300 import adjoint
     w = inputs.WORKLOADS["adjoint-1023"]
     N, n, tau, alpha = w["N"], w["n"], w["tau"], w["alpha"]
@@ -125,6 +129,18 @@ def test_adjoint_1023_against_finite_differences(precision):
             return float(loss(f0, u00, one + e) - loss(f0, u00, one - e)) / (2 * e)
 
         fd_k = (4 * dk(5e-4) - dk(1e-3)) / 3
+        # tangent linear in kappa: A the five-point Laplacian (1/h^2)(4u - sum of the 4
+        # neighbours, zero outside), applied to every time step
+        h = 1.0 / (N + 1)
+        u = step(f0, u00, one)
+        au = 4.0 * u
+        au[:, 1:, :] -= u[:, :-1, :]
+        au[:, :-1, :] -= u[:, 1:, :]
+        au[:, :, 1:] -= u[:, :, :-1]
+        au[:, :, :-1] -= u[:, :, 1:]
+        v = step(-au / h ** 2, torch.zeros_like(u00), one)
+        tl_k = float(torch.sum((u[-1] - tt) * v[-1]))
     assert abs(fd_f - float(torch.sum(gf * df))) <= 1e-6 * abs(fd_f)
     assert abs(fd_u0 - float(torch.sum(gu0 * du0))) <= 1e-6 * abs(fd_u0)
-    assert abs(fd_k - gk) <= 1e-6 * abs(fd_k)
+    assert abs(tl_k - gk) <= 1e-6 * abs(tl_k)
+    assert abs(fd_k - gk) <= 1e-5 * abs(fd_k)
