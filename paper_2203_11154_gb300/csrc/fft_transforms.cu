@@ -96,17 +96,20 @@ __device__ __forceinline__ void fft_column(C *col, const C *__restrict__ tw, int
 }
 
 // threads per grid point: four for n = 128 (both passes have at least eight small DFTs
-// there), two where both passes have at least two, else one
-template <int N1, int N2> __host__ __device__ constexpr int fft_tp() {
-  return (N1 * N2 >= 128 && N1 >= 4 && N2 >= 4) ? 4 : ((N1 >= 2 && N2 >= 2) ? 2 : 1);
+// there) and for the inverse at n = 64 (measured: inverse 3 % faster, forward 3 % slower
+// than with two), two where both passes have at least two, else one
+template <int N1, int N2, bool INV> __host__ __device__ constexpr int fft_tp() {
+  return (N1 >= 4 && N2 >= 4 && (N1 * N2 >= 128 || (INV && N1 * N2 >= 64)))
+             ? 4
+             : ((N1 >= 2 && N2 >= 2) ? 2 : 1);
 }
-// CTAs per SM that the shared memory allows (at most 3), for the register budget
-template <typename T, int n> __host__ __device__ constexpr int fft_min_blocks() {
-  return (229376 / (n * fft_points<T, n>() * (int)sizeof(typename Cx<T>::type))) >= 3
-             ? 3
-             : ((229376 / (n * fft_points<T, n>() * (int)sizeof(typename Cx<T>::type))) < 1
-                    ? 1
-                    : 229376 / (n * fft_points<T, n>() * (int)sizeof(typename Cx<T>::type)));
+// CTAs per SM that the shared memory allows, at most 3 and at most 1024 threads (64
+// registers a thread at least), for the register budget
+template <typename T, int N1, int N2, bool INV> __host__ __device__ constexpr int fft_min_blocks() {
+  constexpr int n = N1 * N2, th = fft_points<T, n>() * fft_tp<N1, N2, INV>();
+  constexpr int by_smem = 229376 / (n * fft_points<T, n>() * (int)sizeof(typename Cx<T>::type));
+  constexpr int a = by_smem < 3 ? by_smem : 3, b = 1024 / th;
+  return (a < b ? a : b) < 1 ? 1 : (a < b ? a : b);
 }
 
 // exact FP32 -> FP64 by bit operations (the conversion instruction issues on the FP64
@@ -128,12 +131,12 @@ template <typename T, typename InT> __device__ __forceinline__ T load_in(const I
 // (t, p) of the CTA (p = threadIdx.x % P) serves point p: its loads and stores are the time
 // slices t, t + TP, ..., so a warp touches 32 consecutive points of one slice.
 template <typename T, int N1, int N2, typename InT>
-__global__ void __launch_bounds__(fft_points<T, N1 * N2>() * fft_tp<N1, N2>(), fft_min_blocks<T, N1 * N2>())
+__global__ void __launch_bounds__(fft_points<T, N1 * N2>() * fft_tp<N1, N2, false>(), fft_min_blocks<T, N1, N2, false>())
 k_fft_forward(int N, View g, const InT *__restrict__ f, const double *__restrict__ u0,
               const double *__restrict__ u0coef, const T *__restrict__ wk,
               const typename Cx<T>::type *__restrict__ tw) {
   using C = typename Cx<T>::type;
-  constexpr int n = N1 * N2, P = fft_points<T, n>(), TP = fft_tp<N1, N2>();
+  constexpr int n = N1 * N2, P = fft_points<T, n>(), TP = fft_tp<N1, N2, false>();
   extern __shared__ __align__(16) unsigned char fft_raw[];
   const int p = threadIdx.x % P, t = threadIdx.x / P;
   C *col = reinterpret_cast<C *>(fft_raw) + p;
@@ -179,12 +182,12 @@ k_fft_forward(int N, View g, const InT *__restrict__ f, const double *__restrict
 // u_k(point) (+)= wk[k] Re(DFT (- exponent) of z)_k, wk[k] = alpha^{-k/n}; z_j from z1 where
 // final_buf[j] is set, else z0; imag_check: atomic max of |wk[k] Im(.)_k| (bits of a double)
 template <typename T, int N1, int N2>
-__global__ void __launch_bounds__(fft_points<T, N1 * N2>() * fft_tp<N1, N2>(), fft_min_blocks<T, N1 * N2>())
+__global__ void __launch_bounds__(fft_points<T, N1 * N2>() * fft_tp<N1, N2, true>(), fft_min_blocks<T, N1, N2, true>())
 k_fft_inverse(int N, double *__restrict__ u, View z0, View z1, const int *__restrict__ final_buf,
               const T *__restrict__ wk, const typename Cx<T>::type *__restrict__ tw, int accumulate,
               int imag_check, unsigned long long *imag_bits) {
   using C = typename Cx<T>::type;
-  constexpr int n = N1 * N2, P = fft_points<T, n>(), TP = fft_tp<N1, N2>();
+  constexpr int n = N1 * N2, P = fft_points<T, n>(), TP = fft_tp<N1, N2, true>();
   extern __shared__ __align__(16) unsigned char fft_raw[];
   __shared__ float red[P * TP / 32];
   const int p = threadIdx.x % P, t = threadIdx.x / P;
@@ -192,6 +195,7 @@ k_fft_inverse(int N, double *__restrict__ u, View z0, View z1, const int *__rest
   const long long m = (long long)N * N;
   constexpr int kPer = n / TP;
   constexpr int kBatch = kPer < 16 ? kPer : 16;
+  constexpr int kOut = kPer < 8 ? kPer : 8;  // outputs (and accumulated u values) per batch
   float imax = 0.f;
   for (long long base = (long long)blockIdx.x * P; base < m; base += (long long)gridDim.x * P) {
     const long long x = base + p;
@@ -213,17 +217,17 @@ k_fft_inverse(int N, double *__restrict__ u, View z0, View z1, const int *__rest
     fft_column<C, N1, N2, P, TP>(col, tw, t);
     if (ok) {
 #pragma unroll 1
-      for (int q0 = 0; q0 < kPer; q0 += kBatch) {
-        double uo[kBatch];
+      for (int q0 = 0; q0 < kPer; q0 += kOut) {
+        double uo[kOut];
         if (accumulate) {
 #pragma unroll
-          for (int q = 0; q < kBatch; q++) {
+          for (int q = 0; q < kOut; q++) {
             const int s = TP * (q0 + q) + t, k = s / N2 + N1 * (s % N2);
             uo[q] = u[(long long)k * m + x];
           }
         }
 #pragma unroll
-        for (int q = 0; q < kBatch; q++) {
+        for (int q = 0; q < kOut; q++) {
           const int s = TP * (q0 + q) + t, k = s / N2 + N1 * (s % N2);
           const C v = col[s * P];
           const T re = v.x * wk[k];
@@ -293,7 +297,7 @@ void launch_fft_forward(cudaStream_t s, int num_sms, int N, int n, View g, const
                         const typename Cx<T>::type *tw) {
 #define PD_FFT_FWD(A, B)                                                                          \
   if (n == A * B) {                                                                               \
-    constexpr int P = fft_points<T, A * B>(), TH = P * fft_tp<A, B>();                           \
+    constexpr int P = fft_points<T, A * B>(), TH = P * fft_tp<A, B, false>();                    \
     const int grid = fft_grid(N, P, num_sms);                                                     \
     const size_t smem = fft_smem<T, A * B>();                                                     \
     if (f32)                                                                                      \
@@ -314,7 +318,7 @@ void launch_fft_inverse(cudaStream_t s, int num_sms, int N, int n, double *u, Vi
                         bool accumulate, bool imag_check, unsigned long long *imag_bits) {
 #define PD_FFT_INV(A, B)                                                                       \
   if (n == A * B) {                                                                            \
-    constexpr int P = fft_points<T, A * B>(), TH = P * fft_tp<A, B>();                        \
+    constexpr int P = fft_points<T, A * B>(), TH = P * fft_tp<A, B, true>();                  \
     const int grid = fft_grid(N, P, num_sms);                                                  \
     const size_t smem = fft_smem<T, A * B>();                                                  \
     k_fft_inverse<T, A, B><<<grid, TH, smem, s>>>(N, u, z0, z1, final_buf, wk, tw,             \
