@@ -7,12 +7,14 @@
 //   inverse:  u_k (+)= alpha^{-k/n} Re sum_j e^{-2 pi i k j / n} z_j
 // are a weighted DFT of length n, O(n log n) per point instead of the O(n^2) dense product.
 //
-// One thread per grid point.  n = N1 N2 (both powers of two): the four-step decomposition
+// TP threads (1, 2 or 4, see fft_tp) per grid point, P points per CTA.  n = N1 N2 (both
+// powers of two): the four-step decomposition
 //   X[k1 + N1 k2] = sum_{j2} w_n^{j2 k1} [sum_{j1} x[N2 j1 + j2] w_{N1}^{j1 k1}] w_{N2}^{j2 k2}
-// with the small DFTs as unrolled radix-2 butterflies in registers and the n values of the
-// thread's point in its own column of shared memory ([n][P], conflict-free, no barrier:
-// no thread reads another thread's column).  Loads and stores of the n time slices are
-// coalesced across the threads of a warp (consecutive grid points).
+// with the small DFTs as unrolled radix-2 butterflies in registers and the n values of a
+// point in its own column of shared memory ([n][P], conflict-free); the TP threads of a
+// point share the small DFTs of each pass, with CTA barriers around the passes.  Loads
+// and stores of the n time slices are coalesced across the threads of a warp (consecutive
+// grid points).
 #include "cplx.cuh"
 #include "pd_internal.h"
 
