@@ -144,7 +144,9 @@ k_fft_forward(int N, View g, const InT *__restrict__ f, const double *__restrict
   C *col = reinterpret_cast<C *>(fft_raw) + p;
   const long long m = (long long)N * N;
   constexpr int kPer = n / TP;                         // slices per thread
-  constexpr int kBatch = kPer < 16 ? kPer : 16;        // loads in flight per thread
+  // loads in flight per thread: all of an FP32 input when there are 32 (measured 5 %
+  // faster at n = 64 than 16), else up to 16
+  constexpr int kBatch = (sizeof(InT) == 4 && kPer >= 32) ? 32 : (kPer < 16 ? kPer : 16);
   for (long long base = (long long)blockIdx.x * P; base < m; base += (long long)gridDim.x * P) {
     const long long x = base + p;
     const bool ok = x < m;
