@@ -253,8 +253,9 @@ pd_status paradiag_solve_host(pd_ctx *ctx, double *h_u, const double *h_f, const
 
 /*
  * count independent steps of eq. (1) with host buffers, pipelined: the host-to-device copy
- * of step k+1's f and u0 and the device-to-host copy of step k-1's u run on a copy stream
- * that the context creates (once) while step k is solved on the context's stream, through
+ * of step k+1's f and u0 and the device-to-host copy of step k-1's u run on two copy
+ * streams (one per direction) that the context creates (once) while step k is solved on
+ * the context's stream, through
  * two device staging sets (2 x (f, u, u0)).  h_u[k], h_f[k]: [n][N][N] double host arrays
  * (pinned for full speed); h_u0 NULL or h_u0[k] NULL for no initial-value term.  h_iters,
  * h_relres: count x n entries; h_stats: count x PD_STATS_LEN (each may be NULL).

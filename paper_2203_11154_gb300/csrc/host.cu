@@ -85,8 +85,9 @@ struct pd_ctx {
   double *h_part = nullptr;    // pinned copy
   unsigned long long *d_imag = nullptr;
   double *d_stage_f = nullptr, *d_stage_u = nullptr, *d_stage_u0 = nullptr;
-  // pipelined host solves: a copy stream and two staging sets (f, u, u0)
-  cudaStream_t copy_stream = nullptr;
+  // pipelined host solves: copy streams (host-to-device, device-to-host: the host link
+  // carries both directions at once) and two staging sets (f, u, u0)
+  cudaStream_t copy_stream = nullptr, copy_stream_out = nullptr;
   double *d_pf[2] = {nullptr, nullptr}, *d_pu[2] = {nullptr, nullptr}, *d_pu0[2] = {nullptr, nullptr};
   cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
   long long launches = 0;
@@ -1233,6 +1234,10 @@ void free_ctx(pd_ctx *c) {
     cudaStreamSynchronize(c->copy_stream);
     cudaStreamDestroy(c->copy_stream);
   }
+  if (c->copy_stream_out) {
+    cudaStreamSynchronize(c->copy_stream_out);
+    cudaStreamDestroy(c->copy_stream_out);
+  }
   for (int q = 0; q < 2; q++) {
     if (c->ev_in[q]) cudaEventDestroy(c->ev_in[q]);
     if (c->ev_done[q]) cudaEventDestroy(c->ev_done[q]);
@@ -1655,6 +1660,7 @@ pd_status paradiag_solve_host_batch(pd_ctx *c, int count, double *const *h_u,
     const size_t b0 = (size_t)c->N * c->N * sizeof(double);
     if (!c->copy_stream) {
       ck(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+      ck(c, cudaStreamCreateWithFlags(&c->copy_stream_out, cudaStreamNonBlocking));
       for (int q = 0; q < 2; q++) {
         c->d_pf[q] = dalloc<double *>(c, bytes);
         c->d_pu[q] = dalloc<double *>(c, bytes);
@@ -1664,9 +1670,10 @@ pd_status paradiag_solve_host_batch(pd_ctx *c, int count, double *const *h_u,
         ck(c, cudaEventCreateWithFlags(&c->ev_out[q], cudaEventDisableTiming));
       }
     }
-    // the copy stream starts after the work queued on the context's stream before the call
+    // the copy streams start after the work queued on the context's stream before the call
     ck(c, cudaEventRecord(c->ev_done[1], c->stream));
     ck(c, cudaStreamWaitEvent(c->copy_stream, c->ev_done[1], 0));
+    ck(c, cudaStreamWaitEvent(c->copy_stream_out, c->ev_done[1], 0));
     auto copy_in = [&](int j) {
       const int q = j & 1;
       if (j >= 2) ck(c, cudaStreamWaitEvent(c->copy_stream, c->ev_done[q], 0));  // solve j-2 done
@@ -1690,11 +1697,12 @@ pd_status paradiag_solve_host_batch(pd_ctx *c, int count, double *const *h_u,
       if (rc == PD_ERR_CUDA) return rc;
       if (worst == PD_OK && rc != PD_OK) worst = rc;
       ck(c, cudaEventRecord(c->ev_done[q], c->stream));
-      ck(c, cudaStreamWaitEvent(c->copy_stream, c->ev_done[q], 0));
-      ck(c, cudaMemcpyAsync(h_u[k], c->d_pu[q], bytes, cudaMemcpyDeviceToHost, c->copy_stream));
-      ck(c, cudaEventRecord(c->ev_out[q], c->copy_stream));
+      ck(c, cudaStreamWaitEvent(c->copy_stream_out, c->ev_done[q], 0));
+      ck(c, cudaMemcpyAsync(h_u[k], c->d_pu[q], bytes, cudaMemcpyDeviceToHost, c->copy_stream_out));
+      ck(c, cudaEventRecord(c->ev_out[q], c->copy_stream_out));
     }
     ck(c, cudaStreamSynchronize(c->copy_stream));
+    ck(c, cudaStreamSynchronize(c->copy_stream_out));
     return worst;
   })
 }
