@@ -265,6 +265,47 @@ def test_refinement_residual32(fx, N, n, alpha):
         assert fn == pytest.approx(np.linalg.norm(fhat), rel=1e-5)
 
 
+def fx_bound(N, n, tau, alpha, u, fhat, r_ld):
+    """Element bound of the fixed-point residual (as in test_refinement_residual32): FP32
+    rounding of r, 2^-43 of the terms, the truncation ih2 2^-54 max|u_k|."""
+    ih2 = float(N + 1) ** 2
+    a = np.abs(u)
+    nb = np.zeros_like(u)
+    nb[:, 1:, :] += u[:, :-1, :]
+    nb[:, :-1, :] += u[:, 1:, :]
+    nb[:, :, 1:] += u[:, :, :-1]
+    nb[:, :, :-1] += u[:, :, 1:]
+    prev = np.roll(a, 1, axis=0)
+    prev[0] *= alpha
+    T = np.abs(fhat) + (a + prev) / tau + ih2 * np.abs(4 * u - nb)
+    umax = np.max(a.reshape(n, -1), axis=1)[:, None, None]
+    return 2.0 ** -24 * np.abs(r_ld) + 2.0 ** -43 * T + ih2 * 2.0 ** -54 * umax
+
+
+@pytest.mark.parametrize("N,n,alpha", [(127, 8, 1e-3), (255, 16, 1e-2), (63, 5, 0.3)])
+def test_refinement_residual32_transposed(N, n, alpha):
+    """The same residual for the adjoint's transposed time matrix, whose kernel walks the
+    time steps downwards: B^T = J B J with J the reversal of the time steps, so the
+    residual of (B^T x I + I x A) u = f is J times the oracle's long-double residual of
+    the forward system for J u and J f."""
+    tau = 1.0 / n
+    c = api.alpha_circulant_context(N, n, tau, alpha, precision=1)
+    adj = c.adjoint()
+    rng = np.random.default_rng(3 * N + n)
+    f = rng.standard_normal((n, N, N))
+    for u in (rng.standard_normal((n, N, N)),
+              np.cumsum(rng.standard_normal((n, N, N)), axis=0) * 1e-3 + 1.0):
+        r32 = torch.empty(n, N, N, dtype=torch.float32, device="cuda")
+        rn, fn = adj.pd_allatonce_residual32(r32, dev(u), dev(f), None)
+        r = host(r32).astype(np.float64)
+        ur, fr = np.ascontiguousarray(u[::-1]), np.ascontiguousarray(f[::-1])
+        rn_ld, r_ld = core.allatonce_residual_ld(N, n, tau, alpha, ur, fr)
+        tol = fx_bound(N, n, tau, alpha, ur, fr, r_ld)
+        assert np.all(np.abs(r[::-1] - r_ld) <= tol)
+        assert abs(rn - rn_ld) <= 1e-5 * rn_ld + np.linalg.norm(tol)
+        assert fn == pytest.approx(np.linalg.norm(f), rel=1e-5)
+
+
 @pytest.mark.parametrize("precision", [1, 0])
 def test_paradiag_host_batch_pipelined(precision):
     """paradiag_solve_host_batch: three independent steps with host buffers, copies of the
