@@ -1,7 +1,7 @@
 """Differentiation form: the adjoint gradients of J = 0.5 ||u_n - u_target||^2 with respect to
 the source f, the initial value u0 and the diffusion coefficient kappa, checked against a
 dense-solve reference gradient and against central finite differences of the GPU
-forward solve (the benchmark spec bar: 1e-6 relative), in FP64 and in the FP32 + refinement form."""
+forward solve (bar: 1e-6 relative), in FP64 and in the FP32 + refinement form."""
 import numpy as np
 import pytest
 
