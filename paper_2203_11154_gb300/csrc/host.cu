@@ -256,7 +256,7 @@ int part_blocks(const pd_ctx *c) { return std::max(allatonce_blocks(), residual_
 
 // Set-up autotuner of the fused kernels: on each global-memory level, times the
 // smoothing+restriction and interpolation+smoothing pair of every candidate (TMA tiles;
-// warp streams with 8, 16, 32, 64, 128 or 256 rows per segment) on the context's own (zeroed)
+// warp streams with 4, 8, 16, 32, 64, 128 or 256 rows per segment) on the context's own (zeroed)
 // buffers, all shifts active, and keeps the fastest; cfg.fused_variant 1 or 2 restricts
 // the candidates to one implementation.
 template <typename T>
@@ -264,7 +264,7 @@ void autotune_fused(pd_ctx *c) {
   Prec<T> &P = prec<T>(c);
   const int n = c->n;
   const FusedGeom g = fused_geom<T>();
-  const int segs[6] = {8, 16, 32, 64, 128, 256};
+  const int segs[7] = {4, 8, 16, 32, 64, 128, 256};
   cudaEvent_t e0, e1;
   ck(c, cudaEventCreate(&e0));
   ck(c, cudaEventCreate(&e1));
@@ -285,7 +285,7 @@ void autotune_fused(pd_ctx *c) {
     const int grid = std::max(1, std::min(c->num_sms, n * fused_tiles(B.N, g.TX, g.TY)));
     float best = 1e30f;
     int bv = 2, bs = 128;
-    for (int cand = 0; cand < 7; cand++) {
+    for (int cand = 0; cand < 8; cand++) {
       const int variant = cand == 0 ? 1 : 2, seg = cand == 0 ? 0 : segs[cand - 1];
       if (c->cfg.fused_variant != 0 && c->cfg.fused_variant != variant) continue;
       if (variant == 2 && seg > 2 * B.N) continue;
@@ -1435,7 +1435,7 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
     // solve state
     const FusedGeom g32 = fused_geom<float>(), g64 = fused_geom<double>();
     const int tiles = std::max({smooth_tiles(N), fused_tiles(N, g32.TX, g32.TY),
-                                fused_tiles(N, g64.TX, g64.TY), stream_units(N, 8)});
+                                fused_tiles(N, g64.TX, g64.TY), stream_units(N, 4)});
     c->st.max_tiles = tiles;
     c->st.active = dalloc<int *>(c, n * sizeof(int));
     c->st.iters = dalloc<int *>(c, n * sizeof(int));
