@@ -133,7 +133,10 @@ template <typename T, typename InT> __device__ __forceinline__ T load_in(const I
 // (t, p) of the CTA (p = threadIdx.x % P) serves point p: its loads and stores are the time
 // slices t, t + TP, ..., so a warp touches 32 consecutive points of one slice.
 template <typename T, int N1, int N2, typename InT>
-__global__ void __launch_bounds__(fft_points<T, N1 * N2>() * fft_tp<N1, N2, false>(), fft_min_blocks<T, N1, N2, false>())
+__global__ void __launch_bounds__(fft_points<T, N1 * N2>() * fft_tp<N1, N2, false>(),
+                                  (sizeof(InT) == 4 && fft_min_blocks<T, N1, N2, false>() > 2)
+                                      ? 2
+                                      : fft_min_blocks<T, N1, N2, false>())
 k_fft_forward(int N, View g, const InT *__restrict__ f, const double *__restrict__ u0,
               const double *__restrict__ u0coef, const T *__restrict__ wk,
               const typename Cx<T>::type *__restrict__ tw) {
@@ -151,6 +154,52 @@ k_fft_forward(int N, View g, const InT *__restrict__ f, const double *__restrict
     const long long x = base + p;
     const bool ok = x < m;
     const double u0x = (ok && u0) ? u0[x] : 0.0;
+    if constexpr (kBatch == kPer && sizeof(InT) == 4) {
+      // The thread's slices k = TP q + t are exactly the inputs of its pass-1 DFTs
+      // (j2 = t + TP r takes x[N2 j1 + j2], i.e. q = (N2/TP) j1 + r), so they go from
+      // registers into pass 1, and pass 2 writes its outputs straight to g: one exchange
+      // through the shared-memory column and two barriers per tile.
+      InT in[kPer];
+#pragma unroll
+      for (int q = 0; q < kPer; q++) in[q] = ok ? f[(long long)(TP * q + t) * m + x] : (InT)0;
+      constexpr int R1 = N2 / TP;
+#pragma unroll
+      for (int r = 0; r < R1; r++) {
+        const int j2 = t + TP * r;
+        C v[N1];
+#pragma unroll
+        for (int j1 = 0; j1 < N1; j1++) {
+          const int q = R1 * j1 + r, k = TP * q + t;
+          const double ck = u0 ? u0coef[k] : 0.0;
+          T val;
+          if (u0 && (__double_as_longlong(ck) << 1) != 0) val = (T)(to_f64(in[q]) + ck * u0x);
+          else val = (T)in[q];
+          v[j1] = cx<C>(val * wk[k], (T)0);
+        }
+        dft_small<C, N1>(v, tw, N2);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; k1++)
+          col[(N2 * k1 + j2) * P] = (k1 == 0 || j2 == 0) ? v[k1] : cmul(tw[(j2 * k1) % n], v[k1]);
+      }
+      __syncthreads();
+      C *gp = nullptr;
+      if (ok) {
+        const int i = (int)(x / N), c = (int)(x - (long long)i * N);
+        gp = reinterpret_cast<C *>(g.p) + (long long)i * g.pitch + c;
+      }
+      for (int k1 = t; k1 < N1; k1 += TP) {
+        C v[N2];
+#pragma unroll
+        for (int j2 = 0; j2 < N2; j2++) v[j2] = col[(N2 * k1 + j2) * P];
+        dft_small<C, N2>(v, tw, N1);
+        if (ok) {
+#pragma unroll
+          for (int k2 = 0; k2 < N2; k2++) gp[(long long)(k1 + N1 * k2) * g.plane] = v[k2];
+        }
+      }
+      __syncthreads();  // the columns are refilled by the next points
+      continue;
+    }
 #pragma unroll 1
     for (int q0 = 0; q0 < kPer; q0 += kBatch) {
       InT in[kBatch];
@@ -205,6 +254,57 @@ k_fft_inverse(int N, double *__restrict__ u, View z0, View z1, const int *__rest
     const long long x = base + p;
     const bool ok = x < m;
     const int i = (int)(x / N), c = (int)(x - (long long)i * N);
+    if constexpr (kPer <= 16 && sizeof(T) == 4) {
+      // as in k_fft_forward: the thread's slices j = TP q + t are the inputs of its pass-1
+      // DFTs, kept in registers; pass 2 writes (or adds) its outputs straight to u
+      C in[kPer];
+#pragma unroll
+      for (int q = 0; q < kPer; q++) {
+        const int j = TP * q + t;
+        const View &zv = (final_buf && final_buf[j]) ? z1 : z0;
+        in[q] = ok ? reinterpret_cast<const C *>(zv.p)[(long long)j * zv.plane + (long long)i * zv.pitch + c]
+                   : czero<C>();
+      }
+      constexpr int R1 = N2 / TP;
+#pragma unroll
+      for (int r = 0; r < R1; r++) {
+        const int j2 = t + TP * r;
+        C v[N1];
+#pragma unroll
+        for (int j1 = 0; j1 < N1; j1++) v[j1] = in[R1 * j1 + r];
+        dft_small<C, N1>(v, tw, N2);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; k1++)
+          col[(N2 * k1 + j2) * P] = (k1 == 0 || j2 == 0) ? v[k1] : cmul(tw[(j2 * k1) % n], v[k1]);
+      }
+      __syncthreads();
+      for (int k1 = t; k1 < N1; k1 += TP) {
+        C v[N2];
+#pragma unroll
+        for (int j2 = 0; j2 < N2; j2++) v[j2] = col[(N2 * k1 + j2) * P];
+        dft_small<C, N2>(v, tw, N1);
+        if (ok) {
+          constexpr int kO = N2 < 4 ? N2 : 4;  // accumulated u values per batch
+#pragma unroll
+          for (int k20 = 0; k20 < N2; k20 += kO) {
+            double uo[kO];
+            if (accumulate) {
+#pragma unroll
+              for (int q = 0; q < kO; q++) uo[q] = u[(long long)(k1 + N1 * (k20 + q)) * m + x];
+            }
+#pragma unroll
+            for (int q = 0; q < kO; q++) {
+              const int k = k1 + N1 * (k20 + q);
+              const T re = v[k20 + q].x * wk[k];
+              u[(long long)k * m + x] = accumulate ? uo[q] + to_f64(re) : to_f64(re);
+              if (imag_check) imax = fmaxf(imax, fabsf((float)(v[k20 + q].y * wk[k])));
+            }
+          }
+        }
+      }
+      __syncthreads();  // the columns are refilled by the next points
+      continue;
+    }
 #pragma unroll 1
     for (int q0 = 0; q0 < kPer; q0 += kBatch) {
       C in[kBatch];
