@@ -86,9 +86,10 @@ typedef struct {
                           stream is not the legacy default stream and profiling is off;
                           0: every kernel launched one by one (default 1) */
     int fx_residual;   /* precision 1 with a bidiagonal B: the refinement residual of eq. (1)
-                          without FP64 instructions (stencil difference exact in 64-bit fixed
-                          point per 16 x 128 tile, the other terms in float-float; more
-                          accurate than the FP64 formula); 0: FP64 (default 1) */
+                          without FP64 instructions (stencil difference exact in fixed point,
+                          three FP32 limbs, one scale per 16 x 128 tile and time step; the
+                          other terms in float-float; more accurate than the FP64 formula);
+                          0: FP64 (default 1) */
     int fft_transforms; /* 1: when V and V^{-1} given at set-up are those of the alpha-
                           circulant B (pd_alpha_circulant, to 1e-12) and n is a power of two
                           <= 128, the time transforms run as Gamma-weighted FFTs (both
@@ -115,6 +116,14 @@ void pd_config_default(pd_config *cfg);
  */
 pd_status pd_alpha_circulant(int n, double tau, double alpha, double *h_B, double *h_shifts,
                              double *h_V, double *h_Vinv, double *h_u0_coef);
+
+/*
+ * The shifts and eigenvector matrices alone (the same closed form as pd_alpha_circulant):
+ * h_shifts 2n doubles, h_V and h_Vinv 2*n*n doubles, complex interleaved (re, im), the
+ * layout of a C99 double _Complex array; any may be NULL.  Errors as pd_alpha_circulant.
+ */
+pd_status pd_shifts_alpha_circulant(int n, double tau, double alpha, double *h_shifts, double *h_V,
+                                    double *h_Vinv);
 
 /*
  * Creates a context for N x N grids and n shifts (Sec. 1, eq. (1)-(2)).

@@ -30,7 +30,8 @@ KERNEL_CLASSES = ["smooth0", "restrict0", "prolong0", "smooth_c", "restrict_c", 
 STATUS = {0: "PD_OK", 1: "PD_ERR_ARG", 2: "PD_ERR_CUDA", 3: "PD_ERR_NOMEM", 4: "PD_ERR_NOCONV",
           5: "PD_ERR_NAN", 6: "PD_ERR_SING", 7: "PD_ERR_STATE"}
 
-EXPORTS = ["pd_config_default", "pd_alpha_circulant", "paradiag_setup", "pd_adjoint_setup",
+EXPORTS = ["pd_config_default", "pd_alpha_circulant", "pd_shifts_alpha_circulant", "paradiag_setup",
+           "pd_adjoint_setup",
            "pd_num_levels",
            "pd_get_omega", "mg_vcycle", "shifted_solve_batched", "paradiag_solve",
            "paradiag_solve_host", "pd_smooth", "pd_residual_restrict", "pd_prolong_add",
@@ -80,6 +81,7 @@ def lib(path=None):
         sig = {
             "pd_config_default": (None, [C.POINTER(pd_config)]),
             "pd_alpha_circulant": (_I, [_I, _D, _D, _P, _P, _P, _P, _P]),
+            "pd_shifts_alpha_circulant": (_I, [_I, _D, _D, _P, _P, _P]),
             "paradiag_setup": (_I, [C.POINTER(_P), _I, _D, _I, _P, _P, _P, _P, _P, _P,
                                     C.POINTER(pd_config), _P]),
             "pd_adjoint_setup": (_I, [_P, C.POINTER(_P)]),
@@ -169,6 +171,16 @@ def pd_alpha_circulant(n, tau, alpha):
                                     _hptr(Vi), _hptr(c0)), "pd_alpha_circulant")
     return B, sh.view(np.complex128), V.view(np.complex128).reshape(n, n), \
         Vi.view(np.complex128).reshape(n, n), c0
+
+
+def pd_shifts_alpha_circulant(n, tau, alpha):
+    """(shifts [n] complex, V, Vinv [n][n] complex)."""
+    sh = np.zeros(2 * n)
+    V = np.zeros(2 * n * n)
+    Vi = np.zeros(2 * n * n)
+    _check(lib().pd_shifts_alpha_circulant(n, float(tau), float(alpha), _hptr(sh), _hptr(V), _hptr(Vi)),
+           "pd_shifts_alpha_circulant")
+    return sh.view(np.complex128), V.view(np.complex128).reshape(n, n), Vi.view(np.complex128).reshape(n, n)
 
 
 class Context:

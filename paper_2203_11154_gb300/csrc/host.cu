@@ -1276,6 +1276,11 @@ void pd_config_default(pd_config *cfg) {
   cfg->fft_transforms = 1;
 }
 
+pd_status pd_shifts_alpha_circulant(int n, double tau, double alpha, double *shifts, double *V,
+                                    double *Vinv) {
+  return pd_alpha_circulant(n, tau, alpha, nullptr, shifts, V, Vinv, nullptr);
+}
+
 pd_status pd_alpha_circulant(int n, double tau, double alpha, double *B, double *shifts,
                              double *V, double *Vinv, double *u0coef) {
   if (n < 1 || !(tau > 0) || !(alpha > 0) || alpha > 1) return PD_ERR_ARG;

@@ -39,6 +39,15 @@ def test_config_defaults():
     assert c.kappa == 1.0 and c.outer_maxit == 0 and c.max_refine == 12 and c.inner_maxit == 2
 
 
+def test_shifts_alpha_circulant_is_the_same_closed_form():
+    for n, tau, alpha in [(16, 1 / 16, 1e-2), (7, 0.3, 0.5)]:
+        sh, V, Vi = api.pd_shifts_alpha_circulant(n, tau, alpha)
+        _, sh2, V2, Vi2, _ = api.pd_alpha_circulant(n, tau, alpha)
+        assert np.array_equal(sh, sh2) and np.array_equal(V, V2) and np.array_equal(Vi, Vi2)
+    with pytest.raises(api.PDError):
+        api.pd_shifts_alpha_circulant(4, 0.1, 0.0)
+
+
 def test_alpha_circulant_matches_oracle():
     for n, tau, alpha in [(16, 1 / 16, 1e-2), (64, 1 / 64, 1e-3), (5, 0.3, 0.5)]:
         B, sh, V, Vi, c0 = api.pd_alpha_circulant(n, tau, alpha)
