@@ -131,7 +131,8 @@ template <typename T, typename InT> __device__ __forceinline__ T load_in(const I
 
 // g_j(point) = wk-weighted DFT (+ exponent) of fhat; wk[k] = s alpha^{k/n} / n.  Thread
 // (t, p) of the CTA (p = threadIdx.x % P) serves point p: its loads and stores are the time
-// slices t, t + TP, ..., so a warp touches 32 consecutive points of one slice.
+// slices t, t + TP, ..., so a warp touches 32 consecutive points of one slice.  With FP32
+// input at most two CTAs a SM: the registers hold a thread's slices (see below).
 template <typename T, int N1, int N2, typename InT>
 __global__ void __launch_bounds__(fft_points<T, N1 * N2>() * fft_tp<N1, N2, false>(),
                                   (sizeof(InT) == 4 && fft_min_blocks<T, N1, N2, false>() > 2)
