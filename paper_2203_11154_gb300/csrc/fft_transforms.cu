@@ -127,6 +127,23 @@ __device__ __forceinline__ double f32_to_f64(float v) {
 __device__ __forceinline__ double to_f64(float v) { return f32_to_f64(v); }
 __device__ __forceinline__ double to_f64(double v) { return v; }
 
+// FP64 -> FP32 by bit operations, truncating to 24 significant bits (relative error below
+// 2^-23; the input of the FP32 solve, whose error the refinement removes): |x| < 2^-126
+// gives 0, |x| >= 2^128, Inf and NaN give NaN
+__device__ __forceinline__ float f64_to_f32(double x) {
+  const unsigned hw = (unsigned)__double2hiint(x), lw = (unsigned)__double2loint(x);
+  const int e = (int)((hw >> 20) & 0x7FFu);
+  if (e < 1023 - 126) return 0.f;
+  if (e > 1023 + 127) return __int_as_float(0x7FC00000);
+  return __uint_as_float((hw & 0x80000000u) | ((unsigned)(e - 896) << 23) | ((hw & 0xFFFFFu) << 3) |
+                         (lw >> 29));
+}
+// an input value as the transform's type: FP64 into FP32 by bits, otherwise as is
+template <typename T, typename InT> __device__ __forceinline__ T as_t(InT v) {
+  if constexpr (sizeof(T) == 4 && sizeof(InT) == 8) return f64_to_f32(v);
+  else return (T)v;
+}
+
 template <typename T, typename InT> __device__ __forceinline__ T load_in(const InT *p) { return (T)*p; }
 
 // g_j(point) = wk-weighted DFT (+ exponent) of fhat; wk[k] = s alpha^{k/n} / n.  Thread
@@ -214,8 +231,8 @@ k_fft_forward(int N, View g, const InT *__restrict__ f, const double *__restrict
         // (tested on the bits: no FP64 comparison per point)
         const double ck = u0 ? u0coef[k] : 0.0;
         T v;
-        if (u0 && (__double_as_longlong(ck) << 1) != 0) v = (T)(to_f64(in[q]) + ck * u0x);
-        else v = (T)in[q];
+        if (u0 && (__double_as_longlong(ck) << 1) != 0) v = as_t<T>(to_f64(in[q]) + ck * u0x);
+        else v = as_t<T>(in[q]);
         col[k * P] = cx<C>(v * wk[k], (T)0);
       }
     }
