@@ -89,7 +89,8 @@ typedef struct {
                           without FP64 instructions (stencil difference exact in fixed point,
                           three FP32 limbs, one scale per 16 x 128 tile and time step; the
                           other terms in float-float; more accurate than the FP64 formula);
-                          0: FP64 (default 1) */
+                          likewise the residuals of the refined shifted solves (eq. (2), per
+                          complex component); 0: FP64 (default 1) */
     int fft_transforms; /* 1: when V and V^{-1} given at set-up are those of the alpha-
                           circulant B (pd_alpha_circulant, to 1e-12) and n is a power of two
                           <= 128, the time transforms run as Gamma-weighted FFTs (both

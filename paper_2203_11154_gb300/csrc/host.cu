@@ -882,10 +882,15 @@ void refine_eval_launch(RefRun &r) {
   const bool first = r.evals == 0;
   const double h = hl(c, 0);
   const double w = 8.0, m = (double)N * N;
-  PD_PROF(PD_KC_RESIDUAL, (first ? 16.0 + w : 32.0 + w) * m, 0,
-          launch_shift_residual(c->stream, N, n, first ? nullptr : r.z, r.b, c->d_c1,
-                                c->kappa / (h * h), (float)rs(c, 0), view(B.b, N, B.P),
-                                first ? nullptr : c->d_frozen, first, c->d_srpart));
+  if (!first && c->cfg.fx_residual)  // without FP64 arithmetic (the first one is r = b)
+    PD_PROF(PD_KC_RESIDUAL, (32.0 + w) * m, 0,
+            launch_shift_residual_fx(c->stream, N, n, r.z, r.b, c->d_c1, c->kappa / (h * h),
+                                     (float)rs(c, 0), view(B.b, N, B.P), c->d_frozen, c->d_srpart));
+  else
+    PD_PROF(PD_KC_RESIDUAL, (first ? 16.0 + w : 32.0 + w) * m, 0,
+            launch_shift_residual(c->stream, N, n, first ? nullptr : r.z, r.b, c->d_c1,
+                                  c->kappa / (h * h), (float)rs(c, 0), view(B.b, N, B.P),
+                                  first ? nullptr : c->d_frozen, first, c->d_srpart));
   ck_launch(c);
   ck(c, cudaMemcpyAsync(c->h_srpart, c->d_srpart, (first ? 2 : 1) * (size_t)n * gx * sizeof(double),
                         cudaMemcpyDeviceToHost, c->stream));

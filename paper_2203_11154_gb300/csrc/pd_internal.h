@@ -90,6 +90,11 @@ void launch_residual_fx(cudaStream_t s, int blocks, int N, int n, int off, doubl
 
 // ---- FP64 refinement of the shifted systems (shift_refine.cu) ----
 int shift_residual_blocks(int N, int n);
+// the same residual without FP64 instructions (residual_fx.cu); z must not be NULL and
+// the sums of |b|^2 are not formed
+void launch_shift_residual_fx(cudaStream_t s, int N, int n, const double2 *z, const double2 *b,
+                              const double2 *c1, double off, float oscale, View out,
+                              const int *frozen, double *part);
 void launch_round_to_float(cudaStream_t s, long long count, const double *x, float *y);
 void launch_shift_residual(cudaStream_t s, int N, int n, const double2 *z, const double2 *b,
                            const double2 *c1, double off, float oscale, View out,

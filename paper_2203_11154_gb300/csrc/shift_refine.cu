@@ -136,8 +136,9 @@ void launch_round_to_float(cudaStream_t s, long long count, const double *x, flo
   k_round_to_float<<<4 * 152, 256, 0, s>>>(count, x, y);
 }
 
+// CTAs per shift: one wave of two CTAs per SM over all shifts
 int shift_residual_blocks(int N, int n) {
-  const int want = (4 * 152 + n - 1) / n;
+  const int want = (2 * 152) / n;
   return want < 1 ? 1 : (want > N ? N : want);
 }
 
