@@ -4,7 +4,7 @@ unit square) on one GB300: shifted solves per second to relative residual 1e-10,
 the FP32-multigrid + FP64-refinement form (the value) and the plain FP64 form (beside
 it), with the roofline of the dominant kernel and the FP64 CPU oracle as a baseline.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload paradiag-1023]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload paradiag-2047]
   python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
 
 One step = one whole paradiag_solve: transforms, n batched multigrid solves, refinement.
@@ -94,38 +94,54 @@ class Clocks:
                 "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows)}
 
 
-def oracle_sample(workload, threads):
+class OracleSample:
     """Times the FP64 CPU oracle on a bounded sample of the workload and scales it to the
-    whole step: the forward transform on 1/16 of the grid points (x16, and x2 for the
-    inverse transform of the same size) plus the multigrid solves of `threads` of the n
-    shifted systems on the full grid, one per thread (x n/threads)."""
-    from oracle import core, lfa
-    from paper_2203_11154_gb300 import inputs
+    whole step: the forward transform on `pts` of the m grid points (x m/pts, and x2 for
+    the inverse transform of the same size) plus the multigrid solves of `threads` of the n
+    shifted systems on the full grid, one per thread (x n/threads).  The inputs, the
+    transformed right-hand sides of the sampled shifts and their relaxation table are
+    prepared once; every call of time() repeats only the timed oracle work."""
 
-    w = inputs.WORKLOADS[workload]
-    N, n, tau, alpha = w["N"], w["n"], w["tau"], w["alpha"]
-    s = max(1, min(threads, n))
-    core.set_threads(threads)
-    f, u0 = inputs.paradiag_problem(N, n, seed=w["seed"])
-    lam, V, Vinv = core.alpha_circulant(n, tau, alpha)
-    fhat = core.assemble_rhs(N, n, tau, f, u0).reshape(n, -1)
-    m = fhat.shape[1]
-    ms = m // 16
-    x = np.ascontiguousarray(fhat[:, :ms])
-    t0 = time.perf_counter()
-    core.time_transform(Vinv, x)
-    t_tr = time.perf_counter() - t0
-    sel = np.linspace(0, n - 1, s).astype(int)
-    g = (Vinv[sel] @ fhat).reshape(s, N, N)
-    om = lfa.omega_table(lam[sel], N, mode="lfa")
-    t0 = time.perf_counter()
-    core.shifted_solve_batch(N, lam[sel], om, g, tol=1e-10)
-    t_mg = time.perf_counter() - t0
-    step = 2 * t_tr * (m / ms) + t_mg * (n / s)
-    desc = ("forward transform of %d of %d grid points (x%.0f, x2 for the inverse) and multigrid "
-            "solves of %d of %d shifted systems on the full %dx%d grid (x%.1f); %s workload"
-            % (ms, m, m / ms, s, n, N, N, n / s, workload))
-    return n / step, t_tr + t_mg, desc
+    def __init__(self, workload, threads, f=None, u0=None):
+        from oracle import core, lfa
+        from paper_2203_11154_gb300 import inputs
+
+        self.core = core
+        w = inputs.WORKLOADS[workload]
+        self.workload = workload
+        N, n, tau, alpha = w["N"], w["n"], w["tau"], w["alpha"]
+        self.N, self.n = N, n
+        self.s = max(1, min(threads, n))
+        core.set_threads(threads)
+        if f is None:
+            f, u0 = inputs.paradiag_problem(N, n, seed=w["seed"])
+        lam, V, Vinv = core.alpha_circulant(n, tau, alpha)
+        fhat = core.assemble_rhs(N, n, tau, f, u0).reshape(n, -1)
+        self.m = fhat.shape[1]
+        self.pts = min(self.m // 16, 65536)
+        self.Vinv = Vinv
+        self.x = np.ascontiguousarray(fhat[:, :self.pts])
+        sel = np.linspace(0, n - 1, self.s).astype(int)
+        self.lam = lam[sel]
+        self.g = (Vinv[sel] @ fhat).reshape(self.s, N, N)
+        del fhat
+        self.om = lfa.omega_table(self.lam, N, mode="lfa")
+
+    def time(self):
+        """(solves/s of the whole step scaled from the sample, seconds of oracle work, text)."""
+        core = self.core
+        t0 = time.perf_counter()
+        core.time_transform(self.Vinv, self.x)
+        t_tr = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        core.shifted_solve_batch(self.N, self.lam, self.om, self.g, tol=1e-10)
+        t_mg = time.perf_counter() - t0
+        m, ms, n, s = self.m, self.pts, self.n, self.s
+        step = 2 * t_tr * (m / ms) + t_mg * (n / s)
+        desc = ("forward transform of %d of %d grid points (x%.0f, x2 for the inverse) and "
+                "multigrid solves of %d of %d shifted systems on the full %dx%d grid (x%.1f); "
+                "%s workload" % (ms, m, m / ms, s, n, self.N, self.N, n / s, self.workload))
+        return n / step, t_tr + t_mg, desc
 
 
 def rank_seed(workload, rank):
@@ -162,6 +178,7 @@ def bench_config(workload):
             "omega": "LFA per shift and level", "tol_allatonce": 1e-10,
             "precision": "FP32 multigrid + FP64 refinement on eq. (1)",
             "l2": "inputs larger than L2 (f: %d MB)" % f_mb,
+            "imag_check": "max |Im((V kron I) z)| formed in every inverse transform",
             "parallelism": "one independent problem per rank"}
 
 
@@ -170,8 +187,9 @@ def run_reference(args, rank, world):
         return
     cores = os.cpu_count() or 1
     vals, secs = [], []
+    sample = OracleSample(args.workload, cores)
     for k in range(args.warmup + args.steps):
-        v, sec, desc = oracle_sample(args.workload, cores)
+        v, sec, desc = sample.time()
         if k >= args.warmup:
             vals.append(v)
             secs.append(sec)
@@ -246,9 +264,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="paradiag-1023",
+    ap.add_argument("--workload", default="paradiag-2047",
                     choices=["paradiag-511", "paradiag-1023", "paradiag-2047", "uneven-8"])
-    ap.add_argument("--fp64-steps", type=int, default=None)
+    ap.add_argument("--fp64-steps", type=int, default=None,
+                    help="timed steps of the FP64 form beside the value (default: the smaller "
+                         "of --steps and 3 at N = 2047, else --steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -318,7 +338,7 @@ def main():
         return ms, out, prof, ctx.launch_count() - l0, ck
 
     # FP32 multigrid inside FP64 refinement (the value)
-    ctx = api.alpha_circulant_context(N, n, tau, alpha, precision=1, imag_check=0)
+    ctx = api.alpha_circulant_context(N, n, tau, alpha, precision=1, imag_check=1)
     clocks = Clocks(local)
     ms_ir, out_ir, _, launches, ck = timed(ctx, args.steps, args.warmup, clocks=clocks)
     value = job_throughput(n, args.steps, world, ms_ir)
@@ -358,9 +378,9 @@ def main():
     ctx.destroy()
 
     # plain FP64 (beside the value)
-    ctx64 = api.alpha_circulant_context(N, n, tau, alpha, precision=0, imag_check=0)
-    k64 = args.fp64_steps or args.steps
-    ms64, out64, _, _, _ = timed(ctx64, k64, args.warmup)
+    ctx64 = api.alpha_circulant_context(N, n, tau, alpha, precision=0, imag_check=1)
+    k64 = args.fp64_steps or (min(args.steps, 3) if N >= 2047 else args.steps)
+    ms64, out64, _, _, _ = timed(ctx64, k64, max(3, min(args.warmup, 3)))
     ctx64.destroy()
     value64 = job_throughput(n, k64, world, ms64)
 
@@ -399,6 +419,7 @@ def main():
             "launch": "multigrid cycles replayed as CUDA graphs on a non-default stream",
             "relres_allatonce": out_ir["relres_allatonce"],
             "refine_steps": out_ir["refine_steps"], "cycles_max": out_ir["cycles_max"],
+            "imag_max": out_ir["imag_max"],
             "fp64": {"value": value64, "unit": "solves/s", "ms_per_step": ms64 / k64,
                      "steps": k64, "relres_shift_max": out64["relres_shift_max"],
                      "relres_allatonce": out64["relres_allatonce"],
@@ -414,8 +435,9 @@ def main():
         # the sample repeated until about 10 s of oracle work (at most 16 times); the median
         cores = os.cpu_count() or 1
         vals, tot = [], 0.0
+        sample = OracleSample(args.workload, cores, f, u0)
         while tot < 10.0 and len(vals) < 16:
-            v, sec, desc = oracle_sample(args.workload, cores)
+            v, sec, desc = sample.time()
             vals.append(v)
             tot += sec
         line["cpu_baseline"] = {"value": float(np.median(vals)), "unit": "solves/s", "cores": cores,

@@ -127,13 +127,31 @@ pd_status pd_shifts_alpha_circulant(int n, double tau, double alpha, double *h_s
                                     double *h_Vinv);
 
 /*
+ * The diagonalisation B = V D V^{-1} of a real time matrix (Sec. 1: it splits the
+ * all-at-once system (1) into the shifted systems (2)), on the host: balancing by powers
+ * of two, Householder reduction to Hessenberg form, complex Schur form by shifted QR
+ * steps, eigenvectors by back substitution on the triangular factor, V^{-1} by
+ * Gauss-Jordan elimination with partial pivoting.  For the boundary-value B of
+ * Example 1 (eq. (9)), the quasi-BVM B of Example 2 (eq. (10)) or any diagonalisable B
+ * with distinct eigenvalues.
+ *   n        1 <= n <= 4096.   h_B  n*n doubles, row-major, real.
+ *   h_shifts 2n doubles (re, im) of D, any order; h_V, h_Vinv 2*n*n doubles, complex
+ *            row-major, the columns of V of unit 2-norm; any output may be NULL.
+ * Host only (no GPU needed).  Errors: PD_ERR_ARG (n, NULL h_B), PD_ERR_SING (non-finite
+ * B, no convergence of the QR steps, or V singular: B not diagonalisable in FP64),
+ * PD_ERR_NOMEM.
+ */
+pd_status pd_diagonalize(int n, const double *h_B, double *h_shifts, double *h_V, double *h_Vinv);
+
+/*
  * Creates a context for N x N grids and n shifts (Sec. 1, eq. (1)-(2)).
  *   N         interior points per side, 2^k - 1 with N >= cfg->coarsest_n.
  *   h         mesh step; must equal 1/(N+1) (the unit square).
  *   n         number of shifts / time steps, 1 <= n <= 128.
- *   h_shifts  2n doubles: lam_j (re, im).  Required.
+ *   h_shifts  2n doubles: lam_j (re, im); or NULL together with h_V and h_Vinv when
+ *             h_B is given: the context then diagonalises B itself (pd_diagonalize).
  *   h_V, h_Vinv  2*n*n doubles each (complex row-major) or both NULL (then only the
- *             shifted-solve calls are valid).
+ *             shifted-solve calls are valid, unless B alone is given).
  *   h_B       n*n real time matrix, row-major, or NULL.  Required by precision 1
  *             (the refinement residual uses B directly, never V).
  *   h_u0_coef n doubles or NULL (zeros): fhat_k = f_k + u0_coef[k] u0.
@@ -142,7 +160,8 @@ pd_status pd_shifts_alpha_circulant(int n, double tau, double alpha, double *h_s
  *   stream    the cudaStream_t every call of this context is ordered on (NULL = the
  *             legacy default stream).  The context never creates or destroys streams.
  * Setup runs on the host (shift tables, LFA, coarsest-grid inverses) and allocates
- * all device memory.  Errors: PD_ERR_ARG, PD_ERR_NOMEM, PD_ERR_CUDA, PD_ERR_SING.
+ * all device memory.  Errors: PD_ERR_ARG, PD_ERR_NOMEM, PD_ERR_CUDA, PD_ERR_SING (also:
+ * B given alone could not be diagonalised).
  */
 pd_status paradiag_setup(pd_ctx **ctx, int N, double h, int n, const double *h_shifts,
                          const double *h_V, const double *h_Vinv, const double *h_B,

@@ -30,7 +30,8 @@ KERNEL_CLASSES = ["smooth0", "restrict0", "prolong0", "smooth_c", "restrict_c", 
 STATUS = {0: "PD_OK", 1: "PD_ERR_ARG", 2: "PD_ERR_CUDA", 3: "PD_ERR_NOMEM", 4: "PD_ERR_NOCONV",
           5: "PD_ERR_NAN", 6: "PD_ERR_SING", 7: "PD_ERR_STATE"}
 
-EXPORTS = ["pd_config_default", "pd_alpha_circulant", "pd_shifts_alpha_circulant", "paradiag_setup",
+EXPORTS = ["pd_config_default", "pd_alpha_circulant", "pd_shifts_alpha_circulant", "pd_diagonalize",
+           "paradiag_setup",
            "pd_adjoint_setup",
            "pd_num_levels",
            "pd_get_omega", "mg_vcycle", "shifted_solve_batched", "paradiag_solve",
@@ -82,6 +83,7 @@ def lib(path=None):
             "pd_config_default": (None, [C.POINTER(pd_config)]),
             "pd_alpha_circulant": (_I, [_I, _D, _D, _P, _P, _P, _P, _P]),
             "pd_shifts_alpha_circulant": (_I, [_I, _D, _D, _P, _P, _P]),
+            "pd_diagonalize": (_I, [_I, _P, _P, _P, _P]),
             "paradiag_setup": (_I, [C.POINTER(_P), _I, _D, _I, _P, _P, _P, _P, _P, _P,
                                     C.POINTER(pd_config), _P]),
             "pd_adjoint_setup": (_I, [_P, C.POINTER(_P)]),
@@ -191,9 +193,14 @@ class Context:
         import torch
         self.N, self.n = int(N), int(n)
         self.cfg = cfg if cfg is not None else config()
-        sh = np.ascontiguousarray(np.asarray(shifts, dtype=np.complex128).reshape(n))
-        self._keep = [sh]
-        args = [_hptr(sh.view(np.float64))]
+        if shifts is None:
+            sh = None
+            self._keep = []
+            args = [None]
+        else:
+            sh = np.ascontiguousarray(np.asarray(shifts, dtype=np.complex128).reshape(n))
+            self._keep = [sh]
+            args = [_hptr(sh.view(np.float64))]
         for a in (V, Vinv):
             if a is None:
                 args.append(None)
@@ -462,16 +469,27 @@ def paradiag2_context(N, n, tau, alpha, **cfg_fields):
     return Context(N, n, sh, V, Vi, B, c0, None, config(**cfg_fields))
 
 
+def pd_diagonalize(B):
+    """(shifts [n] complex, V, Vinv [n][n] complex) of the real n x n B = V D V^{-1},
+    computed by the library on the host."""
+    B = np.ascontiguousarray(np.asarray(B, dtype=np.float64))
+    n = B.shape[0]
+    if B.shape != (n, n):
+        raise ValueError("B must be square")
+    sh = np.zeros(2 * n)
+    V = np.zeros(2 * n * n)
+    Vi = np.zeros(2 * n * n)
+    _check(lib().pd_diagonalize(n, _hptr(B), _hptr(sh), _hptr(V), _hptr(Vi)), "pd_diagonalize")
+    return sh.view(np.complex128), V.view(np.complex128).reshape(n, n), Vi.view(np.complex128).reshape(n, n)
+
+
 def dense_B_context(B, N, u0_coef=None, **cfg_fields):
     """Context for eq. (1) with a general diagonalisable time matrix B (n x n real), e.g.
     the boundary-value-method B of Example 1 (eq. (9)) or the quasi-BVM B of Example 2
-    (eq. (10)).  The eigendecomposition B = V D V^{-1} is set-up work on the host (numpy's
-    LAPACK eig); the library receives the shifts, V and V^{-1} like any other."""
+    (eq. (10)).  Only B is passed: paradiag_setup diagonalises it (B = V D V^{-1})."""
     B = np.ascontiguousarray(np.asarray(B, dtype=np.float64))
     n = B.shape[0]
-    lam, V = np.linalg.eig(B)
-    Vinv = np.linalg.inv(V)
-    return Context(N, n, lam, V, Vinv, B, u0_coef, None, config(**cfg_fields))
+    return Context(N, n, None, None, None, B, u0_coef, None, config(**cfg_fields))
 
 
 class Batch:

@@ -1281,6 +1281,20 @@ void pd_config_default(pd_config *cfg) {
   cfg->fft_transforms = 1;
 }
 
+pd_status pd_diagonalize(int n, const double *B, double *shifts, double *V, double *Vinv) {
+  if (n < 1 || n > 4096 || !B) return PD_ERR_ARG;
+  std::vector<double> lam, v, vi;
+  try {
+    if (diagonalize(n, B, lam, v, vi) != 0) return PD_ERR_SING;
+  } catch (const std::bad_alloc &) {
+    return PD_ERR_NOMEM;
+  }
+  if (shifts) std::memcpy(shifts, lam.data(), lam.size() * sizeof(double));
+  if (V) std::memcpy(V, v.data(), v.size() * sizeof(double));
+  if (Vinv) std::memcpy(Vinv, vi.data(), vi.size() * sizeof(double));
+  return PD_OK;
+}
+
 pd_status pd_shifts_alpha_circulant(int n, double tau, double alpha, double *shifts, double *V,
                                     double *Vinv) {
   return pd_alpha_circulant(n, tau, alpha, nullptr, shifts, V, Vinv, nullptr);
@@ -1334,7 +1348,16 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
   pd_config cfg;
   if (cfg_in) cfg = *cfg_in;
   else pd_config_default(&cfg);
-  if (!is_pow2m1(N) || !shifts || n < 1 || n > kMaxShifts) return PD_ERR_ARG;
+  if (!is_pow2m1(N) || n < 1 || n > kMaxShifts) return PD_ERR_ARG;
+  // B alone: the library diagonalises it (B = V D V^{-1}, Sec. 1)
+  std::vector<double> eig_lam, eig_V, eig_Vinv;
+  if (!shifts) {
+    if (!B || V || Vinv) return PD_ERR_ARG;
+    if (diagonalize(n, B, eig_lam, eig_V, eig_Vinv) != 0) return PD_ERR_SING;
+    shifts = eig_lam.data();
+    V = eig_V.data();
+    Vinv = eig_Vinv.data();
+  }
   if (!(std::fabs(h * (N + 1) - 1.0) <= 1e-12)) return PD_ERR_ARG;
   if ((V == nullptr) != (Vinv == nullptr)) return PD_ERR_ARG;
   if (!(cfg.coarsest_n == 1 || cfg.coarsest_n == 3 || cfg.coarsest_n == 7 || cfg.coarsest_n == 15))

@@ -210,5 +210,10 @@ void launch_tc_inverse(cudaStream_t s, int grid, int N, int n, double *u, View z
 void vanka_abc(double er, double ei, double out[6]);
 double lfa_omega_opt(double er, double ei, int jacobi);
 int invert_dense(int m, std::vector<double> &A /* 2*m*m, complex row-major */);
+// B = V D V^{-1} of the real n x n row-major B (eig.cpp): lam 2n doubles, V and Vinv
+// 2*n*n doubles (complex interleaved, row-major, columns of V of unit 2-norm).  Returns 0,
+// or a negative code (non-finite B, no convergence, a zero eigenvector, singular V).
+int diagonalize(int n, const double *B, std::vector<double> &lam, std::vector<double> &V,
+                std::vector<double> &Vinv);
 
 }  // namespace pd

@@ -118,3 +118,52 @@ def test_status_strings():
     for code in range(8):
         assert L.pd_status_str(code)
     assert L.pd_status_str(99) == b"unknown status"
+
+
+def _qbvm(n, beta):
+    """B of eq. (10), (n+1) x (n+1), tau = 1/n."""
+    B = np.eye(n + 1) - np.eye(n + 1, k=-1)
+    B[0, n] = 1.0 / beta
+    return B * n
+
+
+@pytest.mark.parametrize("which,n", [("ex1", 16), ("ex1", 128), ("ex1", 256), ("ex2", 15),
+                                     ("ex2", 127), ("alpha", 64), ("random", 40)])
+def test_diagonalize_reconstructs_B(which, n):
+    """pd_diagonalize (the set-up diagonalisation of Sec. 1) on Example 1's BVM B (eq. (9)),
+    Example 2's quasi-BVM B (eq. (10)), the alpha-circulant B and a random matrix: V D V^{-1}
+    rebuilds B and V V^{-1} = I to cond(V) times a few ulps, the eigenvalues are numpy's
+    (LAPACK), and Example 1's bound |lam| < n + sqrt(n)/sqrt(2) holds."""
+    from oracle import lfa
+    if which == "ex1":
+        B = lfa.ex1_bvm_matrix(n)
+    elif which == "ex2":
+        B = _qbvm(n, 0.01)
+    elif which == "alpha":
+        B = api.pd_alpha_circulant(n, 1.0 / n, 1e-3)[0]
+    else:
+        B = np.random.default_rng(7).standard_normal((n, n))
+    m = B.shape[0]
+    lam, V, Vi = api.pd_diagonalize(B)
+    condV = np.linalg.cond(V)
+    eps = np.finfo(float).eps
+    nb = np.linalg.norm(B, 2)
+    rec = V @ np.diag(lam) @ Vi
+    assert np.linalg.norm(rec - B, 2) <= 50 * m * eps * condV * nb
+    assert np.linalg.norm(V @ Vi - np.eye(m), 2) <= 50 * m * eps * condV
+    assert np.allclose(np.linalg.norm(V, axis=0), 1.0, rtol=1e-14)
+    ref = np.linalg.eigvals(B)
+    # match every computed eigenvalue to the nearest LAPACK one (distinct eigenvalues)
+    d = np.abs(lam[:, None] - ref[None, :])
+    assert np.array_equal(np.sort(np.argmin(d, axis=1)), np.arange(m))
+    assert np.max(np.min(d, axis=1)) <= 1e-9 * np.max(np.abs(ref))
+    if which == "ex1":
+        assert np.max(np.abs(lam)) < n + np.sqrt(n) / np.sqrt(2)
+
+
+def test_diagonalize_rejects_bad_input():
+    with pytest.raises(api.PDError):
+        api.pd_diagonalize(np.array([[1.0, np.nan], [0.0, 2.0]]))
+    # a Jordan block is not diagonalisable: V comes out singular in FP64
+    with pytest.raises(api.PDError):
+        api.pd_diagonalize(np.array([[1.0, 1.0], [0.0, 1.0]]))
