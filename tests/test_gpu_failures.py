@@ -1,0 +1,116 @@
+"""Failure paths and convergence histories through the C ABI.
+
+Failures are made on the host only (SURVEY-style fault injection without a GPU fault): a
+NaN placed in a right-hand side must come back as PD_ERR_NAN from every solve entry point,
+in both precisions, and the same context must then solve clean data as before.  The
+per-shift residual history of an FP64 shifted solve is compared with the oracle's history
+cycle by cycle (the relative residual of Sec. 3's stopping test)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import core, lfa  # noqa: E402
+from paper_2203_11154_gb300 import api, inputs  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_stream(torch.cuda.Stream())
+
+
+def _expect_nan(fn):
+    with pytest.raises(api.PDError) as e:
+        fn()
+    assert e.value.status == "PD_ERR_NAN", e.value
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_nan_in_source_paradiag_solve(precision):
+    N, n, tau, alpha = 63, 16, 1.0 / 16, 1e-2
+    c = api.alpha_circulant_context(N, n, tau, alpha, precision=precision)
+    f, u0 = inputs.paradiag_problem(N, n, seed=1)
+    u = torch.empty(n, N, N, dtype=torch.float64, device="cuda")
+    bad = f.copy()
+    bad[3, 10, 20] = np.nan
+    _expect_nan(lambda: c.paradiag_solve(u, torch.from_numpy(bad).cuda(), torch.from_numpy(u0).cuda()))
+    out = c.paradiag_solve(u, torch.from_numpy(f).cuda(), torch.from_numpy(u0).cuda())
+    assert out["status"] == "PD_OK"
+    if precision == 1:
+        assert out["relres_allatonce"] <= 1e-10
+    else:
+        assert out["relres_shift_max"] <= 1e-10
+    c.destroy()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_nan_in_rhs_shifted_solves(precision):
+    N, n = 63, 16
+    lam = api.pd_shifts_alpha_circulant(n, 1.0 / 16, 1e-2)[0]
+    b = inputs.shifted_problem(N, n, seed=0)
+    bad = b.copy()
+    bad[5, 30, 31] = complex(np.inf, 0.0)
+    c = api.Context(N, n, lam, cfg=api.config(precision=precision))
+    ct, nt = (torch.complex128, np.complex128) if precision == 0 else (torch.complex64, np.complex64)
+    z = torch.empty(n, N, N, dtype=ct, device="cuda")
+    _expect_nan(lambda: c.shifted_solve_batched(z, torch.from_numpy(bad.astype(nt)).cuda()))
+    it, rr = c.shifted_solve_batched(z, torch.from_numpy(b.astype(nt)).cuda(), raise_on_noconv=False)
+    assert np.all(np.isfinite(rr)) and np.all(it > 0)
+    if precision == 1:
+        z64 = torch.empty(n, N, N, dtype=torch.complex128, device="cuda")
+        _expect_nan(lambda: c.shifted_solve_refined(z64, torch.from_numpy(bad).cuda()))
+        it, rr = c.shifted_solve_refined(z64, torch.from_numpy(b).cuda())
+        assert np.all(rr <= 1e-10)
+    c.destroy()
+
+
+def test_nan_in_one_instance_of_a_batch():
+    probs = inputs.uneven_problem((31, 63), (4, 8), seed=2)
+    bt = api.Batch([p[0] for p in probs], [p[1] for p in probs], api.config(precision=1))
+    bs = [torch.from_numpy(p[2]).cuda() for p in probs]
+    zs = [torch.empty_like(b) for b in bs]
+    bad = [b.clone() for b in bs]
+    bad[1][2, 7, 7] = complex(np.nan, 0.0)
+    _expect_nan(lambda: bt.solve(zs, bad))
+    out = bt.solve(zs, bs)
+    assert all(np.all(rr <= 1e-10) for _, rr in out)
+    bt.destroy()
+
+
+def test_cycle_history_matches_oracle():
+    """FP64 shifted solve: relres before the first cycle (1) and after each cycle, per shift,
+    against the oracle's own history of the same solve."""
+    N, n = 63, 16
+    lam = api.pd_shifts_alpha_circulant(n, 1.0 / 16, 1e-2)[0]
+    b = inputs.shifted_problem(N, n, seed=0)
+    c = api.Context(N, n, lam, cfg=api.config(precision=0))
+    z = torch.empty(n, N, N, dtype=torch.complex128, device="cuda")
+    it, rr = c.shifted_solve_batched(z, torch.from_numpy(b).cuda())
+    hist, outer = c.history()
+    om = lfa.omega_table(lam, N, mode="lfa")
+    for j in range(n):
+        _, ito, _, ho = core.shifted_solve(N, lam[j], om[j], b[j], tol=1e-10)
+        assert it[j] == ito and hist[j].size == ito + 1
+        assert abs(hist[j][0] - 1.0) <= 1e-14
+        assert np.all(np.abs(hist[j] - ho) <= 1e-8 * ho + 1e-15)
+    lines = c.history_jsonl().splitlines()
+    assert len(lines) == n + 1
+    c.destroy()
+
+
+def test_refinement_history():
+    """Precision form: the relative residual of eq. (1) after each refinement step decreases
+    and its last entry is the reported one."""
+    N, n, tau, alpha = 127, 16, 1.0 / 16, 1e-3
+    c = api.alpha_circulant_context(N, n, tau, alpha, precision=1)
+    f, u0 = inputs.paradiag_problem(N, n, seed=1)
+    u = torch.empty(n, N, N, dtype=torch.float64, device="cuda")
+    out = c.paradiag_solve(u, torch.from_numpy(f).cuda(), torch.from_numpy(u0).cuda())
+    _, outer = c.history()
+    assert outer.size == out["refine_steps"]
+    assert outer[-1] == out["relres_allatonce"] and outer[-1] <= 1e-10
+    assert np.all(np.diff(outer) < 0)
+    c.destroy()

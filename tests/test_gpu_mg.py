@@ -272,6 +272,11 @@ def test_mg_vcycle_fp32(fused, N):
     zt = dev(z, torch.complex64)
     c.mg_vcycle(0, zt, dev(b, torch.complex64))
     ref = np.stack([core.mg_cycle(N, SHIFTS[j], [24 / 25] * 16, b[j], z[j]) for j in range(n)])
-    # FP32 rounding of the residuals grows with the grid (the coarse-grid correction of a
-    # cycle amplifies it by up to O(N)): 1e-7 N covers 6e-8 x that growth
-    assert rel_per_vector(host(zt), ref) < 1e-7 * N
+    # FP32 rounding: each level's residual carries a rounding of about 2^-24 of its terms
+    # (up to 8 |z| in the h^2-scaled form), white across the grid; the coarse-grid correction
+    # solves with L^{-1}, whose smallest eigenvalue is 2 pi^2 in the unscaled form, so the
+    # smooth part of that noise comes back amplified in proportion to N relative to |z|,
+    # once per level (log2(N + 1) of them).  Measured per-vector errors on these inputs
+    # (all three kernel paths, deterministic): 5.8e-8 N at N = 127, 8.4e-8 N at 511,
+    # 9.7e-8 N at 2047, i.e. at most 0.93e-8 N log2(N + 1); the bar allows 1.35 times that.
+    assert rel_per_vector(host(zt), ref) < 1.25e-8 * N * np.log2(N + 1)

@@ -1,7 +1,8 @@
 """pd_allatonce_residual_static: the residual check that allocates nothing, for callers
 that cannot call cudaMalloc (their own memory pool owns the device, or a time-critical
 loop cannot take cudaMalloc's synchronisation).  Checked through the C ABI against the
-context-based pd_allatonce_residual on two calls in a row.  This file is collected last."""
+context-based pd_allatonce_residual on two calls in a row, and element by element against
+the oracle's residual of eq. (1).  This file is collected last."""
 import ctypes as C
 
 import numpy as np
@@ -10,6 +11,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+from oracle import core  # noqa: E402
 from paper_2203_11154_gb300 import api, inputs  # noqa: E402
 
 
@@ -44,6 +46,24 @@ def test_static_residual_matches_context_entry_point_twice():
         assert abs(nh[0] - rn) <= 1e-12 * rn and abs(nh[1] - fn) <= 1e-12 * fn
         rel = torch.linalg.norm(r - r_ref) / torch.linalg.norm(r_ref)
         assert float(rel) <= 1e-14
+        # the oracle's FP64 residual: two FP64 evaluations of the same formula differ by
+        # their rounding, 8 eps (|fhat| + |B||u| + |A||u|) per element at most
+        uh = u.cpu().numpy()
+        fhat = core.assemble_rhs(N, n, tau, f, u0)
+        rn_o, fn_o, r_o = core.allatonce_residual(N, n, tau, alpha, uh, fhat, want_r=True)
+        h2 = float((N + 1) ** 2)
+        au = np.abs(uh)
+        nb = np.zeros_like(au)
+        nb[:, 1:, :] += au[:, :-1, :]
+        nb[:, :-1, :] += au[:, 1:, :]
+        nb[:, :, 1:] += au[:, :, :-1]
+        nb[:, :, :-1] += au[:, :, 1:]
+        wprev = np.ones(n)
+        wprev[0] = alpha  # (C_alpha u)_k = u_{k-1}, and alpha u_{n-1} for k = 0
+        bu = (au + wprev[:, None, None] * np.roll(au, 1, axis=0)) / tau
+        bound = 8 * np.finfo(float).eps * (np.abs(fhat) + bu + h2 * (4 * au + nb))
+        assert np.all(np.abs(r.cpu().numpy() - r_o) <= bound)
+        assert abs(nh[0] - rn_o) <= 1e-12 * rn_o and abs(nh[1] - fn_o) <= 1e-12 * fn_o
 
 
 def test_static_residual_rejects_sizes_beyond_its_scratch():
