@@ -258,6 +258,68 @@ def run_batch(args, rank, world, barrier, rank_max, local):
         dist.destroy_process_group()
 
 
+def examples_shifts():
+    """The shifted systems of Sec. 3's examples: Example 1 (the BVM B of eq. (9), n = 256,
+    h = tau = 1/256), Example 2 (the quasi-BVM B of eq. (10), n = 256 plus the extra step,
+    beta = 0.01, h = tau = 1/256) and Example 3 (Helmholtz shifts -j^2 (1 - 0.5 i),
+    j h <= 1/2, h = 1/128).  The library diagonalises the B matrices."""
+    from paper_2203_11154_gb300 import api, inputs
+    n = 256
+    return [("example1", 255, api.pd_diagonalize(inputs.bvm_time_matrix(n))[0]),
+            ("example2", 255, api.pd_diagonalize(inputs.quasi_bvm_time_matrix(n, 0.01))[0]),
+            ("example3", 127, inputs.helmholtz_shifts(1.0 / 128))]
+
+
+def run_examples(args):
+    """Sec. 3's setting (W(1,0) cycles, coarsest h0 = 1/8, fixed omega, relative residual
+    1e-8, FP64) on the shifts of Examples 1-3 with seeded complex U(-1,1) right-hand sides:
+    the cycle count of every shift for the Vanka smoother (omega = 24/25) and damped Jacobi
+    (omega = 4/5), and the GPU-timed solves/s of both (the paper reports Vanka about three
+    times faster in serial MATLAB).  Shifts are solved 128 at a time (one context each)."""
+    import torch
+    from paper_2203_11154_gb300 import api, inputs
+    torch.cuda.set_stream(torch.cuda.Stream())
+    stream = torch.cuda.current_stream()
+    out = {"metric": "cycle counts and solves/s, Vanka vs damped Jacobi (Sec. 3 examples)",
+           "cycle": "W(1,0), coarsest 7x7 (h0 = 1/8), fixed omega, tol 1e-8, FP64", "examples": {}}
+    for name, N, lam in examples_shifts():
+        rng = np.random.default_rng(11)
+        b = inputs.complex_rhs(rng, lam.size, N)
+        ex = {"N": N, "n": int(lam.size)}
+        for sm, sname in ((0, "vanka"), (1, "jacobi")):
+            cfg = api.config(cycle_gamma=2, nu1=1, nu2=0, coarsest_n=7, omega_mode=0, tol=1e-8,
+                             maxit=1000, precision=0, smoother=sm)
+            chunks = []
+            for a in range(0, lam.size, 128):
+                sl = slice(a, min(a + 128, lam.size))
+                c = api.Context(N, lam[sl].size, lam[sl], cfg=cfg)
+                bd = torch.from_numpy(np.ascontiguousarray(b[sl])).cuda()
+                chunks.append((c, bd, torch.empty_like(bd)))
+            its = []
+            for c, bd, z in chunks:  # warm-up and the counts
+                it, _ = c.shifted_solve_batched(z, bd, raise_on_noconv=False)
+                its.append(it)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                for c, bd, z in chunks:
+                    c.shifted_solve_batched(z, bd, raise_on_noconv=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            it = np.concatenate(its)
+            ex[sname] = {"cycles": it.tolist(), "cycles_min": int(it.min()), "cycles_max": int(it.max()),
+                         "cycles_mean": float(it.mean()), "ms_per_solve_of_all_shifts": ms,
+                         "solves_per_s": lam.size / (ms * 1e-3)}
+            for c, _, _ in chunks:
+                c.destroy()
+        ex["vanka_speedup_vs_jacobi"] = ex["vanka"]["solves_per_s"] / ex["jacobi"]["solves_per_s"]
+        out["examples"][name] = ex
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -265,7 +327,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="paradiag-2047",
-                    choices=["paradiag-511", "paradiag-1023", "paradiag-2047", "uneven-8"])
+                    choices=["paradiag-511", "paradiag-1023", "paradiag-2047", "uneven-8", "examples"])
     ap.add_argument("--fp64-steps", type=int, default=None,
                     help="timed steps of the FP64 form beside the value (default: the smaller "
                          "of --steps and 3 at N = 2047, else --steps)")
@@ -278,6 +340,8 @@ def main():
 
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "examples":
+        return run_examples(args)
 
     import torch
     import torch.distributed as dist

@@ -409,6 +409,22 @@ pd_status pd_profile_enable(pd_ctx *ctx, int on);
 pd_status pd_profile_read(pd_ctx *ctx, int kclass, double *total_ms, long long *launches,
                           double *alg_bytes);
 
+/*
+ * Convergence history of the last solve (the paper reports reductions of the relative
+ * residual, Sec. 3; no call of its own).  Synchronises.
+ *   h_cycle_len [n], h_cycle_hist [n][cap]: per shift, the relative residual of eq. (2)
+ *     before the first cycle and after each cycle of the last multigrid solve (for the
+ *     precision form: its last inner FP32 solve; for shifted_solve_refined: the last
+ *     correction's inner solve); entries beyond h_cycle_len[j] are 0, and -1 marks an
+ *     iterate whose residual was not formed (an inner solve's last cycle: the refinement
+ *     evaluates the residual of eq. (1) instead).
+ *   h_outer_len, h_outer [cap_outer]: the relative residual of eq. (1) after each
+ *     refinement (precision 1) or correction (outer_maxit) step of the last paradiag_solve.
+ * Any output pointer may be NULL.  Errors: PD_ERR_ARG (cap < 0), PD_ERR_CUDA.
+ */
+pd_status pd_get_history(pd_ctx *ctx, int cap, int *h_cycle_len, double *h_cycle_hist,
+                         int cap_outer, int *h_outer_len, double *h_outer);
+
 /* Waits for the context stream. */
 pd_status pd_synchronize(pd_ctx *ctx);
 

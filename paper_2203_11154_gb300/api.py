@@ -39,7 +39,7 @@ EXPORTS = ["pd_config_default", "pd_alpha_circulant", "pd_shifts_alpha_circulant
            "pd_coarse_solve", "pd_transform_forward", "pd_transform_inverse",
            "pd_allatonce_residual", "pd_allatonce_residual_static", "pd_laplacian_dot",
            "pd_initial_value_gradient",
-           "pd_profile_enable", "pd_profile_read", "pd_synchronize", "pd_launch_count", "paradiag_destroy",
+           "pd_profile_enable", "pd_profile_read", "pd_get_history", "pd_synchronize", "pd_launch_count", "paradiag_destroy",
            "pd_status_str", "pd_last_error", "shifted_solve_refined", "pd_allatonce_residual32",
            "paradiag_solve_host_batch", "pd_batch_setup",
            "pd_batch_solve", "pd_batch_destroy", "pd_batch_last_error"]
@@ -105,6 +105,7 @@ def lib(path=None):
             "pd_initial_value_gradient": (_I, [_P, _P, _P]),
             "pd_profile_enable": (_I, [_P, _I]),
             "pd_profile_read": (_I, [_P, _I, _P, _P, _P]),
+            "pd_get_history": (_I, [_P, _I, _P, _P, _I, _P, _P]),
             "pd_synchronize": (_I, [_P]),
             "pd_launch_count": (C.c_longlong, [_P]),
             "paradiag_destroy": (_I, [_P]),
@@ -250,6 +251,29 @@ class Context:
         a.N, a.n, a.cfg, a.stream, a._keep = self.N, self.n, self.cfg, self.stream, []
         a.levels, a.Ns, a.ctype = self.levels, list(self.Ns), self.ctype
         return a
+
+    def history(self, cap=None, cap_outer=64):
+        """(cycle_hist: list of n arrays, the per-shift relative residuals before the first
+        and after each cycle of the last multigrid solve; outer: array of the relative
+        residuals of eq. (1) after each step of the last paradiag_solve)."""
+        if cap is None:
+            cap = max(self.cfg.maxit, self.cfg.inner_maxit) + 1
+        ln = np.zeros(self.n, np.int32)
+        h = np.zeros((self.n, cap))
+        lo = C.c_int()
+        ho = np.zeros(cap_outer)
+        _check(lib().pd_get_history(self.h, cap, _hptr(ln), _hptr(h), cap_outer, C.byref(lo), _hptr(ho)),
+               "pd_get_history", self.h)
+        return [h[j, :ln[j]].copy() for j in range(self.n)], ho[:lo.value].copy()
+
+    def history_jsonl(self):
+        """The convergence history of the last solve as JSON lines: one line per shift
+        ({"shift": j, "relres": [...]}), then one for eq. (1) ({"allatonce_relres": [...]})."""
+        import json
+        cyc, outer = self.history()
+        lines = [json.dumps({"shift": j, "relres": [float(x) for x in h]}) for j, h in enumerate(cyc)]
+        lines.append(json.dumps({"allatonce_relres": [float(x) for x in outer]}))
+        return "\n".join(lines)
 
     def launch_count(self):
         return int(lib().pd_launch_count(self.h))

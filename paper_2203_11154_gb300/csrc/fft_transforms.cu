@@ -15,8 +15,11 @@
 // point share the small DFTs of each pass, with CTA barriers around the passes.  Loads
 // and stores of the n time slices are coalesced across the threads of a warp (consecutive
 // grid points).
+#include <algorithm>
+
 #include "cplx.cuh"
 #include "pd_internal.h"
+#include "tma.cuh"
 
 namespace pd {
 namespace {
@@ -38,6 +41,26 @@ __host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x
 
 // in-place DFT of length R (power of two) of v in registers: v_out[k] = sum_j v[j] w^{jk},
 // w = tw[step] (tw[t] = w_n^t, n = R * step), radix-2 decimation in time
+// one radix-2 stage of span M (butterflies (k + j, k + j + M/2), twiddle w^{j R/M}),
+// then the next stage; the stages are a compile-time recursion so that every index is a
+// constant and v stays in registers
+template <typename C, int R, int M>
+__device__ __forceinline__ void dft_stages(C (&v)[R], const C *__restrict__ tw, int step) {
+  if constexpr (M <= R) {
+#pragma unroll
+    for (int k = 0; k < R; k += M) {
+#pragma unroll
+      for (int j = 0; j < M / 2; j++) {
+        C t = v[k + j + M / 2];
+        if (j != 0) t = cmul(tw[j * (R / M) * step], t);
+        v[k + j + M / 2] = csub(v[k + j], t);
+        v[k + j] = cadd(v[k + j], t);
+      }
+    }
+    dft_stages<C, R, 2 * M>(v, tw, step);
+  }
+}
+
 template <typename C, int R>
 __device__ __forceinline__ void dft_small(C (&v)[R], const C *__restrict__ tw, int step) {
   constexpr int bits = ilog2(R);
@@ -50,19 +73,7 @@ __device__ __forceinline__ void dft_small(C (&v)[R], const C *__restrict__ tw, i
       v[r] = t;
     }
   }
-#pragma unroll
-  for (int m = 2; m <= R; m <<= 1) {
-#pragma unroll
-    for (int k = 0; k < R; k += m) {
-#pragma unroll
-      for (int j = 0; j < m / 2; j++) {
-        C t = v[k + j + m / 2];
-        if (j != 0) t = cmul(tw[j * (R / m) * step], t);
-        v[k + j + m / 2] = csub(v[k + j], t);
-        v[k + j] = cadd(v[k + j], t);
-      }
-    }
-  }
+  dft_stages<C, R, 2>(v, tw, step);
 }
 
 // the two passes of the four-step DFT on the point's column col[e * P], shared by the TP
@@ -250,13 +261,15 @@ k_fft_forward(int N, View g, const InT *__restrict__ f, const double *__restrict
   }
 }
 
-// u_k(point) (+)= wk[k] Re(DFT (- exponent) of z)_k, wk[k] = alpha^{-k/n}; z_j from z1 where
-// final_buf[j] is set, else z0; imag_check: atomic max of |wk[k] Im(.)_k| (bits of a double)
+// u_k(point) (+)= dscale wk[k] Re(DFT (- exponent) of z)_k, wk[k] = alpha^{-k/n}, dscale a
+// power of two (the inverse of the scale of the FP32 right-hand side); z_j from z1 where
+// final_buf[j] is set, else z0; imag_check: atomic max of |dscale wk[k] Im(.)_k| (bits of a
+// double)
 template <typename T, int N1, int N2>
 __global__ void __launch_bounds__(fft_points<T, N1 * N2>() * fft_tp<N1, N2, true>(), fft_min_blocks<T, N1, N2, true>())
 k_fft_inverse(int N, double *__restrict__ u, View z0, View z1, const int *__restrict__ final_buf,
-              const T *__restrict__ wk, const typename Cx<T>::type *__restrict__ tw, int accumulate,
-              int imag_check, unsigned long long *imag_bits) {
+              const T *__restrict__ wk, const typename Cx<T>::type *__restrict__ tw, T dscale,
+              int accumulate, int imag_check, unsigned long long *imag_bits) {
   using C = typename Cx<T>::type;
   constexpr int n = N1 * N2, P = fft_points<T, n>(), TP = fft_tp<N1, N2, true>();
   extern __shared__ __align__(16) unsigned char fft_raw[];
@@ -313,9 +326,10 @@ k_fft_inverse(int N, double *__restrict__ u, View z0, View z1, const int *__rest
 #pragma unroll
             for (int q = 0; q < kO; q++) {
               const int k = k1 + N1 * (k20 + q);
-              const T re = v[k20 + q].x * wk[k];
+              const T wd = wk[k] * dscale;
+              const T re = v[k20 + q].x * wd;
               u[(long long)k * m + x] = accumulate ? uo[q] + to_f64(re) : to_f64(re);
-              if (imag_check) imax = fmaxf(imax, fabsf((float)(v[k20 + q].y * wk[k])));
+              if (imag_check) imax = fmaxf(imax, fabsf((float)(v[k20 + q].y * wd)));
             }
           }
         }
@@ -352,9 +366,10 @@ k_fft_inverse(int N, double *__restrict__ u, View z0, View z1, const int *__rest
         for (int q = 0; q < kOut; q++) {
           const int s = TP * (q0 + q) + t, k = s / N2 + N1 * (s % N2);
           const C v = col[s * P];
-          const T re = v.x * wk[k];
+          const T wd = wk[k] * dscale;
+          const T re = v.x * wd;
           u[(long long)k * m + x] = accumulate ? uo[q] + to_f64(re) : to_f64(re);
-          if (imag_check) imax = fmaxf(imax, fabsf((float)(v.y * wk[k])));
+          if (imag_check) imax = fmaxf(imax, fabsf((float)(v.y * wd)));
         }
       }
     }
@@ -370,6 +385,227 @@ k_fft_inverse(int N, double *__restrict__ u, View z0, View z1, const int *__rest
       atomicMax(imag_bits, (unsigned long long)__double_as_longlong((double)mx));
     }
   }
+}
+
+// ---- pipelined FP32 transforms for n = N1 N2 with N2 = 8 (n = 64, 128) ----
+//
+// Tiles of 32 grid points of one grid row, all n slices.  The CTA's eight warps are the
+// N2 = 8 threads of each point (warp t serves the slices t, t + N2, ...: the inputs of its
+// pass-1 DFT, j2 = t), the lanes the 32 points.  The input slices of the CTA's next
+// kPipeS - 1 tiles are in flight in a cp.async ring of shared-memory stages while the
+// current tile is transformed: pass 1 reads its slices from the stage, pass 2 (N1 / N2
+// DFTs of length N2 per thread) reads the exchanged columns and writes to global memory
+// directly.  No registers hold prefetched data, so the loads in flight per SM are the
+// stages (up to 2 x 64 KB at n = 128), not the registers.
+constexpr int kPipeP = 32, kPipeTP = 8, kPipeThreads = kPipeP * kPipeTP, kPipeS = 3;
+
+__device__ __forceinline__ void cpa(uint32_t dst, const void *src, int bytes, bool ok) {
+  if (bytes == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0)
+                 : "memory");
+  else if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(ok ? 8 : 0)
+                 : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(ok ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int K> __device__ __forceinline__ void cpa_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory");
+}
+
+// g_j(point) = wk-weighted DFT (+ exponent) of fhat at the 32 points of a tile, FP32 work.
+// Stage layout [n][32] of the input type; pass 1 writes complex columns into `col`.
+template <int N1, typename InT>
+__global__ void __launch_bounds__(kPipeThreads)
+k_fft_forward_pipe(int N, View g, const InT *__restrict__ f, const double *__restrict__ u0,
+                   const double *__restrict__ u0coef, const float *__restrict__ wk,
+                   const float2 *__restrict__ tw) {
+  constexpr int N2 = kPipeTP, n = N1 * N2, P = kPipeP;
+  constexpr int S = sizeof(InT) == 8 ? 2 : kPipeS;  // stages (FP64 input: the first step only)
+  extern __shared__ __align__(16) unsigned char fft_raw[];
+  InT *stage = reinterpret_cast<InT *>(fft_raw);                     // [S][n][P]
+  float2 *col = reinterpret_cast<float2 *>(fft_raw + (size_t)S * n * P * sizeof(InT));  // [n][P]
+  const int p = threadIdx.x & 31, t = threadIdx.x >> 5;
+  const long long m = (long long)N * N;
+  const int tpr = (N + P - 1) / P, total = N * tpr;
+  // weights of this thread's slices k = N2 j1 + t, and a bit per slice whose initial-value
+  // coefficient is nonzero (tested on the bits: no FP64 comparison)
+  float wq[N1];
+  unsigned has_u0 = 0;
+#pragma unroll
+  for (int j1 = 0; j1 < N1; j1++) {
+    const int k = N2 * j1 + t;
+    wq[j1] = wk[k];
+    if (u0 && (__double_as_longlong(u0coef[k]) << 1) != 0) has_u0 |= 1u << j1;
+  }
+  // copies of one tile: element (k, point q) of the tile, one per thread and step
+  auto issue = [&](int tile, int st) {
+    if (tile < total) {
+      const int i = tile / tpr, c0 = (tile - i * tpr) * P;
+      const uint32_t base = smem_u32(stage + (size_t)st * n * P);
+#pragma unroll
+      for (int e = 0; e < n * P / kPipeThreads; e++) {
+        const int q = threadIdx.x + kPipeThreads * e, k = q / P, pt = q % P;
+        const bool ok = c0 + pt < N;
+        const InT *src = f + (ok ? (long long)k * m + (long long)i * N + c0 + pt : 0);
+        cpa(base + (uint32_t)(q * sizeof(InT)), src, (int)sizeof(InT), ok);
+      }
+    }
+    cpa_commit();
+  };
+  int q = 0;
+  for (int s0 = 0; s0 < S - 1; s0++) issue(blockIdx.x + s0 * gridDim.x, s0);
+  for (int tile = blockIdx.x; tile < total; tile += gridDim.x, q++) {
+    issue(tile + (S - 1) * gridDim.x, (q + S - 1) % S);
+    cpa_wait<S - 1>();
+    __syncthreads();
+    const InT *sq = stage + (size_t)(q % S) * n * P;
+    const int i = tile / tpr, c = (tile - i * tpr) * P + p;
+    const double u0x = (has_u0 && c < N) ? u0[(long long)i * N + c] : 0.0;
+    float2 v[N1];
+#pragma unroll
+    for (int j1 = 0; j1 < N1; j1++) {
+      const InT x = sq[(N2 * j1 + t) * P + p];
+      float val;
+      if (has_u0 >> j1 & 1u) val = as_t<float>(to_f64(x) + u0coef[N2 * j1 + t] * u0x);
+      else val = as_t<float>(x);
+      v[j1] = make_float2(val * wq[j1], 0.f);
+    }
+    dft_small<float2, N1>(v, tw, N2);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; k1++)
+      col[(N2 * k1 + t) * P + p] = (k1 == 0 || t == 0) ? v[k1] : cmul(tw[(t * k1) % n], v[k1]);
+    __syncthreads();
+    float2 *gp = reinterpret_cast<float2 *>(g.p) + (long long)i * g.pitch + c;
+#pragma unroll
+    for (int r = 0; r < N1 / N2; r++) {
+      const int k1 = t + N2 * r;
+      float2 w[N2];
+#pragma unroll
+      for (int j2 = 0; j2 < N2; j2++) w[j2] = col[(N2 * k1 + j2) * P + p];
+      dft_small<float2, N2>(w, tw, N1);
+      if (c < N) {
+#pragma unroll
+        for (int k2 = 0; k2 < N2; k2++) gp[(long long)(k1 + N1 * k2) * g.plane] = w[k2];
+      }
+    }
+    __syncthreads();  // the stage and the column are refilled next
+  }
+  cpa_wait<0>();
+}
+
+// u_k(point) (+)= dscale wk[k] Re(DFT (- exponent) of z)_k at the 32 points of a tile, FP32
+// work.  Stage layout [n][32] complex; pass 1 writes its outputs back into its own slots.
+// PAIRS: copies of two points (16 bytes), for z arrays whose pitch and plane are even and
+// whose bases are 16-byte aligned (the context's padded levels); else one point (8 bytes).
+template <int N1, bool PAIRS>
+__global__ void __launch_bounds__(kPipeThreads, N1 <= 8 ? 3 : 2)
+k_fft_inverse_pipe(int N, double *__restrict__ u, View z0, View z1, const int *__restrict__ final_buf,
+                   const float *__restrict__ wk, const float2 *__restrict__ tw, float dscale,
+                   int accumulate, int imag_check, unsigned long long *imag_bits) {
+  constexpr int N2 = kPipeTP, n = N1 * N2, P = kPipeP, S = kPipeS;
+  constexpr int W = PAIRS ? 2 : 1;                // points per copy
+  constexpr int kCh = n * P / W / kPipeThreads;   // copies per thread
+  extern __shared__ __align__(16) unsigned char fft_raw[];
+  __shared__ float red[kPipeThreads / 32];
+  float2 *stage = reinterpret_cast<float2 *>(fft_raw);  // [S][n][P]
+  const int p = threadIdx.x & 31, t = threadIdx.x >> 5;
+  const long long m = (long long)N * N;
+  const int tpr = (N + P - 1) / P, total = N * tpr;
+  // z0 and z1 share their layout (pitch even, 16-byte aligned rows); a bit per chunk whose
+  // slice is read from z1
+  unsigned from1 = 0;
+  if (final_buf)
+#pragma unroll
+    for (int e = 0; e < kCh; e++) from1 |= (final_buf[(threadIdx.x + kPipeThreads * e) / (P / W)] ? 1u : 0u) << e;
+  const float2 *b0 = reinterpret_cast<const float2 *>(z0.p), *b1 = reinterpret_cast<const float2 *>(z1.p);
+  auto issue = [&](int tile, int st) {
+    if (tile < total) {
+      const int i = tile / tpr, c0 = (tile - i * tpr) * P;
+      const uint32_t base = smem_u32(stage + (size_t)st * n * P);
+#pragma unroll
+      for (int e = 0; e < kCh; e++) {
+        const int q = threadIdx.x + kPipeThreads * e, j = q / (P / W), pt = W * (q % (P / W));
+        const bool ok = c0 + pt < N;  // a pair's second point may be the padding column
+        const float2 *src = ((from1 >> e) & 1u ? b1 : b0) +
+                            (ok ? (long long)j * z0.plane + (long long)i * z0.pitch + c0 + pt : 0);
+        cpa(base + (uint32_t)((j * P + pt) * sizeof(float2)), src, 8 * W, ok);
+      }
+    }
+    cpa_commit();
+  };
+  float imax = 0.f;
+  int q = 0;
+  for (int s0 = 0; s0 < S - 1; s0++) issue(blockIdx.x + s0 * gridDim.x, s0);
+  for (int tile = blockIdx.x; tile < total; tile += gridDim.x, q++) {
+    issue(tile + (S - 1) * gridDim.x, (q + S - 1) % S);
+    cpa_wait<S - 1>();
+    __syncthreads();
+    float2 *col = stage + (size_t)(q % S) * n * P;
+    const int i = tile / tpr, c = (tile - i * tpr) * P + p;
+    const long long x = (long long)i * N + c;
+    float2 v[N1];
+#pragma unroll
+    for (int j1 = 0; j1 < N1; j1++) v[j1] = col[(N2 * j1 + t) * P + p];
+    dft_small<float2, N1>(v, tw, N2);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; k1++)
+      col[(N2 * k1 + t) * P + p] = (k1 == 0 || t == 0) ? v[k1] : cmul(tw[(t * k1) % n], v[k1]);
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < N1 / N2; r++) {
+      const int k1 = t + N2 * r;
+      double uo[N2];
+      if (accumulate && c < N) {
+#pragma unroll
+        for (int k2 = 0; k2 < N2; k2++) uo[k2] = u[(long long)(k1 + N1 * k2) * m + x];
+      }
+      float2 w[N2];
+#pragma unroll
+      for (int j2 = 0; j2 < N2; j2++) w[j2] = col[(N2 * k1 + j2) * P + p];
+      dft_small<float2, N2>(w, tw, N1);
+      if (c < N) {
+#pragma unroll
+        for (int k2 = 0; k2 < N2; k2++) {
+          const int k = k1 + N1 * k2;
+          const float wd = wk[k] * dscale;
+          const float re = w[k2].x * wd;
+          u[(long long)k * m + x] = accumulate ? uo[k2] + to_f64(re) : to_f64(re);
+          if (imag_check) imax = fmaxf(imax, fabsf(w[k2].y * wd));
+        }
+      }
+    }
+    __syncthreads();  // the stage is refilled next
+  }
+  cpa_wait<0>();
+  if (imag_check) {
+    for (int o = 16; o > 0; o >>= 1) imax = fmaxf(imax, __shfl_down_sync(0xffffffffu, imax, o));
+    if (p == 0) red[t] = imax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float mx = 0.f;
+      for (int w = 0; w < kPipeThreads / 32; w++) mx = fmaxf(mx, red[w]);
+      atomicMax(imag_bits, (unsigned long long)__double_as_longlong((double)mx));
+    }
+  }
+}
+
+template <int N1, typename InT> constexpr size_t fwd_pipe_smem() {
+  return (size_t)(sizeof(InT) == 8 ? 2 : kPipeS) * N1 * kPipeTP * kPipeP * sizeof(InT) +
+         (size_t)N1 * kPipeTP * kPipeP * sizeof(float2);
+}
+template <int N1> constexpr size_t inv_pipe_smem() { return (size_t)kPipeS * N1 * kPipeTP * kPipeP * sizeof(float2); }
+
+// CTAs of a pipelined transform: as many as fit on the SMs at once (persistent), at most
+// one per tile
+template <typename K> int pipe_grid(K kernel, size_t smem, int N, int num_sms) {
+  int per = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kPipeThreads, smem);
+  const long long tiles = (long long)N * ((N + kPipeP - 1) / kPipeP);
+  const long long g = (long long)(per < 1 ? 1 : per) * num_sms;
+  return (int)(g < tiles ? g : tiles);
 }
 
 template <typename T, int n> size_t fft_smem() {
@@ -403,9 +639,27 @@ cudaError_t prepare_one() {
 
 bool fft_transforms_supported(int n) { return n >= 2 && n <= 128 && (n & (n - 1)) == 0; }
 
+template <int N1> cudaError_t prepare_pipe() {
+  cudaError_t e = cudaFuncSetAttribute(k_fft_forward_pipe<N1, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)fwd_pipe_smem<N1, float>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_fft_forward_pipe<N1, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)fwd_pipe_smem<N1, double>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_fft_inverse_pipe<N1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)inv_pipe_smem<N1>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_fft_inverse_pipe<N1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)inv_pipe_smem<N1>());
+}
+
 template <typename T>
 cudaError_t prepare_fft_transforms() {
   cudaError_t e = cudaSuccess;
+  if constexpr (sizeof(T) == 4) {
+    e = prepare_pipe<8>();
+    if (e == cudaSuccess) e = prepare_pipe<16>();
+  }
 #define PD_FFT_PREP(A, B)                      \
   if (e == cudaSuccess) e = prepare_one<T, A, B>();
   PD_FFT_SIZES(PD_FFT_PREP)
@@ -413,10 +667,54 @@ cudaError_t prepare_fft_transforms() {
   return e;
 }
 
+// the pipelined FP32 kernels serve n = 64 and 128
+template <int N1>
+void launch_forward_pipe(cudaStream_t s, int num_sms, int N, View g, const void *f, bool f32,
+                         const double *u0, const double *u0coef, const float *wk, const float2 *tw) {
+  const long long tiles = (long long)N * ((N + kPipeP - 1) / kPipeP);
+  if (f32) {
+    constexpr size_t smem = fwd_pipe_smem<N1, float>();
+    static int grid1 = 0;
+    if (!grid1) grid1 = pipe_grid(k_fft_forward_pipe<N1, float>, smem, 1 << 30, num_sms);
+    k_fft_forward_pipe<N1, float><<<(int)std::min<long long>(grid1, tiles), kPipeThreads, smem, s>>>(
+        N, g, static_cast<const float *>(f), u0, u0coef, wk, tw);
+  } else {
+    constexpr size_t smem = fwd_pipe_smem<N1, double>();
+    static int grid1 = 0;
+    if (!grid1) grid1 = pipe_grid(k_fft_forward_pipe<N1, double>, smem, 1 << 30, num_sms);
+    k_fft_forward_pipe<N1, double><<<(int)std::min<long long>(grid1, tiles), kPipeThreads, smem, s>>>(
+        N, g, static_cast<const double *>(f), u0, u0coef, wk, tw);
+  }
+}
+
+template <int N1>
+void launch_inverse_pipe(cudaStream_t s, int num_sms, int N, double *u, View z0, View z1,
+                         const int *final_buf, const float *wk, const float2 *tw, float dscale,
+                         bool accumulate, bool imag_check, unsigned long long *imag_bits) {
+  constexpr size_t smem = inv_pipe_smem<N1>();
+  const long long tiles = (long long)N * ((N + kPipeP - 1) / kPipeP);
+  // z1 is read only for the slices final_buf marks; both share the layout of z0
+  const bool pairs = z0.pitch % 2 == 0 && z0.plane % 2 == 0 &&
+                     reinterpret_cast<uintptr_t>(z0.p) % 16 == 0 && reinterpret_cast<uintptr_t>(z1.p) % 16 == 0;
+  static int grid1 = 0;
+  if (!grid1) grid1 = pipe_grid(k_fft_inverse_pipe<N1, true>, smem, 1 << 30, num_sms);
+  const int grid = (int)std::min<long long>(grid1, tiles);
+  if (pairs)
+    k_fft_inverse_pipe<N1, true><<<grid, kPipeThreads, smem, s>>>(
+        N, u, z0, z1, final_buf, wk, tw, dscale, accumulate ? 1 : 0, imag_check ? 1 : 0, imag_bits);
+  else
+    k_fft_inverse_pipe<N1, false><<<grid, kPipeThreads, smem, s>>>(
+        N, u, z0, z1, final_buf, wk, tw, dscale, accumulate ? 1 : 0, imag_check ? 1 : 0, imag_bits);
+}
+
 template <typename T>
 void launch_fft_forward(cudaStream_t s, int num_sms, int N, int n, View g, const void *f, bool f32,
                         const double *u0, const double *u0coef, const T *wk,
                         const typename Cx<T>::type *tw) {
+  if constexpr (sizeof(T) == 4) {
+    if (n == 128) return launch_forward_pipe<16>(s, num_sms, N, g, f, f32, u0, u0coef, wk, tw);
+    if (n == 64) return launch_forward_pipe<8>(s, num_sms, N, g, f, f32, u0, u0coef, wk, tw);
+  }
 #define PD_FFT_FWD(A, B)                                                                          \
   if (n == A * B) {                                                                               \
     constexpr int P = fft_points<T, A * B>(), TH = P * fft_tp<A, B, false>();                    \
@@ -437,13 +735,21 @@ void launch_fft_forward(cudaStream_t s, int num_sms, int N, int n, View g, const
 template <typename T>
 void launch_fft_inverse(cudaStream_t s, int num_sms, int N, int n, double *u, View z0, View z1,
                         const int *final_buf, const T *wk, const typename Cx<T>::type *tw,
-                        bool accumulate, bool imag_check, unsigned long long *imag_bits) {
+                        T dscale, bool accumulate, bool imag_check, unsigned long long *imag_bits) {
+  if constexpr (sizeof(T) == 4) {
+    if (n == 128)
+      return launch_inverse_pipe<16>(s, num_sms, N, u, z0, z1, final_buf, wk, tw, dscale, accumulate,
+                                     imag_check, imag_bits);
+    if (n == 64)
+      return launch_inverse_pipe<8>(s, num_sms, N, u, z0, z1, final_buf, wk, tw, dscale, accumulate,
+                                    imag_check, imag_bits);
+  }
 #define PD_FFT_INV(A, B)                                                                       \
   if (n == A * B) {                                                                            \
     constexpr int P = fft_points<T, A * B>(), TH = P * fft_tp<A, B, true>();                  \
     const int grid = fft_grid(N, P, num_sms);                                                  \
     const size_t smem = fft_smem<T, A * B>();                                                  \
-    k_fft_inverse<T, A, B><<<grid, TH, smem, s>>>(N, u, z0, z1, final_buf, wk, tw,             \
+    k_fft_inverse<T, A, B><<<grid, TH, smem, s>>>(N, u, z0, z1, final_buf, wk, tw, dscale,     \
                                                  accumulate ? 1 : 0, imag_check ? 1 : 0,       \
                                                  imag_bits);                                   \
     return;                                                                                    \
@@ -458,8 +764,8 @@ void launch_fft_inverse(cudaStream_t s, int num_sms, int N, int n, double *u, Vi
                                       const double *, const double *, const T *,                  \
                                       const typename Cx<T>::type *);                              \
   template void launch_fft_inverse<T>(cudaStream_t, int, int, int, double *, View, View,         \
-                                      const int *, const T *, const typename Cx<T>::type *, bool, \
-                                      bool, unsigned long long *);
+                                      const int *, const T *, const typename Cx<T>::type *, T,    \
+                                      bool, bool, unsigned long long *);
 PD_FFT_INST(double)
 PD_FFT_INST(float)
 

@@ -80,7 +80,13 @@ struct pd_ctx {
   bool bidiag = false;         // B has nonzeros only at (k,k) and (k,k+boff mod n)
   int boff = -1;
   double *d_bd = nullptr, *d_bs = nullptr;
+  float4 *d_kbd = nullptr;     // (bd_k, bs_k) as float-float pairs (FP64-free residual)
+  float2 *d_ku0 = nullptr;     // u0coef_k as float-float pairs
+  float2 ihf{0.f, 0.f};        // kappa / h^2 as a float-float pair
+  int fsig = 0;                // scale exponent of the ||fhat|| sums (kept between solves)
   double fnorm = -1.0;         // ||fhat|| of the running refinement
+  std::vector<double> outer_hist;  // relative residual of eq. (1) after each step of the
+                                   // last paradiag_solve
   double *d_part = nullptr;    // all-at-once residual partial sums
   double *h_part = nullptr;    // pinned copy
   unsigned long long *d_imag = nullptr;
@@ -112,6 +118,7 @@ struct pd_ctx {
   int *d_frozen = nullptr, *h_frozen = nullptr;  // [n] shift done: zero RHS, no update
   double2 *d_c1 = nullptr;                       // [n] lam_j + 4 kappa / h^2
   double *d_srpart = nullptr, *h_srpart = nullptr;  // [2][n][blocks] residual partial sums
+  float *d_rsc = nullptr, *h_rsc = nullptr;  // [n] power-of-two scale of each shift's FP32 RHS
   // CUDA graphs of whole cycles, keyed by everything a cycle's launches depend on
   struct CycleGraph {
     int prec, zzero, cur0, cmax;
@@ -861,35 +868,63 @@ void lockstep_solve(const std::vector<pd_ctx *> &cs, bool inner, std::vector<pd_
   for (size_t i = 0; i < k; i++) rc[i] = solve_end<T>(cs[i], tol_of(cs[i]));
 }
 
+// x as a float-float pair: hi = x rounded to FP32, lo = the rest rounded to FP32
+float2 split_ff(double x) {
+  const float hi = (float)x;
+  return make_float2(hi, (float)(x - (double)hi));
+}
+
+// A sum of squares of `count` values scaled by a power of two is trusted when the rms of
+// the scaled values lies in [2^-24, 2^24]: no square is near the FP32 underflow or
+// overflow.  rescale: the exponent that brings that rms to about 1 (48 bits down when the
+// sum is not finite: an FP32 square overflowed, which the float-float sums turn into NaN,
+// or the data hold NaN/Inf; 48 bits up when every square underflowed or the data are 0).
+bool scale_fits(double sum, double count) {
+  if (!(sum > 0.0) || !std::isfinite(sum)) return false;
+  const double rms = std::sqrt(sum / count);
+  return rms >= 0x1p-24 && rms <= 0x1p24;
+}
+int rescale(double sum, double count, int sig) {
+  int s;
+  if (!std::isfinite(sum)) s = sig - 48;
+  else if (!(sum > 0.0)) s = sig + 48;
+  else s = sig - (int)std::lround(0.5 * std::log2(sum / count));
+  return std::max(-120, std::min(120, s));
+}
+
 // ---- FP64 refinement of the shifted systems around the FP32 multigrid ----
 struct RefRun {
   pd_ctx *c = nullptr;
   double2 *z = nullptr;
   const double2 *b = nullptr;
   std::vector<double> bn, prev, relres;
-  std::vector<int> it_sum;
+  std::vector<int> it_sum, sig;  // sig[j]: the shift's FP32 right-hand side is 2^sig[j] r_j
   int evals = 0;  // residual evaluations done (the first one is ||b||)
   bool done = false;
   pd_status rc = PD_OK;
 };
 
-// queues r = b - L z (z = 0 on the first evaluation) into the FP32 level-0 RHS, its
-// per-shift partial norms and their copy to the host
+// queues r = b - L z (z = 0 on the first evaluation) into the FP32 level-0 RHS, each
+// shift's times 2^sig[j], its per-shift partial norms and their copy to the host
 void refine_eval_launch(RefRun &r) {
   pd_ctx *c = r.c;
   LevelBufs &B = c->p32.lv[0];
-  const int N = c->N, n = c->n, gx = shift_residual_blocks(N, n);
+  const int N = c->N, n = c->n, gx = shift_residual_blocks(N, n, c->num_sms);
   const bool first = r.evals == 0;
   const double h = hl(c, 0);
   const double w = 8.0, m = (double)N * N;
+  if ((int)r.sig.size() != n) r.sig.assign(n, 0);  // a new run; retries keep their scales
+  for (int j = 0; j < n; j++) c->h_rsc[j] = std::ldexp(1.0f, r.sig[j]);
+  ck(c, cudaMemcpyAsync(c->d_rsc, c->h_rsc, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
   if (!first && c->cfg.fx_residual)  // without FP64 arithmetic (the first one is r = b)
     PD_PROF(PD_KC_RESIDUAL, (32.0 + w) * m, 0,
-            launch_shift_residual_fx(c->stream, N, n, r.z, r.b, c->d_c1, c->kappa / (h * h),
-                                     (float)rs(c, 0), view(B.b, N, B.P), c->d_frozen, c->d_srpart));
+            launch_shift_residual_fx(c->stream, gx, N, n, r.z, r.b, c->d_c1, c->kappa / (h * h),
+                                     (float)rs(c, 0), c->d_rsc, view(B.b, N, B.P), c->d_frozen,
+                                     c->d_srpart));
   else
     PD_PROF(PD_KC_RESIDUAL, (first ? 16.0 + w : 32.0 + w) * m, 0,
-            launch_shift_residual(c->stream, N, n, first ? nullptr : r.z, r.b, c->d_c1,
-                                  c->kappa / (h * h), (float)rs(c, 0), view(B.b, N, B.P),
+            launch_shift_residual(c->stream, gx, N, n, first ? nullptr : r.z, r.b, c->d_c1,
+                                  c->kappa / (h * h), (float)rs(c, 0), c->d_rsc, view(B.b, N, B.P),
                                   first ? nullptr : c->d_frozen, first, c->d_srpart));
   ck_launch(c);
   ck(c, cudaMemcpyAsync(c->h_srpart, c->d_srpart, (first ? 2 : 1) * (size_t)n * gx * sizeof(double),
@@ -899,13 +934,39 @@ void refine_eval_launch(RefRun &r) {
 
 // after the evaluation: relative residuals; shifts that converged, stopped contracting or
 // used up max_refine corrections are frozen (their next RHS is zero and they get no
-// update).  Sets r.done when no shift needs another correction.
+// update).  A shift whose scaled residual fell outside the trusted range (scale_fits) gets
+// a corrected scale and the evaluation is repeated (at most three times).  Sets r.done
+// when no shift needs another correction.
 void refine_eval_finish(RefRun &r) {
   pd_ctx *c = r.c;
-  const int N = c->N, n = c->n, gx = shift_residual_blocks(N, n);
-  ck(c, cudaEventSynchronize(c->ev[0]));
-  prof_resolve(c);
+  const int N = c->N, n = c->n, gx = shift_residual_blocks(N, n, c->num_sms);
+  const double m = (double)N * N;
   const bool first = r.evals == 0;
+  std::vector<double> sr(n), sb(n);
+  for (int tries = 0;; tries++) {
+    ck(c, cudaEventSynchronize(c->ev[0]));
+    prof_resolve(c);
+    bool again = false;
+    for (int j = 0; j < n; j++) {
+      if (!first && c->h_frozen[j]) continue;
+      double s = 0.0, b = 0.0;
+      for (int x = 0; x < gx; x++) s += c->h_srpart[(size_t)j * gx + x];
+      if (first)
+        for (int x = 0; x < gx; x++) b += c->h_srpart[(size_t)(n + j) * gx + x];
+      sr[j] = s;
+      sb[j] = b;
+      if (tries >= 3 || scale_fits(s, m)) continue;
+      if (first) {
+        if (!(b > 0.0) || !std::isfinite(b)) continue;  // b_j = 0 or not finite: nothing to scale
+        r.sig[j] = std::max(-120, std::min(120, -(int)std::lround(0.5 * std::log2(b / m))));
+      } else {
+        r.sig[j] = rescale(s, m, r.sig[j]);
+      }
+      again = true;
+    }
+    if (!again) break;
+    refine_eval_launch(r);
+  }
   if (first) {
     r.bn.assign(n, 0.0);
     r.prev.assign(n, 0.0);
@@ -916,13 +977,10 @@ void refine_eval_finish(RefRun &r) {
   bool any = false;
   for (int j = 0; j < n; j++) {
     if (c->h_frozen[j]) continue;
-    double s = 0.0, sb = 0.0;
-    for (int x = 0; x < gx; x++) s += c->h_srpart[(size_t)j * gx + x];
-    if (first) {
-      for (int x = 0; x < gx; x++) sb += c->h_srpart[(size_t)(n + j) * gx + x];
-      r.bn[j] = std::sqrt(sb);
-    }
-    const double rr = r.bn[j] > 0.0 ? std::sqrt(s) / r.bn[j] : 0.0;
+    if (first) r.bn[j] = std::sqrt(sb[j]);
+    const double rn = std::sqrt(sr[j]) * std::ldexp(1.0, -r.sig[j]);
+    const double rr = !(std::isfinite(rn) && std::isfinite(r.bn[j])) ? std::nan("")
+                      : r.bn[j] > 0.0 ? rn / r.bn[j] : 0.0;
     r.relres[j] = rr;
     if (!std::isfinite(rr)) {
       r.rc = PD_ERR_NAN;
@@ -933,6 +991,8 @@ void refine_eval_finish(RefRun &r) {
     if (rr <= c->cfg.tol || stuck || r.evals >= c->cfg.max_refine) c->h_frozen[j] = 1;
     else any = true;
     r.prev[j] = rr;
+    // predicted scale of the next residual (a correction reduces it about 30-fold)
+    r.sig[j] = std::min(120, r.sig[j] + 5);
   }
   r.evals++;
   ck(c, cudaMemcpyAsync(c->d_frozen, c->h_frozen, n * sizeof(int), cudaMemcpyHostToDevice, c->stream));
@@ -969,7 +1029,7 @@ void refine_runs(std::vector<RefRun> &runs) {
       PD_PROF(PD_KC_OTHER, 24.0 * N * N, 0,
               launch_shift_update(c->stream, N, c->n, r.z, view(B.z[0], N, B.P),
                                   view(B.z[1], N, B.P), c->st.final_buf,
-                                  r.evals > 1 ? c->d_frozen : nullptr, r.evals > 1));
+                                  r.evals > 1 ? c->d_frozen : nullptr, c->d_rsc, r.evals > 1));
       ck_launch(c);
       refine_eval_launch(r);
     }
@@ -983,53 +1043,89 @@ void refine_runs(std::vector<RefRun> &runs) {
   }
 }
 
-// ||fhat - A u|| and ||fhat|| from the per-CTA partial sums (fixed order)
+// ||fhat - A u|| and ||fhat|| from the per-CTA partial sums (fixed order):
 // r (FP64, may be NULL) or r32 (FP32) = fhat - A u and the norms; with a bidiagonal B
 // and known_fn >= 0 the ||fhat|| sums are skipped and known_fn returned
 // fcache: 0 none, 1 write fhat (float-float) into the context's cache, 2 read it from there
+// sig_r: r32 is written times 2^(*sig_r), the FP32 right-hand side of the next refinement
+// step kept near unit size; the sums of squares are those of scaled values, checked
+// against scale_fits and recomputed (at most three times) with corrected exponents, the
+// last exponent used is returned in *sig_r.  Only the FP32 outputs are scaled.
 void allatonce_norms(pd_ctx *c, double *r, const double *u, const double *f, const double *u0,
                      double *rn, double *fn, float *r32 = nullptr, double known_fn = -1.0,
-                     int fcache = 0) {
-  const double m = (double)c->N * c->N;
+                     int fcache = 0, int *sig_r = nullptr) {
+  const double m = (double)c->N * c->N, cnt = m * c->n;
   const bool want_f = known_fn < 0.0;
-  int nb = allatonce_blocks();
-  if (c->bidiag && r32 && !r && c->cfg.fx_residual) {
-    nb = residual_fx_blocks(c->num_sms);
-    const bool use = fcache && c->d_fcache;
-    PD_PROF(PD_KC_RESIDUAL,
-            (use && fcache == 1 ? 28.0 : 20.0) * m + (u0 && !(use && fcache == 2) ? 8.0 * m / c->n : 0.0), 0,
-            launch_residual_fx(c->stream, nb, c->N, c->n, c->boff, c->kappa, r32, u, f, u0,
-                               c->d_u0coef, c->d_bd, c->d_bs, want_f, c->d_part,
-                               use && fcache == 2 ? c->d_fcache : nullptr,
-                               use && fcache == 1 ? c->d_fcache : nullptr));
-  } else if (c->bidiag)
-    PD_PROF(PD_KC_RESIDUAL,
-            (r ? 24.0 : r32 ? 20.0 : 16.0) * m + (u0 ? 8.0 * m / c->n : 0.0), 0,
-            launch_residual_bidiag(c->stream, c->N, c->n, c->boff, c->kappa, r, r32, u, f, u0,
-                                   c->d_u0coef, c->d_bd, c->d_bs, want_f, c->d_part));
-  else
-    PD_PROF(PD_KC_RESIDUAL, (r ? 24.0 : 16.0) * m + (u0 ? 8.0 * m / c->n : 0.0), 0,
-            launch_allatonce_residual(c->stream, c->N, c->n, c->kappa, r, u, f, u0, c->d_u0coef,
-                                      c->d_Bptr, c->d_Bcol, c->d_Bval, c->d_part));
-  ck_launch(c);
-  ck(c, cudaMemcpyAsync(c->h_part, c->d_part, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost,
-                        c->stream));
-  ck(c, cudaStreamSynchronize(c->stream));
+  const bool fx = c->bidiag && r32 && !r && c->cfg.fx_residual;
+  const bool scaled = r32 && !r && c->bidiag;
+  int sr = sig_r ? *sig_r : 0, sf = c->fsig;
   double a = 0.0, b = 0.0;
-  for (int k = 0; k < nb; k++) {
-    a += c->h_part[2 * k];
-    b += c->h_part[2 * k + 1];
+  for (int tries = 0;; tries++) {
+    int nb = allatonce_blocks();
+    if (fx) {
+      nb = residual_fx_blocks(c->num_sms);
+      const bool use = fcache && c->d_fcache;
+      PD_PROF(PD_KC_RESIDUAL,
+              (use && fcache == 1 ? 28.0 : 20.0) * m + (u0 && !(use && fcache == 2) ? 8.0 * m / c->n : 0.0), 0,
+              launch_residual_fx(c->stream, nb, c->N, c->n, c->boff, c->ihf, r32, u, f, u0, c->d_kbd,
+                                 c->d_ku0, std::ldexp(1.0f, sr), std::ldexp(1.0f, sf), want_f, c->d_part,
+                                 use && fcache == 2 ? c->d_fcache : nullptr,
+                                 use && fcache == 1 ? c->d_fcache : nullptr));
+    } else if (c->bidiag) {
+      PD_PROF(PD_KC_RESIDUAL,
+              (r ? 24.0 : r32 ? 20.0 : 16.0) * m + (u0 ? 8.0 * m / c->n : 0.0), 0,
+              launch_residual_bidiag(c->stream, c->N, c->n, c->boff, c->kappa, r, r32, u, f, u0,
+                                     c->d_u0coef, c->d_bd, c->d_bs, want_f, c->d_part,
+                                     std::ldexp(1.0, sr)));
+    } else {
+      PD_PROF(PD_KC_RESIDUAL, (r ? 24.0 : 16.0) * m + (u0 ? 8.0 * m / c->n : 0.0), 0,
+              launch_allatonce_residual(c->stream, c->N, c->n, c->kappa, r, u, f, u0, c->d_u0coef,
+                                        c->d_Bptr, c->d_Bcol, c->d_Bval, c->d_part));
+    }
+    ck_launch(c);
+    ck(c, cudaMemcpyAsync(c->h_part, c->d_part, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream));
+    ck(c, cudaStreamSynchronize(c->stream));
+    a = 0.0;
+    b = 0.0;
+    for (int k = 0; k < nb; k++) {
+      a += c->h_part[2 * k];
+      b += c->h_part[2 * k + 1];
+    }
+    prof_resolve(c);
+    if (!scaled) break;
+    // the ||fhat|| sums are scaled only in the FP64-free kernel
+    const bool okr = scale_fits(a, cnt), okf = !(fx && want_f) || scale_fits(b, cnt);
+    if ((okr && okf) || tries >= 3) break;
+    if (!okr) sr = rescale(a, cnt, sr);
+    if (!okf) sf = rescale(b, cnt, sf);
   }
-  *rn = std::sqrt(a);
-  *fn = (c->bidiag && !want_f) ? known_fn : std::sqrt(b);
-  prof_resolve(c);
+  *rn = scaled ? std::sqrt(a) * std::ldexp(1.0, -sr) : std::sqrt(a);
+  if (c->bidiag && !want_f) *fn = known_fn;
+  else *fn = fx ? std::sqrt(b) * std::ldexp(1.0, -sf) : std::sqrt(b);
+  if (sig_r) *sig_r = sr;
+  if (fx && want_f) c->fsig = sf;
+  if (scaled && !sig_r && sr != 0) {
+    // the caller wants r itself: write it once more unscaled (the norms above stand)
+    if (fx)
+      launch_residual_fx(c->stream, residual_fx_blocks(c->num_sms), c->N, c->n, c->boff, c->ihf, r32, u,
+                         f, u0, c->d_kbd, c->d_ku0, 1.0f, 1.0f, false, c->d_part,
+                         fcache == 2 && c->d_fcache ? c->d_fcache : nullptr, nullptr);
+    else
+      launch_residual_bidiag(c->stream, c->N, c->n, c->boff, c->kappa, nullptr, r32, u, f, u0,
+                             c->d_u0coef, c->d_bd, c->d_bs, false, c->d_part, 1.0);
+    ck_launch(c);
+    ck(c, cudaStreamSynchronize(c->stream));
+  }
 }
 
 // forward transform into view g (scaled: the level-0 h^2 scaling; else unscaled);
 // f is FP64, or FP32 when f32 (the refinement residual)
+// in_scale (a power of two) multiplies an FP64 input; the FFT route is only given FP64
+// input unscaled (FP32 inputs arrive scaled already)
 template <typename T>
 void transform_forward(pd_ctx *c, View g, const void *f, const double *u0, bool scaled,
-                       bool f32 = false) {
+                       bool f32 = false, double in_scale = 1.0) {
   Prec<T> &P = prec<T>(c);
   const double h = hl(c, 0);
   if (P.fft) {
@@ -1038,26 +1134,28 @@ void transform_forward(pd_ctx *c, View g, const void *f, const double *u0, bool 
   } else if (P.tc) {
     launch_tc_forward(c->stream, c->num_sms, c->N, c->n, g, f, f32, u0, c->d_u0coef,
                       scaled ? P.tc_fwd_hi : P.tc_fwd1_hi, scaled ? P.tc_fwd_lo : P.tc_fwd1_lo,
-                      c->st.flags);
+                      in_scale, c->st.flags);
   } else {
     launch_transform_forward<T>(c->stream, c->N, c->n, g, f, f32, u0, c->d_u0coef, P.Wf,
-                                scaled ? h * h / c->kappa : 1.0);
+                                (scaled ? h * h / c->kappa : 1.0) * in_scale);
   }
 }
 
+// dscale (a power of two) multiplies the correction: the inverse of the scale of the FP32
+// right-hand side it was solved from
 template <typename T>
 void transform_inverse(pd_ctx *c, double *u, View z0, View z1, const int *final_buf, bool acc,
-                       bool imag) {
+                       bool imag, double dscale = 1.0) {
   Prec<T> &P = prec<T>(c);
   if (P.fft)
     launch_fft_inverse<T>(c->stream, c->num_sms, c->N, c->n, u, z0, z1, final_buf, P.fft_wi,
-                          P.fft_twi, acc, imag, c->d_imag);
+                          P.fft_twi, (T)dscale, acc, imag, c->d_imag);
   else if (P.tc)
     launch_tc_inverse(c->stream, c->num_sms, c->N, c->n, u, z0, z1, final_buf, P.tc_inv_hi,
-                      P.tc_inv_lo, acc, imag, c->d_imag, c->st.flags);
+                      P.tc_inv_lo, (float)dscale, acc, imag, c->d_imag, c->st.flags);
   else
-    launch_transform_inverse<T>(c->stream, c->N, c->n, u, z0, z1, final_buf, P.Wi, acc, imag,
-                                c->d_imag);
+    launch_transform_inverse<T>(c->stream, c->N, c->n, u, z0, z1, final_buf, P.Wi, (T)dscale, acc,
+                                imag, c->d_imag);
 }
 
 void check_wait_flags(pd_ctx *c) {
@@ -1068,6 +1166,13 @@ void check_wait_flags(pd_ctx *c) {
     cudaMemsetAsync(c->st.flags, 0, sizeof(int), c->stream);  // report each timeout once
     throw CudaFail{cudaErrorLaunchTimeout};
   }
+}
+
+// relative residual ||r|| / ||fhat||; NaN when either norm is not finite (a NaN or Inf in
+// the data), 0 for a zero right-hand side
+double rel_of(double rn, double fn) {
+  if (!std::isfinite(rn) || !std::isfinite(fn)) return std::nan("");
+  return fn > 0 ? rn / fn : 0.0;
 }
 
 template <typename T>
@@ -1086,6 +1191,7 @@ pd_status paradiag_impl(pd_ctx *c, double *u, const double *f, const double *u0,
   st_local[PD_STAT_RELRES_ALLATONCE] = -1.0;
   pd_status rc = PD_OK;
   const bool imag = c->cfg.imag_check != 0;
+  c->outer_hist.clear();
   auto accumulate_iters = [&]() {
     int mx = 0;
     for (int j = 0; j < n; j++) {
@@ -1110,7 +1216,8 @@ pd_status paradiag_impl(pd_ctx *c, double *u, const double *f, const double *u0,
       const int outer = c->cfg.outer_maxit;
       double rn, fn;
       allatonce_norms(c, outer > 0 ? c->d_r : nullptr, u, f, u0, &rn, &fn);
-      double relres = fn > 0 ? rn / fn : 0.0;
+      double relres = rel_of(rn, fn);
+      c->outer_hist.push_back(relres);
       int steps = 1;
       // FP64 corrections: d = (V kron I)(D kron I + kappa I kron A)^{-1}(V^{-1} kron I) r
       for (int s = 0; s < outer && rc == PD_OK && relres > c->cfg.tol; s++) {
@@ -1125,7 +1232,8 @@ pd_status paradiag_impl(pd_ctx *c, double *u, const double *f, const double *u0,
         ck_launch(c);
         allatonce_norms(c, c->d_r, u, f, u0, &rn, &fn);
         const double prev = relres;
-        relres = fn > 0 ? rn / fn : 0.0;
+        relres = rel_of(rn, fn);
+        c->outer_hist.push_back(relres);
         steps++;
         if (!std::isfinite(relres)) {
           rc = PD_ERR_NAN;
@@ -1133,15 +1241,19 @@ pd_status paradiag_impl(pd_ctx *c, double *u, const double *f, const double *u0,
         }
         if (relres > 0.9 * prev) break;  // no longer contracts
       }
+      if (rc == PD_OK && !std::isfinite(relres)) rc = PD_ERR_NAN;
       st_local[PD_STAT_RELRES_ALLATONCE] = relres;
       st_local[PD_STAT_REFINE_STEPS] = outer > 0 ? steps : 0;
       if (outer > 0 && rc == PD_OK && !(relres <= c->cfg.tol)) rc = PD_ERR_NOCONV;
     }
   } else {
     // FP64 iterative refinement on eq. (1) around FP32 ParaDIAG steps.  Step 1 transforms
-    // fhat itself; later steps transform the FP64 residual r = fhat - A u.
+    // fhat itself; later steps transform the FP64 residual r = fhat - A u, handed to the
+    // FP32 solve times a power of two 2^sig that keeps it near unit size whatever the
+    // scale of the data (the FP32 norms inside the multigrid neither underflow nor
+    // overflow), the correction added times 2^-sig.
     double relres = 1.0, prev_relres = 1.0;
-    int steps = 0;
+    int steps = 0, sig = 0;
     for (int step = 0; step < std::max(1, c->cfg.max_refine); step++) {
       if (step == 0)
         PD_PROF(PD_KC_FORWARD, fwd_bytes + (u0 ? fwd_u0 : 0.0), 0,
@@ -1150,7 +1262,8 @@ pd_status paradiag_impl(pd_ctx *c, double *u, const double *f, const double *u0,
         PD_PROF(PD_KC_FORWARD, fwd_bytes - 4.0 * m, 0,
                 transform_forward<T>(c, g, c->d_r32, nullptr, true, true));
       else
-        PD_PROF(PD_KC_FORWARD, fwd_bytes, 0, transform_forward<T>(c, g, c->d_r, nullptr, true));
+        PD_PROF(PD_KC_FORWARD, fwd_bytes, 0,
+                transform_forward<T>(c, g, c->d_r, nullptr, true, false, std::ldexp(1.0, sig)));
       ck_launch(c);
       pd_status s = solve_levels<T>(c, c->cfg.inner_tol, c->cfg.inner_maxit, c->cfg.stall_ratio, true);
       if (s == PD_ERR_NAN) {
@@ -1159,18 +1272,25 @@ pd_status paradiag_impl(pd_ctx *c, double *u, const double *f, const double *u0,
       }
       accumulate_iters();
       PD_PROF(PD_KC_INVERSE, (w + (step > 0 ? 16.0 : 8.0)) * m, 0,
-              transform_inverse<T>(c, u, z0, z1, c->st.final_buf, step > 0, imag));
+              transform_inverse<T>(c, u, z0, z1, c->st.final_buf, step > 0, imag, std::ldexp(1.0, -sig)));
       ck_launch(c);
       double rn, fn;
       if (c->bidiag) {
+        // predicted scale of the next residual: a refinement step reduces it about 20-fold
+        sig += 4;
         allatonce_norms(c, nullptr, u, f, u0, &rn, &fn, c->d_r32, step == 0 ? -1.0 : c->fnorm,
-                        step == 0 ? 1 : 2);
+                        step == 0 ? 1 : 2, &sig);
         c->fnorm = fn;
       } else {
         allatonce_norms(c, c->d_r, u, f, u0, &rn, &fn);
+        const double rms = rn / std::sqrt(m * n);
+        sig = rms > 0.0 && std::isfinite(rms)
+                  ? std::max(-120, std::min(120, -(int)std::lround(std::log2(rms))))
+                  : 0;
       }
       steps = step + 1;
-      relres = fn > 0 ? rn / fn : 0.0;
+      relres = rel_of(rn, fn);
+      c->outer_hist.push_back(relres);
       if (!std::isfinite(relres)) {
         rc = PD_ERR_NAN;
         break;
@@ -1230,6 +1350,7 @@ void free_ctx(pd_ctx *c) {
   if (c->h_hist) cudaFreeHost(c->h_hist);
   if (c->h_frozen) cudaFreeHost(c->h_frozen);
   if (c->h_srpart) cudaFreeHost(c->h_srpart);
+  if (c->h_rsc) cudaFreeHost(c->h_rsc);
   for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
   for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
   for (int k = 0; k < 2; k++)
@@ -1452,8 +1573,11 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
     ck(c, cudaMallocHost(&c->h_part, 2 * part_blocks(c) * sizeof(double)));
     ck(c, cudaMallocHost(&c->h_hist, (std::max(cfg.maxit, cfg.inner_maxit) + 2) * sizeof(int)));
     {
-      const int gx = shift_residual_blocks(N, n);
+      ck(c, prepare_shift_residual_fx());
+      const int gx = shift_residual_blocks(N, n, c->num_sms);
       ck(c, cudaMallocHost(&c->h_frozen, n * sizeof(int)));
+      ck(c, cudaMallocHost(&c->h_rsc, n * sizeof(float)));
+      c->d_rsc = dalloc<float *>(c, n * sizeof(float));
       ck(c, cudaMallocHost(&c->h_srpart, 2 * (size_t)n * gx * sizeof(double)));
       c->d_frozen = dalloc<int *>(c, n * sizeof(int));
       c->d_srpart = dalloc<double *>(c, 2 * (size_t)n * gx * sizeof(double));
@@ -1480,6 +1604,8 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
     c->st.bn2 = dalloc<double *>(c, n * sizeof(double));
     c->st.relres = dalloc<double *>(c, n * sizeof(double));
     c->st.partials = dalloc<double *>(c, (size_t)n * tiles * sizeof(double));
+    c->st.hist_stride = std::max(cfg.maxit, cfg.inner_maxit) + 1;
+    c->st.hist = dalloc<double *>(c, (size_t)n * c->st.hist_stride * sizeof(double));
     c->d_u0coef = dalloc<double *>(c, n * sizeof(double));
     ck(c, cudaMemcpy(c->d_u0coef, c->u0coef.data(), n * sizeof(double), cudaMemcpyHostToDevice));
     c->d_part = dalloc<double *>(c, 2 * part_blocks(c) * sizeof(double));
@@ -1506,6 +1632,20 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
         c->d_bs = dalloc<double *>(c, n * sizeof(double));
         ck(c, cudaMemcpy(c->d_bd, bd.data(), n * sizeof(double), cudaMemcpyHostToDevice));
         ck(c, cudaMemcpy(c->d_bs, bs.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+        // the same constants as float-float pairs for the FP64-free residual
+        std::vector<float4> kbd(n);
+        std::vector<float2> ku0(n);
+        for (int k = 0; k < n; k++) {
+          const float2 a = split_ff(bd[k]), b = split_ff(bs[k]);
+          kbd[k] = make_float4(a.x, a.y, b.x, b.y);
+          ku0[k] = split_ff(c->u0coef[k]);
+        }
+        const double hh = 1.0 / (N + 1);
+        c->ihf = split_ff(cfg.kappa / (hh * hh));
+        c->d_kbd = dalloc<float4 *>(c, n * sizeof(float4));
+        c->d_ku0 = dalloc<float2 *>(c, n * sizeof(float2));
+        ck(c, cudaMemcpy(c->d_kbd, kbd.data(), n * sizeof(float4), cudaMemcpyHostToDevice));
+        ck(c, cudaMemcpy(c->d_ku0, ku0.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
       }
       std::vector<int> ptr(n + 1, 0), col;
       std::vector<double> val;
@@ -1900,6 +2040,30 @@ pd_status pd_profile_read(pd_ctx *c, int kc, double *ms, long long *launches, do
     if (ms) *ms = c->prof_ms[kc];
     if (launches) *launches = c->prof_n[kc];
     if (bytes) *bytes = c->prof_bytes[kc];
+    return PD_OK;
+  })
+}
+
+pd_status pd_get_history(pd_ctx *c, int cap, int *h_cycle_len, double *h_cycle_hist, int cap_outer,
+                         int *h_outer_len, double *h_outer) {
+  if (!c || cap < 0 || cap_outer < 0) return PD_ERR_ARG;
+  PD_TRY(c, {
+    const int n = c->n, stride = c->st.hist_stride;
+    ck(c, cudaStreamSynchronize(c->stream));
+    std::vector<int> it(n);
+    std::vector<double> h((size_t)n * stride);
+    ck(c, cudaMemcpy(it.data(), c->st.iters, n * sizeof(int), cudaMemcpyDeviceToHost));
+    ck(c, cudaMemcpy(h.data(), c->st.hist, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int j = 0; j < n; j++) {
+      const int len = std::min(std::min(it[j] + 1, stride), cap);
+      if (h_cycle_len) h_cycle_len[j] = len;
+      if (h_cycle_hist)
+        for (int k = 0; k < cap; k++) h_cycle_hist[(size_t)j * cap + k] = k < len ? h[(size_t)j * stride + k] : 0.0;
+    }
+    const int lo = std::min((int)c->outer_hist.size(), cap_outer);
+    if (h_outer_len) *h_outer_len = lo;
+    if (h_outer)
+      for (int k = 0; k < cap_outer; k++) h_outer[k] = k < lo ? c->outer_hist[k] : 0.0;
     return PD_OK;
   })
 }

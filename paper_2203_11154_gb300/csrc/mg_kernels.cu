@@ -163,6 +163,7 @@ __global__ void k_converge(int n, int ntiles, SolveState st, double tol, int max
   const double rr = bn2 > 0.0 ? sqrt(s / bn2) : 0.0;
   const double prev = st.relres[j];
   st.relres[j] = rr;
+  if (st.hist && k < st.hist_stride) st.hist[(long long)j * st.hist_stride + k] = rr;
   const bool bad = !isfinite(s);
   if (bad) atomicOr(st.flags, 1);
   const bool stalled = stall > 0.0 && k >= 2 && rr > stall * prev;
@@ -435,6 +436,7 @@ k_coarse(CoarseArgs<T> a, View b, T bscale, View zio, const int *__restrict__ ac
       if (threadIdx.x == 0) {
         if (k == 0) bn2 = s;
         rr = bn2 > 0.0 ? sqrt(s / bn2) : 0.0;
+        if (st.hist && k < st.hist_stride) st.hist[(long long)j * st.hist_stride + k] = rr;
         const bool bad = !isfinite(s);
         if (bad) atomicOr(st.flags, 1);
         stop = (bad || rr <= tol || k >= maxit);
@@ -500,6 +502,8 @@ __global__ void k_finalize(int n, SolveState st, int cur_buf) {
   if (j < n && st.active[j]) {
     st.active[j] = 0;
     st.final_buf[j] = cur_buf;
+    const int k = st.iters[j];
+    if (st.hist && k < st.hist_stride) st.hist[(long long)j * st.hist_stride + k] = -1.0;
     atomicSub(st.nactive, 1);
   }
 }

@@ -48,6 +48,8 @@ struct SolveState {
   double *relres;     // [n] last relative residual
   double *partials;   // [n][max_tiles] per-CTA squared residual sums
   int max_tiles;
+  double *hist;       // [n][hist_stride] relative residual before the first cycle and
+  int hist_stride;    // after each one (entry k = after k cycles), or NULL
 };
 
 // ---- multigrid kernels (mg_kernels.cu), T = double or float ----
@@ -79,28 +81,34 @@ void launch_fft_forward(cudaStream_t s, int num_sms, int N, int n, View g, const
 template <typename T>
 void launch_fft_inverse(cudaStream_t s, int num_sms, int N, int n, double *u, View z0, View z1,
                         const int *final_buf, const T *wk, const typename Cx<T>::type *tw,
-                        bool accumulate, bool imag_check, unsigned long long *imag_bits);
+                        T dscale, bool accumulate, bool imag_check, unsigned long long *imag_bits);
 
-// ---- residual of eq. (1) without FP64 arithmetic (residual_fx.cu) ----
+// ---- residual of eq. (1) without FP64 arithmetic (residual_ws.cu) ----
 int residual_fx_blocks(int num_sms);
-void launch_residual_fx(cudaStream_t s, int blocks, int N, int n, int off, double kappa, float *r,
-                        const double *u, const double *f, const double *u0, const double *u0coef,
-                        const double *bd, const double *bs, bool want_f, double *part,
+// r = oscale (fhat - (B kron I + kappa I kron A) u) in FP32 for the bidiagonal B with
+// nonzeros at (k,k) and (k, k+off mod n); kbd[k] = (bd_k, bs_k), ku0[k] = u0coef_k and ihf =
+// kappa/h^2 as float-float pairs; part[2b], part[2b+1] = per-CTA sums of |oscale r|^2 and
+// (want_f) |fscale fhat|^2 over residual_fx_blocks() CTAs; fc_out/fc_in: fhat cache
+void launch_residual_fx(cudaStream_t s, int blocks, int N, int n, int off, float2 ihf, float *r,
+                        const double *u, const double *f, const double *u0, const float4 *kbd,
+                        const float2 *ku0, float oscale, float fscale, bool want_f, double *part,
                         const float2 *fc_in, float2 *fc_out);
 
 // ---- FP64 refinement of the shifted systems (shift_refine.cu) ----
-int shift_residual_blocks(int N, int n);
+// CTAs per shift of the shifted residuals (gx): one wave of two CTAs per SM over all shifts
+int shift_residual_blocks(int N, int n, int num_sms);
 // the same residual without FP64 instructions (residual_fx.cu); z must not be NULL and
-// the sums of |b|^2 are not formed
-void launch_shift_residual_fx(cudaStream_t s, int N, int n, const double2 *z, const double2 *b,
-                              const double2 *c1, double off, float oscale, View out,
+// the sums of |b|^2 are not formed; sc[j]: per-shift power-of-two scale of the output
+cudaError_t prepare_shift_residual_fx();
+void launch_shift_residual_fx(cudaStream_t s, int gx, int N, int n, const double2 *z, const double2 *b,
+                              const double2 *c1, double off, float oscale, const float *sc, View out,
                               const int *frozen, double *part);
 void launch_round_to_float(cudaStream_t s, long long count, const double *x, float *y);
-void launch_shift_residual(cudaStream_t s, int N, int n, const double2 *z, const double2 *b,
-                           const double2 *c1, double off, float oscale, View out,
+void launch_shift_residual(cudaStream_t s, int gx, int N, int n, const double2 *z, const double2 *b,
+                           const double2 *c1, double off, float oscale, const float *sc, View out,
                            const int *frozen, bool want_b, double *part);
 void launch_shift_update(cudaStream_t s, int N, int n, double2 *z, View z0, View z1,
-                         const int *final_buf, const int *frozen, bool accumulate);
+                         const int *final_buf, const int *frozen, const float *sc, bool accumulate);
 
 struct CoarsePlan {
   int lc;                   // first level handled inside one CTA per shift
@@ -169,7 +177,7 @@ void launch_transform_forward(cudaStream_t s, int N, int n, View g, const void *
 // (final_buf may be NULL: all from z0); imag_check: atomicMax of max|Im| bits
 template <typename T>
 void launch_transform_inverse(cudaStream_t s, int N, int n, double *u, View z0, View z1,
-                              const int *final_buf, const typename Cx<T>::type *W,
+                              const int *final_buf, const typename Cx<T>::type *W, T dscale,
                               bool accumulate, bool imag_check, unsigned long long *imag_max_bits);
 // r = fhat - (B kron I + I kron A) u in FP64 (r may be NULL); part[2b], part[2b+1] =
 // per-CTA sums of r^2 and fhat^2 over allatonce_blocks() CTAs
@@ -180,12 +188,13 @@ void launch_allatonce_residual(cudaStream_t s, int N, int n, double kappa, doubl
                                double *part);
 
 // r = fhat - (B kron I + kappa I kron A) u for B with nonzeros only at (k,k) (bd) and
-// (k, k+off mod n) (bs), off = -1 or +1; r written as FP64 (r64) or FP32 (r32), or not at
-// all; part as above, the fhat sums only when want_f
+// (k, k+off mod n) (bs), off = -1 or +1; r written as FP64 (r64) or FP32 (r32, times the
+// power of two oscale, its sums those of the scaled values), or not at all; part as above,
+// the fhat sums only when want_f
 void launch_residual_bidiag(cudaStream_t s, int N, int n, int off, double kappa, double *r64,
                             float *r32, const double *u, const double *f, const double *u0,
                             const double *u0coef, const double *bd, const double *bs, bool want_f,
-                            double *part);
+                            double *part, double oscale = 1.0);
 
 // gu0 = sum_k u0coef[k] w_k
 void launch_initial_value_gradient(cudaStream_t s, int N, int n, const double *w,
@@ -201,10 +210,10 @@ void tc_build_operands(int n, const double *Vinv, const double *V, double scale,
                        float *fwd_lo, float *inv_hi, float *inv_lo);
 void launch_tc_forward(cudaStream_t s, int grid, int N, int n, View g, const void *f, bool f32,
                        const double *u0, const double *u0coef, const float *Ahi, const float *Alo,
-                       int *errflag);
+                       double in_scale, int *errflag);
 void launch_tc_inverse(cudaStream_t s, int grid, int N, int n, double *u, View z0, View z1,
-                       const int *final_buf, const float *Ahi, const float *Alo, bool accumulate,
-                       bool imag_check, unsigned long long *imag_bits, int *errflag);
+                       const int *final_buf, const float *Ahi, const float *Alo, float dscale,
+                       bool accumulate, bool imag_check, unsigned long long *imag_bits, int *errflag);
 
 // ---- host-side setup (setup.cpp) ----
 void vanka_abc(double er, double ei, double out[6]);

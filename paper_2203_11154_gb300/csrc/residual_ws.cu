@@ -1,0 +1,266 @@
+// Residual of eq. (1) for the refinement without FP64 instructions (GB300 issues FP64 at
+// 1/58 of its FP32 rate), for a bidiagonal time matrix, as warp streams:
+//
+//   r_k = fhat_k - bd_k u_k - bs_k u_{k+off} - (kappa/h^2)(4 u_k - sum of the 4 neighbours),
+//   fhat_k = f_k + u0coef_k u0,
+//
+// output in FP32 times a power of two `oscale` (the refinement keeps its FP32 right-hand
+// sides near unit size whatever the scale of the data), with the sums of |oscale r|^2 and
+// of |fscale fhat|^2.
+//
+//   - Work item of a warp: a strip of 30 output columns (lanes 1..30; lanes 0 and 31 carry
+//     the halo columns) by kWsR rows, walked through a run of consecutive time steps in
+//     the order in which u_{k+off} precedes u_k (ascending k for off = -1, descending for
+//     off = +1).  A lane holds its column's kWsR + 2 values of u_k in registers: vertical
+//     neighbours are its own, horizontal ones come from the adjacent lanes by shuffles.
+//     The next step's column is loaded while the current one is computed, and a lane keeps
+//     its points' u_k for the next step's bs term, so u is read from memory once (plus the
+//     halo rows and columns, from L2).  No shared memory and no barrier until the final
+//     CTA sum.
+//   - Fixed point: one scale per warp tile and step, 2^-S with S = 1081 - (largest biased
+//     exponent of the tile's (kWsR + 2) x 32 values, a warp max); every value becomes three
+//     exact FP32 limbs (ff::to_limbs), so the stencil difference 4 u_k - (sum of the
+//     neighbours), where the cancellation happens, is exact in FP32 arithmetic.
+//   - The other terms are float-float pairs: fhat (split from FP64 by bit operations, or
+//     read back from the float-float cache the first residual of a solve writes), the three
+//     products with constants split on the host; their hi parts are summed with TwoSum and
+//     the low parts and rounding errors in FP32, so r carries an error near 2^-47 of the
+//     terms' size, far below the FP64 rounding of the same formula.
+//   - Range: a tile whose largest |u| is 2^186 or more, Inf or NaN gives NaN residuals;
+//     below about 2^-88 (kappa/h^2 = 2^20) the u terms lose relative accuracy.
+#include <cstdint>
+
+#include "ff.cuh"
+#include "pd_internal.h"
+
+namespace pd {
+namespace {
+
+using namespace ff;
+
+constexpr int kWsR = 6;      // output rows of a warp tile
+constexpr int kWsOut = 30;   // output columns of a warp strip
+constexpr int kWsWarps = 8;  // warps per CTA
+constexpr int kWsThreads = 32 * kWsWarps;
+
+// item = chunk * tiles + tile, tile = row block * tx + strip; chunk q covers the positions
+// [q n / nch, (q + 1) n / nch) of the time walk, position p being step p (off = -1) or
+// n - 1 - p (off = +1)
+struct WsGeom {
+  int N, n, off, tx, tiles, nch, items;
+};
+
+__device__ __forceinline__ int ws_step(const WsGeom &g, int p) { return g.off < 0 ? p : g.n - 1 - p; }
+
+// FMODE 0: fhat from f and u0; 1: the same, also written to the cache fc_out as float-float
+// pairs; 2: fhat read from the cache fc_in.  kbd[k] = (bd_k, bs_k) and ku0[k] = u0coef_k as
+// float-float pairs, ihf = kappa / h^2 likewise.  part[2 blockIdx.x] = sum |oscale r|^2,
+// part[2 blockIdx.x + 1] = sum |fscale fhat|^2 (when want_f).
+template <int FMODE>
+__global__ void __launch_bounds__(kWsThreads, 2)
+k_residual_ws(WsGeom g, float *__restrict__ r, const double *__restrict__ u,
+              const double *__restrict__ f, const double *__restrict__ u0,
+              const float4 *__restrict__ kbd, const float2 *__restrict__ ku0, float2 ihf,
+              float oscale, float fscale, int want_f, double *__restrict__ part,
+              const float2 *__restrict__ fc_in, float2 *__restrict__ fc_out) {
+  constexpr int R = kWsR;
+  __shared__ float2 red[2][kWsWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int N = g.N;
+  const long long m = (long long)N * N;
+  const DF ihd = {ihf.x, ihf.y};
+  DF ar = {0.f, 0.f}, af = {0.f, 0.f};
+  for (int it = blockIdx.x * kWsWarps + warp; it < g.items; it += gridDim.x * kWsWarps) {
+    const int q = it / g.tiles, t0 = it - q * g.tiles;
+    const int by = t0 / g.tx, sx = t0 - by * g.tx;
+    const int pbeg = (int)((long long)q * g.n / g.nch), pend = (int)((long long)(q + 1) * g.n / g.nch);
+    const int i0 = by * R;
+    const int c = sx * kWsOut - 1 + lane;
+    const bool cin = (unsigned)c < (unsigned)N;
+    const bool outc = lane >= 1 && lane <= kWsOut && cin;
+    const int nr = min(R, N - i0);  // output rows inside the grid
+    const long long cc = cin ? c : 0;
+    // the lane's column of one time step, rows i0 - 1 .. i0 + R (zero outside the grid)
+    unsigned long long raw[R + 2];
+    auto load_u = [&](int k) {
+      const double *uk = u + (long long)k * m + cc;
+#pragma unroll
+      for (int e = 0; e < R + 2; e++) {
+        const int i = i0 - 1 + e;
+        const bool ok = cin && (unsigned)i < (unsigned)N;
+        raw[e] = ok ? (unsigned long long)__double_as_longlong(uk[(long long)i * N]) : 0ull;
+      }
+    };
+    load_u(ws_step(g, pbeg));
+    DF un[R];  // u_{k+off} of the lane's points, in the previous step's units
+    int s_prev = 0;
+    bool bad_prev = false;
+    for (int p = pbeg; p < pend; p++) {
+      const int k = ws_step(g, p);
+      const bool first = p == pbeg;
+      const long long kx0 = (long long)k * m + (long long)i0 * N + cc;  // the lane's row i0 in plane k
+      // this step's fhat (cache) or f of the lane's points: 64-bit words
+      unsigned long long fb[R];
+#pragma unroll
+      for (int t = 0; t < R; t++) {
+        const bool ok = outc && t < nr;
+        if (FMODE == 2)
+          fb[t] = ok ? *reinterpret_cast<const unsigned long long *>(fc_in + kx0 + (long long)t * N) : 0ull;
+        else
+          fb[t] = ok ? (unsigned long long)__double_as_longlong(f[kx0 + (long long)t * N]) : 0ull;
+      }
+      // first step of the item: u_{k+off} from memory (FP64, split below)
+      unsigned long long ub[R];
+      if (first) {
+        const int kp = (k + g.off + g.n) % g.n;
+        const double *up = u + (long long)kp * m + (long long)i0 * N + cc;
+#pragma unroll
+        for (int t = 0; t < R; t++)
+          ub[t] = (outc && t < nr) ? (unsigned long long)__double_as_longlong(up[(long long)t * N]) : 0ull;
+      }
+      // largest exponent of the warp tile (the largest high word without its sign bit has
+      // the largest exponent), then the limbs
+      unsigned em = 0;
+#pragma unroll
+      for (int e = 0; e < R + 2; e++) em = max(em, (unsigned)(raw[e] >> 32) & 0x7FFFFFFFu);
+      em = __reduce_max_sync(0xffffffffu, em) >> 20;
+      float lx[R + 2], ly[R + 2], lz[R + 2];
+#pragma unroll
+      for (int e = 0; e < R + 2; e++) {
+        const float4 l4 = to_limbs(raw[e], em);
+        lx[e] = l4.x;
+        ly[e] = l4.y;
+        lz[e] = l4.z;
+      }
+      // the next step's column, while this one is computed
+      if (p + 1 < pend) load_u(ws_step(g, p + 1));
+      const float4 kb = kbd[k];
+      // (kappa/h^2) 2^-S and bd_k 2^-S multiply fixed-point values, bs_k 2^-S' those of the
+      // previous step (beyond S = 252, |u| < 2^-170: the products are 0)
+      const bool bad = em > 1081 + 126;  // Inf/NaN or |u| >= 2^186 in the tile
+      const int S = 1081 - (int)em, sc = S > 252 ? 252 : S;
+      const DF c3 = df_scale_down(ihd, sc);
+      const DF cb = df_scale_down(DF{kb.x, kb.y}, sc);
+      const DF cs = first ? DF{kb.z, kb.w} : df_scale_down(DF{kb.z, kb.w}, s_prev > 252 ? 252 : s_prev);
+      const bool nan_out = bad || (!first && bad_prev);
+      DF ck = {0.f, 0.f};
+      bool has_u0 = false;
+      if (FMODE != 2 && u0) {
+        const float2 c2 = ku0[k];
+        ck = DF{c2.x, c2.y};
+        has_u0 = c2.x != 0.f || c2.y != 0.f;
+      }
+      if (first) {
+#pragma unroll
+        for (int t = 0; t < R; t++) un[t] = split_bits((uint32_t)(ub[t] >> 32), (uint32_t)ub[t]);
+      }
+      float rowr = 0.f, rowf = 0.f;
+#pragma unroll
+      for (int t = 0; t < R; t++) {
+        // the exact stencil difference per limb, then as a float-float pair
+        const float hx = __shfl_up_sync(0xffffffffu, lx[t + 1], 1) + __shfl_down_sync(0xffffffffu, lx[t + 1], 1);
+        const float hy = __shfl_up_sync(0xffffffffu, ly[t + 1], 1) + __shfl_down_sync(0xffffffffu, ly[t + 1], 1);
+        const float hz = __shfl_up_sync(0xffffffffu, lz[t + 1], 1) + __shfl_down_sync(0xffffffffu, lz[t + 1], 1);
+        const float a2 = __fmaf_rn(4.f, lx[t + 1], -__fadd_rn(__fadd_rn(lx[t], lx[t + 2]), hx));
+        const float a1 = __fmaf_rn(4.f, ly[t + 1], -__fadd_rn(__fadd_rn(ly[t], ly[t + 2]), hy));
+        const float a0 = __fmaf_rn(4.f, lz[t + 1], -__fadd_rn(__fadd_rn(lz[t], lz[t + 2]), hz));
+        DF t1 = two_sum(a2, a1);
+        t1.lo = __fadd_rn(t1.lo, a0);
+        DF uc = fast_two_sum(lx[t + 1], ly[t + 1]);
+        uc.lo = __fadd_rn(uc.lo, lz[t + 1]);
+        const DF unt = un[t];
+        un[t] = uc;
+        const bool ok = outc && t < nr;
+        const long long kx = kx0 + (long long)t * N;
+        DF fh;
+        if (FMODE == 2) {
+          fh = DF{__uint_as_float((uint32_t)fb[t]), __uint_as_float((uint32_t)(fb[t] >> 32))};
+        } else {
+          fh = split_bits((uint32_t)(fb[t] >> 32), (uint32_t)fb[t]);
+          if (has_u0 && ok) fh = df_add(fh, df_mul(ck, split(u0[(long long)(i0 + t) * N + cc])));
+          if (FMODE == 1 && ok) fc_out[kx] = make_float2(fh.hi, fh.lo);
+        }
+        const DF p1 = df_mul_un(cb, uc), p2 = df_mul_un(cs, unt), p3 = df_mul_un(c3, t1);
+        // fhat - p1 - p2 - p3: the hi parts summed exactly, the low parts and errors in FP32
+        const float lo = __fsub_rn(fh.lo, __fadd_rn(__fadd_rn(p1.lo, p2.lo), p3.lo));
+        DF s = two_sum(fh.hi, -p1.hi);
+        float el = s.lo;
+        s = two_sum(s.hi, -p2.hi);
+        el = __fadd_rn(el, s.lo);
+        s = two_sum(s.hi, -p3.hi);
+        el = __fadd_rn(el, s.lo);
+        float rv = __fmul_rn(__fadd_rn(s.hi, __fadd_rn(lo, el)), oscale);
+        if (nan_out) rv = __int_as_float(0x7FC00000);
+        if (ok) {
+          r[kx] = rv;
+          rowr = __fmaf_rn(rv, rv, rowr);
+          if (want_f) {
+            const float fv = __fmul_rn(__fadd_rn(fh.hi, fh.lo), fscale);
+            rowf = __fmaf_rn(fv, fv, rowf);
+          }
+        }
+      }
+      ar = df_add(ar, DF{rowr, 0.f});
+      if (want_f) af = df_add(af, DF{rowf, 0.f});
+      s_prev = S;
+      bad_prev = bad;
+    }
+  }
+  // CTA sums: float-float over the warps, one conversion to FP64 per CTA
+  for (int o = 16; o > 0; o >>= 1) {
+    ar = df_add(ar, df_shfl_down(ar, o));
+    af = df_add(af, df_shfl_down(af, o));
+  }
+  if (lane == 0) {
+    red[0][warp] = make_float2(ar.hi, ar.lo);
+    red[1][warp] = make_float2(af.hi, af.lo);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    DF s0 = {0.f, 0.f}, s1 = {0.f, 0.f};
+    for (int w = 0; w < kWsWarps; w++) {
+      s0 = df_add(s0, DF{red[0][w].x, red[0][w].y});
+      s1 = df_add(s1, DF{red[1][w].x, red[1][w].y});
+    }
+    part[2 * blockIdx.x] = (double)s0.hi + (double)s0.lo;
+    part[2 * blockIdx.x + 1] = (double)s1.hi + (double)s1.lo;
+  }
+}
+
+template <int FMODE>
+void launch_ws(cudaStream_t s, int blocks, const WsGeom &g, float *r, const double *u, const double *f,
+               const double *u0, const float4 *kbd, const float2 *ku0, float2 ihf, float oscale,
+               float fscale, bool want_f, double *part, const float2 *fc_in, float2 *fc_out) {
+  k_residual_ws<FMODE><<<blocks, kWsThreads, 0, s>>>(g, r, u, f, u0, kbd, ku0, ihf, oscale, fscale,
+                                                     want_f ? 1 : 0, part, fc_in, fc_out);
+}
+
+}  // namespace
+
+int residual_fx_blocks(int num_sms) { return 2 * num_sms; }
+
+void launch_residual_fx(cudaStream_t s, int blocks, int N, int n, int off, float2 ihf, float *r,
+                        const double *u, const double *f, const double *u0, const float4 *kbd,
+                        const float2 *ku0, float oscale, float fscale, bool want_f, double *part,
+                        const float2 *fc_in, float2 *fc_out) {
+  WsGeom g;
+  g.N = N;
+  g.n = n;
+  g.off = off < 0 ? -1 : 1;
+  g.tx = (N + kWsOut - 1) / kWsOut;
+  g.tiles = g.tx * ((N + kWsR - 1) / kWsR);
+  // time-step runs: enough items for about eight per warp (the tail of a static
+  // distribution then costs little), runs of at least two steps
+  const long long warps = (long long)blocks * kWsWarps;
+  g.nch = 1;
+  while ((long long)g.tiles * g.nch < 8 * warps && n / (2 * g.nch) >= 2) g.nch *= 2;
+  g.items = g.tiles * g.nch;
+  if (fc_in)
+    launch_ws<2>(s, blocks, g, r, u, f, u0, kbd, ku0, ihf, oscale, fscale, want_f, part, fc_in, nullptr);
+  else if (fc_out)
+    launch_ws<1>(s, blocks, g, r, u, f, u0, kbd, ku0, ihf, oscale, fscale, want_f, part, nullptr, fc_out);
+  else
+    launch_ws<0>(s, blocks, g, r, u, f, u0, kbd, ku0, ihf, oscale, fscale, want_f, part, nullptr, nullptr);
+}
+
+}  // namespace pd

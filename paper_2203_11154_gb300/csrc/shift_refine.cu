@@ -36,24 +36,28 @@ __device__ __forceinline__ float to_f32(double x) {
                          (lw >> 29));
 }
 
-// grid (gx, n): CTA x of shift j strides over the grid rows of shift j.  part[j][x] gets
-// the CTA's sum of |r|^2 (and of |b|^2 in part[n + j][x] when want_b); frozen shifts
-// (already converged) get a zero right-hand side and no sums.
+// grid (gx, n): CTA x of shift j strides over the grid rows of shift j.  The FP32 output
+// is sc_j r (sc_j a power of two that keeps the shift's FP32 right-hand side near unit
+// size) times oscale; part[j][x] gets the CTA's sum of |sc_j r|^2 (and of |b|^2, in FP64,
+// in part[n + j][x] when want_b); frozen shifts (already converged) get a zero right-hand
+// side and no sums.
 __global__ void __launch_bounds__(kSrThreads)
 k_shift_residual(int N, const double2 *__restrict__ z, const double2 *__restrict__ b,
-                 const double2 *__restrict__ c1, double off, float oscale, View out,
-                 const int *__restrict__ frozen, int want_b, double *__restrict__ part) {
+                 const double2 *__restrict__ c1, double off, float oscale, const float *__restrict__ sc,
+                 View out, const int *__restrict__ frozen, int want_b, double *__restrict__ part) {
   __shared__ double red[2][kSrThreads / 32];
   const int j = blockIdx.y;
   const long long m = (long long)N * N;
   const bool fz = frozen && frozen[j];
   const double2 cj = c1[j];
+  const double scj = (double)sc[j];
   float2 *o = reinterpret_cast<float2 *>(out.p) + (long long)j * out.plane;
   double ar = 0.0, ab = 0.0;
   for (int i = blockIdx.x; i < N; i += gridDim.x) {
     const double2 *br = b + j * m + (long long)i * N;
     const double2 *zr = z ? z + j * m + (long long)i * N : nullptr;
-    float rowr = 0.f, rowb = 0.f;
+    float rowr = 0.f;
+    double rowb = 0.0;
     for (int c = threadIdx.x; c < N; c += kSrThreads) {
       if (fz) {
         o[(long long)i * out.pitch + c] = make_float2(0.f, 0.f);
@@ -72,16 +76,13 @@ k_shift_residual(int N, const double2 *__restrict__ z, const double2 *__restrict
         r.x = fma(off, nb.x, fma(-cj.x, zv.x, fma(cj.y, zv.y, bv.x)));
         r.y = fma(off, nb.y, fma(-cj.x, zv.y, fma(-cj.y, zv.x, bv.y)));
       }
-      const float2 rf = make_float2(to_f32(r.x), to_f32(r.y));
+      const float2 rf = make_float2(to_f32(r.x * scj), to_f32(r.y * scj));
       rowr = fmaf(rf.x, rf.x, fmaf(rf.y, rf.y, rowr));
-      if (want_b) {
-        const float2 bf = make_float2(to_f32(bv.x), to_f32(bv.y));
-        rowb = fmaf(bf.x, bf.x, fmaf(bf.y, bf.y, rowb));
-      }
+      if (want_b) rowb = fma(bv.x, bv.x, fma(bv.y, bv.y, rowb));
       o[(long long)i * out.pitch + c] = make_float2(rf.x * oscale, rf.y * oscale);
     }
     ar += (double)rowr;
-    ab += (double)rowb;
+    ab += rowb;
   }
   for (int s = 16; s > 0; s >>= 1) {
     ar += __shfl_down_sync(0xffffffffu, ar, s);
@@ -103,18 +104,21 @@ k_shift_residual(int N, const double2 *__restrict__ z, const double2 *__restrict
   }
 }
 
-// z_j (+)= d_j for the shifts that are not frozen; d_j is the FP32 answer of the multigrid
-// in z0 or z1 (final_buf[j])
+// z_j (+)= d_j / sc_j for the shifts that are not frozen; d_j is the FP32 answer of the
+// multigrid in z0 or z1 (final_buf[j]) for the right-hand side scaled by sc_j
 __global__ void k_shift_update(int N, double2 *__restrict__ z, View z0, View z1,
                                const int *__restrict__ final_buf, const int *__restrict__ frozen,
-                               int accumulate) {
+                               const float *__restrict__ sc, int accumulate) {
   const int j = blockIdx.z;
   if (frozen && frozen[j]) return;
   const int i = blockIdx.y * 8 + threadIdx.y, c = blockIdx.x * 32 + threadIdx.x;
   if (i >= N || c >= N) return;
   const View &src = final_buf[j] ? z1 : z0;
-  const float2 d =
+  const float isc = 1.0f / sc[j];  // a power of two: exact
+  float2 d =
       reinterpret_cast<const float2 *>(src.p)[(long long)j * src.plane + (long long)i * src.pitch + c];
+  d.x *= isc;
+  d.y *= isc;
   double2 &dst = z[(long long)j * N * N + (long long)i * N + c];
   if (accumulate) {
     dst.x += to_f64(d.x);
@@ -137,23 +141,23 @@ void launch_round_to_float(cudaStream_t s, long long count, const double *x, flo
 }
 
 // CTAs per shift: one wave of two CTAs per SM over all shifts
-int shift_residual_blocks(int N, int n) {
-  const int want = (2 * 152) / n;
+int shift_residual_blocks(int N, int n, int num_sms) {
+  const int want = (2 * num_sms) / n;
   return want < 1 ? 1 : (want > N ? N : want);
 }
 
-void launch_shift_residual(cudaStream_t s, int N, int n, const double2 *z, const double2 *b,
-                           const double2 *c1, double off, float oscale, View out,
+void launch_shift_residual(cudaStream_t s, int gx, int N, int n, const double2 *z, const double2 *b,
+                           const double2 *c1, double off, float oscale, const float *sc, View out,
                            const int *frozen, bool want_b, double *part) {
-  dim3 grid(shift_residual_blocks(N, n), n);
-  k_shift_residual<<<grid, kSrThreads, 0, s>>>(N, z, b, c1, off, oscale, out, frozen,
+  dim3 grid(gx, n);
+  k_shift_residual<<<grid, kSrThreads, 0, s>>>(N, z, b, c1, off, oscale, sc, out, frozen,
                                                want_b ? 1 : 0, part);
 }
 
 void launch_shift_update(cudaStream_t s, int N, int n, double2 *z, View z0, View z1,
-                         const int *final_buf, const int *frozen, bool accumulate) {
+                         const int *final_buf, const int *frozen, const float *sc, bool accumulate) {
   dim3 grid((N + 31) / 32, (N + 7) / 8, n);
-  k_shift_update<<<grid, dim3(32, 8), 0, s>>>(N, z, z0, z1, final_buf, frozen, accumulate ? 1 : 0);
+  k_shift_update<<<grid, dim3(32, 8), 0, s>>>(N, z, z0, z1, final_buf, frozen, sc, accumulate ? 1 : 0);
 }
 
 }  // namespace pd

@@ -147,13 +147,14 @@ __device__ __forceinline__ unsigned char *align1024(unsigned char *p) {
   return p + ((1024 - (smem_u32(p) & 1023)) & 1023);
 }
 
-// g_j(p) = h^2 sum_k V^{-1}[j][k] fhat_k(p), fhat_k = f_k + u0coef[k] u0, for the points
-// p = (i, c0..c0+127) of grid row i; written into the h^2-scaled level-0 RHS view.
+// g_j(p) = h^2 sum_k V^{-1}[j][k] fhat_k(p), fhat_k = in_scale (f_k + u0coef[k] u0), for the
+// points p = (i, c0..c0+127) of grid row i; written into the h^2-scaled level-0 RHS view
+// (in_scale: a power of two that brings the refinement's FP64 residual near unit size).
 template <typename InT>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_tc_forward(int N, int n, View g, const InT *__restrict__ f, const double *__restrict__ u0,
              const double *__restrict__ u0coef, const float *__restrict__ Ahi,
-             const float *__restrict__ Alo, int *__restrict__ errflag) {
+             const float *__restrict__ Alo, double in_scale, int *__restrict__ errflag) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *sm = align1024(smem_raw);
   unsigned char *sAhi = sm, *sAlo = sm + kFwdA, *sBhi = sm + 2 * kFwdA, *sBlo = sBhi + kFwdB;
@@ -197,7 +198,8 @@ k_tc_forward(int N, int n, View g, const InT *__restrict__ f, const double *__re
         float v = 0.f;
         if (k < n && c < N) {
           const double ck = u0 ? u0coef[k] : 0.0;
-          if (ck != 0.0) v = (float)((double)f[k * m + x] + ck * u0[x]);
+          if (ck != 0.0) v = (float)(((double)f[k * m + x] + ck * u0[x]) * in_scale);
+          else if (in_scale != 1.0) v = (float)((double)f[k * m + x] * in_scale);
           else v = (float)f[k * m + x];
         }
         pre[q][e] = v;
@@ -270,7 +272,7 @@ k_tc_forward(int N, int n, View g, const InT *__restrict__ f, const double *__re
 // final_buf[j] is set, else from z0; imag_check: atomic max of |Im| (bits of a double).
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_tc_inverse(int N, int n, double *__restrict__ u, View z0, View z1, const int *__restrict__ final_buf,
-             const float *__restrict__ Ahi, const float *__restrict__ Alo, int accumulate,
+             const float *__restrict__ Ahi, const float *__restrict__ Alo, float dscale, int accumulate,
              int imag_check, unsigned long long *imag_bits, int *__restrict__ errflag) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *sm = align1024(smem_raw);
@@ -379,8 +381,8 @@ k_tc_inverse(int N, int n, double *__restrict__ u, View z0, View z1, const int *
       const int k = it / kInvNt, cc = it % kInvNt;
       const int c = c0 + cc;
       if (k < n && c < N) {
-        u[(long long)k * m + (long long)i * N + c] = uacc[q] + (double)S[k * (kInvNt + 1) + cc];
-        if (imag_check) imax = fmaxf(imax, fabsf(S[(64 + k) * (kInvNt + 1) + cc]));
+        u[(long long)k * m + (long long)i * N + c] = uacc[q] + (double)(S[k * (kInvNt + 1) + cc] * dscale);
+        if (imag_check) imax = fmaxf(imax, fabsf(S[(64 + k) * (kInvNt + 1) + cc] * dscale));
       }
     }
     __syncthreads();
@@ -449,19 +451,19 @@ void tc_build_operands(int n, const double *Vinv, const double *V, double scale,
 
 void launch_tc_forward(cudaStream_t s, int grid, int N, int n, View g, const void *f, bool f32,
                        const double *u0, const double *u0coef, const float *Ahi, const float *Alo,
-                       int *errflag) {
+                       double in_scale, int *errflag) {
   if (f32)
     k_tc_forward<float><<<grid, kTcThreads, kFwdSmem, s>>>(N, n, g, static_cast<const float *>(f), u0,
-                                                           u0coef, Ahi, Alo, errflag);
+                                                           u0coef, Ahi, Alo, in_scale, errflag);
   else
     k_tc_forward<double><<<grid, kTcThreads, kFwdSmem, s>>>(N, n, g, static_cast<const double *>(f), u0,
-                                                            u0coef, Ahi, Alo, errflag);
+                                                            u0coef, Ahi, Alo, in_scale, errflag);
 }
 
 void launch_tc_inverse(cudaStream_t s, int grid, int N, int n, double *u, View z0, View z1,
-                       const int *final_buf, const float *Ahi, const float *Alo, bool accumulate,
-                       bool imag_check, unsigned long long *imag_bits, int *errflag) {
-  k_tc_inverse<<<grid, kTcThreads, kInvSmem, s>>>(N, n, u, z0, z1, final_buf, Ahi, Alo,
+                       const int *final_buf, const float *Ahi, const float *Alo, float dscale,
+                       bool accumulate, bool imag_check, unsigned long long *imag_bits, int *errflag) {
+  k_tc_inverse<<<grid, kTcThreads, kInvSmem, s>>>(N, n, u, z0, z1, final_buf, Ahi, Alo, dscale,
                                                   accumulate ? 1 : 0, imag_check ? 1 : 0, imag_bits,
                                                   errflag);
 }

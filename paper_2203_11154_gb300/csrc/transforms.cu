@@ -62,13 +62,13 @@ k_transform_forward(int N, int n, View g, const InT *__restrict__ f,
   }
 }
 
-// u_k (+)= Re sum_j W[k][j] z_j; with imag_check also max |Im sum_j W[k][j] z_j|.
-// z_j is read from z1 where final_buf[j] is set, else from z0.
+// u_k (+)= dscale Re sum_j W[k][j] z_j; with imag_check also max |dscale Im sum_j W[k][j] z_j|.
+// z_j is read from z1 where final_buf[j] is set, else from z0.  dscale is a power of two.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_transform_inverse(int N, int n, double *__restrict__ u, View z0, View z1,
                     const int *__restrict__ final_buf, const typename Cx<T>::type *__restrict__ W,
-                    int accumulate, int imag_check, unsigned long long *imag_bits) {
+                    T dscale, int accumulate, int imag_check, unsigned long long *imag_bits) {
   using C = typename Cx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *zs = reinterpret_cast<C *>(smem_raw);  // [n][kPts]
@@ -103,10 +103,10 @@ k_transform_inverse(int N, int n, double *__restrict__ u, View z0, View z1,
           im = fmadd(wj.y, zv.x, im);
         }
       }
-      double out = (double)re;
+      double out = (double)(re * dscale);
       if (accumulate) out += u[k * m + x];
       u[k * m + x] = out;
-      imax = fmax(imax, fabs((double)im));
+      imax = fmax(imax, fabs((double)(im * dscale)));
     }
   }
   if (imag_check) {
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(kResThreads)
 k_residual_bidiag(int N, int n, int off, OutT *__restrict__ r, const double *__restrict__ u,
                   const double *__restrict__ f, const double *__restrict__ u0,
                   const double *__restrict__ u0coef, const double *__restrict__ bd,
-                  const double *__restrict__ bs, double ih2, double *__restrict__ part) {
+                  const double *__restrict__ bs, double ih2, double oscale, double *__restrict__ part) {
   __shared__ double red[2][kResThreads / 32];
   const long long m = (long long)N * N;
   double ar = 0.0, af = 0.0;
@@ -210,11 +210,13 @@ k_residual_bidiag(int N, int n, int off, OutT *__restrict__ r, const double *__r
       if (i > 0) nb += uk[c - N];
       if (i < N - 1) nb += uk[c + N];
       const double rv = fma(ih2, nb, fma(-sk, up[c], fma(-c1, uk[c], fh)));
-      if (r) r[(long long)k * m + (long long)i * N + c] = (OutT)rv;
       if (sizeof(OutT) == 4) {
-        const float rf = (float)rv;
+        // the FP32 output times the power of two oscale (kept near unit size)
+        const float rf = (float)(rv * oscale);
+        if (r) r[(long long)k * m + (long long)i * N + c] = (OutT)rf;
         arow = fmaf(rf, rf, arow);
       } else {
+        if (r) r[(long long)k * m + (long long)i * N + c] = (OutT)rv;
         arow64 = fma(rv, rv, arow64);
       }
       if (WANT_F) af = fma(fh, fh, af);
@@ -302,19 +304,19 @@ void launch_laplacian_dot(cudaStream_t s, int N, int n, const double *w, const d
 void launch_residual_bidiag(cudaStream_t s, int N, int n, int off, double kappa, double *r64,
                             float *r32, const double *u, const double *f, const double *u0,
                             const double *u0coef, const double *bd, const double *bs, bool want_f,
-                            double *part) {
+                            double *part, double oscale) {
   const double h = 1.0 / (N + 1), ih2 = kappa / (h * h);
   const int g = allatonce_blocks();
   if (r32) {
     if (want_f)
-      k_residual_bidiag<float, true><<<g, kResThreads, 0, s>>>(N, n, off, r32, u, f, u0, u0coef, bd, bs, ih2, part);
+      k_residual_bidiag<float, true><<<g, kResThreads, 0, s>>>(N, n, off, r32, u, f, u0, u0coef, bd, bs, ih2, oscale, part);
     else
-      k_residual_bidiag<float, false><<<g, kResThreads, 0, s>>>(N, n, off, r32, u, f, u0, u0coef, bd, bs, ih2, part);
+      k_residual_bidiag<float, false><<<g, kResThreads, 0, s>>>(N, n, off, r32, u, f, u0, u0coef, bd, bs, ih2, oscale, part);
   } else {
     if (want_f)
-      k_residual_bidiag<double, true><<<g, kResThreads, 0, s>>>(N, n, off, r64, u, f, u0, u0coef, bd, bs, ih2, part);
+      k_residual_bidiag<double, true><<<g, kResThreads, 0, s>>>(N, n, off, r64, u, f, u0, u0coef, bd, bs, ih2, oscale, part);
     else
-      k_residual_bidiag<double, false><<<g, kResThreads, 0, s>>>(N, n, off, r64, u, f, u0, u0coef, bd, bs, ih2, part);
+      k_residual_bidiag<double, false><<<g, kResThreads, 0, s>>>(N, n, off, r64, u, f, u0, u0coef, bd, bs, ih2, oscale, part);
   }
 }
 
@@ -348,14 +350,14 @@ void launch_transform_forward(cudaStream_t s, int N, int n, View g, const void *
 
 template <typename T>
 void launch_transform_inverse(cudaStream_t s, int N, int n, double *u, View z0, View z1,
-                              const int *final_buf, const typename Cx<T>::type *W,
+                              const int *final_buf, const typename Cx<T>::type *W, T dscale,
                               bool accumulate, bool imag_check,
                               unsigned long long *imag_max_bits) {
   using C = typename Cx<T>::type;
   const long long m = (long long)N * N;
   const unsigned blocks = (unsigned)((m + kPts - 1) / kPts);
   k_transform_inverse<T><<<blocks, kThreads, n * kPts * sizeof(C), s>>>(
-      N, n, u, z0, z1, final_buf, W, accumulate ? 1 : 0, imag_check ? 1 : 0, imag_max_bits);
+      N, n, u, z0, z1, final_buf, W, dscale, accumulate ? 1 : 0, imag_check ? 1 : 0, imag_max_bits);
 }
 
 int allatonce_blocks() { return 4 * 152; }
@@ -378,10 +380,10 @@ template void launch_transform_forward<float>(cudaStream_t, int, int, View, cons
                                               const double *, const double *, const float2 *,
                                               double);
 template void launch_transform_inverse<double>(cudaStream_t, int, int, double *, View, View,
-                                               const int *, const double2 *, bool, bool,
+                                               const int *, const double2 *, double, bool, bool,
                                                unsigned long long *);
 template void launch_transform_inverse<float>(cudaStream_t, int, int, double *, View, View,
-                                              const int *, const float2 *, bool, bool,
+                                              const int *, const float2 *, float, bool, bool,
                                               unsigned long long *);
 
 }  // namespace pd

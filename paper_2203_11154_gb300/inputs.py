@@ -21,6 +21,8 @@ Workloads (unit square, homogeneous Dirichlet, N x N interior, h = 1/(N+1)):
   adjoint-1023   as paradiag-1023 (seed 1 for f), plus a target u_target = sum of 8
                  modes A_q sin(k_q pi x) sin(l_q pi y), k_q, l_q ~ U{1..8}, A_q ~ N(0,1),
                  seed 3 (drawn k, then l, then A).
+  examples       the time matrices of Sec. 3: Example 1's boundary-value B (eq. (9)) and
+                 Example 2's quasi-BVM B (eq. (10)), and Example 3's Helmholtz shifts.
 Smaller variants of the same recipes serve the parity tests.
 """
 import numpy as np
@@ -101,3 +103,31 @@ def sine_modes_target(N, seed=3, modes=8):
     for q in range(modes):
         out += A[q] * np.sin(k[q] * np.pi * x) * np.sin(l[q] * np.pi * y)
     return out
+
+
+def bvm_time_matrix(n):
+    """Example 1's time matrix (eq. (9)), tau = 1/n: rows 1..n-2 are the central
+    difference (-1/2, 0, 1/2), the first row (0, 1/2, 0, ...) (its -1/2 u_0 moves to the
+    right-hand side), the last row the backward difference (..., -1, 1); all over tau."""
+    B = np.zeros((n, n))
+    for k in range(n - 1):
+        B[k, k + 1] = 0.5
+        if k > 0:
+            B[k, k - 1] = -0.5
+    B[n - 1, n - 2] = -1.0
+    B[n - 1, n - 1] = 1.0
+    return B * n
+
+
+def quasi_bvm_time_matrix(n, beta):
+    """Example 2's time matrix (eq. (10)), (n+1) x (n+1), tau = 1/n: 1 on the diagonal,
+    -1 below it, 1/beta in the top-right corner, all over tau."""
+    B = np.eye(n + 1) - np.eye(n + 1, k=-1)
+    B[0, n] = 1.0 / beta
+    return B * n
+
+
+def helmholtz_shifts(h):
+    """Example 3's shifts -j^2 (1 - 0.5 i) for j = 1, 2, ... with j h <= 1/2."""
+    js = np.arange(1, int(np.floor(0.5 / h + 1e-12)) + 1)
+    return -(js.astype(float) ** 2) * (1 - 0.5j)

@@ -114,3 +114,43 @@ def test_refinement_history():
     assert outer[-1] == out["relres_allatonce"] and outer[-1] <= 1e-10
     assert np.all(np.diff(outer) < 0)
     c.destroy()
+
+
+@pytest.mark.parametrize("scale", [1e-15, 1e20])
+def test_precision_form_does_not_depend_on_the_data_scale(scale):
+    """The FP32 solves inside the FP64 refinement see right-hand sides scaled by powers of two
+    to unit size, so a source and initial value scaled by 1e-15 or 1e20 still reach the
+    oracle's relative residual of eq. (1) <= 1e-10 (the solve of eq. (1) is linear)."""
+    N, n, tau, alpha = 127, 16, 1.0 / 16, 1e-3
+    c = api.alpha_circulant_context(N, n, tau, alpha, precision=1)
+    f, u0 = inputs.paradiag_problem(N, n, seed=1)
+    f = f * scale
+    u0 = u0 * scale
+    u = torch.empty(n, N, N, dtype=torch.float64, device="cuda")
+    out = c.paradiag_solve(u, torch.from_numpy(f).cuda(), torch.from_numpy(u0).cuda())
+    assert out["relres_allatonce"] <= 1e-10
+    torch.cuda.synchronize()
+    fhat = core.assemble_rhs(N, n, tau, f, u0)
+    rn, fn = core.allatonce_residual(N, n, tau, alpha, u.cpu().numpy(), fhat)
+    assert rn / fn <= 1e-10
+    assert abs(rn / fn - out["relres_allatonce"]) <= 0.05 * rn / fn + 1e-13
+    c.destroy()
+
+
+@pytest.mark.parametrize("scale", [1e-15, 1e20])
+def test_refined_shifted_solve_does_not_depend_on_the_data_scale(scale):
+    """shifted_solve_refined with right-hand sides scaled by 1e-15 or 1e20: every shift reaches
+    the oracle's FP64 relative residual <= 1e-10."""
+    N, n = 127, 16
+    lam = api.pd_shifts_alpha_circulant(n, 1.0 / 16, 1e-2)[0]
+    b = inputs.shifted_problem(N, n, seed=0) * scale
+    c = api.Context(N, n, lam, cfg=api.config(precision=1))
+    z = torch.empty(n, N, N, dtype=torch.complex128, device="cuda")
+    it, rr = c.shifted_solve_refined(z, torch.from_numpy(b).cuda())
+    assert np.all(rr <= 1e-10)
+    torch.cuda.synchronize()
+    zh = z.cpu().numpy()
+    for j in range(n):
+        r = core.residual(N, lam[j], b[j], zh[j])
+        assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(b[j])
+    c.destroy()
