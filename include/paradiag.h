@@ -220,12 +220,14 @@ pd_status shifted_solve_refined(pd_ctx *ctx, void *d_z, const void *d_b, int *h_
 /*
  * A batch of independent shifted-system problems of uneven sizes (several PDE instances,
  * each with its own grid N_i = 2^k - 1 and n_i shifts): one context per instance with the
- * common cfg (omega_mode 0 or 1; no V, B or tables), each on a stream of its own that the
- * batch creates, so that the instances' kernels overlap on the GPU.  pd_batch_solve
- * advances all instances together, one multigrid cycle of every unfinished instance per
- * round (each a replayed CUDA graph when cfg.cuda_graphs), with the solve of
- * shifted_solve_refined per instance; it is ordered after the work queued on `stream`
- * before the call, and work queued on `stream` after it waits for it.
+ * common cfg (omega_mode 0 or 1; no V, B or tables).  pd_batch_solve advances all
+ * instances together with the solve of shifted_solve_refined per instance.  With FP32
+ * V(1,1) cycles (precision 1) every cycle of all instances runs as one launch per
+ * multigrid level over all instances (see pd_batch_info), replayed as a CUDA graph when
+ * cfg.cuda_graphs; otherwise each instance runs on a stream of its own that the batch
+ * creates, one cycle of every unfinished instance per round, so that their kernels
+ * overlap.  The solve is ordered after the work queued on `stream` before the call, and
+ * work queued on `stream` after it waits for it.
  *   h_N, h_n: count sizes; h_shifts[i]: n_i complex shifts (host, copied).
  *   d_z[i], d_b[i]: FP64 complex [n_i][N_i][N_i] device arrays of instance i.
  *   h_iters, h_relres (may be NULL): sum n_i entries, instance by instance.
@@ -240,6 +242,16 @@ pd_status pd_batch_solve(pd_batch *batch, void *const *d_z, const void *const *d
                          double *h_relres);
 pd_status pd_batch_destroy(pd_batch *batch);
 const char *pd_batch_last_error(const pd_batch *batch);
+/*
+ * How a batch runs its cycles: *h_batched = 1 when every cycle of all instances is one
+ * launch per multigrid level over all instances (FP32 V(1,1) cycles with the warp-stream
+ * kernels, cfg.fused_variant 0 or 2: the instances share one stream, and a cycle is
+ * 2 G + 2 launches, G the most global-memory levels of an instance, returned in
+ * *h_launches_per_cycle), 0 when the instances run side by side on streams of their own
+ * (-1 per cycle).  *h_launches: batched multigrid launches so far.  Any pointer may be NULL.
+ */
+pd_status pd_batch_info(const pd_batch *batch, int *h_batched, int *h_launches_per_cycle,
+                        long long *h_launches);
 
 /* Indices of the values paradiag_solve writes to h_stats (PD_STATS_LEN doubles). */
 enum {
@@ -335,6 +347,17 @@ pd_status pd_allatonce_residual(pd_ctx *ctx, double *d_r, const double *d_u, con
  */
 pd_status pd_allatonce_residual32(pd_ctx *ctx, float *d_r32, const double *d_u, const double *d_f,
                                   const double *d_u0, double *h_norms);
+
+/*
+ * The residual of the shifted systems of eq. (2) as the refined shifted solves hand it to
+ * the FP32 multigrid: d_r32 [n][N][N] complex float = b_j - (kappa A + lam_j I) z_j
+ * rounded to FP32 (unscaled), h_norms[j] = ||r_j||_2 of the FP32 values (n doubles, may
+ * be NULL).  d_z, d_b: [n][N][N] complex double, device.  With cfg.fx_residual the exact
+ * stencil difference per complex component without FP64 arithmetic, else the FP64
+ * formula.  Needs precision 1 (else PD_ERR_STATE).  Synchronises.
+ */
+pd_status pd_shifted_residual32(pd_ctx *ctx, float *d_r32, const void *d_z, const void *d_b,
+                                double *h_norms);
 
 /*
  * Gradient reduction of the adjoint (differentiation with respect to a coefficient

@@ -65,6 +65,7 @@ def lib():
                                        _D, _P, _P, _P, _P, _P]),
             "or_allatonce_residual": (_D, [_I, _I, _D, _D, _P, _P, _P, _P]),
             "or_allatonce_residual_ld": (_D, [_I, _I, _D, _D, _P, _P, _P]),
+            "or_residual_ld": (_D, [_I, _D, _Cplx, _P, _P, _P]),
             "or_set_threads": (None, [_I]),
             "or_max_threads": (_I, []),
         }
@@ -287,6 +288,16 @@ def allatonce_residual(N, n, tau, alpha, u, fhat, want_r=False):
     rn = lib().or_allatonce_residual(N, n, float(tau), float(alpha), _ptr(u), _ptr(fhat),
                                      _ptr(r) if want_r else None, C.byref(fn))
     return (rn, fn.value, r) if want_r else (rn, fn.value)
+
+
+def residual_ld(N, lam, b, z):
+    """r = b - (A + lam I) z of eq. (2) evaluated in long double and rounded to double at the
+    end (a reference below the FP64 rounding of the formula)."""
+    b = _cvec(b, (N, N))
+    z = _cvec(z, (N, N))
+    r = np.empty_like(z)
+    lib().or_residual_ld(N, 1.0 / (N + 1), _c(lam), _ptr(b), _ptr(z), _ptr(r))
+    return r
 
 
 def allatonce_residual_ld(N, n, tau, alpha, u, fhat):

@@ -457,6 +457,31 @@ double or_allatonce_residual_ld(int N, int n, double tau, double alpha, const do
     return sqrt(rs);
 }
 
+/* r = b - (A + lam I) z of one shifted system (eq. (2)) evaluated in long double, each
+ * component and term separately (a reference for residual kernels whose error lies below
+ * the FP64 rounding of the formula); r receives the residual rounded to double, the
+ * return value is ||r||_2 of the rounded values.  b, z, r: N x N complex. */
+double or_residual_ld(int N, double h, cplx lam, const cplx *b, const cplx *z, cplx *r)
+{
+    long double ih2 = 1.0L / ((long double)h * (long double)h);
+    long double lr = creal(lam), li = cimag(lam);
+    double rs = 0.0;
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++) {
+            size_t p = (size_t)i * N + j;
+            long double cr = creal(z[p]), ci = cimag(z[p]);
+            long double nr = (long double)creal(at(z, N, i - 1, j)) + (long double)creal(at(z, N, i + 1, j))
+                             + (long double)creal(at(z, N, i, j - 1)) + (long double)creal(at(z, N, i, j + 1));
+            long double ni = (long double)cimag(at(z, N, i - 1, j)) + (long double)cimag(at(z, N, i + 1, j))
+                             + (long double)cimag(at(z, N, i, j - 1)) + (long double)cimag(at(z, N, i, j + 1));
+            long double rr = (long double)creal(b[p]) - (lr * cr - li * ci) - ih2 * (4.0L * cr - nr);
+            long double ri = (long double)cimag(b[p]) - (lr * ci + li * cr) - ih2 * (4.0L * ci - ni);
+            r[p] = (double)rr + I * (double)ri;
+            rs += (double)rr * (double)rr + (double)ri * (double)ri;
+        }
+    return sqrt(rs);
+}
+
 /* OpenMP thread count used by the batched routines (reported with CPU timings). */
 void or_set_threads(int k)
 {

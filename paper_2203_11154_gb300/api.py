@@ -40,9 +40,9 @@ EXPORTS = ["pd_config_default", "pd_alpha_circulant", "pd_shifts_alpha_circulant
            "pd_allatonce_residual", "pd_allatonce_residual_static", "pd_laplacian_dot",
            "pd_initial_value_gradient",
            "pd_profile_enable", "pd_profile_read", "pd_get_history", "pd_synchronize", "pd_launch_count", "paradiag_destroy",
-           "pd_status_str", "pd_last_error", "shifted_solve_refined", "pd_allatonce_residual32",
+           "pd_status_str", "pd_last_error", "shifted_solve_refined", "pd_allatonce_residual32", "pd_shifted_residual32",
            "paradiag_solve_host_batch", "pd_batch_setup",
-           "pd_batch_solve", "pd_batch_destroy", "pd_batch_last_error"]
+           "pd_batch_solve", "pd_batch_destroy", "pd_batch_last_error", "pd_batch_info"]
 
 
 class PDError(RuntimeError):
@@ -113,11 +113,13 @@ def lib(path=None):
             "pd_last_error": (C.c_char_p, [_P]),
             "shifted_solve_refined": (_I, [_P, _P, _P, _P, _P]),
             "pd_allatonce_residual32": (_I, [_P, _P, _P, _P, _P, _P]),
+            "pd_shifted_residual32": (_I, [_P, _P, _P, _P, _P]),
             "paradiag_solve_host_batch": (_I, [_P, _I, _P, _P, _P, _P, _P, _P]),
             "pd_batch_setup": (_I, [C.POINTER(_P), _I, _P, _P, _P, C.POINTER(pd_config), _P]),
             "pd_batch_solve": (_I, [_P, _P, _P, _P, _P]),
             "pd_batch_destroy": (_I, [_P]),
             "pd_batch_last_error": (C.c_char_p, [_P]),
+            "pd_batch_info": (_I, [_P, _P, _P, _P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -467,6 +469,17 @@ class Context:
                "pd_allatonce_residual32", self.h)
         return norms[0], norms[1]
 
+    def pd_shifted_residual32(self, r32, z, b):
+        """r32: complex64 [n][N][N]; z, b: complex128 [n][N][N] device tensors.  Returns the
+        per-shift ||r_j||."""
+        import torch
+        m = self.n * self.N * self.N
+        norms = np.zeros(self.n)
+        _check(lib().pd_shifted_residual32(self.h, _dptr(r32, torch.complex64, m),
+                                           _dptr(z, torch.complex128, m), _dptr(b, torch.complex128, m),
+                                           _hptr(norms)), "pd_shifted_residual32", self.h)
+        return norms
+
 
 def paradiag_setup(N, n, shifts, V=None, Vinv=None, B=None, u0_coef=None, omega=None, cfg=None,
                    stream=None):
@@ -563,6 +576,15 @@ class Batch:
             out.append((it[o:o + n].copy(), rr[o:o + n].copy()))
             o += n
         return out
+
+    def info(self):
+        """(batched: one launch per level over all instances, launches per cycle, batched
+        launches so far)."""
+        b = C.c_int()
+        lpc = C.c_int()
+        tot = C.c_longlong()
+        _check(lib().pd_batch_info(self.h, C.byref(b), C.byref(lpc), C.byref(tot)), "pd_batch_info")
+        return bool(b.value), lpc.value, tot.value
 
     def destroy(self):
         if getattr(self, "h", None):

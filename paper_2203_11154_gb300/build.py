@@ -13,7 +13,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "libparadiag.so")
 CU_SOURCES = ["mg_kernels.cu", "fused_kernels.cu", "stream_kernels.cu", "transforms.cu",
               "tc_transforms.cu", "host.cu", "static_residual.cu", "shift_refine.cu",
-              "residual_fx.cu", "residual_ws.cu", "fft_transforms.cu"]
+              "residual_ws.cu", "fft_transforms.cu"]
 CPP_SOURCES = ["setup.cpp", "eig.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -117,6 +117,7 @@ struct pd_ctx {
   // FP64 refinement of the shifted systems (shifted_solve_refined, batches)
   int *d_frozen = nullptr, *h_frozen = nullptr;  // [n] shift done: zero RHS, no update
   double2 *d_c1 = nullptr;                       // [n] lam_j + 4 kappa / h^2
+  double2 *d_lam = nullptr;                      // [n] lam_j
   double *d_srpart = nullptr, *h_srpart = nullptr;  // [2][n][blocks] residual partial sums
   float *d_rsc = nullptr, *h_rsc = nullptr;  // [n] power-of-two scale of each shift's FP32 RHS
   // CUDA graphs of whole cycles, keyed by everything a cycle's launches depend on
@@ -918,7 +919,7 @@ void refine_eval_launch(RefRun &r) {
   ck(c, cudaMemcpyAsync(c->d_rsc, c->h_rsc, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
   if (!first && c->cfg.fx_residual)  // without FP64 arithmetic (the first one is r = b)
     PD_PROF(PD_KC_RESIDUAL, (32.0 + w) * m, 0,
-            launch_shift_residual_fx(c->stream, gx, N, n, r.z, r.b, c->d_c1, c->kappa / (h * h),
+            launch_shift_residual_fx(c->stream, gx, N, n, r.z, r.b, c->d_lam, c->kappa / (h * h),
                                      (float)rs(c, 0), c->d_rsc, view(B.b, N, B.P), c->d_frozen,
                                      c->d_srpart));
   else
@@ -999,8 +1000,266 @@ void refine_eval_finish(RefRun &r) {
   r.done = !any || r.rc != PD_OK;
 }
 
-// shifted_solve_refined for a set of runs (one per context), advanced together
-void refine_runs(std::vector<RefRun> &runs) {
+// ---- batches of uneven instances: one launch per multigrid level over all instances ----
+//
+// With V(1,1) cycles of FP32 warp-stream kernels on every global level, a cycle of all
+// instances is 2 G + 2 launches (G = the most global levels of an instance), aligned at
+// the finest level: the smoothing + restriction of level s of every instance that has it,
+// the convergence test of all shifts after level 0, the coarse levels of all instances
+// (one CTA per shift), then the interpolation + smoothing of level s for s = G-1 .. 0.
+// The tasks (views, coefficient tables, states) are tables in device memory built once;
+// a cycle is captured as one CUDA graph per kind and replayed.
+struct BatchPlan {
+  std::vector<pd_ctx *> ctx;   // every instance
+  std::vector<pd_ctx *> cyc;   // those with global levels (the others solve inside k_coarse)
+  cudaStream_t stream = nullptr;
+  bool ok = false;
+  int gmax = 0, total = 0, grid = 0;
+  size_t coarse_smem = 0;
+  std::vector<int> sr_off, sr_cnt, sr_units, ps_off, ps_cnt, ps_units;
+  StreamTask<float> *d_stream = nullptr;
+  CoarseTask<float> *d_coarse = nullptr;
+  ConvTask *d_conv = nullptr;
+  int *d_bnact = nullptr, *h_bnact = nullptr;  // active shifts of all instances (pinned [cycles + 2])
+  int *h_total = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  std::vector<char> zeroed;  // level-0 RHS of a finished instance already cleared
+  std::vector<cudaEvent_t> join;  // per instance: its stream's work before the batched cycles
+  cudaEvent_t done = nullptr;     // the batched cycles, for the instances' streams
+  struct Graph {
+    int zzero, cmax;
+    double tol, stall;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;
+  bool graphs_ok = true;
+  long long launches = 0;
+  std::vector<void *> allocs;
+};
+
+void free_plan(BatchPlan &bp) {
+  for (auto &g : bp.graphs) cudaGraphExecDestroy(g.exec);
+  bp.graphs.clear();
+  for (void *q : bp.allocs) cudaFree(q);
+  bp.allocs.clear();
+  if (bp.h_bnact) cudaFreeHost(bp.h_bnact);
+  if (bp.h_total) cudaFreeHost(bp.h_total);
+  bp.h_bnact = bp.h_total = nullptr;
+  for (int k = 0; k < 2; k++)
+    if (bp.ev[k]) cudaEventDestroy(bp.ev[k]);
+  bp.ev[0] = bp.ev[1] = nullptr;
+  for (cudaEvent_t e : bp.join)
+    if (e) cudaEventDestroy(e);
+  bp.join.clear();
+  if (bp.done) cudaEventDestroy(bp.done);
+  bp.done = nullptr;
+}
+
+// Builds the task tables; leaves bp.ok false (launches instance by instance) unless every
+// instance runs FP32 V(1,1) cycles with warp-stream kernels on at least one global level.
+void build_plan(BatchPlan &bp) {
+  bp.ok = false;
+  bp.cyc.clear();
+  if (bp.ctx.empty()) return;
+  for (pd_ctx *c : bp.ctx) {
+    const pd_config &cf = c->cfg;
+    if (cf.precision != 1 || cf.nu1 != 1 || cf.nu2 != 1 || cf.cycle_gamma != 1) return;
+    if (c->lc < 1) continue;  // the whole solve runs in k_coarse at solve_begin
+    for (int l = 0; l < c->lc; l++)
+      if (!c->p32.lv[l].maps || c->p32.lv[l].variant != 2) return;
+    bp.gmax = std::max(bp.gmax, c->lc);
+    bp.cyc.push_back(c);
+  }
+  pd_ctx *c0 = bp.ctx[0];
+  std::vector<StreamTask<float>> st;
+  for (int pass = 0; pass < 2; pass++)
+    for (int sl = 0; sl < bp.gmax; sl++) {
+      (pass == 0 ? bp.sr_off : bp.ps_off).push_back((int)st.size());
+      int units = 0, cnt = 0;
+      for (pd_ctx *c : bp.cyc) {
+        if (c->lc <= sl) continue;
+        const LevelBufs &B = c->p32.lv[sl], &Bc = c->p32.lv[sl + 1];
+        StreamTask<float> t{};
+        t.N = B.N;
+        t.n = c->n;
+        t.seg = B.seg;
+        t.ubegin = units;
+        t.b = view(B.b, B.N, B.P);
+        t.coef = c->p32.coef + (size_t)sl * c->n;
+        t.active = c->st.active;
+        if (pass == 0) {
+          t.z = view(B.z[0], B.N, B.P);
+          t.zout = view(B.z[1], B.N, B.P);
+          t.x = view(Bc.b, Bc.N, Bc.P);
+          t.partials = sl == 0 ? c->st.partials : nullptr;
+          t.part_stride = c->st.max_tiles;
+        } else {
+          t.z = view(B.z[1], B.N, B.P);
+          t.zout = view(B.z[0], B.N, B.P);
+          t.x = view(Bc.z[0], Bc.N, Bc.P);
+        }
+        units += c->n * stream_units(B.N, B.seg);
+        st.push_back(t);
+        cnt++;
+      }
+      (pass == 0 ? bp.sr_cnt : bp.ps_cnt).push_back(cnt);
+      (pass == 0 ? bp.sr_units : bp.ps_units).push_back(units);
+    }
+  std::vector<CoarseTask<float>> co;
+  std::vector<ConvTask> cv;
+  int j0 = 0;
+  for (pd_ctx *c : bp.cyc) {
+    const LevelBufs &B = c->p32.lv[c->lc];
+    CoarseTask<float> t{};
+    t.a.plan = c->plan;
+    t.a.n = c->n;
+    t.a.start = c->lc;
+    t.a.block0 = j0;
+    t.a.coef = c->p32.coef;
+    t.a.cinv = c->p32.cinv;
+    t.b = view(B.b, B.N, B.P);
+    t.z = view(B.z[0], B.N, B.P);
+    t.active = c->st.active;
+    co.push_back(t);
+    bp.coarse_smem = std::max(bp.coarse_smem, coarse_smem_bytes<float>(c->plan, c->lc));
+    ConvTask k{};
+    k.st = c->st;
+    k.n = c->n;
+    k.ntiles = stream_units(c->N, c->p32.lv[0].seg);
+    k.j0 = j0;
+    cv.push_back(k);
+    j0 += c->n;
+  }
+  bp.total = j0;
+  bp.grid = c0->stream_grid;
+  auto upload = [&](const void *src, size_t bytes) {
+    void *d = nullptr;
+    ck(c0, cudaMalloc(&d, std::max<size_t>(bytes, 16)));
+    bp.allocs.push_back(d);
+    ck(c0, cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice));
+    return d;
+  };
+  bp.d_stream = static_cast<StreamTask<float> *>(upload(st.data(), st.size() * sizeof(st[0])));
+  bp.d_coarse = static_cast<CoarseTask<float> *>(upload(co.data(), co.size() * sizeof(co[0])));
+  bp.d_conv = static_cast<ConvTask *>(upload(cv.data(), cv.size() * sizeof(cv[0])));
+  {
+    void *d = nullptr;
+    ck(c0, cudaMalloc(&d, sizeof(int)));
+    bp.allocs.push_back(d);
+    bp.d_bnact = static_cast<int *>(d);
+  }
+  const int hist = std::max(c0->cfg.maxit, c0->cfg.inner_maxit) + 2;
+  ck(c0, cudaMallocHost(&bp.h_bnact, hist * sizeof(int)));
+  ck(c0, cudaMallocHost(&bp.h_total, sizeof(int)));
+  for (int k = 0; k < 2; k++) ck(c0, cudaEventCreateWithFlags(&bp.ev[k], cudaEventDisableTiming));
+  bp.join.assign(bp.ctx.size(), nullptr);
+  for (auto &e : bp.join) ck(c0, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  ck(c0, cudaEventCreateWithFlags(&bp.done, cudaEventDisableTiming));
+  bp.zeroed.assign(bp.ctx.size(), 0);
+  bp.ok = true;
+}
+
+// One cycle of every instance (see BatchPlan).
+void plan_cycle(BatchPlan &bp, bool zzero, double tol, int cmax, double stall) {
+  pd_ctx *c0 = bp.ctx[0];
+  const int k = (int)bp.cyc.size();
+  for (int sl = 0; sl < bp.gmax; sl++) {
+    // the coarser levels start every cycle from a zero correction
+    launch_sr_multi<float>(bp.stream, bp.grid, bp.d_stream + bp.sr_off[sl], bp.sr_cnt[sl], bp.sr_units[sl],
+                           sl == 0 ? zzero : true, sl == 0);
+    if (sl == 0) launch_converge_multi(bp.stream, bp.d_conv, k, bp.total, tol, cmax, stall, 0, bp.d_bnact);
+  }
+  launch_coarse_multi<float>(bp.stream, bp.d_coarse, k, bp.total, bp.coarse_smem, 1);
+  for (int sl = bp.gmax - 1; sl >= 0; sl--)
+    launch_ps_multi<float>(bp.stream, bp.grid, bp.d_stream + bp.ps_off[sl], bp.ps_cnt[sl], bp.ps_units[sl]);
+  bp.launches += 2 * bp.gmax + 2;
+  ck(c0, cudaGetLastError());
+}
+
+// plan_cycle through a CUDA graph per (zzero, tol, cmax, stall), captured the first time
+void plan_cycle_graph(BatchPlan &bp, bool zzero, double tol, int cmax, double stall) {
+  pd_ctx *c0 = bp.ctx[0];
+  if (c0->cfg.cuda_graphs && bp.graphs_ok) {
+    for (const auto &g : bp.graphs)
+      if (g.zzero == (int)zzero && g.cmax == cmax && g.tol == tol && g.stall == stall) {
+        ck(c0, cudaGraphLaunch(g.exec, bp.stream));
+        bp.launches += 2 * bp.gmax + 2;
+        return;
+      }
+    if (bp.graphs.size() < 16 &&
+        cudaStreamBeginCapture(bp.stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      cudaGraph_t graph = nullptr;
+      bool fine = true;
+      try {
+        plan_cycle(bp, zzero, tol, cmax, stall);
+      } catch (const CudaFail &) {
+        fine = false;
+      }
+      bp.launches -= 2 * bp.gmax + 2;
+      BatchPlan::Graph g{(int)zzero, cmax, tol, stall, nullptr};
+      if (cudaStreamEndCapture(bp.stream, &graph) == cudaSuccess && graph && fine &&
+          cudaGraphInstantiate(&g.exec, graph, 0) == cudaSuccess) {
+        cudaGraphDestroy(graph);
+        bp.graphs.push_back(g);
+        ck(c0, cudaGraphLaunch(g.exec, bp.stream));
+        bp.launches += 2 * bp.gmax + 2;
+        return;
+      }
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      bp.graphs_ok = false;
+    }
+  }
+  plan_cycle(bp, zzero, tol, cmax, stall);
+}
+
+// The inner FP32 solves of the refinement for the instances in `act`, every instance's
+// cycle in the same launches on the plan's stream (joined with the instances' own
+// streams, on which their residual evaluations and updates run side by side); the others
+// get a zero right-hand side, so their shifts stop at the first test.
+void plan_solve(BatchPlan &bp, const std::vector<pd_ctx *> &act, std::vector<pd_status> &rc) {
+  pd_ctx *c0 = bp.ctx[0];
+  int cmax = -1;
+  for (size_t i = 0; i < bp.ctx.size(); i++) {
+    pd_ctx *c = bp.ctx[i];
+    const bool on = std::find(act.begin(), act.end(), c) != act.end();
+    if (!on && !bp.zeroed[i]) {
+      LevelBufs &B = c->p32.lv[0];
+      ck(c, cudaMemsetAsync(B.b, 0, (size_t)c->n * B.N * B.P * sizeof(float2), c->stream));
+      bp.zeroed[i] = 1;
+    }
+    if (on) bp.zeroed[i] = 0;
+    cmax = std::max(cmax, solve_begin<float>(c, c->cfg.inner_tol, c->cfg.inner_maxit, c->cfg.stall_ratio));
+    ck(c, cudaEventRecord(bp.join[i], c->stream));
+    ck(c, cudaStreamWaitEvent(bp.stream, bp.join[i], 0));
+  }
+  const double tol = c0->cfg.inner_tol, stall = c0->cfg.stall_ratio;
+  *bp.h_total = bp.total;
+  ck(c0, cudaMemcpyAsync(bp.d_bnact, bp.h_total, sizeof(int), cudaMemcpyHostToDevice, bp.stream));
+  for (int cyc = 0; cyc <= cmax; cyc++) {
+    if (cyc == cmax && cyc > 0) {
+      launch_finalize_multi(bp.stream, bp.d_conv, (int)bp.cyc.size(), bp.total, 0, bp.d_bnact);
+      bp.launches++;
+      ck(c0, cudaGetLastError());
+    } else {
+      plan_cycle_graph(bp, cyc == 0, tol, cmax, stall);
+    }
+    ck(c0, cudaMemcpyAsync(&bp.h_bnact[cyc], bp.d_bnact, sizeof(int), cudaMemcpyDeviceToHost, bp.stream));
+    ck(c0, cudaEventRecord(bp.ev[cyc & 1], bp.stream));
+    if (cyc >= 1) {
+      ck(c0, cudaEventSynchronize(bp.ev[(cyc - 1) & 1]));
+      if (bp.h_bnact[cyc - 1] == 0) break;
+    }
+  }
+  ck(c0, cudaEventRecord(bp.done, bp.stream));
+  for (pd_ctx *c : bp.ctx) ck(c, cudaStreamWaitEvent(c->stream, bp.done, 0));
+  rc.assign(act.size(), PD_OK);
+  for (size_t i = 0; i < act.size(); i++) rc[i] = solve_end<float>(act[i], act[i]->cfg.inner_tol);
+}
+
+// shifted_solve_refined for a set of runs (one per context), advanced together; with a
+// plan (all runs' contexts in it) the inner solves are batched launches
+void refine_runs(std::vector<RefRun> &runs, BatchPlan *bp = nullptr) {
   for (auto &r : runs) refine_eval_launch(r);
   for (auto &r : runs) refine_eval_finish(r);
   for (;;) {
@@ -1013,7 +1272,8 @@ void refine_runs(std::vector<RefRun> &runs) {
       }
     if (act.empty()) break;
     std::vector<pd_status> rc;
-    lockstep_solve<float>(act, true, rc);
+    if (bp && bp->ok) plan_solve(*bp, act, rc);
+    else lockstep_solve<float>(act, true, rc);
     for (size_t i = 0; i < ar.size(); i++) {
       RefRun &r = *ar[i];
       pd_ctx *c = r.c;
@@ -1573,7 +1833,6 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
     ck(c, cudaMallocHost(&c->h_part, 2 * part_blocks(c) * sizeof(double)));
     ck(c, cudaMallocHost(&c->h_hist, (std::max(cfg.maxit, cfg.inner_maxit) + 2) * sizeof(int)));
     {
-      ck(c, prepare_shift_residual_fx());
       const int gx = shift_residual_blocks(N, n, c->num_sms);
       ck(c, cudaMallocHost(&c->h_frozen, n * sizeof(int)));
       ck(c, cudaMallocHost(&c->h_rsc, n * sizeof(float)));
@@ -1587,6 +1846,8 @@ pd_status paradiag_setup(pd_ctx **out, int N, double h, int n, const double *shi
       for (int j = 0; j < n; j++)
         c1[j] = make_double2(shifts[2 * j] + 4.0 * cfg.kappa / (hh * hh), shifts[2 * j + 1]);
       ck(c, cudaMemcpy(c->d_c1, c1.data(), n * sizeof(double2), cudaMemcpyHostToDevice));
+      c->d_lam = dalloc<double2 *>(c, n * sizeof(double2));
+      ck(c, cudaMemcpy(c->d_lam, shifts, n * sizeof(double2), cudaMemcpyHostToDevice));
       ck(c, cudaMemset(c->d_frozen, 0, n * sizeof(int)));
     }
     // solve state
@@ -2125,6 +2386,37 @@ pd_status pd_allatonce_residual32(pd_ctx *c, float *r32, const double *u, const 
   })
 }
 
+pd_status pd_shifted_residual32(pd_ctx *c, float *r32, const void *z, const void *b, double *h_norms) {
+  if (!c || !r32 || !z || !b) return PD_ERR_ARG;
+  if (c->cfg.precision != 1) return PD_ERR_STATE;
+  PD_TRY(c, {
+    const int N = c->N, n = c->n, gx = shift_residual_blocks(N, n, c->num_sms);
+    const double h = hl(c, 0);
+    for (int j = 0; j < n; j++) c->h_rsc[j] = 1.0f;
+    ck(c, cudaMemcpyAsync(c->d_rsc, c->h_rsc, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    const View out = uview(r32, N);
+    if (c->cfg.fx_residual)
+      launch_shift_residual_fx(c->stream, gx, N, n, static_cast<const double2 *>(z),
+                               static_cast<const double2 *>(b), c->d_lam, c->kappa / (h * h), 1.0f,
+                               c->d_rsc, out, nullptr, c->d_srpart);
+    else
+      launch_shift_residual(c->stream, gx, N, n, static_cast<const double2 *>(z),
+                            static_cast<const double2 *>(b), c->d_c1, c->kappa / (h * h), 1.0f, c->d_rsc,
+                            out, nullptr, false, c->d_srpart);
+    ck_launch(c);
+    ck(c, cudaMemcpyAsync(c->h_srpart, c->d_srpart, (size_t)n * gx * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream));
+    ck(c, cudaStreamSynchronize(c->stream));
+    if (h_norms)
+      for (int j = 0; j < n; j++) {
+        double sum = 0.0;
+        for (int x = 0; x < gx; x++) sum += c->h_srpart[(size_t)j * gx + x];
+        h_norms[j] = std::sqrt(sum);
+      }
+    return PD_OK;
+  })
+}
+
 pd_status shifted_solve_refined(pd_ctx *c, void *z, const void *b, int *h_iters, double *h_relres) {
   if (!c || !z || !b) return PD_ERR_ARG;
   if (c->cfg.precision == 0) return shifted_solve_batched(c, z, b, h_iters, h_relres);
@@ -2153,6 +2445,7 @@ struct pd_batch {
   cudaEvent_t fork = nullptr;
   cudaStream_t user = nullptr;
   std::string err;
+  BatchPlan plan;  // batched launches over all instances (all instances share one stream)
 };
 
 namespace {
@@ -2160,6 +2453,7 @@ namespace {
 void free_batch(pd_batch *bt) {
   for (cudaStream_t s : bt->streams)
     if (s) cudaStreamSynchronize(s);
+  free_plan(bt->plan);
   for (pd_ctx *c : bt->ctx) free_ctx(c);
   for (cudaEvent_t e : bt->done)
     if (e) cudaEventDestroy(e);
@@ -2187,8 +2481,15 @@ pd_status pd_batch_setup(pd_batch **out, int count, const int *h_N, const int *h
   pd_batch *bt = new (std::nothrow) pd_batch();
   if (!bt) return PD_ERR_NOMEM;
   bt->user = (cudaStream_t)stream;
-  bt->streams.assign(count, nullptr);
-  bt->done.assign(count, nullptr);
+  // FP32 V(1,1) cycles with the warp-stream kernels: every cycle of all instances in
+  // batched launches on one stream; otherwise one stream per instance, cycles side by side
+  const bool merge = cfg.precision == 1 && cfg.nu1 == 1 && cfg.nu2 == 1 && cfg.cycle_gamma == 1 &&
+                     cfg.fused != 0 && cfg.fused_variant != 1;
+  if (merge) cfg.fused_variant = 2;
+  // one stream per instance, and in batched mode one more for the batched cycles
+  const int nstreams = merge ? count + 1 : count;
+  bt->streams.assign(nstreams, nullptr);
+  bt->done.assign(nstreams, nullptr);
   auto fail = [&](pd_status st) {
     free_batch(bt);
     return st;
@@ -2197,17 +2498,28 @@ pd_status pd_batch_setup(pd_batch **out, int count, const int *h_N, const int *h
     cudaGetLastError();
     return fail(PD_ERR_CUDA);
   }
-  for (int i = 0; i < count; i++) {
+  for (int i = 0; i < nstreams; i++)
     if (cudaStreamCreateWithFlags(&bt->streams[i], cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&bt->done[i], cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
       return fail(PD_ERR_CUDA);
     }
+  for (int i = 0; i < count; i++) {
     pd_ctx *c = nullptr;
     const pd_status st = paradiag_setup(&c, h_N[i], 1.0 / (h_N[i] + 1), h_n[i], h_shifts[i], nullptr,
                                         nullptr, nullptr, nullptr, nullptr, &cfg, bt->streams[i]);
     if (st != PD_OK) return fail(st);
     bt->ctx.push_back(c);
+  }
+  if (merge) {
+    bt->plan.ctx = bt->ctx;
+    bt->plan.stream = bt->streams[count];
+    try {
+      build_plan(bt->plan);
+    } catch (const CudaFail &) {
+      bt->err = bt->ctx[0]->err;
+      return fail(PD_ERR_CUDA);
+    }
   }
   *out = bt;
   return PD_OK;
@@ -2223,7 +2535,7 @@ pd_status pd_batch_solve(pd_batch *bt, void *const *d_z, const void *const *d_b,
   pd_ctx *c = c0;  // context whose error text a failure reports
   try {
     ck(c0, cudaEventRecord(bt->fork, bt->user));
-    for (size_t i = 0; i < k; i++) ck(bt->ctx[i], cudaStreamWaitEvent(bt->streams[i], bt->fork, 0));
+    for (size_t i = 0; i < bt->streams.size(); i++) ck(c0, cudaStreamWaitEvent(bt->streams[i], bt->fork, 0));
     std::vector<pd_status> rc(k, PD_OK);
     std::vector<std::vector<int>> its(k);
     std::vector<std::vector<double>> rel(k);
@@ -2254,17 +2566,19 @@ pd_status pd_batch_solve(pd_batch *bt, void *const *d_z, const void *const *d_b,
         runs[i].z = static_cast<double2 *>(d_z[i]);
         runs[i].b = static_cast<const double2 *>(d_b[i]);
       }
-      refine_runs(runs);
+      refine_runs(runs, bt->plan.ok ? &bt->plan : nullptr);
       for (size_t i = 0; i < k; i++) {
         rc[i] = runs[i].rc;
         its[i] = runs[i].it_sum;
         rel[i] = runs[i].relres;
       }
     }
+    for (size_t i = 0; i < bt->streams.size(); i++) {
+      ck(c0, cudaEventRecord(bt->done[i], bt->streams[i]));
+      ck(c0, cudaStreamWaitEvent(bt->user, bt->done[i], 0));
+    }
     for (size_t i = 0; i < k; i++) {
       c = bt->ctx[i];
-      ck(c, cudaEventRecord(bt->done[i], bt->streams[i]));
-      ck(c, cudaStreamWaitEvent(bt->user, bt->done[i], 0));
       check_wait_flags(c);
     }
     size_t o = 0;
@@ -2300,5 +2614,14 @@ pd_status pd_batch_destroy(pd_batch *bt) {
 }
 
 const char *pd_batch_last_error(const pd_batch *bt) { return bt ? bt->err.c_str() : ""; }
+
+pd_status pd_batch_info(const pd_batch *bt, int *h_batched, int *h_launches_per_cycle, long long *h_launches) {
+  if (!bt) return PD_ERR_ARG;
+  const BatchPlan &bp = bt->plan;
+  if (h_batched) *h_batched = bp.ok ? 1 : 0;
+  if (h_launches_per_cycle) *h_launches_per_cycle = bp.ok ? 2 * bp.gmax + 2 : -1;
+  if (h_launches) *h_launches = bp.launches;
+  return PD_OK;
+}
 
 }  // extern "C"

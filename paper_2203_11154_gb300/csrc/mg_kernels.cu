@@ -176,6 +176,62 @@ __global__ void k_converge(int n, int ntiles, SolveState st, double tol, int max
   }
 }
 
+// the convergence test of several instances in one launch: warp w of the launch tests the
+// global shift w; task t owns the shifts j0 .. j0 + n - 1; batch_nactive counts down with
+// every shift that stops
+__global__ void k_converge_multi(const ConvTask *__restrict__ tasks, int ntasks, int total, double tol,
+                                 int maxit, double stall, int cur_buf, int *batch_nactive) {
+  const int g = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (g >= total) return;
+  int t = 0;
+  while (t + 1 < ntasks && g >= tasks[t + 1].j0) t++;
+  const ConvTask &k = tasks[t];
+  const SolveState &st = k.st;
+  const int j = g - k.j0;
+  if (!st.active[j]) return;
+  double s = 0.0;
+  for (int q = lane; q < k.ntiles; q += 32) s += st.partials[(long long)j * st.max_tiles + q];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane != 0) return;
+  const int it = st.iters[j];
+  if (it == 0) st.bn2[j] = s;
+  const double bn2 = st.bn2[j];
+  const double rr = bn2 > 0.0 ? sqrt(s / bn2) : 0.0;
+  const double prev = st.relres[j];
+  st.relres[j] = rr;
+  if (st.hist && it < st.hist_stride) st.hist[(long long)j * st.hist_stride + it] = rr;
+  const bool bad = !isfinite(s);
+  if (bad) atomicOr(st.flags, 1);
+  const bool stalled = stall > 0.0 && it >= 2 && rr > stall * prev;
+  if (bad || rr <= tol || it >= maxit || stalled) {
+    st.active[j] = 0;
+    st.final_buf[j] = cur_buf;
+    atomicSub(st.nactive, 1);
+    atomicSub(batch_nactive, 1);
+  } else {
+    st.iters[j] = it + 1;
+  }
+}
+
+// k_finalize for several instances (one thread per global shift)
+__global__ void k_finalize_multi(const ConvTask *__restrict__ tasks, int ntasks, int total, int cur_buf,
+                                 int *batch_nactive) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
+  int t = 0;
+  while (t + 1 < ntasks && g >= tasks[t + 1].j0) t++;
+  const SolveState &st = tasks[t].st;
+  const int j = g - tasks[t].j0;
+  if (st.active[j]) {
+    st.active[j] = 0;
+    st.final_buf[j] = cur_buf;
+    const int k = st.iters[j];
+    if (st.hist && k < st.hist_stride) st.hist[(long long)j * st.hist_stride + k] = -1.0;
+    atomicSub(st.nactive, 1);
+    atomicSub(batch_nactive, 1);
+  }
+}
+
 constexpr int kRsCT = 16;  // coarse points per tile side
 
 // bt_c(I,J) = oscale * (1/4) sum_{di,dj} w rt(2I+1+di, 2J+1+dj), w = [1 2 1; 2 4 2; 1 2 1]
@@ -309,13 +365,7 @@ __device__ void cta_smooth(int N, typename Cx<T>::type *z, const typename Cx<T>:
   __syncthreads();
 }
 
-template <typename T> struct CoarseArgs {
-  CoarsePlan plan;
-  int n;
-  int start;  // level the launch starts at
-  const Coef<T> *coef;
-  const typename Cx<T>::type *cinv;
-};
+
 
 // shared-memory base and per-level element offsets of z_l (bt_l = z_l + N_l^2,
 // rt_l = z_l + 2 N_l^2)
@@ -330,7 +380,7 @@ template <typename T> struct CtaMem {
 template <typename T, int D>
 __device__ __forceinline__ void cta_cycle(int l, const CoarseArgs<T> &a, const CtaMem<T> &g) {
   using C = typename Cx<T>::type;
-  const int j = blockIdx.x;
+  const int j = blockIdx.x - a.block0;
   const int N = a.plan.Ns[l];
   if (l == a.plan.L - 1) {
     const int m = N * N;
@@ -394,15 +444,15 @@ __device__ __forceinline__ void cta_cycle(int l, const CoarseArgs<T> &a, const C
 // mode 1: the whole solve of eq. (2) at level start = 0 with the relative-residual
 // test of Sec. 3 before each cycle; writes iters/relres/final_buf of the state.
 template <typename T>
-__global__ void __launch_bounds__(kCoThreads)
-k_coarse(CoarseArgs<T> a, View b, T bscale, View zio, const int *__restrict__ active, int ncycles,
-         int load_z, int solve_mode, double tol, int maxit, SolveState st) {
+__device__ __forceinline__ void coarse_run(const CoarseArgs<T> &a, View b, T bscale, View zio,
+                                           const int *__restrict__ active, int ncycles, int load_z,
+                                           int solve_mode, double tol, int maxit, SolveState st) {
   using C = typename Cx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[kCoThreads / 32];
   __shared__ int off[kMaxLevels];
   __shared__ int stop;
-  const int j = blockIdx.x;
+  const int j = blockIdx.x - a.block0;
   if (active && !active[j]) return;
   if (threadIdx.x == 0) {
     int o = 0;
@@ -459,6 +509,24 @@ k_coarse(CoarseArgs<T> a, View b, T bscale, View zio, const int *__restrict__ ac
     const int i = q / N, c = q - i * N;
     stv<C>(zio, j, i, c, z0[q]);
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCoThreads)
+k_coarse(CoarseArgs<T> a, View b, T bscale, View zio, const int *__restrict__ active, int ncycles,
+         int load_z, int solve_mode, double tol, int maxit, SolveState st) {
+  coarse_run<T>(a, b, bscale, zio, active, ncycles, load_z, solve_mode, tol, maxit, st);
+}
+
+// the coarse levels of several instances in one launch (mode 0, from z = 0): task t owns
+// the CTAs block0 .. block0 + n - 1 of its arguments
+template <typename T>
+__global__ void __launch_bounds__(kCoThreads)
+k_coarse_multi(const CoarseTask<T> *__restrict__ tasks, int ntasks, int ncycles) {
+  int t = 0;
+  while (t + 1 < ntasks && (int)blockIdx.x >= tasks[t + 1].a.block0) t++;
+  const CoarseTask<T> &k = tasks[t];
+  coarse_run<T>(k.a, k.b, (T)1, k.z, k.active, ncycles, 0, 0, 0.0, 0, SolveState{});
 }
 
 template <typename T>
@@ -578,7 +646,9 @@ size_t coarse_smem_bytes(const CoarsePlan &plan, int start) {
 
 template <typename T>
 cudaError_t prepare_coarse(size_t smem) {
-  return cudaFuncSetAttribute(k_coarse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const cudaError_t e = cudaFuncSetAttribute(k_coarse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_coarse_multi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 template <typename T>
@@ -590,11 +660,29 @@ void launch_coarse(cudaStream_t s, const CoarsePlan &plan, int start, int n, Vie
   a.plan = plan;
   a.n = n;
   a.start = start;
+  a.block0 = 0;
   a.coef = coef;
   a.cinv = cinv;
   const size_t smem = coarse_smem_bytes<T>(plan, start);
   k_coarse<T><<<n, kCoThreads, smem, s>>>(a, b, bscale, z, active, ncycles, load_z, solve_mode,
                                           tol, maxit, st);
+}
+
+template <typename T>
+void launch_coarse_multi(cudaStream_t s, const CoarseTask<T> *tasks, int ntasks, int blocks, size_t smem,
+                         int ncycles) {
+  k_coarse_multi<T><<<blocks, kCoThreads, smem, s>>>(tasks, ntasks, ncycles);
+}
+
+void launch_converge_multi(cudaStream_t s, const ConvTask *tasks, int ntasks, int total, double tol,
+                           int maxit, double stall, int cur_buf, int *batch_nactive) {
+  k_converge_multi<<<(total + 3) / 4, 128, 0, s>>>(tasks, ntasks, total, tol, maxit, stall, cur_buf,
+                                                   batch_nactive);
+}
+
+void launch_finalize_multi(cudaStream_t s, const ConvTask *tasks, int ntasks, int total, int cur_buf,
+                           int *batch_nactive) {
+  k_finalize_multi<<<(total + 127) / 128, 128, 0, s>>>(tasks, ntasks, total, cur_buf, batch_nactive);
 }
 
 template <typename T>
@@ -623,6 +711,7 @@ void launch_gather_final(cudaStream_t s, int N, int n, View dst, View z0, View z
   template void launch_coarse<T>(cudaStream_t, const CoarsePlan &, int, int, View, T, View,        \
                                  const Coef<T> *, const typename Cx<T>::type *, const int *, int,  \
                                  int, int, double, int, SolveState);                               \
+  template void launch_coarse_multi<T>(cudaStream_t, const CoarseTask<T> *, int, int, size_t, int); \
   template void launch_copy_scale<T>(cudaStream_t, int, int, View, View, T);                       \
   template void launch_gather_final<T>(cudaStream_t, int, int, View, View, View, const int *);
 

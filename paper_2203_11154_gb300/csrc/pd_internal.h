@@ -97,11 +97,10 @@ void launch_residual_fx(cudaStream_t s, int blocks, int N, int n, int off, float
 // ---- FP64 refinement of the shifted systems (shift_refine.cu) ----
 // CTAs per shift of the shifted residuals (gx): one wave of two CTAs per SM over all shifts
 int shift_residual_blocks(int N, int n, int num_sms);
-// the same residual without FP64 instructions (residual_fx.cu); z must not be NULL and
+// the same residual without FP64 instructions (residual_ws.cu); z must not be NULL and
 // the sums of |b|^2 are not formed; sc[j]: per-shift power-of-two scale of the output
-cudaError_t prepare_shift_residual_fx();
 void launch_shift_residual_fx(cudaStream_t s, int gx, int N, int n, const double2 *z, const double2 *b,
-                              const double2 *c1, double off, float oscale, const float *sc, View out,
+                              const double2 *lam, double off, float oscale, const float *sc, View out,
                               const int *frozen, double *part);
 void launch_round_to_float(cudaStream_t s, long long count, const double *x, float *y);
 void launch_shift_residual(cudaStream_t s, int gx, int N, int n, const double2 *z, const double2 *b,
@@ -117,6 +116,20 @@ struct CoarsePlan {
   int gamma, nu1, nu2;
   int jacobi;
 };
+template <typename T> struct CoarseArgs {
+  CoarsePlan plan;
+  int n;
+  int start;   // level the launch starts at
+  int block0;  // first CTA of these shifts in the launch (shift j runs in CTA block0 + j)
+  const Coef<T> *coef;
+  const typename Cx<T>::type *cinv;
+};
+// one instance's coarse levels in a batched launch (k_coarse_multi)
+template <typename T> struct CoarseTask {
+  CoarseArgs<T> a;
+  View b, z;  // bt and z of the first coarse level
+  const int *active;
+};
 template <typename T>
 size_t coarse_smem_bytes(const CoarsePlan &plan, int start);
 template <typename T>
@@ -127,6 +140,20 @@ void launch_coarse(cudaStream_t s, const CoarsePlan &plan, int start, int n, Vie
                    View z, const Coef<T> *coef /*[L][n]*/, const typename Cx<T>::type *cinv,
                    const int *active, int ncycles, int load_z, int solve_mode, double tol,
                    int maxit, SolveState st);
+// batched launches over several instances (tasks in device memory): the coarse levels
+// (ncycles cycles from z = 0, CTAs = total shifts), the convergence test and the end of a
+// solve without a final residual (batch_nactive: the count of active shifts of all tasks)
+template <typename T>
+void launch_coarse_multi(cudaStream_t s, const CoarseTask<T> *tasks, int ntasks, int blocks, size_t smem,
+                         int ncycles);
+struct ConvTask {
+  SolveState st;
+  int n, ntiles, j0;  // shifts, norm partials per shift, first global shift index
+};
+void launch_converge_multi(cudaStream_t s, const ConvTask *tasks, int ntasks, int total, double tol,
+                           int maxit, double stall, int cur_buf, int *batch_nactive);
+void launch_finalize_multi(cudaStream_t s, const ConvTask *tasks, int ntasks, int total, int cur_buf,
+                           int *batch_nactive);
 template <typename T>
 void launch_copy_scale(cudaStream_t s, int N, int n, View dst, View src, T scale);
 template <typename T>
@@ -153,6 +180,23 @@ void launch_prolong_smooth(cudaStream_t s, int grid, const CUtensorMap &zmap,
                            View zout, const Coef<T> *coef, const int *active, int *errflag);
 
 // ---- warp-streaming fused kernels (stream_kernels.cu) ----
+// one instance-level of a batched launch: units ubegin .. ubegin + n stream_units(N, seg)
+// of the launch; x = the coarse RHS bt_c (smoothing + restriction) or the coarse
+// correction e (interpolation + smoothing); partials (smoothing + restriction of a finest
+// level only) receive the per-unit |rt|^2 sums
+template <typename T> struct StreamTask {
+  int N, n, seg, ubegin;
+  View z, b, zout, x;
+  const Coef<T> *coef;
+  const int *active;
+  double *partials;
+  int part_stride;
+};
+template <typename T>
+void launch_sr_multi(cudaStream_t s, int grid, const StreamTask<T> *tasks, int ntasks, int total, bool z_zero,
+                     bool norm);
+template <typename T>
+void launch_ps_multi(cudaStream_t s, int grid, const StreamTask<T> *tasks, int ntasks, int total);
 // work units (strips x segments of `seg` rows) per shift = norm partials per shift
 int stream_units(int N, int seg);
 template <typename T> int stream_grid(int num_sms);

@@ -235,9 +235,167 @@ void launch_ws(cudaStream_t s, int blocks, const WsGeom &g, float *r, const doub
                                                      want_f ? 1 : 0, part, fc_in, fc_out);
 }
 
+// ---------------------------------------------------------------------------------------
+// The residual of the shifted systems of eq. (2) for the refined solves, as warp tiles:
+//   r_j = b_j - lam_j z_j - (kappa/h^2)(4 z_j - sum of the 4 neighbours of z_j),
+// complex, z_j and b_j in FP64; output in FP32 times sc_j oscale (sc_j the power of two
+// keeping shift j's FP32 right-hand side near unit size, oscale the scaling of the level-0
+// right-hand side) with the sums of |sc_j r|^2.  The arithmetic is that of the residual of
+// eq. (1) above, per complex component.  A warp tile is 30 output columns (lanes
+// 1..30) by kSwR rows of one shift; each complex component has its own fixed-point scale
+// (warp max of the tile's exponents), its exact stencil difference in three FP32 limbs,
+// and z itself in the tile's units from the limbs; lam_j z_j and the sums are float-float
+// with the constants scaled to those units.  The next tile's z is loaded while the
+// current one is computed.  Grid (gx, n): CTA x of shift j takes the tiles x, x + gx, ...
+// (one per warp); frozen shifts get a zero right-hand side and no sums.
+constexpr int kSwR = 4;
+
+__global__ void __launch_bounds__(kWsThreads, 2)
+k_shift_residual_ws(int N, const double2 *__restrict__ z, const double2 *__restrict__ b,
+                    const double2 *__restrict__ lam, double off, float oscale,
+                    const float *__restrict__ sc, View out, const int *__restrict__ frozen,
+                    double *__restrict__ part) {
+  constexpr int R = kSwR;
+  __shared__ float2 red[kWsWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = blockIdx.y;
+  const long long m = (long long)N * N;
+  const int tx = (N + kWsOut - 1) / kWsOut, tiles = tx * ((N + R - 1) / R);
+  float2 *o = reinterpret_cast<float2 *>(out.p) + (long long)j * out.plane;
+  const int t_first = blockIdx.x * kWsWarps + warp, t_step = gridDim.x * kWsWarps;
+  if (frozen && frozen[j]) {
+    for (int t = t_first; t < tiles; t += t_step) {
+      const int i0 = (t / tx) * R, c = (t % tx) * kWsOut - 1 + lane;
+      if (lane >= 1 && lane <= kWsOut && c < N)
+#pragma unroll
+        for (int q = 0; q < R; q++)
+          if (i0 + q < N) o[(long long)(i0 + q) * out.pitch + c] = make_float2(0.f, 0.f);
+    }
+    if (threadIdx.x == 0) part[(long long)j * gridDim.x + blockIdx.x] = 0.0;
+    return;
+  }
+  const double2 *zj = z + (long long)j * m, *bj = b + (long long)j * m;
+  const double2 lj = lam[j];
+  const DF lr = split(lj.x), li = split(lj.y), offd = split(off);
+  const float scj = sc[j];
+  DF ar = {0.f, 0.f};
+  ulonglong2 raw[R + 2];
+  auto load_z = [&](int t) {
+    const int i0 = (t / tx) * R, c = (t % tx) * kWsOut - 1 + lane;
+    const bool cin = (unsigned)c < (unsigned)N;
+#pragma unroll
+    for (int e = 0; e < R + 2; e++) {
+      const int i = i0 - 1 + e;
+      const bool ok = cin && (unsigned)i < (unsigned)N;
+      raw[e] = ok ? *reinterpret_cast<const ulonglong2 *>(zj + (long long)i * N + c) : make_ulonglong2(0ull, 0ull);
+    }
+  };
+  if (t_first < tiles) load_z(t_first);
+  for (int t = t_first; t < tiles; t += t_step) {
+    const int i0 = (t / tx) * R, c = (t % tx) * kWsOut - 1 + lane;
+    const bool outc = lane >= 1 && lane <= kWsOut && c < N;
+    const int nr = min(R, N - i0);
+    double2 bq[R];
+#pragma unroll
+    for (int q = 0; q < R; q++)
+      bq[q] = (outc && q < nr) ? bj[(long long)(i0 + q) * N + c] : make_double2(0.0, 0.0);
+    // largest exponent of each component over the warp tile, then the limbs
+    unsigned er = 0, ei = 0;
+#pragma unroll
+    for (int e = 0; e < R + 2; e++) {
+      er = max(er, (unsigned)(raw[e].x >> 32) & 0x7FFFFFFFu);
+      ei = max(ei, (unsigned)(raw[e].y >> 32) & 0x7FFFFFFFu);
+    }
+    er = __reduce_max_sync(0xffffffffu, er) >> 20;
+    ei = __reduce_max_sync(0xffffffffu, ei) >> 20;
+    float rx2[R + 2], rx1[R + 2], rx0[R + 2], ix2[R + 2], ix1[R + 2], ix0[R + 2];
+#pragma unroll
+    for (int e = 0; e < R + 2; e++) {
+      const float4 a = to_limbs(raw[e].x, er), q = to_limbs(raw[e].y, ei);
+      rx2[e] = a.x;
+      rx1[e] = a.y;
+      rx0[e] = a.z;
+      ix2[e] = q.x;
+      ix1[e] = q.y;
+      ix0[e] = q.z;
+    }
+    if (t + t_step < tiles) load_z(t + t_step);  // the next tile, while this one is computed
+    const bool bad = er > 1081 + 126 || ei > 1081 + 126;
+    const int Sr = 1081 - (int)er, Si = 1081 - (int)ei;
+    const int sr = Sr > 252 ? 252 : Sr, si = Si > 252 ? 252 : Si;
+    // constants in the units of the component they multiply
+    const DF qr = df_scale_down(offd, sr), qi = df_scale_down(offd, si);
+    const DF lrr = df_scale_down(lr, sr), lri = df_scale_down(lr, si);
+    const DF lir = df_scale_down(li, sr), lii = df_scale_down(li, si);
+    float rowr = 0.f;
+#pragma unroll
+    for (int q = 0; q < R; q++) {
+      // exact stencil differences of both components, as float-float pairs
+      const float h2r = __shfl_up_sync(0xffffffffu, rx2[q + 1], 1) + __shfl_down_sync(0xffffffffu, rx2[q + 1], 1);
+      const float h1r = __shfl_up_sync(0xffffffffu, rx1[q + 1], 1) + __shfl_down_sync(0xffffffffu, rx1[q + 1], 1);
+      const float h0r = __shfl_up_sync(0xffffffffu, rx0[q + 1], 1) + __shfl_down_sync(0xffffffffu, rx0[q + 1], 1);
+      const float h2i = __shfl_up_sync(0xffffffffu, ix2[q + 1], 1) + __shfl_down_sync(0xffffffffu, ix2[q + 1], 1);
+      const float h1i = __shfl_up_sync(0xffffffffu, ix1[q + 1], 1) + __shfl_down_sync(0xffffffffu, ix1[q + 1], 1);
+      const float h0i = __shfl_up_sync(0xffffffffu, ix0[q + 1], 1) + __shfl_down_sync(0xffffffffu, ix0[q + 1], 1);
+      DF tr = two_sum(__fmaf_rn(4.f, rx2[q + 1], -__fadd_rn(__fadd_rn(rx2[q], rx2[q + 2]), h2r)),
+                      __fmaf_rn(4.f, rx1[q + 1], -__fadd_rn(__fadd_rn(rx1[q], rx1[q + 2]), h1r)));
+      tr.lo = __fadd_rn(tr.lo, __fmaf_rn(4.f, rx0[q + 1], -__fadd_rn(__fadd_rn(rx0[q], rx0[q + 2]), h0r)));
+      DF ti = two_sum(__fmaf_rn(4.f, ix2[q + 1], -__fadd_rn(__fadd_rn(ix2[q], ix2[q + 2]), h2i)),
+                      __fmaf_rn(4.f, ix1[q + 1], -__fadd_rn(__fadd_rn(ix1[q], ix1[q + 2]), h1i)));
+      ti.lo = __fadd_rn(ti.lo, __fmaf_rn(4.f, ix0[q + 1], -__fadd_rn(__fadd_rn(ix0[q], ix0[q + 2]), h0i)));
+      // z in the tile's units
+      DF zr = fast_two_sum(rx2[q + 1], rx1[q + 1]);
+      zr.lo = __fadd_rn(zr.lo, rx0[q + 1]);
+      DF zi = fast_two_sum(ix2[q + 1], ix1[q + 1]);
+      zi.lo = __fadd_rn(zi.lo, ix0[q + 1]);
+      const DF br = split(bq[q].x), bi = split(bq[q].y);
+      // real: br - lr zr + li zi - off T1r; imaginary: bi - lr zi - li zr - off T1i
+      const DF p1 = df_mul_un(lrr, zr), p2 = df_mul_un(lii, zi), p3 = df_mul_un(qr, tr);
+      const DF p4 = df_mul_un(lri, zi), p5 = df_mul_un(lir, zr), p6 = df_mul_un(qi, ti);
+      float lo = __fadd_rn(__fsub_rn(br.lo, p1.lo), __fsub_rn(p2.lo, p3.lo));
+      DF s1 = two_sum(br.hi, -p1.hi);
+      float el = s1.lo;
+      s1 = two_sum(s1.hi, p2.hi);
+      el = __fadd_rn(el, s1.lo);
+      s1 = two_sum(s1.hi, -p3.hi);
+      el = __fadd_rn(el, s1.lo);
+      float rxv = __fmul_rn(__fadd_rn(s1.hi, __fadd_rn(lo, el)), scj);
+      lo = __fsub_rn(bi.lo, __fadd_rn(__fadd_rn(p4.lo, p5.lo), p6.lo));
+      DF s2 = two_sum(bi.hi, -p4.hi);
+      el = s2.lo;
+      s2 = two_sum(s2.hi, -p5.hi);
+      el = __fadd_rn(el, s2.lo);
+      s2 = two_sum(s2.hi, -p6.hi);
+      el = __fadd_rn(el, s2.lo);
+      float ryv = __fmul_rn(__fadd_rn(s2.hi, __fadd_rn(lo, el)), scj);
+      if (bad) rxv = ryv = __int_as_float(0x7FC00000);
+      if (outc && q < nr) {
+        o[(long long)(i0 + q) * out.pitch + c] = make_float2(rxv * oscale, ryv * oscale);
+        rowr = __fmaf_rn(rxv, rxv, __fmaf_rn(ryv, ryv, rowr));
+      }
+    }
+    ar = df_add(ar, DF{rowr, 0.f});
+  }
+  for (int o2 = 16; o2 > 0; o2 >>= 1) ar = df_add(ar, df_shfl_down(ar, o2));
+  if (lane == 0) red[warp] = make_float2(ar.hi, ar.lo);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    DF s0 = {0.f, 0.f};
+    for (int w = 0; w < kWsWarps; w++) s0 = df_add(s0, DF{red[w].x, red[w].y});
+    part[(long long)j * gridDim.x + blockIdx.x] = (double)s0.hi + (double)s0.lo;
+  }
+}
+
 }  // namespace
 
 int residual_fx_blocks(int num_sms) { return 2 * num_sms; }
+
+void launch_shift_residual_fx(cudaStream_t s, int gx, int N, int n, const double2 *z, const double2 *b,
+                              const double2 *lam, double off, float oscale, const float *sc, View out,
+                              const int *frozen, double *part) {
+  dim3 grid(gx, n);
+  k_shift_residual_ws<<<grid, kWsThreads, 0, s>>>(N, z, b, lam, off, oscale, sc, out, frozen, part);
+}
 
 void launch_residual_fx(cudaStream_t s, int blocks, int N, int n, int off, float2 ihf, float *r,
                         const double *u, const double *f, const double *u0, const float4 *kbd,

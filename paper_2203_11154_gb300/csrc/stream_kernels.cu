@@ -444,6 +444,59 @@ k_ps_stream(int N, int n, int seg, View z, View e, View b, View zout,
   }
 }
 
+// The same two kernels over the units of several instance-levels in one launch (batches
+// of uneven instances): unit u belongs to the task whose range [ubegin, next ubegin)
+// holds it.
+template <typename T, bool ZZERO, bool NORM>
+__global__ void __launch_bounds__(kWarpsPerCta * kLanes, sizeof(T) == 4 ? 2 : 1)
+k_sr_multi(const StreamTask<T> *__restrict__ tasks, int ntasks, int total) {
+  using C = typename Cx<T>::type;
+  extern __shared__ __align__(16) unsigned char ring_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  C *ring = reinterpret_cast<C *>(ring_raw) + (size_t)wib * kDepth * 2 * kLanes * 2;
+  const int gw = blockIdx.x * kWarpsPerCta + wib, nw = gridDim.x * kWarpsPerCta;
+  int t = 0;
+  for (int u = gw; u < total; u += nw) {
+    while (t + 1 < ntasks && u >= tasks[t + 1].ubegin) t++;
+    const StreamTask<T> &k = tasks[t];
+    const int N = k.N, seg = k.seg, ul = u - k.ubegin;
+    const int nsx = (N + kStripOut - 1) / kStripOut, nsy = (N + seg - 1) / seg;
+    const int sx = ul % nsx, sy = (ul / nsx) % nsy, j = ul / (nsx * nsy);
+    if (k.active && !k.active[j]) continue;
+    const int x0 = sx * kStripOut, y0 = sy * seg, y1 = min(y0 + seg, N), Nc = (N - 1) / 2;
+    if (interior_unit(N, x0, y0, y1))
+      sr_unit<T, ZZERO, NORM, true>(N, seg, ul, nsx, nsy, Nc, lane, ring, k.z, k.b, k.zout, k.x, k.coef,
+                                    k.partials, k.part_stride);
+    else
+      sr_unit<T, ZZERO, NORM, false>(N, seg, ul, nsx, nsy, Nc, lane, ring, k.z, k.b, k.zout, k.x, k.coef,
+                                     k.partials, k.part_stride);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kWarpsPerCta * kLanes, sizeof(T) == 4 ? 2 : 1)
+k_ps_multi(const StreamTask<T> *__restrict__ tasks, int ntasks, int total) {
+  using C = typename Cx<T>::type;
+  extern __shared__ __align__(16) unsigned char ring_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  C *ring = reinterpret_cast<C *>(ring_raw) + (size_t)wib * kDepth * 3 * kLanes * 2;
+  const int gw = blockIdx.x * kWarpsPerCta + wib, nw = gridDim.x * kWarpsPerCta;
+  int t = 0;
+  for (int u = gw; u < total; u += nw) {
+    while (t + 1 < ntasks && u >= tasks[t + 1].ubegin) t++;
+    const StreamTask<T> &k = tasks[t];
+    const int N = k.N, seg = k.seg, ul = u - k.ubegin;
+    const int nsx = (N + kStripOut - 1) / kStripOut, nsy = (N + seg - 1) / seg;
+    const int sx = ul % nsx, sy = (ul / nsx) % nsy, j = ul / (nsx * nsy);
+    if (k.active && !k.active[j]) continue;
+    const int x0 = sx * kStripOut, y0 = sy * seg, y1 = min(y0 + seg, N), Nc = (N - 1) / 2;
+    if (interior_unit(N, x0, y0, y1))
+      ps_unit<T, true>(N, seg, ul, nsx, nsy, Nc, lane, ring, k.z, k.x, k.b, k.zout, k.coef);
+    else
+      ps_unit<T, false>(N, seg, ul, nsx, nsy, Nc, lane, ring, k.z, k.x, k.b, k.zout, k.coef);
+  }
+}
+
 template <int ROWS> constexpr int ring_bytes(int elem) { return kWarpsPerCta * kDepth * ROWS * kLanes * 2 * elem; }
 
 }  // namespace
@@ -478,6 +531,26 @@ void launch_ps_stream(cudaStream_t s, int grid, int N, int n, int seg, View z, V
   k_ps_stream<T><<<grid, kWarpsPerCta * kLanes, smem, s>>>(N, n, seg, z, e, b, zout, coef, active);
 }
 
+template <typename T>
+void launch_sr_multi(cudaStream_t s, int grid, const StreamTask<T> *tasks, int ntasks, int total, bool z_zero,
+                     bool norm) {
+  const int smem = ring_bytes<2>((int)sizeof(typename Cx<T>::type));
+  const int th = kWarpsPerCta * kLanes;
+  if (z_zero) {
+    if (norm) k_sr_multi<T, true, true><<<grid, th, smem, s>>>(tasks, ntasks, total);
+    else k_sr_multi<T, true, false><<<grid, th, smem, s>>>(tasks, ntasks, total);
+  } else {
+    if (norm) k_sr_multi<T, false, true><<<grid, th, smem, s>>>(tasks, ntasks, total);
+    else k_sr_multi<T, false, false><<<grid, th, smem, s>>>(tasks, ntasks, total);
+  }
+}
+
+template <typename T>
+void launch_ps_multi(cudaStream_t s, int grid, const StreamTask<T> *tasks, int ntasks, int total) {
+  const int smem = ring_bytes<3>((int)sizeof(typename Cx<T>::type));
+  k_ps_multi<T><<<grid, kWarpsPerCta * kLanes, smem, s>>>(tasks, ntasks, total);
+}
+
 template <typename T> cudaError_t prepare_stream() {
   const int a = ring_bytes<2>((int)sizeof(typename Cx<T>::type));
   const int b = ring_bytes<3>((int)sizeof(typename Cx<T>::type));
@@ -490,6 +563,11 @@ template <typename T> cudaError_t prepare_stream() {
   PD_ATTR((k_sr_stream<T, true, false>), a)
   PD_ATTR((k_sr_stream<T, true, true>), a)
   PD_ATTR((k_ps_stream<T>), b)
+  PD_ATTR((k_sr_multi<T, false, false>), a)
+  PD_ATTR((k_sr_multi<T, false, true>), a)
+  PD_ATTR((k_sr_multi<T, true, false>), a)
+  PD_ATTR((k_sr_multi<T, true, true>), a)
+  PD_ATTR((k_ps_multi<T>), b)
 #undef PD_ATTR
   return cudaSuccess;
 }
@@ -510,6 +588,8 @@ template <typename T> int stream_grid(int num_sms) {
                                     const Coef<T> *, const int *, bool, double *, int);          \
   template void launch_ps_stream<T>(cudaStream_t, int, int, int, int, View, View, View, View,   \
                                     const Coef<T> *, const int *);                               \
+  template void launch_sr_multi<T>(cudaStream_t, int, const StreamTask<T> *, int, int, bool, bool); \
+  template void launch_ps_multi<T>(cudaStream_t, int, const StreamTask<T> *, int, int);          \
   template int stream_grid<T>(int);                                                              \
   template cudaError_t prepare_stream<T>();
 

@@ -137,3 +137,32 @@ def test_batch_uneven8_full_size_sampled():
             rel, noise = oracle_relres(N, lam[j], b[j], zj)
             assert rel <= 1e-10 and abs(rr[j] - rel) <= 1e-6 * rel + noise
     bt.destroy()
+
+
+@pytest.mark.parametrize("graphs", [1, 0])
+def test_batched_launches_per_level(graphs):
+    """FP32 V(1,1) batches run every cycle of all instances as one launch per multigrid level
+    (2 G + 2 launches, G the most global levels of an instance): uneven grids 63 (solved
+    inside the coarse kernel), 127, 255, 511 with 4 to 16 shifts, every shift refined to the
+    oracle's FP64 relative residual <= 1e-10; graphs on and off give the same answers."""
+    probs = inputs.uneven_problem((63, 127, 255, 511), (4, 8, 8, 16), seed=9)
+    bt = api.Batch([p[0] for p in probs], [p[1] for p in probs], api.config(precision=1, cuda_graphs=graphs))
+    batched, per_cycle, _ = bt.info()
+    assert batched and per_cycle == 2 * 3 + 2  # 511: global levels 511, 255, 127
+    zs = [torch.empty(lam.size, N, N, dtype=torch.complex128, device="cuda") for N, lam, _ in probs]
+    bs = [dev(b) for _, _, b in probs]
+    out = bt.solve(zs, bs)
+    torch.cuda.synchronize()
+    assert bt.info()[2] > 0
+    for (N, lam, b), z, (it, rr) in zip(probs, zs, out):
+        assert np.all(rr <= 1e-10)
+        for j in range(lam.size):
+            rel, noise = oracle_relres(N, lam[j], b[j], z.cpu().numpy()[j])
+            assert rel <= 1e-10 and abs(rr[j] - rel) <= 1e-6 * rel + noise
+    # the same batch once more: identical answers (the graphs or launches replay)
+    zs2 = [torch.empty_like(z) for z in zs]
+    out2 = bt.solve(zs2, bs)
+    torch.cuda.synchronize()
+    for z, z2, (it, rr), (it2, rr2) in zip(zs, zs2, out, out2):
+        assert torch.equal(z, z2) and np.array_equal(it, it2)
+    bt.destroy()

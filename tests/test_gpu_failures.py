@@ -154,3 +154,51 @@ def test_refined_shifted_solve_does_not_depend_on_the_data_scale(scale):
         r = core.residual(N, lam[j], b[j], zh[j])
         assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(b[j])
     c.destroy()
+
+
+@pytest.mark.parametrize("fx", [0, 1])
+@pytest.mark.parametrize("N,n", [(127, 8), (255, 4)])
+def test_shifted_residual32_against_long_double_oracle(fx, N, n):
+    """The FP32 residual of eq. (2) the refined shifted solves hand to the multigrid, element
+    by element against the oracle's long-double residual, on a random z and on a converged
+    one.  Without FP64 arithmetic (fx = 1) the bound is the FP32 rounding of r plus 2^-43
+    of the terms and the fixed-point truncation ih2 2^-54 max|z_j| per component; the FP64
+    formula (fx = 0) is bound by its rounding, 4 eps of the terms, and its FP32 output is
+    truncated (not rounded) to 24 bits: 2^-23 |r|."""
+    lam = inputs.random_shifts(np.random.default_rng(N), n)
+    b = inputs.complex_rhs(np.random.default_rng(N + 1), n, N)
+    c = api.Context(N, n, lam, cfg=api.config(precision=1, fx_residual=fx))
+    ih2 = float(N + 1) ** 2
+    z_conv = torch.empty(n, N, N, dtype=torch.complex128, device="cuda")
+    c.shifted_solve_refined(z_conv, torch.from_numpy(b).cuda())
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(N + 2)
+    for z in (inputs.complex_rhs(rng, n, N), z_conv.cpu().numpy()):
+        r32 = torch.empty(n, N, N, dtype=torch.complex64, device="cuda")
+        norms = c.pd_shifted_residual32(r32, torch.from_numpy(z).cuda(), torch.from_numpy(b).cuda())
+        r = r32.cpu().numpy().astype(np.complex128)
+        for j in range(n):
+            r_ld = core.residual_ld(N, lam[j], b[j], z[j])
+            for part in (np.real, np.imag):
+                zc = part(z[j])
+                nb = np.zeros_like(zc)
+                nb[1:, :] += zc[:-1, :]
+                nb[:-1, :] += zc[1:, :]
+                nb[:, 1:] += zc[:, :-1]
+                nb[:, :-1] += zc[:, 1:]
+                anb = np.zeros_like(zc)
+                az = np.abs(zc)
+                anb[1:, :] += az[:-1, :]
+                anb[:-1, :] += az[1:, :]
+                anb[:, 1:] += az[:, :-1]
+                anb[:, :-1] += az[:, 1:]
+                lz = np.abs(lam[j]) * np.abs(z[j])
+                if fx:
+                    T = np.abs(part(b[j])) + lz + ih2 * np.abs(4 * zc - nb)
+                    tol = 2.0 ** -24 * np.abs(part(r_ld)) + 2.0 ** -43 * T + ih2 * 2.0 ** -54 * np.max(az)
+                else:
+                    T = np.abs(part(b[j])) + lz + ih2 * (4 * az + anb)
+                    tol = 2.0 ** -23 * np.abs(part(r_ld)) + 4 * np.finfo(float).eps * T
+                assert np.all(np.abs(part(r[j]) - part(r_ld)) <= tol)
+            assert norms[j] == pytest.approx(np.linalg.norm(r[j]), rel=1e-5)
+    c.destroy()

@@ -471,3 +471,38 @@ def test_extended_precision_residual():
     rn_ld, r_ld = core.allatonce_residual_ld(N, n, tau, alpha, u, fhat)
     rn64, _, r64 = core.allatonce_residual(N, n, tau, alpha, u, fhat, want_r=True)
     assert np.max(np.abs(r_ld - r64)) <= 1e-13 * np.max(np.abs(r64))
+
+
+def test_long_double_shifted_residual_exact_on_dyadic_data():
+    """core.residual_ld (eq. (2) in long double): exact on dyadic data, where every term is
+    an integer multiple of 1/64 and the result is computed by integer arithmetic here; equal
+    to the FP64 residual up to its rounding on random data."""
+    N = 7
+    rng = np.random.default_rng(21)
+    lam = complex(3.0, -1.5)
+    zr = rng.integers(-64, 64, (N, N)) / 8.0
+    zi = rng.integers(-64, 64, (N, N)) / 8.0
+    br = rng.integers(-64, 64, (N, N)) / 8.0
+    bi = rng.integers(-64, 64, (N, N)) / 8.0
+    r = core.residual_ld(N, lam, br + 1j * bi, zr + 1j * zi)
+    Zr, Zi = (zr * 8).astype(np.int64), (zi * 8).astype(np.int64)
+    Br, Bi = (br * 8).astype(np.int64), (bi * 8).astype(np.int64)
+
+    def nb(Z):
+        s = np.zeros_like(Z)
+        s[1:, :] += Z[:-1, :]
+        s[:-1, :] += Z[1:, :]
+        s[:, 1:] += Z[:, :-1]
+        s[:, :-1] += Z[:, 1:]
+        return s
+    ih2 = (N + 1) ** 2
+    # lam = 3 - 1.5 i: (lam z) * 16 = 48 z - 24 i z  (times 8 for the dyadic scale)
+    ex_r = 2 * Br - (6 * Zr + 3 * Zi) - 2 * ih2 * (4 * Zr - nb(Zr))
+    ex_i = 2 * Bi - (6 * Zi - 3 * Zr) - 2 * ih2 * (4 * Zi - nb(Zi))
+    assert np.array_equal(r.real * 16, ex_r.astype(float))
+    assert np.array_equal(r.imag * 16, ex_i.astype(float))
+    z = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
+    b = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
+    r_ld = core.residual_ld(N, lam, b, z)
+    r64 = core.residual(N, lam, b, z)
+    assert np.max(np.abs(r_ld - r64)) <= 1e-13 * np.max(np.abs(r64))
