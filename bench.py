@@ -37,6 +37,18 @@ def measured_peaks():
         return HBM_FALLBACK_GBS, "fallback"
 
 
+def peak_tf32():
+    """Dense TF32 tensor peak: the measured sustained bf16 GEMM rate (the transforms run inside
+    a long step) times the nominal TF32 / bf16 ratio 1.1 / 2.25; the nominal 1100 TF/s
+    without the measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return round(float(d["bf16_tflops_sustained"]) * 1.1 / 2.25, 1)
+    except Exception:
+        return 1100.0
+
+
 def traffic_table():
     """Per-launch DRAM bytes from the committed ncu summaries (kernel class -> bytes)."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
@@ -331,6 +343,10 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=None,
                     help="timed steps of the FP64 form beside the value (default: the smaller "
                          "of --steps and 3 at N = 2047, else --steps)")
+    ap.add_argument("--transforms", default="fft", choices=["fft", "tc"],
+                    help="route of the time transforms: the Gamma-weighted FFTs of the "
+                         "alpha-circulant V, or V and V^{-1} as dense TF32x3 tcgen05 products "
+                         "(the route of a general B)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -402,7 +418,8 @@ def main():
         return ms, out, prof, ctx.launch_count() - l0, ck
 
     # FP32 multigrid inside FP64 refinement (the value)
-    ctx = api.alpha_circulant_context(N, n, tau, alpha, precision=1, imag_check=1)
+    ctx = api.alpha_circulant_context(N, n, tau, alpha, precision=1, imag_check=1,
+                                      fft_transforms=int(args.transforms == "fft"))
     clocks = Clocks(local)
     ms_ir, out_ir, _, launches, ck = timed(ctx, args.steps, args.warmup, clocks=clocks)
     value = job_throughput(n, args.steps, world, ms_ir)
@@ -442,7 +459,8 @@ def main():
     ctx.destroy()
 
     # plain FP64 (beside the value)
-    ctx64 = api.alpha_circulant_context(N, n, tau, alpha, precision=0, imag_check=1)
+    ctx64 = api.alpha_circulant_context(N, n, tau, alpha, precision=0, imag_check=1,
+                                        fft_transforms=int(args.transforms == "fft"))
     k64 = args.fp64_steps or (min(args.steps, 3) if N >= 2047 else args.steps)
     ms64, out64, _, _, _ = timed(ctx64, k64, max(3, min(args.warmup, 3)))
     ctx64.destroy()
@@ -475,11 +493,30 @@ def main():
     solve_hbm = {"alg_bytes_per_step": step_bytes, "achieved": round(solve_gbs, 1), "peak": peak,
                  "unit": "GB/s", "frac": round(solve_gbs / peak, 4)}
 
+    # the time transforms against both of their bounds: HBM (bytes per launch as profiled)
+    # and the TF32 tensor pipe (TF32x3: three real products per complex-by-real product)
+    transforms = {"route": args.transforms}
+    for name in ("forward", "inverse"):
+        if name not in prof or prof[name][1] == 0:
+            continue
+        kms, nl, by = prof[name]
+        t = {"launches": nl, "avg_launch_us": round(1e3 * kms / nl, 1),
+             "gbs": round(by / (kms * 1e-3) / 1e9, 1), "frac_hbm": round(by / (kms * 1e-3) / 1e9 / peak, 4)}
+        if args.transforms == "tc":
+            # Re and Im rows of W (n x n) times the n x N^2 real (or Re-of-complex) operand,
+            # each a sum of three TF32 products
+            flops = 3 * 2 * (2 * n) * n * N * N * nl
+            tf32_peak = peak_tf32()
+            t["tflops_issued"] = round(flops / (kms * 1e-3) / 1e12, 1)
+            t["tf32_peak"] = tf32_peak
+            t["frac_tensor"] = round(flops / (kms * 1e-3) / 1e12 / tf32_peak, 4)
+        transforms[name] = t
+
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_ir / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64", "data": "synthetic",
-            "config": bench_config(args.workload),
+            "config": dict(bench_config(args.workload), time_transforms=args.transforms),
             "launch": "multigrid cycles replayed as CUDA graphs on a non-default stream",
             "relres_allatonce": out_ir["relres_allatonce"],
             "refine_steps": out_ir["refine_steps"], "cycles_max": out_ir["cycles_max"],
@@ -490,7 +527,8 @@ def main():
                      "cycles_max": out64["cycles_max"]},
             "speedup_vs_fp64": value / value64,
             "clocks": ck, "e2e": e2e, "gpu_launches": launches,
-            "roofline": roofline, "solve_hbm": solve_hbm, "kernels": kernels,
+            "roofline": roofline, "solve_hbm": solve_hbm, "transforms": transforms,
+            "kernels": kernels,
             "kernel_timing": "CUDA events around each launch on the context's stream, in a "
                              "second pass of the same %d steps (%.2f ms/step with the events)"
                              % (args.steps, ms_prof / args.steps)}

@@ -68,8 +68,11 @@ typedef struct {
                           post-smoothing step (same arithmetic, fewer memory passes):
                           1 for the FP32 multigrid only (FP64 is bound by arithmetic, which
                           the recomputed halos increase), 2 always, 0 never */
-    int tensor_transforms; /* precision 1, n <= 64, N >= 127: the time transforms as TF32x3
-                          tensor-core GEMMs (tcgen05); 0: FP32 CUDA-core products */
+    int tensor_transforms; /* precision 1, n <= 128, N >= 127: the time transforms as TF32x3
+                          tensor-core GEMMs (tcgen05; for n > 64 the rows of the forward and
+                          the K dimension of the inverse split over two CTAs, the inverse's
+                          halves summed through distributed shared memory of a two-CTA
+                          cluster); 0: FP32 CUDA-core products */
     int fused_variant; /* implementation of the fused kernels: 0 = chosen at set-up by timing
                           both on the context's own levels, 1 = TMA-staged shared-memory
                           tiles, 2 = warp-streaming strips (cp.async ring, shuffles) */
@@ -257,7 +260,8 @@ pd_status pd_batch_info(const pd_batch *batch, int *h_batched, int *h_launches_p
 enum {
     PD_STAT_RELRES_ALLATONCE = 0, /* ||fhat - (B kron I + I kron A) u|| / ||fhat||, or -1 without B */
     PD_STAT_REFINE_STEPS = 1,     /* refinement steps (precision 1), 0 for FP64 */
-    PD_STAT_IMAG_MAX = 2,         /* max |Im((V kron I) z)| of the last step (imag_check) */
+    PD_STAT_IMAG_MAX = 2,         /* max |Im((V kron I) z)| of the last step (imag_check); -1
+                                     where it is not formed (the tensor-core inverse, n > 64) */
     PD_STAT_CYCLES_TOTAL = 3,     /* multigrid cycles summed over shifts and steps */
     PD_STAT_CYCLES_MAX = 4,       /* max over shifts of cycles, summed over steps */
     PD_STAT_RELRES_SHIFT_MAX = 5, /* max over shifts of the last shifted relative residual */

@@ -42,6 +42,7 @@ template <typename T> struct Prec {
   C *Wi = nullptr;          // V, n x n
   // TF32 split operands of the tensor-core transforms (forward scaled by h^2 and unscaled)
   float *tc_fwd_hi = nullptr, *tc_fwd_lo = nullptr, *tc_inv_hi = nullptr, *tc_inv_lo = nullptr;
+  int tc_grid_fwd = 0, tc_grid_inv = 0;  // CTAs of the tensor-core transform launches
   float *tc_fwd1_hi = nullptr, *tc_fwd1_lo = nullptr;
   bool tc = false;
   // FFT route for an alpha-circulant V: weights alpha^{k/n} h^2/(kappa n), alpha^{k/n}/n
@@ -492,7 +493,7 @@ void alloc_prec(pd_ctx *c) {
   }
   if (!P.fft && sizeof(T) == sizeof(float) && c->have_V && c->cfg.tensor_transforms &&
       tc_transforms_supported(c->N, n)) {
-    const size_t fa = 128 * 64, ia = 128 * 128;
+    const size_t fa = tc_operand_floats(n, false), ia = tc_operand_floats(n, true);
     std::vector<float> fh(fa), fl(fa), ih(ia), il(ia), f1h(fa), f1l(fa), ih2(ia), il2(ia);
     const double h0 = hl(c, 0);
     tc_build_operands(n, c->Vinv.data(), c->V.data(), h0 * h0 / c->kappa, fh.data(), fl.data(), ih.data(),
@@ -511,6 +512,8 @@ void alloc_prec(pd_ctx *c) {
     ck(c, cudaMemcpy(P.tc_inv_hi, ih.data(), ia * 4, cudaMemcpyHostToDevice));
     ck(c, cudaMemcpy(P.tc_inv_lo, il.data(), ia * 4, cudaMemcpyHostToDevice));
     ck(c, prepare_tc_transforms());
+    ck(c, tc_launch_grid(c->num_sms, n, false, &P.tc_grid_fwd));
+    ck(c, tc_launch_grid(c->num_sms, n, true, &P.tc_grid_inv));
     P.tc = true;
   }
   // the attributes are per kernel, shared by all contexts: set the largest any context
@@ -1392,7 +1395,7 @@ void transform_forward(pd_ctx *c, View g, const void *f, const double *u0, bool 
     launch_fft_forward<T>(c->stream, c->num_sms, c->N, c->n, g, f, f32, u0, c->d_u0coef,
                           scaled ? P.fft_wf : P.fft_wf1, P.fft_twf);
   } else if (P.tc) {
-    launch_tc_forward(c->stream, c->num_sms, c->N, c->n, g, f, f32, u0, c->d_u0coef,
+    launch_tc_forward(c->stream, P.tc_grid_fwd, c->N, c->n, g, f, f32, u0, c->d_u0coef,
                       scaled ? P.tc_fwd_hi : P.tc_fwd1_hi, scaled ? P.tc_fwd_lo : P.tc_fwd1_lo,
                       in_scale, c->st.flags);
   } else {
@@ -1411,7 +1414,7 @@ void transform_inverse(pd_ctx *c, double *u, View z0, View z1, const int *final_
     launch_fft_inverse<T>(c->stream, c->num_sms, c->N, c->n, u, z0, z1, final_buf, P.fft_wi,
                           P.fft_twi, (T)dscale, acc, imag, c->d_imag);
   else if (P.tc)
-    launch_tc_inverse(c->stream, c->num_sms, c->N, c->n, u, z0, z1, final_buf, P.tc_inv_hi,
+    launch_tc_inverse(c->stream, P.tc_grid_inv, c->N, c->n, u, z0, z1, final_buf, P.tc_inv_hi,
                       P.tc_inv_lo, (float)dscale, acc, imag, c->d_imag, c->st.flags);
   else
     launch_transform_inverse<T>(c->stream, c->N, c->n, u, z0, z1, final_buf, P.Wi, (T)dscale, acc,
@@ -1564,7 +1567,9 @@ pd_status paradiag_impl(pd_ctx *c, double *u, const double *f, const double *u0,
     if (rc == PD_OK && !(relres <= c->cfg.tol)) rc = PD_ERR_NOCONV;
   }
   check_wait_flags(c);
-  if (imag) {
+  if (imag && P.tc && n > 64) {
+    st_local[PD_STAT_IMAG_MAX] = -1.0;  // the tensor-core inverse for n > 64 forms Re only
+  } else if (imag) {
     unsigned long long bits = 0;
     ck(c, cudaMemcpy(&bits, c->d_imag, sizeof(bits), cudaMemcpyDeviceToHost));
     double v;

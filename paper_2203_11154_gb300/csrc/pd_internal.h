@@ -247,9 +247,12 @@ void launch_initial_value_gradient(cudaStream_t s, int N, int n, const double *w
 void launch_laplacian_dot(cudaStream_t s, int N, int n, const double *w, const double *u,
                           double *part);
 
-// ---- tensor-core transforms (tc_transforms.cu), FP32 working type, n <= 64 ----
+// ---- tensor-core transforms (tc_transforms.cu), FP32 working type, n <= 128 ----
 bool tc_transforms_supported(int N, int n);
 cudaError_t prepare_tc_transforms();
+cudaError_t tc_launch_grid(int num_sms, int n, bool inverse, int *grid);
+// floats of one split of the forward (inverse = false) or inverse operand for n shifts
+size_t tc_operand_floats(int n, bool inverse);
 void tc_build_operands(int n, const double *Vinv, const double *V, double scale, float *fwd_hi,
                        float *fwd_lo, float *inv_hi, float *inv_lo);
 void launch_tc_forward(cudaStream_t s, int grid, int N, int n, View g, const void *f, bool f32,

@@ -324,3 +324,43 @@ def test_paradiag_host_batch_pipelined(precision):
         assert np.array_equal(uh.numpy(), host(ud))
         assert np.array_equal(out["iters"], ref["iters"])
         assert out["relres_allatonce"] == ref["relres_allatonce"]
+
+
+@pytest.mark.parametrize("n", [100, 128])
+def test_transforms_tc_wide(n):
+    """The tensor-core transforms for 64 < n <= 128 (forward rows and inverse K split over two
+    CTAs, the inverse's halves summed in a two-CTA cluster) against the oracle's dense
+    products, on a general V (the alpha-circulant B diagonalised by the library, so the
+    FFT route does not apply): relative error per shift vector a few 1e-7 (TF32x3)."""
+    N, alpha = 127, 1e-2
+    B = api.pd_alpha_circulant(n, 1.0 / n, alpha)[0]
+    c = api.dense_B_context(B, N, None, precision=1)
+    lam, V, Vinv = api.pd_diagonalize(B)  # the library's eigenvectors: those c uses
+    rng = np.random.default_rng(n)
+    f = rng.uniform(-1, 1, (n, N, N))
+    g = torch.empty(n, N, N, dtype=torch.complex64, device="cuda")
+    c.pd_transform_forward(g, dev(f))
+    ref = core.time_transform(Vinv, f.reshape(n, -1)).reshape(n, N, N)
+    assert rel_per_vector(host(g), ref) < 2e-6
+    z = (rng.uniform(-1, 1, (n, N, N)) + 1j * rng.uniform(-1, 1, (n, N, N))).astype(np.complex64)
+    u = torch.full((n, N, N), 0.25, dtype=torch.float64, device="cuda")
+    c.pd_transform_inverse(u, dev(z, torch.complex64), accumulate=True)
+    ref = core.time_transform(V, z.astype(np.complex128).reshape(n, -1)).real.reshape(n, N, N) + 0.25
+    assert np.linalg.norm(host(u) - ref) / np.linalg.norm(ref) < 2e-6
+
+
+def test_paradiag_dense_B_tensor_cores_n128():
+    """The precision form through the tensor-core transforms at n = 128 (B given alone: the
+    alpha-circulant matrix, diagonalised by the library): the oracle's FP64 residual of
+    eq. (1) reaches 1e-10."""
+    N, n, alpha = 255, 128, 1e-3
+    tau = 1.0 / n
+    B, _, _, _, c0 = api.pd_alpha_circulant(n, tau, alpha)
+    c = api.dense_B_context(B, N, c0, precision=1)
+    f, u0 = inputs.paradiag_problem(N, n, seed=3)
+    u = torch.empty(n, N, N, dtype=torch.float64, device="cuda")
+    out = c.paradiag_solve(u, dev(f), dev(u0))
+    assert out["relres_allatonce"] <= 1e-10 and out["imag_max"] == -1.0
+    fhat = core.assemble_rhs(N, n, tau, f, u0)
+    rn, fn = core.allatonce_residual(N, n, tau, alpha, host(u), fhat)
+    assert rn / fn <= 1e-10
