@@ -255,6 +255,9 @@ const char *pd_batch_last_error(const pd_batch *batch);
  */
 pd_status pd_batch_info(const pd_batch *batch, int *h_batched, int *h_launches_per_cycle,
                         long long *h_launches);
+/* Every kernel launch of the batch so far: the batched multigrid launches and those of the
+ * instances' own evaluations (residuals, updates, norms); 0 for a NULL batch. */
+long long pd_batch_launch_count(const pd_batch *batch);
 
 /* Indices of the values paradiag_solve writes to h_stats (PD_STATS_LEN doubles). */
 enum {

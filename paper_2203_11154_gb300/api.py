@@ -39,7 +39,7 @@ EXPORTS = ["pd_config_default", "pd_alpha_circulant", "pd_shifts_alpha_circulant
            "pd_coarse_solve", "pd_transform_forward", "pd_transform_inverse",
            "pd_allatonce_residual", "pd_allatonce_residual_static", "pd_laplacian_dot",
            "pd_initial_value_gradient",
-           "pd_profile_enable", "pd_profile_read", "pd_get_history", "pd_synchronize", "pd_launch_count", "paradiag_destroy",
+           "pd_profile_enable", "pd_profile_read", "pd_get_history", "pd_synchronize", "pd_launch_count", "pd_batch_launch_count", "paradiag_destroy",
            "pd_status_str", "pd_last_error", "shifted_solve_refined", "pd_allatonce_residual32", "pd_shifted_residual32",
            "paradiag_solve_host_batch", "pd_batch_setup",
            "pd_batch_solve", "pd_batch_destroy", "pd_batch_last_error", "pd_batch_info"]
@@ -108,6 +108,7 @@ def lib(path=None):
             "pd_get_history": (_I, [_P, _I, _P, _P, _I, _P, _P]),
             "pd_synchronize": (_I, [_P]),
             "pd_launch_count": (C.c_longlong, [_P]),
+            "pd_batch_launch_count": (C.c_longlong, [_P]),
             "paradiag_destroy": (_I, [_P]),
             "pd_status_str": (C.c_char_p, [_I]),
             "pd_last_error": (C.c_char_p, [_P]),
@@ -585,6 +586,10 @@ class Batch:
         tot = C.c_longlong()
         _check(lib().pd_batch_info(self.h, C.byref(b), C.byref(lpc), C.byref(tot)), "pd_batch_info")
         return bool(b.value), lpc.value, tot.value
+
+    def launch_count(self):
+        """Every kernel launch of the batch so far (batched multigrid and per instance)."""
+        return int(lib().pd_batch_launch_count(self.h))
 
     def destroy(self):
         if getattr(self, "h", None):

@@ -2629,4 +2629,11 @@ pd_status pd_batch_info(const pd_batch *bt, int *h_batched, int *h_launches_per_
   return PD_OK;
 }
 
+long long pd_batch_launch_count(const pd_batch *bt) {
+  if (!bt) return 0;
+  long long n = bt->plan.launches;
+  for (const pd_ctx *c : bt->ctx) n += c->launches;
+  return n;
+}
+
 }  // extern "C"

@@ -33,6 +33,8 @@
 #include "ff.cuh"
 #include "pd_internal.h"
 
+#include <algorithm>
+
 namespace pd {
 namespace {
 
@@ -389,6 +391,16 @@ k_shift_residual_ws(int N, const double2 *__restrict__ z, const double2 *__restr
 }  // namespace
 
 int residual_fx_blocks(int num_sms) { return 2 * num_sms; }
+
+// CTAs per shift of the shifted residuals: about eight waves of two CTAs per SM over all
+// shifts (the CTAs of a wave do equal work, so a last partial wave costs at most an
+// eighth), but no more CTAs than give each warp one warp tile, nor more than grid rows
+int shift_residual_blocks(int N, int n, int num_sms) {
+  const int want = (16 * num_sms + n - 1) / n;
+  const long long tiles = (long long)((N + kWsOut - 1) / kWsOut) * ((N + kSwR - 1) / kSwR);
+  const int cap = (int)std::min<long long>(N, (tiles + kWsWarps - 1) / kWsWarps);
+  return std::max(1, std::min(want, cap));
+}
 
 void launch_shift_residual_fx(cudaStream_t s, int gx, int N, int n, const double2 *z, const double2 *b,
                               const double2 *lam, double off, float oscale, const float *sc, View out,

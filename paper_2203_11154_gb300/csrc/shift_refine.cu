@@ -140,12 +140,6 @@ void launch_round_to_float(cudaStream_t s, long long count, const double *x, flo
   k_round_to_float<<<4 * 152, 256, 0, s>>>(count, x, y);
 }
 
-// CTAs per shift: one wave of two CTAs per SM over all shifts
-int shift_residual_blocks(int N, int n, int num_sms) {
-  const int want = (2 * num_sms) / n;
-  return want < 1 ? 1 : (want > N ? N : want);
-}
-
 void launch_shift_residual(cudaStream_t s, int gx, int N, int n, const double2 *z, const double2 *b,
                            const double2 *c1, double off, float oscale, const float *sc, View out,
                            const int *frozen, bool want_b, double *part) {
