@@ -18,6 +18,7 @@
 #include <algorithm>
 
 #include "cplx.cuh"
+#include "fpbits.cuh"
 #include "pd_internal.h"
 #include "tma.cuh"
 
@@ -125,30 +126,9 @@ template <typename T, int N1, int N2, bool INV> __host__ __device__ constexpr in
   return (a < b ? a : b) < 1 ? 1 : (a < b ? a : b);
 }
 
-// exact FP32 -> FP64 by bit operations (the conversion instruction issues on the FP64
-// pipe); zero and subnormal inputs give 0, Inf/NaN give NaN
-__device__ __forceinline__ double f32_to_f64(float v) {
-  const unsigned b = __float_as_uint(v);
-  const unsigned e = (b >> 23) & 0xFFu;
-  if (e == 0) return 0.0;
-  if (e == 0xFFu) return __longlong_as_double(0x7FF8000000000000ll);
-  const unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b >> 3) & 0xFFFFFu);
-  return __hiloint2double((int)hi, (int)(b << 29));
-}
 __device__ __forceinline__ double to_f64(float v) { return f32_to_f64(v); }
 __device__ __forceinline__ double to_f64(double v) { return v; }
 
-// FP64 -> FP32 by bit operations, truncating to 24 significant bits (relative error below
-// 2^-23; the input of the FP32 solve, whose error the refinement removes): |x| < 2^-126
-// gives 0, |x| >= 2^128, Inf and NaN give NaN
-__device__ __forceinline__ float f64_to_f32(double x) {
-  const unsigned hw = (unsigned)__double2hiint(x), lw = (unsigned)__double2loint(x);
-  const int e = (int)((hw >> 20) & 0x7FFu);
-  if (e < 1023 - 126) return 0.f;
-  if (e > 1023 + 127) return __int_as_float(0x7FC00000);
-  return __uint_as_float((hw & 0x80000000u) | ((unsigned)(e - 896) << 23) | ((hw & 0xFFFFFu) << 3) |
-                         (lw >> 29));
-}
 // an input value as the transform's type: FP64 into FP32 by bits, otherwise as is
 template <typename T, typename InT> __device__ __forceinline__ T as_t(InT v) {
   if constexpr (sizeof(T) == 4 && sizeof(InT) == 8) return f64_to_f32(v);
@@ -399,22 +379,6 @@ k_fft_inverse(int N, double *__restrict__ u, View z0, View z1, const int *__rest
 // stages (up to 2 x 64 KB at n = 128), not the registers.
 constexpr int kPipeP = 32, kPipeTP = 8, kPipeThreads = kPipeP * kPipeTP, kPipeS = 3;
 
-__device__ __forceinline__ void cpa(uint32_t dst, const void *src, int bytes, bool ok) {
-  if (bytes == 16)
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0)
-                 : "memory");
-  else if (bytes == 8)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(ok ? 8 : 0)
-                 : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(ok ? 4 : 0)
-                 : "memory");
-}
-__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int K> __device__ __forceinline__ void cpa_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory");
-}
-
 // g_j(point) = wk-weighted DFT (+ exponent) of fhat at the 32 points of a tile, FP32 work.
 // Stage layout [n][32] of the input type; pass 1 writes complex columns into `col`.
 template <int N1, typename InT>
@@ -449,7 +413,10 @@ k_fft_forward_pipe(int N, View g, const InT *__restrict__ f, const double *__res
       for (int e = 0; e < n * P / kPipeThreads; e++) {
         const int q = threadIdx.x + kPipeThreads * e, k = q / P, pt = q % P;
         const bool ok = c0 + pt < N;
-        const InT *src = f + (ok ? (long long)k * m + (long long)i * N + c0 + pt : 0);
+        // beyond the grid: zero fill, from the row's last element (a valid address near the
+        // data: zero-fill copies still send their source address, and one shared address
+        // for all of them would become a hot spot)
+        const InT *src = f + (long long)k * m + (long long)i * N + min(c0 + pt, N - 1);
         cpa(base + (uint32_t)(q * sizeof(InT)), src, (int)sizeof(InT), ok);
       }
     }
@@ -529,8 +496,9 @@ k_fft_inverse_pipe(int N, double *__restrict__ u, View z0, View z1, const int *_
       for (int e = 0; e < kCh; e++) {
         const int q = threadIdx.x + kPipeThreads * e, j = q / (P / W), pt = W * (q % (P / W));
         const bool ok = c0 + pt < N;  // a pair's second point may be the padding column
-        const float2 *src = ((from1 >> e) & 1u ? b1 : b0) +
-                            (ok ? (long long)j * z0.plane + (long long)i * z0.pitch + c0 + pt : 0);
+        // beyond the grid: zero fill from the row's last W-aligned point (no shared hot spot)
+        const float2 *src = ((from1 >> e) & 1u ? b1 : b0) + (long long)j * z0.plane + (long long)i * z0.pitch +
+                            min(c0 + pt, (N - 1) & ~(W - 1));
         cpa(base + (uint32_t)((j * P + pt) * sizeof(float2)), src, 8 * W, ok);
       }
     }

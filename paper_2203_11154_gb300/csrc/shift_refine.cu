@@ -8,33 +8,13 @@
 // 4 kappa/h^2 and off = kappa/h^2, in FP64 complex; the FP32 copy handed to the multigrid
 // is scaled by h^2/kappa, the scaling of the level-0 right-hand side.
 #include "cplx.cuh"
+#include "fpbits.cuh"
 #include "pd_internal.h"
 
 namespace pd {
 namespace {
 
 constexpr int kSrThreads = 256;
-
-// FP32 <-> FP64 by bit operations (the conversion instructions issue on GB300's slow FP64
-// pipe).  to_f64 is exact (zero and subnormal inputs give 0, Inf/NaN give NaN); to_f32
-// truncates to 24 significant bits (relative error below 2^-23, ample for a right-hand
-// side of the FP32 multigrid), flushing |x| < 2^-126 to 0 and overflowing to NaN.
-__device__ __forceinline__ double to_f64(float v) {
-  const unsigned b = __float_as_uint(v);
-  const unsigned e = (b >> 23) & 0xFFu;
-  if (e == 0) return 0.0;
-  if (e == 0xFFu) return __longlong_as_double(0x7FF8000000000000ll);
-  return __hiloint2double((int)((b & 0x80000000u) | ((e + 896u) << 20) | ((b >> 3) & 0xFFFFFu)),
-                          (int)(b << 29));
-}
-__device__ __forceinline__ float to_f32(double x) {
-  const unsigned hw = (unsigned)__double2hiint(x), lw = (unsigned)__double2loint(x);
-  const int e = (int)((hw >> 20) & 0x7FFu);
-  if (e < 1023 - 126) return 0.f;
-  if (e > 1023 + 127) return __int_as_float(0x7FC00000);
-  return __uint_as_float((hw & 0x80000000u) | ((unsigned)(e - 896) << 23) | ((hw & 0xFFFFFu) << 3) |
-                         (lw >> 29));
-}
 
 // grid (gx, n): CTA x of shift j strides over the grid rows of shift j.  The FP32 output
 // is sc_j r (sc_j a power of two that keeps the shift's FP32 right-hand side near unit
@@ -50,7 +30,7 @@ k_shift_residual(int N, const double2 *__restrict__ z, const double2 *__restrict
   const long long m = (long long)N * N;
   const bool fz = frozen && frozen[j];
   const double2 cj = c1[j];
-  const double scj = (double)sc[j];
+  const int sce = (int)((__float_as_uint(sc[j]) >> 23) & 0xFFu) - 127;  // sc_j = 2^sce
   float2 *o = reinterpret_cast<float2 *>(out.p) + (long long)j * out.plane;
   double ar = 0.0, ab = 0.0;
   for (int i = blockIdx.x; i < N; i += gridDim.x) {
@@ -76,7 +56,7 @@ k_shift_residual(int N, const double2 *__restrict__ z, const double2 *__restrict
         r.x = fma(off, nb.x, fma(-cj.x, zv.x, fma(cj.y, zv.y, bv.x)));
         r.y = fma(off, nb.y, fma(-cj.x, zv.y, fma(-cj.y, zv.x, bv.y)));
       }
-      const float2 rf = make_float2(to_f32(r.x * scj), to_f32(r.y * scj));
+      const float2 rf = make_float2(f64_to_f32(r.x, sce), f64_to_f32(r.y, sce));
       rowr = fmaf(rf.x, rf.x, fmaf(rf.y, rf.y, rowr));
       if (want_b) rowb = fma(bv.x, bv.x, fma(bv.y, bv.y, rowb));
       o[(long long)i * out.pitch + c] = make_float2(rf.x * oscale, rf.y * oscale);
@@ -121,10 +101,10 @@ __global__ void k_shift_update(int N, double2 *__restrict__ z, View z0, View z1,
   d.y *= isc;
   double2 &dst = z[(long long)j * N * N + (long long)i * N + c];
   if (accumulate) {
-    dst.x += to_f64(d.x);
-    dst.y += to_f64(d.y);
+    dst.x += f32_to_f64(d.x);
+    dst.y += f32_to_f64(d.y);
   } else {
-    dst = make_double2(to_f64(d.x), to_f64(d.y));
+    dst = make_double2(f32_to_f64(d.x), f32_to_f64(d.y));
   }
 }
 

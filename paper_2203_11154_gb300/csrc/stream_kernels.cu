@@ -72,7 +72,10 @@ template <typename C, bool IN = false>
 __device__ __forceinline__ void load_pair(uint32_t dst, const C *base, long long pitch, int N, int row,
                                           int a) {
   const bool ok = IN || ((unsigned)row < (unsigned)N && a >= 0 && a < N);
-  const C *src = base + (ok ? (long long)row * pitch + a : 0);
+  // zero fill outside the grid from the nearest pair inside it (zero-fill copies still send
+  // their source address; one shared address per plane would become a hot spot)
+  const C *src = base + (IN ? (long long)row * pitch + a
+                            : (long long)min(max(row, 0), N - 1) * pitch + min(max(a, 0), (N - 1) & ~1));
   if (sizeof(C) == 8) {
     cp_async16(dst, src, ok ? 16 : 0);  // a+1 may be the padding column: masked on use
   } else {
@@ -311,7 +314,8 @@ __device__ __forceinline__ void ps_unit(int N, int seg, int u, int nsx, int nsy,
   // coarse row m (complex at column J) into the slot's third row; zero outside
   auto load_coarse = [&](uint32_t dst, int m) {
     const bool ok = IN || ((unsigned)m < (unsigned)Nc && (unsigned)J < (unsigned)Nc);
-    const C *src = eb + (ok ? (long long)m * e.pitch + J : 0);
+    const C *src = eb + (IN ? (long long)m * e.pitch + J
+                            : (long long)min(max(m, 0), Nc - 1) * e.pitch + min(max(J, 0), Nc - 1));
     if (sizeof(C) == 8) cp_async8(dst, src, ok ? 8 : 0);
     else cp_async16(dst, src, ok ? 16 : 0);
   };

@@ -1,23 +1,29 @@
-// Time-direction transforms of eq. (1) on the 5th-generation tensor cores (tcgen05),
-// for n <= 128 shifts (the forms for 64 < n <= 128 are described where they are defined).  Both are real GEMMs D[128 x Nt] = A[128 x K] B[K x Nt] over tiles
-// of Nt grid points of one grid row, in TF32 with the 3-product split
+// Time-direction transforms of eq. (1) on the 5th-generation tensor cores (tcgen05), for
+// n <= 128 shifts.  Both are real GEMMs D[128 x Nt] = A[128 x K] B[K x Nt] over tiles of Nt
+// grid points of one grid row, in TF32 with the 3-product split
 //   A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi,  x_hi = x rounded to TF32, x_lo = x - x_hi,
 // accumulated in FP32 in tensor memory: about 2^-21 relative per product, the
 // FP32-compensated product the refinement needs because V can be ill-conditioned.
 //
 //   forward:  K = 64 (k < n),  rows 2j / 2j+1 of A = Re / Im of h^2 V^{-1}[j][k],
 //             B[k][p] = fhat_k at point p (FP64 or FP32 input, rounded to FP32 then split);
-//             g_j(p) = (D[2j][p], D[2j+1][p]).
+//             g_j(p) = (D[2j][p], D[2j+1][p]).  For n > 64, K = 128 and two CTAs take
+//             the shifts 0..63 and 64..127 of a tile.
 //   inverse:  K = 128 (2j + re/im), row k of A = (Re V[k][j], -Im V[k][j]) and row 64 + k =
 //             (Im V[k][j], Re V[k][j]), B[2j+q][p] = component q of z_j(p);
-//             u_k(p) (+)= D[k][p], max |D[64+k][p]| is the imaginary-part check.
+//             u_k(p) (+)= D[k][p], max |D[64+k][p]| is the imaginary-part check.  For n > 64
+//             the rows are the 128 time steps (real part only) and K = 2n is split over the
+//             two CTAs of a cluster.
 //
 // Operands live in shared memory in the K-major layout with 128-byte swizzling (8-row x
 // 128-byte atoms, 16-byte chunk c of row r stored at chunk c ^ (r mod 8)); A is loaded
-// once per CTA, B is built per tile by all threads.  One thread issues the MMAs and
-// commits them to an mbarrier; the epilogue reads the accumulators with tcgen05.ld
-// through a padded shared-memory stage so that the global stores are coalesced.
+// once per CTA, B is built per tile by all threads from inputs that cp.async brought into
+// a shared-memory stage one tile ahead.  One thread issues the MMAs and commits them to an
+// mbarrier; two accumulators in tensor memory let the epilogue of one tile (tcgen05.ld
+// through a padded shared-memory stage, so that the global stores are coalesced) run while
+// the MMAs of the next one do.
 #include "cplx.cuh"
+#include "fpbits.cuh"
 #include "pd_internal.h"
 #include "tma.cuh"
 
@@ -26,7 +32,7 @@
 namespace pd {
 namespace {
 
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 512;
 constexpr int kM = 128;
 
 __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
@@ -44,13 +50,15 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accumulate) {
+// D (+)= A B, kind::tf32: A in tensor memory (lane = row of A, one TF32 element per column),
+// B in shared memory (descriptor)
+__device__ __forceinline__ void mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                            uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
@@ -84,6 +92,26 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
   for (int q = 0; q < 32; q++) v[q] = __uint_as_float(r[q]);
 }
 
+// stores 32 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float *v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+      "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+      "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])),
+      "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])),
+      "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])),
+      "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])),
+      "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])),
+      "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+      : "memory");
+}
+
 // TF32 split: hi = x rounded to 10 explicit mantissa bits, lo = x - hi (exact)
 __device__ __forceinline__ void split_tf32(float x, float &hi, float &lo) {
   const uint32_t b = (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
@@ -98,13 +126,27 @@ __device__ __forceinline__ uint32_t sw_off(int row, int q, int rows) {
   return (uint32_t)(atom * rows * 128 + row * 128 + ((ch ^ (row & 7)) << 4));
 }
 
-// copies a row-major [128][K] float matrix from global memory into the swizzled layout
+// A (row-major [128][K] floats in global memory) into tensor memory at column col0: lane r
+// holds row r, one element per column; warps 0-3 (lanes 32w..32w+31) store it
 template <int K>
-__device__ void load_a(const float *__restrict__ src, unsigned char *dst) {
-  for (int it = threadIdx.x; it < kM * (K / 4); it += kTcThreads) {
-    const int row = it / (K / 4), q = it % (K / 4);
-    const float4 v = *reinterpret_cast<const float4 *>(src + (size_t)row * K + 4 * q);
-    *reinterpret_cast<float4 *>(dst + sw_off(row, q, kM)) = v;
+__device__ void load_a_tmem(const float *__restrict__ src, uint32_t tmem, int col0) {
+  const int warp = (int)threadIdx.x >> 5, row = (int)threadIdx.x;
+  if (warp < 4) {
+#pragma unroll 1
+    for (int c = 0; c < K / 32; c++) {
+      float v[32];
+      const float4 *p = reinterpret_cast<const float4 *>(src + (size_t)row * K + 32 * c);
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        const float4 x = p[q];
+        v[4 * q] = x.x;
+        v[4 * q + 1] = x.y;
+        v[4 * q + 2] = x.z;
+        v[4 * q + 3] = x.w;
+      }
+      tmem_st32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(col0 + 32 * c), v);
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
   }
 }
 
@@ -119,31 +161,49 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
-// issues the 3 x (K/8) MMAs of one tile and commits them to `bar` (one thread)
+// issues the 3 x (K/8) MMAs of one tile and commits them to `bar` (one thread); A hi/lo in
+// tensor memory at columns a_hi, a_lo (8 columns per K step), B hi/lo in shared memory
 template <int K, int NT>
-__device__ __forceinline__ void issue_tile(uint32_t tmem, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
+__device__ __forceinline__ void issue_tile(uint32_t d_tmem, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
                                            uint32_t b_lo, uint64_t *bar) {
   constexpr uint32_t idesc = idesc_tf32(kM, NT);
   uint32_t acc = 0;
 #pragma unroll
   for (int ks = 0; ks < K / 8; ks++) {
-    const uint32_t ao = (uint32_t)((ks >> 2) * kM * 128 + (ks & 3) * 32);
     const uint32_t bo = (uint32_t)((ks >> 2) * NT * 128 + (ks & 3) * 32);
-    mma_tf32(tmem, desc_sw128(a_hi + ao), desc_sw128(b_hi + bo), idesc, acc);
+    mma_tf32_ta(d_tmem, a_hi + 8u * ks, desc_sw128(b_hi + bo), idesc, acc);
     acc = 1;
-    mma_tf32(tmem, desc_sw128(a_hi + ao), desc_sw128(b_lo + bo), idesc, 1);
-    mma_tf32(tmem, desc_sw128(a_lo + ao), desc_sw128(b_hi + bo), idesc, 1);
+    mma_tf32_ta(d_tmem, a_hi + 8u * ks, desc_sw128(b_lo + bo), idesc, 1);
+    mma_tf32_ta(d_tmem, a_lo + 8u * ks, desc_sw128(b_hi + bo), idesc, 1);
   }
   mma_commit(bar);
 }
 
-constexpr int kFwdK = 64, kFwdNt = 128, kInvK = 128, kInvNt = 64;
-constexpr int kFwdA = kM * kFwdK * 4, kFwdB = kFwdNt * kFwdK * 4;  // bytes per split
-constexpr int kInvA = kM * kInvK * 4, kInvB = kInvNt * kInvK * 4;
-constexpr int kFwdS = 64 * 66 * 4;   // epilogue stage: 64 j rows x 32 complex (stride 66 floats)
-constexpr int kInvS = kM * (kInvNt + 1) * 4;  // epilogue stage: 128 rows x 64 columns (stride 65)
-constexpr int kFwdSmem = 2 * kFwdA + 2 * kFwdB + kFwdS + 1024;
-constexpr int kInvSmem = 2 * kInvA + 2 * kInvB + kInvS + 1024;
+constexpr int kFwdK = 64, kFwdNt = 128;   // forward, n <= 64
+constexpr int kFwd2K = 128, kFwd2Nt = 64;  // forward, 64 < n <= 128 (two CTAs per tile)
+constexpr int kInvK = 128, kInvNt = 64;    // inverse, n <= 64
+constexpr int kInv2K = 128, kInv2Nt = 64;  // inverse, 64 < n <= 128 (two-CTA cluster)
+constexpr int kFwdS = 64 * 66 * 4;         // forward epilogue stage: 64 j rows x 32 complex
+// tensor memory: A hi at column 0, A lo at column K, the two accumulators from column 2K
+constexpr int kTmemCols = 512;
+static_assert(2 * 128 + 2 * 64 <= kTmemCols && 2 * 64 + 2 * 128 <= kTmemCols, "tensor memory");
+
+// shared memory of the forward: B hi/lo, epilogue stage, input stage [K][NT] of the input
+// type and the initial values of the tile's points, alignment slack
+template <int K, int NT, typename InT> constexpr int fwd_smem() {
+  return 2 * NT * K * 4 + kFwdS + NT * K * (int)sizeof(InT) + NT * 8 + 1024;
+}
+// the inverse: B hi/lo, stage [rows][NT + 1] (rows: 128, or 2 x 64 in the cluster form),
+// z stage [64 shifts][NT] complex, u stage [64 rows][NT], slack
+constexpr int kInvSmem = 2 * kInvNt * kInvK * 4 + kM * (kInvNt + 1) * 4 + 64 * kInvNt * 8 + 64 * kInvNt * 8 + 1024;
+constexpr int kInv2Smem =
+    2 * kInv2Nt * kInv2K * 4 + 2 * 64 * (kInv2Nt + 1) * 4 + 64 * kInv2Nt * 8 + 64 * kInv2Nt * 8 + 1024;
+// the opt-in limit per block less the kernels' static shared memory
+constexpr int kSmemLimit = 227 * 1024 - 1024;
+static_assert(fwd_smem<kFwdK, kFwdNt, double>() <= kSmemLimit, "forward (n <= 64) exceeds shared memory");
+static_assert(fwd_smem<kFwd2K, kFwd2Nt, double>() <= kSmemLimit, "forward (n > 64) exceeds shared memory");
+static_assert(kInvSmem <= kSmemLimit, "inverse (n <= 64) exceeds shared memory");
+static_assert(kInv2Smem <= kSmemLimit, "inverse (n > 64) exceeds shared memory");
 
 __device__ __forceinline__ unsigned char *align1024(unsigned char *p) {
   return p + ((1024 - (smem_u32(p) & 1023)) & 1023);
@@ -155,104 +215,93 @@ __device__ __forceinline__ unsigned char *align1024(unsigned char *p) {
 // The rows of A are (Re, Im) of 64 shifts: with HALVES = 2 (n <= 128, K = 128) CTA x takes
 // the shifts 64 (x mod 2) .. + 63, its A the matching half of the operand, and the tiles
 // x / 2, x / 2 + gridDim.x / 2, ... (the two CTAs of a tile read its input once from DRAM).
+// Pipeline: the input of tile t + 1 is copied into a shared-memory stage by cp.async
+// (no registers hold it) and the accumulator of tile t - 1 is drained from the second
+// accumulator in tensor memory while the MMAs of tile t run.  FP64 inputs become FP32 by
+// bit operations (no FP64-pipe conversion per element).
 template <typename InT, int K, int NT, int HALVES>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_tc_forward(int N, int n, View g, const InT *__restrict__ f, const double *__restrict__ u0,
              const double *__restrict__ u0coef, const float *__restrict__ Ahi,
              const float *__restrict__ Alo, double in_scale, int *__restrict__ errflag) {
-  constexpr int kA = kM * K * 4, kB = NT * K * 4;
+  constexpr int kB = NT * K * 4;
+  constexpr int kItems = NT * (K / 4) / kTcThreads;  // (point, 4 consecutive k) items per thread
+  constexpr int kCopies = NT * K / kTcThreads;       // input elements copied per thread
+  static_assert(kItems * 4 <= 32, "the item masks hold 32 bits");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *sm = align1024(smem_raw);
-  unsigned char *sAhi = sm, *sAlo = sm + kA, *sBhi = sm + 2 * kA, *sBlo = sBhi + kB;
+  unsigned char *sBhi = sm, *sBlo = sm + kB;
   float *S = reinterpret_cast<float *>(sBlo + kB);
+  InT *stage = reinterpret_cast<InT *>(reinterpret_cast<unsigned char *>(S) + kFwdS);  // [K][NT]
+  double *su0 = reinterpret_cast<double *>(stage + NT * K);                           // [NT]
   __shared__ uint64_t bar;
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int half = (int)blockIdx.x % HALVES, jbase = 64 * half;
   const int t0 = (int)blockIdx.x / HALVES, tstep = (int)gridDim.x / HALVES;
-  if (warp == 0) tmem_alloc(&tmem_slot, NT);
+  if (warp == 0) tmem_alloc(&tmem_slot, kTmemCols);
   if (tid == 0) {
     mbar_init(&bar, 1);
     fence_barrier_init();
   }
-  load_a<K>(Ahi + (size_t)half * kM * K, sAhi);
-  load_a<K>(Alo + (size_t)half * kM * K, sAlo);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
+  load_a_tmem<K>(Ahi + (size_t)half * kM * K, tmem, 0);
+  load_a_tmem<K>(Alo + (size_t)half * kM * K, tmem, K);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t acc0 = tmem + 2 * K;  // first accumulator column
   const long long m = (long long)N * N;
   const int tpr = (int)((g.pitch + NT - 1) / NT);  // tiles per grid row
   const int total = N * tpr;
   const int nj = min(64, n - jbase);  // shifts of this CTA
-  uint32_t phase = 0;
-  bool ok = true;
-  // each thread owns kFwdItems (point, 4 consecutive k) items of a tile; the FP64 inputs of
-  // the next tile are loaded into registers while the current tile is multiplied
-  constexpr int kFwdItems = NT * (K / 4) / kTcThreads;
-  // held in FP32 (the operand precision); FP64 arithmetic only for the initial-value
-  // term of the rows where it is nonzero (GB300's FP64 rate is 1/58 of FP32)
-  float pre[kFwdItems][4];
+  // which of a thread's item time steps carry the initial-value term (u0coef[k] != 0,
+  // tested on the bits): the same in every tile
+  unsigned cmask = 0;
+  if (u0)
+    for (int q = 0; q < kItems; q++)
+      for (int e = 0; e < 4; e++) {
+        const int k = 4 * ((tid + q * kTcThreads) / NT) + e;
+        if (k < n && (__double_as_longlong(u0coef[k]) << 1) != 0) cmask |= 1u << (4 * q + e);
+      }
+  const int s_in = pow2_exponent(in_scale);
+  const float fs_in = __uint_as_float((unsigned)(s_in + 127) << 23);  // FP32 inputs: |s_in| < 127
+  // copies of tile t into the stage (element (k, p) of the tile) and of its initial values
+  // where the term is used.  Elements outside the grid or with k >= n are not copied: the
+  // rows k >= n keep the zeros written below (A is zero there too), the columns beyond the
+  // grid produce outputs that are not stored (each output column depends on its own B
+  // column only)
   auto fetch = [&](int t) {
     const int i = t / tpr, c0 = (t % tpr) * NT;
+    const uint32_t sbase = smem_u32(stage);
 #pragma unroll
-    for (int q = 0; q < kFwdItems; q++) {
-      const int it = tid + q * kTcThreads;
-      const int p = it % NT, kq = it / NT;
-      const int c = c0 + p;
-      const long long x = (long long)i * N + c;
-#pragma unroll
-      for (int e = 0; e < 4; e++) {
-        const int k = 4 * kq + e;
-        float v = 0.f;
-        if (k < n && c < N) {
-          const double ck = u0 ? u0coef[k] : 0.0;
-          if (ck != 0.0) v = (float)(((double)f[k * m + x] + ck * u0[x]) * in_scale);
-          else if (in_scale != 1.0) v = (float)((double)f[k * m + x] * in_scale);
-          else v = (float)f[k * m + x];
-        }
-        pre[q][e] = v;
-      }
+    for (int e = 0; e < kCopies; e++) {
+      const int q = tid + e * kTcThreads, k = q / NT, p = q % NT;
+      if (k < n && c0 + p < N)
+        cpa(sbase + (uint32_t)(q * (int)sizeof(InT)), f + (long long)k * m + (long long)i * N + c0 + p,
+            (int)sizeof(InT), true);
     }
+    if (u0 && tid < NT && c0 + tid < N) cpa(smem_u32(su0 + tid), u0 + (long long)i * N + c0 + tid, 8, true);
+    cpa_commit();
   };
-  int t = t0;
-  if (t < total) fetch(t);
-  for (; t < total; t += tstep) {
+  for (int q = tid; q < NT * K; q += kTcThreads) stage[q] = (InT)0;
+  for (int q = tid; q < NT; q += kTcThreads) su0[q] = 0.0;
+  __syncthreads();
+  auto to_op = [&](InT v) -> float {
+    if constexpr (sizeof(InT) == 8) return f64_to_f32(v, s_in);
+    else return v * fs_in;
+  };
+  // g of tile t from accumulator buf, 32 columns at a time: lanes of warps 0-3 hold the
+  // rows 2j+q of D, the stage makes the stores coalesced
+  auto epilogue = [&](int t, int buf) {
     const int i = t / tpr, c0 = (t % tpr) * NT;
-    // B[p][k] = fhat_k(i, c0 + p), split into TF32 hi/lo, 16-byte swizzled chunks
-#pragma unroll
-    for (int q = 0; q < kFwdItems; q++) {
-      const int it = tid + q * kTcThreads;
-      const int p = it % NT, kq = it / NT;
-      float4 hi, lo;
-      split_tf32(pre[q][0], hi.x, lo.x);
-      split_tf32(pre[q][1], hi.y, lo.y);
-      split_tf32(pre[q][2], hi.z, lo.z);
-      split_tf32(pre[q][3], hi.w, lo.w);
-      *reinterpret_cast<float4 *>(sBhi + sw_off(p, kq, NT)) = hi;
-      *reinterpret_cast<float4 *>(sBlo + sw_off(p, kq, NT)) = lo;
-    }
-    fence_proxy_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-      issue_tile<K, NT>(tmem, smem_u32(sAhi), smem_u32(sAlo), smem_u32(sBhi), smem_u32(sBlo),
-                                &bar);
-    }
-    if (t + tstep < total) fetch(t + tstep);
-    ok = mbar_wait_bounded(&bar, phase);
-    if (!__syncthreads_and(ok)) {
-      if (tid == 0) atomicOr(errflag, 4);
-      break;
-    }
-    phase ^= 1;
-    tc_fence_after();
-    // epilogue, 32 columns at a time: lanes of warps 0-3 hold rows 2j+q of D
     for (int chunk = 0; chunk < NT / 32; chunk++) {
       if (warp < 4) {
         float v[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * chunk), v);
+        tmem_ld32(acc0 + ((uint32_t)(32 * warp) << 16) + (uint32_t)(buf * NT + 32 * chunk), v);
         const int row = 32 * warp + lane, j = row >> 1, q = row & 1;
         if (j < nj)
 #pragma unroll
@@ -269,147 +318,255 @@ k_tc_forward(int N, int n, View g, const InT *__restrict__ f, const double *__re
       }
       __syncthreads();
     }
+  };
+  bool ok = true;
+  int idx = 0, tprev = 0;
+  int t = t0;
+  if (t < total) fetch(t);
+  for (; t < total; t += tstep, idx++) {
+    bool w = true;
+    if (idx > 0) w = mbar_wait_bounded(&bar, (uint32_t)((idx - 1) & 1));  // B free
+    cpa_wait<0>();                                                          // stage full
+    if (!__syncthreads_and(w)) {
+      ok = false;
+      break;
+    }
+    tc_fence_after();
+    // B[p][k] = fhat_k(i, c0 + p), split into TF32 hi/lo, 16-byte swizzled chunks
+#pragma unroll
+    for (int q = 0; q < kItems; q++) {
+      const int it = tid + q * kTcThreads;
+      const int p = it % NT, kq = it / NT;
+      float x[4];
+#pragma unroll
+      for (int e = 0; e < 4; e++) {
+        const InT v = stage[(4 * kq + e) * NT + p];
+        x[e] = (cmask >> (4 * q + e) & 1u)
+                   ? f64_to_f32(((double)v + u0coef[4 * kq + e] * su0[p]) * in_scale)
+                   : to_op(v);
+      }
+      float4 hi, lo;
+      split_tf32(x[0], hi.x, lo.x);
+      split_tf32(x[1], hi.y, lo.y);
+      split_tf32(x[2], hi.z, lo.z);
+      split_tf32(x[3], hi.w, lo.w);
+      *reinterpret_cast<float4 *>(sBhi + sw_off(p, kq, NT)) = hi;
+      *reinterpret_cast<float4 *>(sBlo + sw_off(p, kq, NT)) = lo;
+    }
+    fence_proxy_async_smem();
     tc_fence_before();
+    __syncthreads();  // B complete, the stage free
+    if (tid == 0) {
+      tc_fence_after();
+      issue_tile<K, NT>(acc0 + (uint32_t)((idx & 1) * NT), tmem, tmem + K, smem_u32(sBhi), smem_u32(sBlo),
+                        &bar);
+    }
+    if (t + tstep < total) fetch(t + tstep);
+    if (idx > 0) epilogue(tprev, (idx - 1) & 1);
+    tc_fence_before();
+    tprev = t;
   }
-  if (!ok && tid == 0) mbar_wait_bounded(&bar, phase);  // let an MMA in flight finish
+  if (ok && idx > 0) {
+    const bool w = mbar_wait_bounded(&bar, (uint32_t)((idx - 1) & 1));
+    if (__syncthreads_and(w)) {
+      tc_fence_after();
+      epilogue(tprev, (idx - 1) & 1);
+    } else {
+      ok = false;
+    }
+  }
+  cpa_wait<0>();
+  if (!ok && tid == 0) {
+    atomicOr(errflag, 4);
+    mbar_wait_bounded(&bar, (uint32_t)((idx - 1) & 1));  // let the MMAs in flight finish
+  }
+  tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) tmem_dealloc(tmem, NT);
+  if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
-// u_k(p) (+)= Re sum_j V[k][j] z_j(p) for p = (i, c0..c0+63); z_j is read from z1 where
-// final_buf[j] is set, else from z0; imag_check: atomic max of |Im| (bits of a double).
+// copies of the z values of 64 shifts (jbase ..) at the NT points of a tile into the
+// stage [64][NT] (complex, from z1 where final_buf is set).  Shifts j >= n and points
+// beyond the grid are not copied: the rows j >= n keep the zeros the kernel writes first
+// (V is zero there too), the columns beyond the grid give outputs that are not stored.
+template <int NT>
+__device__ __forceinline__ void copy_z(const View &z0, const View &z1, const int *final_buf, int n, int N,
+                                       int jbase, int i, int c0, uint32_t sbase) {
+#pragma unroll
+  for (int e = 0; e < 64 * NT / kTcThreads; e++) {
+    const int q = (int)threadIdx.x + e * kTcThreads, jl = q / NT, p = q % NT, jj = jbase + jl;
+    if (jj < n && c0 + p < N) {
+      const bool use1 = final_buf && final_buf[jj];
+      const float2 *zp = reinterpret_cast<const float2 *>(use1 ? z1.p : z0.p);
+      const long long plane = use1 ? z1.plane : z0.plane, pitch = use1 ? z1.pitch : z0.pitch;
+      cpa(sbase + (uint32_t)(q * 8), zp + jj * plane + (long long)i * pitch + c0 + p, 8, true);
+    }
+  }
+}
+// copies of u at rows kbase .. kbase + 63 (< n) and the NT points of a tile into [64][NT]
+// (only the entries that exist: the others are not read); thread tid copies the elements
+// it later reads (it = tid + e * threads)
+template <int NT>
+__device__ __forceinline__ void copy_u(const double *u, int n, int N, long long m, int kbase, int i, int c0,
+                                       uint32_t sbase) {
+#pragma unroll
+  for (int e = 0; e < 64 * NT / kTcThreads; e++) {
+    const int q = (int)threadIdx.x + e * kTcThreads, k = kbase + q / NT, c = c0 + q % NT;
+    if (k < n && c < N) cpa(sbase + (uint32_t)(q * 8), u + (long long)k * m + (long long)i * N + c, 8, true);
+  }
+}
+
+// B of the inverse from the z stage: B[p][2 jl + q] = component q of z_jl(p), TF32 split
+template <int NT>
+__device__ __forceinline__ void build_b_inv(const float2 *zst, unsigned char *sBhi, unsigned char *sBlo) {
+#pragma unroll
+  for (int q = 0; q < NT * 32 / kTcThreads; q++) {
+    const int it = (int)threadIdx.x + q * kTcThreads;
+    const int p = it % NT, qq = it / NT;
+    const float2 a = zst[(2 * qq) * NT + p], b = zst[(2 * qq + 1) * NT + p];
+    float4 hi, lo;
+    split_tf32(a.x, hi.x, lo.x);
+    split_tf32(a.y, hi.y, lo.y);
+    split_tf32(b.x, hi.z, lo.z);
+    split_tf32(b.y, hi.w, lo.w);
+    *reinterpret_cast<float4 *>(sBhi + sw_off(p, qq, NT)) = hi;
+    *reinterpret_cast<float4 *>(sBlo + sw_off(p, qq, NT)) = lo;
+  }
+}
+
+// u_k(p) (+)= dscale Re sum_j V[k][j] z_j(p) for p = (i, c0..c0+NT-1); z_j is read from
+// z1 where final_buf[j] is set, else from z0; imag_check: atomic max of |Im| (bits of a
+// double).  The forward's pipeline: z of tile t + 1 and the u values tile t accumulates
+// into arrive in shared-memory stages by cp.async while the MMAs of tile t run and u of
+// tile t - 1 is written from the other accumulator.  FP32 -> FP64 by bit operations; one
+// FP64 add per output when accumulating.
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_tc_inverse(int N, int n, double *__restrict__ u, View z0, View z1, const int *__restrict__ final_buf,
              const float *__restrict__ Ahi, const float *__restrict__ Alo, float dscale, int accumulate,
              int imag_check, unsigned long long *imag_bits, int *__restrict__ errflag) {
+  constexpr int NT = kInvNt, K = kInvK, SR = NT + 1;
+  constexpr int kB = NT * K * 4;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *sm = align1024(smem_raw);
-  unsigned char *sAhi = sm, *sAlo = sm + kInvA, *sBhi = sm + 2 * kInvA, *sBlo = sBhi + kInvB;
-  float *S = reinterpret_cast<float *>(sBlo + kInvB);
+  unsigned char *sBhi = sm, *sBlo = sm + kB;
+  float *S = reinterpret_cast<float *>(sBlo + kB);                   // [128][NT + 1]
+  float2 *zst = reinterpret_cast<float2 *>(S + kM * SR);             // [64][NT]
+  double *ust = reinterpret_cast<double *>(zst + 64 * NT);           // [64][NT]
   __shared__ uint64_t bar;
   __shared__ uint32_t tmem_slot;
   __shared__ float red[kTcThreads / 32];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (warp == 0) tmem_alloc(&tmem_slot, kInvNt);
+  if (warp == 0) tmem_alloc(&tmem_slot, kTmemCols);
   if (tid == 0) {
     mbar_init(&bar, 1);
     fence_barrier_init();
   }
-  load_a<kInvK>(Ahi, sAhi);
-  load_a<kInvK>(Alo, sAlo);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
+  load_a_tmem<K>(Ahi, tmem, 0);
+  load_a_tmem<K>(Alo, tmem, K);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t acc0 = tmem + 2 * K;
+  for (int q = tid; q < 64 * NT; q += kTcThreads) zst[q] = make_float2(0.f, 0.f);
+  __syncthreads();
   const long long m = (long long)N * N;
-  const int tpr = (int)((z0.pitch + kInvNt - 1) / kInvNt);
+  const int tpr = (int)((z0.pitch + NT - 1) / NT);
   const int total = N * tpr;
-  uint32_t phase = 0;
-  bool ok = true;
   float imax = 0.f;
-  // each thread owns kInvItems (point, 2 shifts) items of a tile; the z values of the
-  // next tile are loaded into registers while the current tile is multiplied
-  constexpr int kInvItems = kInvNt * (kInvK / 4) / kTcThreads;
-  float2 pre[kInvItems][2];
-  auto fetch = [&](int t) {
-    const int i = t / tpr, c0 = (t % tpr) * kInvNt;
+  constexpr int kAcc = 64 * NT / kTcThreads;  // u values of a tile per thread (rows k < 64)
+  auto epilogue = [&](int t, int buf) {
+    const int i = t / tpr, c0 = (t % tpr) * NT;
+    if (warp < 4 * (NT / 32)) {  // warps w and w + 4 read the same lanes, columns 32 (w / 4) ..
+      float v[32];
+      const int chunk = warp >> 2, row = 32 * (warp & 3) + lane;
+      tmem_ld32(acc0 + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(buf * NT + 32 * chunk), v);
 #pragma unroll
-    for (int q = 0; q < kInvItems; q++) {
+      for (int cc = 0; cc < 32; cc++) S[row * SR + 32 * chunk + cc] = v[cc];
+    }
+    if (accumulate) cpa_wait<1>();  // this thread's u copies of tile t (the z copies of t + 2 may pend)
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kAcc; q++) {
       const int it = tid + q * kTcThreads;
-      const int p = it % kInvNt, qq = it / kInvNt;
-      const int c = c0 + p;
-#pragma unroll
-      for (int e = 0; e < 2; e++) {
-        const int jj = 2 * qq + e;
-        float2 v = make_float2(0.f, 0.f);
-        if (c < N && jj < n) {
-          const View &zv = (final_buf && final_buf[jj]) ? z1 : z0;
-          v = reinterpret_cast<const float2 *>(zv.p)[jj * zv.plane + (long long)i * zv.pitch + c];
-        }
-        pre[q][e] = v;
+      const int k = it / NT, cc = it % NT, c = c0 + cc;
+      if (k < n && c < N) {
+        const double d = f32_to_f64(S[k * SR + cc] * dscale);
+        u[(long long)k * m + (long long)i * N + c] = accumulate ? ust[it] + d : d;
+        if (imag_check) imax = fmaxf(imax, fabsf(S[(64 + k) * SR + cc] * dscale));
       }
     }
+    __syncthreads();
   };
-  // u values this thread accumulates into in the epilogue (n x 64 per tile)
-  constexpr int kAccItems = 64 * kInvNt / kTcThreads;
-  double uacc[kAccItems];
+  bool ok = true;
+  int idx = 0, tprev = 0;
   int t = blockIdx.x;
-  if (t < total) fetch(t);
-  for (; t < total; t += gridDim.x) {
-    const int i = t / tpr, c0 = (t % tpr) * kInvNt;
-#pragma unroll
-    for (int q = 0; q < kInvItems; q++) {
-      const int it = tid + q * kTcThreads;
-      const int p = it % kInvNt, qq = it / kInvNt;
-      float4 hi, lo;
-      split_tf32(pre[q][0].x, hi.x, lo.x);
-      split_tf32(pre[q][0].y, hi.y, lo.y);
-      split_tf32(pre[q][1].x, hi.z, lo.z);
-      split_tf32(pre[q][1].y, hi.w, lo.w);
-      *reinterpret_cast<float4 *>(sBhi + sw_off(p, qq, kInvNt)) = hi;
-      *reinterpret_cast<float4 *>(sBlo + sw_off(p, qq, kInvNt)) = lo;
+  if (t < total) {
+    copy_z<NT>(z0, z1, final_buf, n, N, 0, t / tpr, (t % tpr) * NT, smem_u32(zst));
+    cpa_commit();
+  }
+  for (; t < total; t += gridDim.x, idx++) {
+    bool w = true;
+    if (idx > 0) w = mbar_wait_bounded(&bar, (uint32_t)((idx - 1) & 1));
+    if (accumulate && idx > 0) cpa_wait<1>();  // z of tile t (the u copies of tprev may pend)
+    else cpa_wait<0>();
+    if (!__syncthreads_and(w)) {
+      ok = false;
+      break;
     }
+    tc_fence_after();
+    build_b_inv<NT>(zst, sBhi, sBlo);
     fence_proxy_async_smem();
     tc_fence_before();
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
-      issue_tile<kInvK, kInvNt>(tmem, smem_u32(sAhi), smem_u32(sAlo), smem_u32(sBhi), smem_u32(sBlo),
-                                &bar);
+      issue_tile<K, NT>(acc0 + (uint32_t)((idx & 1) * NT), tmem, tmem + K, smem_u32(sBhi), smem_u32(sBlo),
+                        &bar);
     }
-    // accumulator inputs of this tile and z of the next one, while the MMAs run
-#pragma unroll
-    for (int q = 0; q < kAccItems; q++) {
-      const int it = tid + q * kTcThreads;
-      const int k = it / kInvNt, cc = it % kInvNt;
-      const int c = c0 + cc;
-      uacc[q] = (accumulate && k < n && c < N) ? u[(long long)k * m + (long long)i * N + c] : 0.0;
+    const int tn = t + (int)gridDim.x;
+    if (tn < total) copy_z<NT>(z0, z1, final_buf, n, N, 0, tn / tpr, (tn % tpr) * NT, smem_u32(zst));
+    cpa_commit();
+    if (idx > 0) epilogue(tprev, (idx - 1) & 1);
+    if (accumulate) {
+      copy_u<NT>(u, n, N, m, 0, t / tpr, (t % tpr) * NT, smem_u32(ust));
+      cpa_commit();
     }
-    if (t + (int)gridDim.x < total) fetch(t + gridDim.x);
-    ok = mbar_wait_bounded(&bar, phase);
-    if (!__syncthreads_and(ok)) {
-      if (tid == 0) atomicOr(errflag, 4);
-      break;
-    }
-    phase ^= 1;
-    tc_fence_after();
-    for (int chunk = 0; chunk < kInvNt / 32; chunk++) {
-      if (warp < 4) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * chunk), v);
-        const int row = 32 * warp + lane;
-#pragma unroll
-        for (int cc = 0; cc < 32; cc++) S[row * (kInvNt + 1) + 32 * chunk + cc] = v[cc];
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < kAccItems; q++) {
-      const int it = tid + q * kTcThreads;
-      const int k = it / kInvNt, cc = it % kInvNt;
-      const int c = c0 + cc;
-      if (k < n && c < N) {
-        u[(long long)k * m + (long long)i * N + c] = uacc[q] + (double)(S[k * (kInvNt + 1) + cc] * dscale);
-        if (imag_check) imax = fmaxf(imax, fabsf(S[(64 + k) * (kInvNt + 1) + cc] * dscale));
-      }
-    }
-    __syncthreads();
     tc_fence_before();
+    tprev = t;
   }
-  if (!ok && tid == 0) mbar_wait_bounded(&bar, phase);
+  if (ok && idx > 0) {
+    const bool w = mbar_wait_bounded(&bar, (uint32_t)((idx - 1) & 1));
+    if (__syncthreads_and(w)) {
+      tc_fence_after();
+      if (accumulate) cpa_wait<0>();
+      epilogue(tprev, (idx - 1) & 1);
+    } else {
+      ok = false;
+    }
+  }
+  cpa_wait<0>();
+  if (!ok && tid == 0) {
+    atomicOr(errflag, 4);
+    mbar_wait_bounded(&bar, (uint32_t)((idx - 1) & 1));
+  }
   if (imag_check) {
     for (int o = 16; o > 0; o >>= 1) imax = fmaxf(imax, __shfl_down_sync(0xffffffffu, imax, o));
     if (lane == 0) red[warp] = imax;
   }
+  tc_fence_before();
   __syncthreads();
   if (imag_check && tid == 0) {
     float mx = 0.f;
     for (int w = 0; w < kTcThreads / 32; w++) mx = fmaxf(mx, red[w]);
-    atomicMax(imag_bits, (unsigned long long)__double_as_longlong((double)mx));
+    atomicMax(imag_bits, (unsigned long long)__double_as_longlong(f32_to_f64(mx)));
   }
   tc_fence_after();
-  if (warp == 0) tmem_dealloc(tmem, kInvNt);
+  if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
 // ---- the inverse for 64 < n <= 128: K = 2n split over the two CTAs of a cluster ----
@@ -432,182 +589,167 @@ __device__ __forceinline__ void st_cluster(uint32_t addr, float v) {
   asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
 }
 
-constexpr int kInv2K = 128, kInv2Nt = 32;
-constexpr int kInv2A = kM * kInv2K * 4, kInv2B = kInv2Nt * kInv2K * 4;
-constexpr int kInv2S = kM * (kInv2Nt + 1) * 4;
-constexpr int kInv2Smem = 2 * kInv2A + 2 * kInv2B + kInv2S + 1024;
-
 // u_k(p) (+)= dscale Re sum_j V[k][j] z_j(p) for k < 128 and the points p = (i, c0..c0+31):
 // CTA r of a cluster of two multiplies the shifts j = 64 r .. 64 r + 63 (its half of K,
-// A = its half of the operand), both accumulate D[128 x 32] in tensor memory; CTA 1 stores
-// its D into CTA 0's stage through distributed shared memory, CTA 0 adds its own and writes
-// u.  The imaginary part is not formed on this route.  Both CTAs of a cluster walk the same
-// tiles and meet at every cluster barrier, also after a bounded wait ran out (then they only
-// skip the work), so neither can wait for the other forever.
+// A = its half of the operand) into D_r[128 x 32]; CTA r owns the rows k = 64 r .. 64 r + 63
+// of u: it keeps those rows of D_r and stores the other half into its peer's stage through
+// distributed shared memory; after a cluster barrier it writes u_k = D_0[k] + D_1[k] for its
+// own rows, and a second barrier frees the stage for the next tile.  The imaginary part is
+// not formed on this route.  Both CTAs walk the same tiles and meet at every cluster
+// barrier, also after a bounded wait ran out (then they only skip the work), so neither
+// can wait for the other forever.  The pipeline is the one of k_tc_inverse.
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
 k_tc_inverse2(int N, int n, double *__restrict__ u, View z0, View z1, const int *__restrict__ final_buf,
               const float *__restrict__ Ahi, const float *__restrict__ Alo, float dscale, int accumulate,
               int *__restrict__ errflag) {
+  constexpr int NT = kInv2Nt, K = kInv2K, SR = NT + 1;
+  constexpr int kB = NT * K * 4;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *sm = align1024(smem_raw);
-  unsigned char *sAhi = sm, *sAlo = sm + kInv2A, *sBhi = sm + 2 * kInv2A, *sBlo = sBhi + kInv2B;
-  float *S = reinterpret_cast<float *>(sBlo + kInv2B);
+  unsigned char *sBhi = sm, *sBlo = sm + kB;
+  float *S = reinterpret_cast<float *>(sBlo + kB);          // [2 sources][64][NT + 1]
+  float2 *zst = reinterpret_cast<float2 *>(S + 2 * 64 * SR);  // [64][NT]
+  double *ust = reinterpret_cast<double *>(zst + 64 * NT);   // [64][NT]
   __shared__ uint64_t bar;
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t rank = cluster_rank();
-  const int jbase = 64 * (int)rank;
-  if (warp == 0) tmem_alloc(&tmem_slot, kInv2Nt);
+  const int jbase = 64 * (int)rank, kbase = 64 * (int)rank;
+  if (warp == 0) tmem_alloc(&tmem_slot, kTmemCols);
   if (tid == 0) {
     mbar_init(&bar, 1);
     fence_barrier_init();
   }
-  load_a<kInv2K>(Ahi + (size_t)rank * kM * kInv2K, sAhi);
-  load_a<kInv2K>(Alo + (size_t)rank * kM * kInv2K, sAlo);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
-  const uint32_t S_peer = peer_addr(smem_u32(S), 0);  // CTA 0's stage
+  load_a_tmem<K>(Ahi + (size_t)rank * kM * K, tmem, 0);
+  load_a_tmem<K>(Alo + (size_t)rank * kM * K, tmem, K);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t acc0 = tmem + 2 * K;
+  for (int q = tid; q < 64 * NT; q += kTcThreads) zst[q] = make_float2(0.f, 0.f);
+  __syncthreads();
+  const uint32_t S_peer = peer_addr(smem_u32(S), rank ^ 1u);
   const long long m = (long long)N * N;
-  const int tpr = (int)((z0.pitch + kInv2Nt - 1) / kInv2Nt);
+  const int tpr = (int)((z0.pitch + NT - 1) / NT);
   const int total = N * tpr;
   const int t0 = (int)blockIdx.x / 2, tstep = (int)gridDim.x / 2;
-  uint32_t phase = 0;
+  constexpr int kAcc = 64 * NT / kTcThreads;  // own u values of a tile per thread
   bool ok = true;
-  // each thread owns kItems (point, 2 shifts) items of a tile; the z values of the next
-  // tile are loaded into registers while the current tile is multiplied
-  constexpr int kItems = kInv2Nt * (kInv2K / 4) / kTcThreads;
-  float2 pre[kItems][2];
-  auto fetch = [&](int t) {
-    const int i = t / tpr, c0 = (t % tpr) * kInv2Nt;
+  auto epilogue = [&](int t, int buf) {
+    const int i = t / tpr, c0 = (t % tpr) * NT;
+    if (ok && warp < 4 * (NT / 32)) {  // warps w and w + 4 read the same lanes, columns 32 (w / 4) ..
+      float v[32];
+      const int chunk = warp >> 2, row = 32 * (warp & 3) + lane, r64 = row & 63;
+      tmem_ld32(acc0 + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(buf * NT + 32 * chunk), v);
+      if ((row >> 6) == (int)rank) {
 #pragma unroll
-    for (int q = 0; q < kItems; q++) {
-      const int it = tid + q * kTcThreads;
-      const int p = it % kInv2Nt, qq = it / kInv2Nt;
-      const int c = c0 + p;
+        for (int cc = 0; cc < 32; cc++) S[r64 * SR + 32 * chunk + cc] = v[cc];
+      } else {
+        const uint32_t base = S_peer + (uint32_t)(((64 + r64) * SR + 32 * chunk) * 4);
 #pragma unroll
-      for (int e = 0; e < 2; e++) {
-        const int jj = jbase + 2 * qq + e;
-        float2 v = make_float2(0.f, 0.f);
-        if (c < N && jj < n) {
-          const View &zv = (final_buf && final_buf[jj]) ? z1 : z0;
-          v = reinterpret_cast<const float2 *>(zv.p)[jj * zv.plane + (long long)i * zv.pitch + c];
-        }
-        pre[q][e] = v;
+        for (int cc = 0; cc < 32; cc++) st_cluster(base + 4u * cc, v[cc]);
       }
     }
-  };
-  constexpr int kAcc = kM * kInv2Nt / kTcThreads;  // u values of a tile per thread (CTA 0)
-  double uacc[kAcc];
-  int t = t0;
-  if (t < total) fetch(t);
-  for (; t < total; t += tstep) {
-    const int i = t / tpr, c0 = (t % tpr) * kInv2Nt;
+    if (accumulate) cpa_wait<1>();
+    cluster_sync();  // both partials of this CTA's rows are in its stage
     if (ok) {
-#pragma unroll
-      for (int q = 0; q < kItems; q++) {
-        const int it = tid + q * kTcThreads;
-        const int p = it % kInv2Nt, qq = it / kInv2Nt;
-        float4 hi, lo;
-        split_tf32(pre[q][0].x, hi.x, lo.x);
-        split_tf32(pre[q][0].y, hi.y, lo.y);
-        split_tf32(pre[q][1].x, hi.z, lo.z);
-        split_tf32(pre[q][1].y, hi.w, lo.w);
-        *reinterpret_cast<float4 *>(sBhi + sw_off(p, qq, kInv2Nt)) = hi;
-        *reinterpret_cast<float4 *>(sBlo + sw_off(p, qq, kInv2Nt)) = lo;
-      }
-      fence_proxy_async_smem();
-      tc_fence_before();
-    }
-    __syncthreads();
-    if (ok && tid == 0) {
-      tc_fence_after();
-      issue_tile<kInv2K, kInv2Nt>(tmem, smem_u32(sAhi), smem_u32(sAlo), smem_u32(sBhi), smem_u32(sBlo), &bar);
-    }
-    if (rank == 0) {
 #pragma unroll
       for (int q = 0; q < kAcc; q++) {
         const int it = tid + q * kTcThreads;
-        const int k = it / kInv2Nt, c = c0 + it % kInv2Nt;
-        uacc[q] = (accumulate && k < n && c < N) ? u[(long long)k * m + (long long)i * N + c] : 0.0;
-      }
-    }
-    if (t + tstep < total) fetch(t + tstep);
-    if (ok) {
-      const bool w = mbar_wait_bounded(&bar, phase);
-      ok = __syncthreads_and(w);
-      if (!ok && tid == 0) atomicOr(errflag, 4);
-      if (w) phase ^= 1;
-    } else {
-      __syncthreads();
-    }
-    tc_fence_after();
-    cluster_sync();  // CTA 0's stage is free
-    if (rank == 1 && ok && warp < 4) {
-      float v[32];
-      tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16), v);
-      const int row = 32 * warp + lane;
-#pragma unroll
-      for (int cc = 0; cc < 32; cc++) st_cluster(S_peer + (uint32_t)((row * (kInv2Nt + 1) + cc) * 4), v[cc]);
-    }
-    cluster_sync();  // CTA 1's half of D is in CTA 0's stage
-    if (rank == 0) {
-      if (ok && warp < 4) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16), v);
-        const int row = 32 * warp + lane;
-#pragma unroll
-        for (int cc = 0; cc < 32; cc++) S[row * (kInv2Nt + 1) + cc] += v[cc];
-      }
-      __syncthreads();
-      if (ok) {
-#pragma unroll
-        for (int q = 0; q < kAcc; q++) {
-          const int it = tid + q * kTcThreads;
-          const int k = it / kInv2Nt, cc = it % kInv2Nt, c = c0 + cc;
-          if (k < n && c < N)
-            u[(long long)k * m + (long long)i * N + c] = uacc[q] + (double)(S[k * (kInv2Nt + 1) + cc] * dscale);
+        const int r64 = it / NT, cc = it % NT, k = kbase + r64, c = c0 + cc;
+        if (k < n && c < N) {
+          const double d = f32_to_f64((S[r64 * SR + cc] + S[(64 + r64) * SR + cc]) * dscale);
+          u[(long long)k * m + (long long)i * N + c] = accumulate ? ust[it] + d : d;
         }
       }
     }
-    __syncthreads();
-    tc_fence_before();
+    cluster_sync();  // the stages are free again
+  };
+  int idx = 0, tprev = 0, fail_par = 0;
+  int t = t0;
+  if (t < total) {
+    copy_z<NT>(z0, z1, final_buf, n, N, jbase, t / tpr, (t % tpr) * NT, smem_u32(zst));
+    cpa_commit();
   }
-  if (!ok && tid == 0) mbar_wait_bounded(&bar, phase);  // let an MMA in flight finish
+  for (; t < total; t += tstep, idx++) {
+    if (idx > 0 && ok) {
+      const bool w = mbar_wait_bounded(&bar, (uint32_t)((idx - 1) & 1));
+      ok = __syncthreads_and(w);
+      fail_par = (idx - 1) & 1;
+    }
+    if (accumulate && idx > 0) cpa_wait<1>();
+    else cpa_wait<0>();
+    __syncthreads();
+    tc_fence_after();
+    if (ok) {
+      build_b_inv<NT>(zst, sBhi, sBlo);
+      fence_proxy_async_smem();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (ok && tid == 0) {
+      tc_fence_after();
+      issue_tile<K, NT>(acc0 + (uint32_t)((idx & 1) * NT), tmem, tmem + K, smem_u32(sBhi), smem_u32(sBlo),
+                        &bar);
+    }
+    const int tn = t + tstep;
+    if (tn < total) copy_z<NT>(z0, z1, final_buf, n, N, jbase, tn / tpr, (tn % tpr) * NT, smem_u32(zst));
+    cpa_commit();
+    if (idx > 0) epilogue(tprev, (idx - 1) & 1);
+    if (accumulate) {
+      copy_u<NT>(u, n, N, m, kbase, t / tpr, (t % tpr) * NT, smem_u32(ust));
+      cpa_commit();
+    }
+    tc_fence_before();
+    tprev = t;
+  }
+  if (idx > 0) {
+    if (ok) {
+      const bool w = mbar_wait_bounded(&bar, (uint32_t)((idx - 1) & 1));
+      ok = __syncthreads_and(w);
+      fail_par = (idx - 1) & 1;
+    }
+    tc_fence_after();
+    if (accumulate) cpa_wait<0>();
+    epilogue(tprev, (idx - 1) & 1);
+  }
+  cpa_wait<0>();
+  if (!ok && tid == 0) {
+    atomicOr(errflag, 4);
+    mbar_wait_bounded(&bar, (uint32_t)fail_par);  // let the MMAs in flight finish
+  }
+  tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) tmem_dealloc(tmem, kInv2Nt);
-  cluster_sync();  // CTA 0's shared memory stays until CTA 1 is done with it
+  if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+  cluster_sync();  // no CTA leaves while its peer may still address its shared memory
 }
 
 }  // namespace
 
 bool tc_transforms_supported(int N, int n) { return n <= 128 && N >= 127; }
 
-// the forward for 64 < n <= 128: K = 128, tiles of 64 points, two CTAs (halves of the rows)
-constexpr int kFwd2K = 128, kFwd2Nt = 64;
-constexpr int kFwd2Smem = 2 * kM * kFwd2K * 4 + 2 * kFwd2Nt * kFwd2K * 4 + kFwdS + 1024;
-static_assert(kFwd2Smem <= 227 * 1024 - 256, "forward operands exceed shared memory");
-static_assert(kInv2Smem <= 227 * 1024 - 256, "inverse operands exceed shared memory");
-
 cudaError_t prepare_tc_transforms() {
   cudaError_t e;
 #define PD_TC_ATTR(K_, S_)                                                         \
   e = cudaFuncSetAttribute(K_, cudaFuncAttributeMaxDynamicSharedMemorySize, S_); \
   if (e != cudaSuccess) return e;
-  PD_TC_ATTR((k_tc_forward<double, kFwdK, kFwdNt, 1>), kFwdSmem)
-  PD_TC_ATTR((k_tc_forward<float, kFwdK, kFwdNt, 1>), kFwdSmem)
-  PD_TC_ATTR((k_tc_forward<double, kFwd2K, kFwd2Nt, 2>), kFwd2Smem)
-  PD_TC_ATTR((k_tc_forward<float, kFwd2K, kFwd2Nt, 2>), kFwd2Smem)
+  PD_TC_ATTR((k_tc_forward<double, kFwdK, kFwdNt, 1>), (fwd_smem<kFwdK, kFwdNt, double>()))
+  PD_TC_ATTR((k_tc_forward<float, kFwdK, kFwdNt, 1>), (fwd_smem<kFwdK, kFwdNt, float>()))
+  PD_TC_ATTR((k_tc_forward<double, kFwd2K, kFwd2Nt, 2>), (fwd_smem<kFwd2K, kFwd2Nt, double>()))
+  PD_TC_ATTR((k_tc_forward<float, kFwd2K, kFwd2Nt, 2>), (fwd_smem<kFwd2K, kFwd2Nt, float>()))
   PD_TC_ATTR(k_tc_inverse, kInvSmem)
   PD_TC_ATTR(k_tc_inverse2, kInv2Smem)
 #undef PD_TC_ATTR
   return cudaSuccess;
 }
 
-// A operands (host): TF32 splits of the scaled forward matrix [128][64] and of the
-// inverse matrix [128][128] in the row layouts described at the top of this file.
+// A operands (host): TF32 splits of the scaled forward matrix and of the inverse matrix
+// in the row layouts described at the top of this file.
 static void split_host(double x, float &hi, float &lo) {
   const float xf = (float)x;
   uint32_t b;
@@ -698,18 +840,18 @@ void launch_tc_forward(cudaStream_t s, int grid, int N, int n, View g, const voi
                        double in_scale, int *errflag) {
   if (n > 64) {  // grid even: two CTAs (row halves) per tile
     if (f32)
-      k_tc_forward<float, kFwd2K, kFwd2Nt, 2><<<grid, kTcThreads, kFwd2Smem, s>>>(
+      k_tc_forward<float, kFwd2K, kFwd2Nt, 2><<<grid, kTcThreads, fwd_smem<kFwd2K, kFwd2Nt, float>(), s>>>(
           N, n, g, static_cast<const float *>(f), u0, u0coef, Ahi, Alo, in_scale, errflag);
     else
-      k_tc_forward<double, kFwd2K, kFwd2Nt, 2><<<grid, kTcThreads, kFwd2Smem, s>>>(
+      k_tc_forward<double, kFwd2K, kFwd2Nt, 2><<<grid, kTcThreads, fwd_smem<kFwd2K, kFwd2Nt, double>(), s>>>(
           N, n, g, static_cast<const double *>(f), u0, u0coef, Ahi, Alo, in_scale, errflag);
     return;
   }
   if (f32)
-    k_tc_forward<float, kFwdK, kFwdNt, 1><<<grid, kTcThreads, kFwdSmem, s>>>(
+    k_tc_forward<float, kFwdK, kFwdNt, 1><<<grid, kTcThreads, fwd_smem<kFwdK, kFwdNt, float>(), s>>>(
         N, n, g, static_cast<const float *>(f), u0, u0coef, Ahi, Alo, in_scale, errflag);
   else
-    k_tc_forward<double, kFwdK, kFwdNt, 1><<<grid, kTcThreads, kFwdSmem, s>>>(
+    k_tc_forward<double, kFwdK, kFwdNt, 1><<<grid, kTcThreads, fwd_smem<kFwdK, kFwdNt, double>(), s>>>(
         N, n, g, static_cast<const double *>(f), u0, u0coef, Ahi, Alo, in_scale, errflag);
 }
 
