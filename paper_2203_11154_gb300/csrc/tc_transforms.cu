@@ -193,11 +193,11 @@ static_assert(2 * 128 + 2 * 64 <= kTmemCols && 2 * 64 + 2 * 128 <= kTmemCols, "t
 template <int K, int NT, typename InT> constexpr int fwd_smem() {
   return 2 * NT * K * 4 + kFwdS + NT * K * (int)sizeof(InT) + NT * 8 + 1024;
 }
-// the inverse: B hi/lo, stage [rows][NT + 1] (rows: 128, or 2 x 64 in the cluster form),
-// z stage [64 shifts][NT] complex, u stage [64 rows][NT], slack
+// the inverse: B hi/lo, stage [rows][NT + 1] (rows: 128, or 2 tile parities x 2 sources x 64
+// in the cluster form), z stage [64 shifts][NT] complex, u stage [64 rows][NT], slack
 constexpr int kInvSmem = 2 * kInvNt * kInvK * 4 + kM * (kInvNt + 1) * 4 + 64 * kInvNt * 8 + 64 * kInvNt * 8 + 1024;
 constexpr int kInv2Smem =
-    2 * kInv2Nt * kInv2K * 4 + 2 * 64 * (kInv2Nt + 1) * 4 + 64 * kInv2Nt * 8 + 64 * kInv2Nt * 8 + 1024;
+    2 * kInv2Nt * kInv2K * 4 + 2 * 2 * 64 * (kInv2Nt + 1) * 4 + 64 * kInv2Nt * 8 + 64 * kInv2Nt * 8 + 1024;
 // the opt-in limit per block less the kernels' static shared memory
 constexpr int kSmemLimit = 227 * 1024 - 1024;
 static_assert(fwd_smem<kFwdK, kFwdNt, double>() <= kSmemLimit, "forward (n <= 64) exceeds shared memory");
@@ -594,8 +594,8 @@ __device__ __forceinline__ void st_cluster(uint32_t addr, float v) {
 // A = its half of the operand) into D_r[128 x 32]; CTA r owns the rows k = 64 r .. 64 r + 63
 // of u: it keeps those rows of D_r and stores the other half into its peer's stage through
 // distributed shared memory; after a cluster barrier it writes u_k = D_0[k] + D_1[k] for its
-// own rows, and a second barrier frees the stage for the next tile.  The imaginary part is
-// not formed on this route.  Both CTAs walk the same tiles and meet at every cluster
+// own rows (the stage slot alternates with the tile parity, which is also the accumulator's).
+// The imaginary part is not formed on this route.  Both CTAs walk the same tiles and meet at every cluster
 // barrier, also after a bounded wait ran out (then they only skip the work), so neither
 // can wait for the other forever.  The pipeline is the one of k_tc_inverse.
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
@@ -607,8 +607,8 @@ k_tc_inverse2(int N, int n, double *__restrict__ u, View z0, View z1, const int 
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *sm = align1024(smem_raw);
   unsigned char *sBhi = sm, *sBlo = sm + kB;
-  float *S = reinterpret_cast<float *>(sBlo + kB);          // [2 sources][64][NT + 1]
-  float2 *zst = reinterpret_cast<float2 *>(S + 2 * 64 * SR);  // [64][NT]
+  float *S = reinterpret_cast<float *>(sBlo + kB);          // [2 parities][2 sources][64][NT + 1]
+  float2 *zst = reinterpret_cast<float2 *>(S + 4 * 64 * SR);  // [64][NT]
   double *ust = reinterpret_cast<double *>(zst + 64 * NT);   // [64][NT]
   __shared__ uint64_t bar;
   __shared__ uint32_t tmem_slot;
@@ -639,17 +639,22 @@ k_tc_inverse2(int N, int n, double *__restrict__ u, View z0, View z1, const int 
   const int t0 = (int)blockIdx.x / 2, tstep = (int)gridDim.x / 2;
   constexpr int kAcc = 64 * NT / kTcThreads;  // own u values of a tile per thread
   bool ok = true;
+  // the stage of tile parity sb: own partial rows at [sb][0], the peer's at [sb][1]; one slot
+  // per parity, so one cluster barrier per tile orders both the stores and the reuse (the
+  // peer writes slot sb again two tiles later, after passing the next barrier, which this
+  // CTA reaches only when it has read slot sb)
   auto epilogue = [&](int t, int buf) {
     const int i = t / tpr, c0 = (t % tpr) * NT;
+    float *Sb = S + buf * 2 * 64 * SR;
     if (ok && warp < 4 * (NT / 32)) {  // warps w and w + 4 read the same lanes, columns 32 (w / 4) ..
       float v[32];
       const int chunk = warp >> 2, row = 32 * (warp & 3) + lane, r64 = row & 63;
       tmem_ld32(acc0 + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(buf * NT + 32 * chunk), v);
       if ((row >> 6) == (int)rank) {
 #pragma unroll
-        for (int cc = 0; cc < 32; cc++) S[r64 * SR + 32 * chunk + cc] = v[cc];
+        for (int cc = 0; cc < 32; cc++) Sb[r64 * SR + 32 * chunk + cc] = v[cc];
       } else {
-        const uint32_t base = S_peer + (uint32_t)(((64 + r64) * SR + 32 * chunk) * 4);
+        const uint32_t base = S_peer + (uint32_t)(((buf * 2 * 64 + 64 + r64) * SR + 32 * chunk) * 4);
 #pragma unroll
         for (int cc = 0; cc < 32; cc++) st_cluster(base + 4u * cc, v[cc]);
       }
@@ -662,12 +667,11 @@ k_tc_inverse2(int N, int n, double *__restrict__ u, View z0, View z1, const int 
         const int it = tid + q * kTcThreads;
         const int r64 = it / NT, cc = it % NT, k = kbase + r64, c = c0 + cc;
         if (k < n && c < N) {
-          const double d = f32_to_f64((S[r64 * SR + cc] + S[(64 + r64) * SR + cc]) * dscale);
+          const double d = f32_to_f64((Sb[r64 * SR + cc] + Sb[(64 + r64) * SR + cc]) * dscale);
           u[(long long)k * m + (long long)i * N + c] = accumulate ? ust[it] + d : d;
         }
       }
     }
-    cluster_sync();  // the stages are free again
   };
   int idx = 0, tprev = 0, fail_par = 0;
   int t = t0;
