@@ -351,7 +351,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="paradiag-2047",
-                    choices=["paradiag-511", "paradiag-1023", "paradiag-2047", "uneven-8", "examples"])
+                    choices=["paradiag-511", "paradiag-511-128", "paradiag-1023", "paradiag-2047", "uneven-8",
+                             "examples"])
     ap.add_argument("--fp64-steps", type=int, default=None,
                     help="timed steps of the FP64 form beside the value (default: the smaller "
                          "of --steps and 3 at N = 2047, else --steps)")

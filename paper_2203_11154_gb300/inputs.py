@@ -11,6 +11,8 @@ Workloads (unit square, homogeneous Dirichlet, N x N interior, h = 1/(N+1)):
                  b_j = U(-1,1) + i U(-1,1), real parts of all shifts first, seed 0.
   paradiag-511   as paradiag-1023 on N=511 (arrays of 134 MB, still larger than L2): the
                  smaller case of the same kernels for profiler captures.
+  paradiag-511-128  as paradiag-2047 (n=128, tau=1/128) on N=511: the smaller case of the
+                 n = 128 kernels for profiler captures.
   paradiag-1023  N=1023, n=64 time steps (tau=1/64, alpha=1e-3);
                  u0 = sin(pi x) sin(pi y), f = U(-1,1) [n][N][N], seed 1.
   paradiag-2047  N=2047, n=128 (tau=1/128, alpha=1e-3); as paradiag-1023.
@@ -30,6 +32,7 @@ import numpy as np
 WORKLOADS = {
     "shifted-63": dict(kind="shifted", N=63, n=16, tau=1.0 / 16, alpha=1e-2, seed=0),
     "paradiag-511": dict(kind="paradiag", N=511, n=64, tau=1.0 / 64, alpha=1e-3, seed=1),
+    "paradiag-511-128": dict(kind="paradiag", N=511, n=128, tau=1.0 / 128, alpha=1e-3, seed=1),
     "paradiag-1023": dict(kind="paradiag", N=1023, n=64, tau=1.0 / 64, alpha=1e-3, seed=1),
     "paradiag-2047": dict(kind="paradiag", N=2047, n=128, tau=1.0 / 128, alpha=1e-3, seed=1),
     "adjoint-1023": dict(kind="adjoint", N=1023, n=64, tau=1.0 / 64, alpha=1e-3, seed=1,
