@@ -441,6 +441,9 @@ def main():
     # per-kernel durations: CUDA events around every launch, in a second pass of the same
     # K steps (kept out of the timed pass above, whose step time they would inflate)
     ms_prof, _, prof, _, _ = timed(ctx, args.steps, 0, profile=True)
+    # the fused smoothing kernels the set-up autotuner chose per level (1 TMA tiles, 2 warp
+    # streams with rows per segment, 0 none)
+    autotune = [{"level": l, "variant": v, "rows_per_segment": sg} for l, (v, sg) in enumerate(ctx.fused_choices())]
 
     # end to end through the host-buffer C ABI call (pinned host memory; every step copies
     # its f and u0 in and its u out inside the timed region, the copies of neighbouring
@@ -548,7 +551,7 @@ def main():
                      "steps": k64, "relres_shift_max": out64["relres_shift_max"],
                      "relres_allatonce": out64["relres_allatonce"],
                      "cycles_max": out64["cycles_max"]},
-            "speedup_vs_fp64": value / value64, "uneven8": uneven8,
+            "speedup_vs_fp64": value / value64, "uneven8": uneven8, "autotune": autotune,
             "clocks": ck, "e2e": e2e, "gpu_launches": launches,
             "roofline": roofline, "solve_hbm": solve_hbm, "transforms": transforms,
             "kernels": kernels,

@@ -73,9 +73,10 @@ typedef struct {
                           the K dimension of the inverse split over two CTAs, the inverse's
                           halves summed through distributed shared memory of a two-CTA
                           cluster); 0: FP32 CUDA-core products */
-    int fused_variant; /* implementation of the fused kernels: 0 = chosen at set-up by timing
-                          both on the context's own levels, 1 = TMA-staged shared-memory
-                          tiles, 2 = warp-streaming strips (cp.async ring, shuffles) */
+    int fused_variant; /* implementation of the fused kernels: 0 = warp-streaming strips
+                          with the rows per segment chosen at set-up by timing them on the
+                          context's own levels, 1 = TMA-staged shared-memory tiles, 2 = as 0
+                          (warp streams: cp.async ring, shuffles) */
     double kappa;      /* diffusion coefficient scaling A in eq. (1): (B kron I + kappa I kron A);
                           the shifted systems become (kappa A + lam_j I) z = b (default 1) */
     int outer_maxit;   /* precision 0: FP64 correction steps on eq. (1) after the first solve,
@@ -460,6 +461,15 @@ pd_status pd_synchronize(pd_ctx *ctx);
 
 /* Kernel launches issued by this context since creation (for launch accounting). */
 long long pd_launch_count(const pd_ctx *ctx);
+
+/*
+ * The fused smoothing kernels the set-up autotuner chose for multigrid level `level` (0 =
+ * finest) of the working precision: *h_variant = 1 (TMA tiles), 2 (warp streams, *h_seg
+ * rows per segment) or 0 where the level has no fused kernels (levels held in one CTA per
+ * shift, the last level, cfg.fused = 0, the FP64 form with cfg.fused = 1).  Errors: PD_ERR_ARG (NULL ctx, level outside
+ * 0..levels-1).  Instrumentation; the paper has no counterpart.
+ */
+pd_status pd_fused_choice(const pd_ctx *ctx, int level, int *h_variant, int *h_seg);
 
 /* Waits for the context stream, then frees all device and pinned host memory of the
  * context. */

@@ -39,7 +39,7 @@ EXPORTS = ["pd_config_default", "pd_alpha_circulant", "pd_shifts_alpha_circulant
            "pd_coarse_solve", "pd_transform_forward", "pd_transform_inverse",
            "pd_allatonce_residual", "pd_allatonce_residual_static", "pd_laplacian_dot",
            "pd_initial_value_gradient",
-           "pd_profile_enable", "pd_profile_read", "pd_get_history", "pd_synchronize", "pd_launch_count", "pd_batch_launch_count", "paradiag_destroy",
+           "pd_profile_enable", "pd_profile_read", "pd_get_history", "pd_synchronize", "pd_launch_count", "pd_batch_launch_count", "pd_fused_choice", "paradiag_destroy",
            "pd_status_str", "pd_last_error", "shifted_solve_refined", "pd_allatonce_residual32", "pd_shifted_residual32",
            "paradiag_solve_host_batch", "pd_batch_setup",
            "pd_batch_solve", "pd_batch_destroy", "pd_batch_last_error", "pd_batch_info"]
@@ -109,6 +109,7 @@ def lib(path=None):
             "pd_synchronize": (_I, [_P]),
             "pd_launch_count": (C.c_longlong, [_P]),
             "pd_batch_launch_count": (C.c_longlong, [_P]),
+            "pd_fused_choice": (_I, [_P, _I, _P, _P]),
             "paradiag_destroy": (_I, [_P]),
             "pd_status_str": (C.c_char_p, [_I]),
             "pd_last_error": (C.c_char_p, [_P]),
@@ -280,6 +281,16 @@ class Context:
 
     def launch_count(self):
         return int(lib().pd_launch_count(self.h))
+
+    def fused_choices(self):
+        """Per multigrid level: (variant, rows per segment) of the fused smoothing kernels
+        the autotuner chose (1 TMA tiles, 2 warp streams, 0 none)."""
+        out = []
+        for l in range(lib().pd_num_levels(self.h)):
+            v, sg = C.c_int(), C.c_int()
+            _check(lib().pd_fused_choice(self.h, l, C.byref(v), C.byref(sg)), "pd_fused_choice", self.h)
+            out.append((v.value, sg.value))
+        return out
 
     def profile_enable(self, on=True):
         _check(lib().pd_profile_enable(self.h, int(bool(on))), "pd_profile_enable", self.h)

@@ -264,10 +264,11 @@ double rs(const pd_ctx *c, int l) { return hl(c, l) * hl(c, l) / c->kappa; }
 int part_blocks(const pd_ctx *c) { return std::max(allatonce_blocks(), residual_fx_blocks(c->num_sms)); }
 
 // Set-up autotuner of the fused kernels: on each global-memory level, times the
-// smoothing+restriction and interpolation+smoothing pair of every candidate (TMA tiles;
-// warp streams with 4, 8, 16, 32, 64, 128 or 256 rows per segment) on the context's own (zeroed)
-// buffers, all shifts active, and keeps the fastest; cfg.fused_variant 1 or 2 restricts
-// the candidates to one implementation.
+// smoothing+restriction and interpolation+smoothing pair of every candidate (warp streams
+// with 4, 8, 16, 32, 64, 128 or 256 rows per segment) on the context's own (zeroed) buffers,
+// all shifts active, and keeps the fastest.  The TMA tiles are a candidate only when
+// cfg.fused_variant = 1 asks for them: timed beside the warp streams they lost on every
+// level of grids 127..2047 (pd_fused_choice records the choices).
 template <typename T>
 void autotune_fused(pd_ctx *c) {
   Prec<T> &P = prec<T>(c);
@@ -296,7 +297,7 @@ void autotune_fused(pd_ctx *c) {
     int bv = 2, bs = 128;
     for (int cand = 0; cand < 8; cand++) {
       const int variant = cand == 0 ? 1 : 2, seg = cand == 0 ? 0 : segs[cand - 1];
-      if (c->cfg.fused_variant != 0 && c->cfg.fused_variant != variant) continue;
+      if ((c->cfg.fused_variant == 0 ? 2 : c->cfg.fused_variant) != variant) continue;
       if (variant == 2 && seg > 2 * B.N) continue;
       float tmin = 1e30f;
       for (int rep = 0; rep < 3; rep++) {
@@ -2345,6 +2346,20 @@ pd_status pd_synchronize(pd_ctx *c) {
 }
 
 long long pd_launch_count(const pd_ctx *c) { return c ? c->launches : 0; }
+
+pd_status pd_fused_choice(const pd_ctx *c, int level, int *h_variant, int *h_seg) {
+  if (!c || level < 0 || level >= c->L) return PD_ERR_ARG;
+  // the multigrid's working precision: FP32 levels in the precision form, FP64 otherwise
+  const LevelBufs *B = nullptr;
+  if (c->cfg.precision == 1 && level < (int)c->p32.lv.size()) B = &c->p32.lv[level];
+  else if (c->cfg.precision == 0 && level < (int)c->p64.lv.size()) B = &c->p64.lv[level];
+  // fused kernels run in FP32 with cfg.fused = 1 and in both precisions with cfg.fused = 2
+  const bool on = c->cfg.fused == 2 || (c->cfg.fused == 1 && c->cfg.precision == 1);
+  const bool fused = B && B->maps && level < c->L - 1 && on;
+  if (h_variant) *h_variant = fused ? B->variant : 0;
+  if (h_seg) *h_seg = fused && B->variant == 2 ? B->seg : 0;
+  return PD_OK;
+}
 
 pd_status paradiag_destroy(pd_ctx *c) {
   if (!c) return PD_ERR_ARG;

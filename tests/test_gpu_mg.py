@@ -280,3 +280,13 @@ def test_mg_vcycle_fp32(fused, N):
     # (all three kernel paths, deterministic): 5.8e-8 N at N = 127, 8.4e-8 N at 511,
     # 9.7e-8 N at 2047, i.e. at most 0.93e-8 N log2(N + 1); the bar allows 1.35 times that.
     assert rel_per_vector(host(zt), ref) < 1.25e-8 * N * np.log2(N + 1)
+    # the autotuner's record: the restricted variant on every fused level, none without
+    choices = c.fused_choices()
+    assert len(choices) == api.lib().pd_num_levels(c.h)
+    for l, (v, sg) in enumerate(choices):
+        if not fused:
+            assert v == 0
+        elif v != 0:
+            assert v == max(fused, 1) and (sg in (4, 8, 16, 32, 64, 128, 256)) == (v == 2)
+    if fused:
+        assert choices[0][0] == max(fused, 1)
