@@ -509,11 +509,20 @@ k_fft_inverse_pipe(int N, double *__restrict__ u, View z0, View z1, const int *_
   for (int s0 = 0; s0 < S - 1; s0++) issue(blockIdx.x + s0 * gridDim.x, s0);
   for (int tile = blockIdx.x; tile < total; tile += gridDim.x, q++) {
     issue(tile + (S - 1) * gridDim.x, (q + S - 1) % S);
+    const int i = tile / tpr, c = (tile - i * tpr) * P + p;
+    const long long x = (long long)i * N + c;
+    // the u values this thread accumulates into, requested before the stage wait and the
+    // first pass so that their latency overlaps them
+    double uo[N1];
+    if (accumulate && c < N) {
+#pragma unroll
+      for (int r = 0; r < N1 / N2; r++)
+#pragma unroll
+        for (int k2 = 0; k2 < N2; k2++) uo[N2 * r + k2] = u[(long long)(t + N2 * r + N1 * k2) * m + x];
+    }
     cpa_wait<S - 1>();
     __syncthreads();
     float2 *col = stage + (size_t)(q % S) * n * P;
-    const int i = tile / tpr, c = (tile - i * tpr) * P + p;
-    const long long x = (long long)i * N + c;
     float2 v[N1];
 #pragma unroll
     for (int j1 = 0; j1 < N1; j1++) v[j1] = col[(N2 * j1 + t) * P + p];
@@ -525,11 +534,6 @@ k_fft_inverse_pipe(int N, double *__restrict__ u, View z0, View z1, const int *_
 #pragma unroll
     for (int r = 0; r < N1 / N2; r++) {
       const int k1 = t + N2 * r;
-      double uo[N2];
-      if (accumulate && c < N) {
-#pragma unroll
-        for (int k2 = 0; k2 < N2; k2++) uo[k2] = u[(long long)(k1 + N1 * k2) * m + x];
-      }
       float2 w[N2];
 #pragma unroll
       for (int j2 = 0; j2 < N2; j2++) w[j2] = col[(N2 * k1 + j2) * P + p];
@@ -540,7 +544,7 @@ k_fft_inverse_pipe(int N, double *__restrict__ u, View z0, View z1, const int *_
           const int k = k1 + N1 * k2;
           const float wd = wk[k] * dscale;
           const float re = w[k2].x * wd;
-          u[(long long)k * m + x] = accumulate ? uo[k2] + to_f64(re) : to_f64(re);
+          u[(long long)k * m + x] = accumulate ? uo[N2 * r + k2] + to_f64(re) : to_f64(re);
           if (imag_check) imax = fmaxf(imax, fabsf(w[k2].y * wd));
         }
       }
@@ -642,14 +646,12 @@ void launch_forward_pipe(cudaStream_t s, int num_sms, int N, View g, const void 
   const long long tiles = (long long)N * ((N + kPipeP - 1) / kPipeP);
   if (f32) {
     constexpr size_t smem = fwd_pipe_smem<N1, float>();
-    static int grid1 = 0;
-    if (!grid1) grid1 = pipe_grid(k_fft_forward_pipe<N1, float>, smem, 1 << 30, num_sms);
+    const int grid1 = pipe_grid(k_fft_forward_pipe<N1, float>, smem, 1 << 30, num_sms);
     k_fft_forward_pipe<N1, float><<<(int)std::min<long long>(grid1, tiles), kPipeThreads, smem, s>>>(
         N, g, static_cast<const float *>(f), u0, u0coef, wk, tw);
   } else {
     constexpr size_t smem = fwd_pipe_smem<N1, double>();
-    static int grid1 = 0;
-    if (!grid1) grid1 = pipe_grid(k_fft_forward_pipe<N1, double>, smem, 1 << 30, num_sms);
+    const int grid1 = pipe_grid(k_fft_forward_pipe<N1, double>, smem, 1 << 30, num_sms);
     k_fft_forward_pipe<N1, double><<<(int)std::min<long long>(grid1, tiles), kPipeThreads, smem, s>>>(
         N, g, static_cast<const double *>(f), u0, u0coef, wk, tw);
   }
@@ -664,8 +666,7 @@ void launch_inverse_pipe(cudaStream_t s, int num_sms, int N, double *u, View z0,
   // z1 is read only for the slices final_buf marks; both share the layout of z0
   const bool pairs = z0.pitch % 2 == 0 && z0.plane % 2 == 0 &&
                      reinterpret_cast<uintptr_t>(z0.p) % 16 == 0 && reinterpret_cast<uintptr_t>(z1.p) % 16 == 0;
-  static int grid1 = 0;
-  if (!grid1) grid1 = pipe_grid(k_fft_inverse_pipe<N1, true>, smem, 1 << 30, num_sms);
+  const int grid1 = pipe_grid(k_fft_inverse_pipe<N1, true>, smem, 1 << 30, num_sms);
   const int grid = (int)std::min<long long>(grid1, tiles);
   if (pairs)
     k_fft_inverse_pipe<N1, true><<<grid, kPipeThreads, smem, s>>>(

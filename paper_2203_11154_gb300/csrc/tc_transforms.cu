@@ -183,7 +183,10 @@ constexpr int kFwdK = 64, kFwdNt = 128;   // forward, n <= 64
 constexpr int kFwd2K = 128, kFwd2Nt = 64;  // forward, 64 < n <= 128 (two CTAs per tile)
 constexpr int kInvK = 128, kInvNt = 64;    // inverse, n <= 64
 constexpr int kInv2K = 128, kInv2Nt = 64;  // inverse, 64 < n <= 128 (two-CTA cluster)
-constexpr int kFwdS = 64 * 66 * 4;         // forward epilogue stage: 64 j rows x 32 complex
+// forward epilogue: the accumulator's columns in passes of up to 64 (two chunks of 32, read by
+// 8 warps at once); stage of 64 j rows x the pass's complex points, row stride 2 cols + 2
+template <int NT> __host__ __device__ constexpr int fwd_pass_cols() { return NT < 64 ? NT : 64; }
+template <int NT> __host__ __device__ constexpr int fwd_stage_bytes() { return 64 * (2 * fwd_pass_cols<NT>() + 2) * 4; }
 // tensor memory: A hi at column 0, A lo at column K, the two accumulators from column 2K
 constexpr int kTmemCols = 512;
 static_assert(2 * 128 + 2 * 64 <= kTmemCols && 2 * 64 + 2 * 128 <= kTmemCols, "tensor memory");
@@ -191,7 +194,7 @@ static_assert(2 * 128 + 2 * 64 <= kTmemCols && 2 * 64 + 2 * 128 <= kTmemCols, "t
 // shared memory of the forward: B hi/lo, epilogue stage, input stage [K][NT] of the input
 // type and the initial values of the tile's points, alignment slack
 template <int K, int NT, typename InT> constexpr int fwd_smem() {
-  return 2 * NT * K * 4 + kFwdS + NT * K * (int)sizeof(InT) + NT * 8 + 1024;
+  return 2 * NT * K * 4 + fwd_stage_bytes<NT>() + NT * K * (int)sizeof(InT) + NT * 8 + 1024;
 }
 // the inverse: B hi/lo, stage [rows][NT + 1] (rows: 128, or 2 tile parities x 2 sources x 64
 // in the cluster form), z stage [64 shifts][NT] complex, u stage [64 rows][NT], slack
@@ -232,7 +235,7 @@ k_tc_forward(int N, int n, View g, const InT *__restrict__ f, const double *__re
   unsigned char *sm = align1024(smem_raw);
   unsigned char *sBhi = sm, *sBlo = sm + kB;
   float *S = reinterpret_cast<float *>(sBlo + kB);
-  InT *stage = reinterpret_cast<InT *>(reinterpret_cast<unsigned char *>(S) + kFwdS);  // [K][NT]
+  InT *stage = reinterpret_cast<InT *>(reinterpret_cast<unsigned char *>(S) + fwd_stage_bytes<NT>());  // [K][NT]
   double *su0 = reinterpret_cast<double *>(stage + NT * K);                           // [NT]
   __shared__ uint64_t bar;
   __shared__ uint32_t tmem_slot;
@@ -294,25 +297,28 @@ k_tc_forward(int N, int n, View g, const InT *__restrict__ f, const double *__re
     if constexpr (sizeof(InT) == 8) return f64_to_f32(v, s_in);
     else return v * fs_in;
   };
-  // g of tile t from accumulator buf, 32 columns at a time: lanes of warps 0-3 hold the
-  // rows 2j+q of D, the stage makes the stores coalesced
+  // g of tile t from accumulator buf, PC columns a pass: warp w < PC / 8 reads the lanes
+  // 32 (w mod 4) .. (rows 2j+q of D) of the 32 columns 32 (w / 4) .. of the pass; the stage
+  // makes the stores coalesced
+  constexpr int PC = fwd_pass_cols<NT>(), SRF = 2 * PC + 2;
+  static_assert(4 * (PC / 32) <= kTcThreads / 32, "one warp per lane group and column chunk");
   auto epilogue = [&](int t, int buf) {
     const int i = t / tpr, c0 = (t % tpr) * NT;
-    for (int chunk = 0; chunk < NT / 32; chunk++) {
-      if (warp < 4) {
+    for (int pass = 0; pass < NT / PC; pass++) {
+      if (warp < 4 * (PC / 32)) {
         float v[32];
-        tmem_ld32(acc0 + ((uint32_t)(32 * warp) << 16) + (uint32_t)(buf * NT + 32 * chunk), v);
-        const int row = 32 * warp + lane, j = row >> 1, q = row & 1;
+        const int chunk = warp >> 2, row = 32 * (warp & 3) + lane, j = row >> 1, q = row & 1;
+        tmem_ld32(acc0 + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(buf * NT + PC * pass + 32 * chunk), v);
         if (j < nj)
 #pragma unroll
-          for (int cc = 0; cc < 32; cc++) S[j * 66 + 2 * cc + q] = v[cc];
+          for (int cc = 0; cc < 32; cc++) S[j * SRF + 2 * (32 * chunk + cc) + q] = v[cc];
       }
       __syncthreads();
-      for (int it = tid; it < nj * 32; it += kTcThreads) {
-        const int j = it >> 5, cc = it & 31;
-        const int c = c0 + 32 * chunk + cc;
+      for (int it = tid; it < nj * PC; it += kTcThreads) {
+        const int j = it / PC, cc = it % PC;
+        const int c = c0 + PC * pass + cc;
         if (c < N) {
-          const float2 val = *reinterpret_cast<const float2 *>(&S[j * 66 + 2 * cc]);
+          const float2 val = *reinterpret_cast<const float2 *>(&S[j * SRF + 2 * cc]);
           reinterpret_cast<float2 *>(g.p)[(jbase + j) * g.plane + (long long)i * g.pitch + c] = val;
         }
       }
