@@ -396,14 +396,26 @@ k_tc_forward(int N, int n, View g, const InT *__restrict__ f, const double *__re
 // stage [64][NT] (complex, from z1 where final_buf is set).  Shifts j >= n and points
 // beyond the grid are not copied: the rows j >= n keep the zeros the kernel writes first
 // (V is zero there too), the columns beyond the grid give outputs that are not stored.
+// zsel: bit e set where the thread's e-th copy reads z1 (z1_select, the same in every tile)
 template <int NT>
-__device__ __forceinline__ void copy_z(const View &z0, const View &z1, const int *final_buf, int n, int N,
+__device__ __forceinline__ unsigned z1_select(const int *final_buf, int n, int jbase) {
+  unsigned m = 0;
+  if (final_buf)
+    for (int e = 0; e < 64 * NT / kTcThreads; e++) {
+      const int jj = jbase + ((int)threadIdx.x + e * kTcThreads) / NT;
+      if (jj < n && final_buf[jj]) m |= 1u << e;
+    }
+  return m;
+}
+template <int NT>
+__device__ __forceinline__ void copy_z(const View &z0, const View &z1, unsigned zsel, int n, int N,
                                        int jbase, int i, int c0, uint32_t sbase) {
+  static_assert(64 * NT / kTcThreads <= 32, "the selection mask holds 32 bits");
 #pragma unroll
   for (int e = 0; e < 64 * NT / kTcThreads; e++) {
     const int q = (int)threadIdx.x + e * kTcThreads, jl = q / NT, p = q % NT, jj = jbase + jl;
     if (jj < n && c0 + p < N) {
-      const bool use1 = final_buf && final_buf[jj];
+      const bool use1 = (zsel >> e) & 1u;
       const float2 *zp = reinterpret_cast<const float2 *>(use1 ? z1.p : z0.p);
       const long long plane = use1 ? z1.plane : z0.plane, pitch = use1 ? z1.pitch : z0.pitch;
       cpa(sbase + (uint32_t)(q * 8), zp + jj * plane + (long long)i * pitch + c0 + p, 8, true);
@@ -479,6 +491,7 @@ k_tc_inverse(int N, int n, double *__restrict__ u, View z0, View z1, const int *
   tc_fence_after();
   const uint32_t acc0 = tmem + 2 * K;
   for (int q = tid; q < 64 * NT; q += kTcThreads) zst[q] = make_float2(0.f, 0.f);
+  const unsigned zsel = z1_select<NT>(final_buf, n, 0);
   __syncthreads();
   const long long m = (long long)N * N;
   const int tpr = (int)((z0.pitch + NT - 1) / NT);
@@ -512,7 +525,7 @@ k_tc_inverse(int N, int n, double *__restrict__ u, View z0, View z1, const int *
   int idx = 0, tprev = 0;
   int t = blockIdx.x;
   if (t < total) {
-    copy_z<NT>(z0, z1, final_buf, n, N, 0, t / tpr, (t % tpr) * NT, smem_u32(zst));
+    copy_z<NT>(z0, z1, zsel, n, N, 0, t / tpr, (t % tpr) * NT, smem_u32(zst));
     cpa_commit();
   }
   for (; t < total; t += gridDim.x, idx++) {
@@ -535,7 +548,7 @@ k_tc_inverse(int N, int n, double *__restrict__ u, View z0, View z1, const int *
                         &bar);
     }
     const int tn = t + (int)gridDim.x;
-    if (tn < total) copy_z<NT>(z0, z1, final_buf, n, N, 0, tn / tpr, (tn % tpr) * NT, smem_u32(zst));
+    if (tn < total) copy_z<NT>(z0, z1, zsel, n, N, 0, tn / tpr, (tn % tpr) * NT, smem_u32(zst));
     cpa_commit();
     if (idx > 0) epilogue(tprev, (idx - 1) & 1);
     if (accumulate) {
@@ -637,6 +650,7 @@ k_tc_inverse2(int N, int n, double *__restrict__ u, View z0, View z1, const int 
   tc_fence_after();
   const uint32_t acc0 = tmem + 2 * K;
   for (int q = tid; q < 64 * NT; q += kTcThreads) zst[q] = make_float2(0.f, 0.f);
+  const unsigned zsel = z1_select<NT>(final_buf, n, jbase);
   __syncthreads();
   const uint32_t S_peer = peer_addr(smem_u32(S), rank ^ 1u);
   const long long m = (long long)N * N;
@@ -682,7 +696,7 @@ k_tc_inverse2(int N, int n, double *__restrict__ u, View z0, View z1, const int 
   int idx = 0, tprev = 0, fail_par = 0;
   int t = t0;
   if (t < total) {
-    copy_z<NT>(z0, z1, final_buf, n, N, jbase, t / tpr, (t % tpr) * NT, smem_u32(zst));
+    copy_z<NT>(z0, z1, zsel, n, N, jbase, t / tpr, (t % tpr) * NT, smem_u32(zst));
     cpa_commit();
   }
   for (; t < total; t += tstep, idx++) {
@@ -707,7 +721,7 @@ k_tc_inverse2(int N, int n, double *__restrict__ u, View z0, View z1, const int 
                         &bar);
     }
     const int tn = t + tstep;
-    if (tn < total) copy_z<NT>(z0, z1, final_buf, n, N, jbase, tn / tpr, (tn % tpr) * NT, smem_u32(zst));
+    if (tn < total) copy_z<NT>(z0, z1, zsel, n, N, jbase, tn / tpr, (tn % tpr) * NT, smem_u32(zst));
     cpa_commit();
     if (idx > 0) epilogue(tprev, (idx - 1) & 1);
     if (accumulate) {
