@@ -196,11 +196,12 @@ static_assert(2 * 128 + 2 * 64 <= kTmemCols && 2 * 64 + 2 * 128 <= kTmemCols, "t
 template <int K, int NT, typename InT> constexpr int fwd_smem() {
   return 2 * NT * K * 4 + fwd_stage_bytes<NT>() + NT * K * (int)sizeof(InT) + NT * 8 + 1024;
 }
-// the inverse: B hi/lo, stage [rows][NT + 1] (rows: 128, or 2 tile parities x 2 sources x 64
-// in the cluster form), z stage [64 shifts][NT] complex, u stage [64 rows][NT], slack
-constexpr int kInvSmem = 2 * kInvNt * kInvK * 4 + kM * (kInvNt + 1) * 4 + 64 * kInvNt * 8 + 64 * kInvNt * 8 + 1024;
+// the inverse: B hi/lo, stage [rows][NT + 4] (rows: 128, or 2 tile parities x 2 sources x 64
+// in the cluster form; the row stride keeps 16-byte stores aligned and free of bank
+// conflicts), z stage [64 shifts][NT] complex, u stage [64 rows][NT], slack
+constexpr int kInvSmem = 2 * kInvNt * kInvK * 4 + kM * (kInvNt + 4) * 4 + 64 * kInvNt * 8 + 64 * kInvNt * 8 + 1024;
 constexpr int kInv2Smem =
-    2 * kInv2Nt * kInv2K * 4 + 2 * 2 * 64 * (kInv2Nt + 1) * 4 + 64 * kInv2Nt * 8 + 64 * kInv2Nt * 8 + 1024;
+    2 * kInv2Nt * kInv2K * 4 + 2 * 2 * 64 * (kInv2Nt + 4) * 4 + 64 * kInv2Nt * 8 + 64 * kInv2Nt * 8 + 1024;
 // the opt-in limit per block less the kernels' static shared memory
 constexpr int kSmemLimit = 227 * 1024 - 1024;
 static_assert(fwd_smem<kFwdK, kFwdNt, double>() <= kSmemLimit, "forward (n <= 64) exceeds shared memory");
@@ -463,12 +464,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 k_tc_inverse(int N, int n, double *__restrict__ u, View z0, View z1, const int *__restrict__ final_buf,
              const float *__restrict__ Ahi, const float *__restrict__ Alo, float dscale, int accumulate,
              int imag_check, unsigned long long *imag_bits, int *__restrict__ errflag) {
-  constexpr int NT = kInvNt, K = kInvK, SR = NT + 1;
+  constexpr int NT = kInvNt, K = kInvK, SR = NT + 4;
   constexpr int kB = NT * K * 4;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *sm = align1024(smem_raw);
   unsigned char *sBhi = sm, *sBlo = sm + kB;
-  float *S = reinterpret_cast<float *>(sBlo + kB);                   // [128][NT + 1]
+  float *S = reinterpret_cast<float *>(sBlo + kB);                   // [128][NT + 4]
   float2 *zst = reinterpret_cast<float2 *>(S + kM * SR);             // [64][NT]
   double *ust = reinterpret_cast<double *>(zst + 64 * NT);           // [64][NT]
   __shared__ uint64_t bar;
@@ -505,7 +506,8 @@ k_tc_inverse(int N, int n, double *__restrict__ u, View z0, View z1, const int *
       const int chunk = warp >> 2, row = 32 * (warp & 3) + lane;
       tmem_ld32(acc0 + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(buf * NT + 32 * chunk), v);
 #pragma unroll
-      for (int cc = 0; cc < 32; cc++) S[row * SR + 32 * chunk + cc] = v[cc];
+      for (int cc = 0; cc < 32; cc += 4)
+        *reinterpret_cast<float4 *>(&S[row * SR + 32 * chunk + cc]) = make_float4(v[cc], v[cc + 1], v[cc + 2], v[cc + 3]);
     }
     if (accumulate) cpa_wait<1>();  // this thread's u copies of tile t (the z copies of t + 2 may pend)
     __syncthreads();
@@ -604,8 +606,10 @@ __device__ __forceinline__ uint32_t peer_addr(uint32_t saddr, uint32_t rank) {
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
   return r;
 }
-__device__ __forceinline__ void st_cluster(uint32_t addr, float v) {
-  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+// 16 bytes into the shared memory of a CTA of the cluster (addr 16-byte aligned)
+__device__ __forceinline__ void st_cluster4(uint32_t addr, float a, float b, float c, float d) {
+  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
+               : "memory");
 }
 
 // u_k(p) (+)= dscale Re sum_j V[k][j] z_j(p) for k < 128 and the points p = (i, c0..c0+31):
@@ -621,12 +625,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
 k_tc_inverse2(int N, int n, double *__restrict__ u, View z0, View z1, const int *__restrict__ final_buf,
               const float *__restrict__ Ahi, const float *__restrict__ Alo, float dscale, int accumulate,
               int *__restrict__ errflag) {
-  constexpr int NT = kInv2Nt, K = kInv2K, SR = NT + 1;
+  constexpr int NT = kInv2Nt, K = kInv2K, SR = NT + 4;
   constexpr int kB = NT * K * 4;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *sm = align1024(smem_raw);
   unsigned char *sBhi = sm, *sBlo = sm + kB;
-  float *S = reinterpret_cast<float *>(sBlo + kB);          // [2 parities][2 sources][64][NT + 1]
+  float *S = reinterpret_cast<float *>(sBlo + kB);          // [2 parities][2 sources][64][NT + 4]
   float2 *zst = reinterpret_cast<float2 *>(S + 4 * 64 * SR);  // [64][NT]
   double *ust = reinterpret_cast<double *>(zst + 64 * NT);   // [64][NT]
   __shared__ uint64_t bar;
@@ -672,11 +676,12 @@ k_tc_inverse2(int N, int n, double *__restrict__ u, View z0, View z1, const int 
       tmem_ld32(acc0 + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(buf * NT + 32 * chunk), v);
       if ((row >> 6) == (int)rank) {
 #pragma unroll
-        for (int cc = 0; cc < 32; cc++) Sb[r64 * SR + 32 * chunk + cc] = v[cc];
+        for (int cc = 0; cc < 32; cc += 4)
+          *reinterpret_cast<float4 *>(&Sb[r64 * SR + 32 * chunk + cc]) = make_float4(v[cc], v[cc + 1], v[cc + 2], v[cc + 3]);
       } else {
         const uint32_t base = S_peer + (uint32_t)(((buf * 2 * 64 + 64 + r64) * SR + 32 * chunk) * 4);
 #pragma unroll
-        for (int cc = 0; cc < 32; cc++) st_cluster(base + 4u * cc, v[cc]);
+        for (int cc = 0; cc < 32; cc += 4) st_cluster4(base + 4u * cc, v[cc], v[cc + 1], v[cc + 2], v[cc + 3]);
       }
     }
     if (accumulate) cpa_wait<1>();
