@@ -117,7 +117,8 @@ __global__ void k_round_to_float(long long count, const double *__restrict__ x, 
 }  // namespace
 
 void launch_round_to_float(cudaStream_t s, long long count, const double *x, float *y) {
-  k_round_to_float<<<4 * 152, 256, 0, s>>>(count, x, y);
+  const long long blocks = (count + 255) / 256;
+  k_round_to_float<<<(int)(blocks < 1 ? 1 : (blocks > 65535 ? 65535 : blocks)), 256, 0, s>>>(count, x, y);
 }
 
 void launch_shift_residual(cudaStream_t s, int gx, int N, int n, const double2 *z, const double2 *b,
