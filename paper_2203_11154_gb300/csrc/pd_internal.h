@@ -103,6 +103,8 @@ void launch_shift_residual_fx(cudaStream_t s, int gx, int N, int n, const double
                               const double2 *lam, double off, float oscale, const float *sc, View out,
                               const int *frozen, double *part);
 void launch_round_to_float(cudaStream_t s, long long count, const double *x, float *y);
+// dst = src for n16 16-byte words (both 16-byte aligned), streaming loads and stores
+void launch_stream_copy(cudaStream_t s, int blocks, const void *src, void *dst, long long n16);
 void launch_shift_residual(cudaStream_t s, int gx, int N, int n, const double2 *z, const double2 *b,
                            const double2 *c1, double off, float oscale, const float *sc, View out,
                            const int *frozen, bool want_b, double *part);

@@ -114,7 +114,20 @@ __global__ void k_round_to_float(long long count, const double *__restrict__ x, 
     y[i] = (float)x[i];
 }
 
+// dst = src, 16 bytes a thread and step, with streaming (evict-first) loads and stores:
+// the device-to-host copy of a result into mapped pinned memory, run beside a solve, then
+// displaces less of the solve's L2 working set than a copy-engine transfer does
+__global__ void k_stream_copy(const float4 *__restrict__ src, float4 *__restrict__ dst, long long n16) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n16;
+       i += (long long)gridDim.x * blockDim.x)
+    __stcs(dst + i, __ldcs(src + i));
+}
+
 }  // namespace
+
+void launch_stream_copy(cudaStream_t s, int blocks, const void *src, void *dst, long long n16) {
+  k_stream_copy<<<blocks, 512, 0, s>>>(static_cast<const float4 *>(src), static_cast<float4 *>(dst), n16);
+}
 
 void launch_round_to_float(cudaStream_t s, long long count, const double *x, float *y) {
   const long long blocks = (count + 255) / 256;

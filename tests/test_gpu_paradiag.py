@@ -306,17 +306,24 @@ def test_refinement_residual32_transposed(N, n, alpha):
         assert fn == pytest.approx(np.linalg.norm(f), rel=1e-5)
 
 
-@pytest.mark.parametrize("precision", [1, 0])
-def test_paradiag_host_batch_pipelined(precision):
+@pytest.mark.parametrize("precision,n,out_mem", [(1, 8, "pinned"), (0, 8, "pinned"), (1, 8, "pageable"),
+                                                   (1, 5, "pinned")])
+def test_paradiag_host_batch_pipelined(precision, n, out_mem):
     """paradiag_solve_host_batch: three independent steps with host buffers, copies of the
     neighbouring steps overlapping each solve, each result identical to paradiag_solve on
-    the same input."""
-    N, n, tau, alpha = 63, 8, 1.0 / 8, 1e-3
+    the same input.  u goes out by the streaming copy kernel into pinned memory (n = 8), by
+    the copy engine into pageable memory and for a size that is not a multiple of 16 bytes
+    (n = 5)."""
+    N, tau, alpha = 63, 1.0 / 8, 1e-3
     c = api.alpha_circulant_context(N, n, tau, alpha, precision=precision)
     probs = [inputs.paradiag_problem(N, n, seed=20 + k) for k in range(3)]
     fs = [torch.from_numpy(f).pin_memory() for f, _ in probs]
     u0s = [torch.from_numpy(u0).pin_memory() for _, u0 in probs]
-    us = [torch.empty_like(fs[0]).pin_memory() for _ in range(3)]
+    if out_mem == "pinned":
+        us = [torch.empty_like(fs[0]).pin_memory() for _ in range(3)]
+    else:
+        us = [torch.empty_like(fs[0]) for _ in range(3)]
+        assert not us[0].is_pinned()
     outs = c.paradiag_solve_host_batch(us, fs, u0s)
     for (f, u0), uh, out in zip(probs, us, outs):
         ud = torch.empty(n, N, N, dtype=torch.float64, device="cuda")
