@@ -305,8 +305,11 @@ pd_status paradiag_solve_host(pd_ctx *ctx, double *h_u, const double *h_f, const
  * of step k+1's f and u0 and the device-to-host copy of step k-1's u run on two copy
  * streams (one per direction) that the context creates (once) while step k is solved on
  * the context's stream, through
- * two device staging sets (2 x (f, u, u0)).  h_u[k], h_f[k]: [n][N][N] double host arrays
- * (pinned for full speed); h_u0 NULL or h_u0[k] NULL for no initial-value term.  h_iters,
+ * two device staging sets (2 x (f, u, u0)).  Where h_u[k] is page-locked and 16-byte aligned
+ * (and the array a multiple of 16 bytes), u goes out by a copy kernel of the library writing
+ * the mapped host memory with streaming stores, which disturbs the concurrent solve less than
+ * a copy-engine transfer; otherwise by the copy engine.  h_u[k], h_f[k]: [n][N][N] double host
+ * arrays (pinned for full speed); h_u0 NULL or h_u0[k] NULL for no initial-value term.  h_iters,
  * h_relres: count x n entries; h_stats: count x PD_STATS_LEN (each may be NULL).
  * Synchronises.  Returns the first non-OK status of the steps (PD_ERR_CUDA at once).
  */
