@@ -1,6 +1,6 @@
 """Failure paths and convergence histories through the C ABI.
 
-Failures are made on the host only (SURVEY-style fault injection without a GPU fault): a
+Failures are made on the host only (no kernel is made to fault, trap or hang): a
 NaN placed in a right-hand side must come back as PD_ERR_NAN from every solve entry point,
 in both precisions, and the same context must then solve clean data as before.  The
 per-shift residual history of an FP64 shifted solve is compared with the oracle's history
