@@ -1,8 +1,8 @@
 // Float-float (pairs of FP32) and fixed-point helpers of the residual kernels that avoid
 // FP64 instructions (GB300 issues FP64 at 1/58 of its FP32 rate): the error-free
 // transformations of Knuth (TwoSum), Dekker (FastTwoSum) and the FMA product split, exact
-// power-of-two scaling, FP64 bits -> float-float, and FP64 bits -> three FP32 limbs of a
-// fixed-point value.
+// power-of-two scaling, FP64 bits -> float-float, FP64 bits -> three FP32 limbs of a
+// fixed-point value, and packed (FP32x2) forms of the float-float operations.
 #pragma once
 
 #include <cstdint>
@@ -112,6 +112,63 @@ __device__ __forceinline__ float4 to_limbs(unsigned long long bits, unsigned ema
   l.y = __fmaf_rn(sg, __uint_as_float(E1 | t1), __fmul_rn(sg, -0x1p44f));
   l.z = __fmaf_rn(sg, __uint_as_float(E0 | t0), __fmul_rn(sg, -0x1p23f));
   l.w = 0.f;
+  return l;
+}
+
+// The integer part of to_limbs: the FP32 words X_j (t_j in the mantissa of 2^(23 + 21 j))
+// and the sign as +-1, so that the limbs are sg (X_j - 2^(23 + 21 j)).
+struct LimbBits {
+  uint32_t x2, x1, x0;
+  float sg;
+};
+__device__ __forceinline__ LimbBits limb_bits(unsigned long long bits, unsigned emax) {
+  const uint32_t hw = (uint32_t)(bits >> 32), lw = (uint32_t)bits;
+  const unsigned e = (hw >> 20) & 0x7FFu;
+  const unsigned long long m = ((unsigned long long)((hw & 0xFFFFFu) | 0x100000u) << 32) | lw;
+  const unsigned long long v = shr64(m << 6, emax - e);
+  const uint32_t vl = (uint32_t)v, vh = (uint32_t)(v >> 32);
+  LimbBits b;
+  b.x0 = (150u << 23) | (vl & 0x1FFFFFu);
+  b.x1 = (171u << 23) | (__funnelshift_r(vl, vh, 21) & 0x1FFFFFu);
+  b.x2 = (192u << 23) | (vh >> 10);
+  b.sg = __uint_as_float((hw & 0x80000000u) | 0x3F800000u);
+  return b;
+}
+
+// Packed FP32x2 arithmetic (sm_100 and later: one FADD2 / FMUL2 / FFMA2 instruction does
+// the operation on both components, each rounded as its scalar form), for kernels that
+// carry two independent points (or the two components of a complex value) side by side.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+struct DF2 {  // two float-float values: (hi.x, lo.x) and (hi.y, lo.y)
+  float2 hi, lo;
+};
+__device__ __forceinline__ DF2 two_sum2(float2 a, float2 b) {
+  const float2 s = add2(a, b), bb = sub2(s, a);
+  return {s, add2(sub2(a, sub2(s, bb)), sub2(b, bb))};
+}
+__device__ __forceinline__ DF2 fast_two_sum2(float2 a, float2 b) {
+  const float2 s = add2(a, b);
+  return {s, sub2(b, sub2(s, a))};
+}
+__device__ __forceinline__ DF2 mul_un2(DF2 c, DF2 x) {
+  const float2 p = mul2(c.hi, x.hi);
+  return {p, add2(fma2(c.hi, x.hi, neg2(p)), fma2(c.hi, x.lo, mul2(c.lo, x.hi)))};
+}
+// the three limbs of two values (components x and y), from their LimbBits
+struct Limbs2 {
+  float2 l2, l1, l0;
+};
+__device__ __forceinline__ Limbs2 limbs2(const LimbBits &a, const LimbBits &b) {
+  const float2 sg = make_float2(a.sg, b.sg);
+  Limbs2 l;
+  l.l2 = fma2(sg, make_float2(__uint_as_float(a.x2), __uint_as_float(b.x2)), mul2(sg, bc2(-0x1p65f)));
+  l.l1 = fma2(sg, make_float2(__uint_as_float(a.x1), __uint_as_float(b.x1)), mul2(sg, bc2(-0x1p44f)));
+  l.l0 = fma2(sg, make_float2(__uint_as_float(a.x0), __uint_as_float(b.x0)), mul2(sg, bc2(-0x1p23f)));
   return l;
 }
 

@@ -84,6 +84,8 @@ void launch_fft_inverse(cudaStream_t s, int num_sms, int N, int n, double *u, Vi
                         T dscale, bool accumulate, bool imag_check, unsigned long long *imag_bits);
 
 // ---- residual of eq. (1) without FP64 arithmetic (residual_ws.cu) ----
+// CTAs of one residual: the interior-tile kernel takes two thirds, the edge-tile kernel the
+// rest (part[] holds two sums per CTA of both)
 int residual_fx_blocks(int num_sms);
 // r = oscale (fhat - (B kron I + kappa I kron A) u) in FP32 for the bidiagonal B with
 // nonzeros at (k,k) and (k, k+off mod n); kbd[k] = (bd_k, bs_k), ku0[k] = u0coef_k and ihf =

@@ -9,7 +9,7 @@
 // of |fscale fhat|^2.
 //
 //   - Work item of a warp: a strip of 30 output columns (lanes 1..30; lanes 0 and 31 carry
-//     the halo columns) by kWsR rows, walked through a run of consecutive time steps in
+//     the halo columns) by kWsR = 6 rows, walked through a run of consecutive time steps in
 //     the order in which u_{k+off} precedes u_k (ascending k for off = -1, descending for
 //     off = +1).  A lane holds its column's kWsR + 2 values of u_k in registers: vertical
 //     neighbours are its own, horizontal ones come from the adjacent lanes by shuffles.
@@ -17,6 +17,13 @@
 //     its points' u_k for the next step's bs term, so u is read from memory once (plus the
 //     halo rows and columns, from L2).  No shared memory and no barrier until the final
 //     CTA sum.
+//   - Packed arithmetic: output rows t and t + 3 of a tile are the two components of every
+//     FP32 operation (FADD2 / FMUL2 / FFMA2), each component rounded exactly as the scalar
+//     operation, so the results are those of the scalar formulas bit for bit.
+//   - Interior and edge tiles are two kernels: the interior one (every row and column the
+//     tile reads inside the grid) loads without bounds checks; the edge one walks the
+//     remaining tiles in short runs of time steps.  Compiled apart, each keeps its state in
+//     registers (compiled together they spilled).
 //   - Fixed point: one scale per warp tile and step, 2^-S with S = 1081 - (largest biased
 //     exponent of the tile's (kWsR + 2) x 32 values, a warp max); every value becomes three
 //     exact FP32 limbs (ff::to_limbs), so the stencil difference 4 u_k - (sum of the
@@ -56,159 +63,219 @@ __device__ __forceinline__ int ws_step(const WsGeom &g, int p) { return g.off < 
 
 // FMODE 0: fhat from f and u0; 1: the same, also written to the cache fc_out as float-float
 // pairs; 2: fhat read from the cache fc_in.  kbd[k] = (bd_k, bs_k) and ku0[k] = u0coef_k as
-// float-float pairs, ihf = kappa / h^2 likewise.  part[2 blockIdx.x] = sum |oscale r|^2,
-// part[2 blockIdx.x + 1] = sum |fscale fhat|^2 (when want_f).
-template <int FMODE>
-__global__ void __launch_bounds__(kWsThreads, 2)
-k_residual_ws(WsGeom g, float *__restrict__ r, const double *__restrict__ u,
-              const double *__restrict__ f, const double *__restrict__ u0,
-              const float4 *__restrict__ kbd, const float2 *__restrict__ ku0, float2 ihf,
-              float oscale, float fscale, int want_f, double *__restrict__ part,
-              const float2 *__restrict__ fc_in, float2 *__restrict__ fc_out) {
+// float-float pairs, ihd = kappa / h^2 likewise.  part[2 b] = sum |oscale r|^2,
+// part[2 b + 1] = sum |fscale fhat|^2 (when want_f) of CTA b.
+struct WsArgs {
+  float *r;
+  const double *u, *f, *u0;
+  const float4 *kbd;
+  const float2 *ku0;
+  DF ihd;
+  float oscale, fscale;
+  int want_f;
+  const float2 *fc_in;
+  float2 *fc_out;
+};
+
+// horizontal neighbours of both components from the adjacent lanes, summed
+__device__ __forceinline__ float2 shfl_sum2(float2 v) {
+  return add2(make_float2(__shfl_up_sync(0xffffffffu, v.x, 1), __shfl_up_sync(0xffffffffu, v.y, 1)),
+              make_float2(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1)));
+}
+// 4 c - (u + d + the horizontal neighbours of c) of one limb, exact
+__device__ __forceinline__ float2 stencil2(float2 u, float2 c, float2 d) {
+  return fma2(bc2(4.f), c, neg2(add2(add2(u, d), shfl_sum2(c))));
+}
+
+// A tile is interior when its rows i0 - 1 .. i0 + kWsR and the strip's 32 columns c0 ..
+// c0 + 31 all lie inside the grid: row blocks by in [1, (N - 1) / kWsR - 1], strips sx in
+// [1, (N - 31) / kWsOut].
+__host__ __device__ __forceinline__ bool ws_interior(int N, int i0, int c0) {
+  return i0 >= 1 && i0 + kWsR < N && c0 >= 0 && c0 + 31 < N;
+}
+
+// One work item: the tile at rows i0.., the lane's column c, time-walk chunk q.  Output rows
+// t and t + 3 (t < 3) are the components of the packed operations; Q[e] holds the limbs of
+// rows e and e + 3 of the column (rows i0 - 1 + e), so output pair t reads Q[t] (above),
+// Q[t + 1] (centre) and Q[t + 2] (below).
+template <int FMODE, bool FULL>
+__device__ __forceinline__ void ws_item(const WsGeom &g, const WsArgs &A, int q, int i0, int c,
+                                        int lane, DF &ar, DF &af) {
   constexpr int R = kWsR;
-  __shared__ float2 red[2][kWsWarps];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int H = R / 2;
+  static_assert(R == 6, "packed row pairs (t, t + 3)");
   const int N = g.N;
   const long long m = (long long)N * N;
-  const DF ihd = {ihf.x, ihf.y};
-  DF ar = {0.f, 0.f}, af = {0.f, 0.f};
-  for (int it = blockIdx.x * kWsWarps + warp; it < g.items; it += gridDim.x * kWsWarps) {
-    const int q = it / g.tiles, t0 = it - q * g.tiles;
-    const int by = t0 / g.tx, sx = t0 - by * g.tx;
-    const int pbeg = (int)((long long)q * g.n / g.nch), pend = (int)((long long)(q + 1) * g.n / g.nch);
-    const int i0 = by * R;
-    const int c = sx * kWsOut - 1 + lane;
-    const bool cin = (unsigned)c < (unsigned)N;
-    const bool outc = lane >= 1 && lane <= kWsOut && cin;
-    const int nr = min(R, N - i0);  // output rows inside the grid
-    const long long cc = cin ? c : 0;
-    // the lane's column of one time step, rows i0 - 1 .. i0 + R (zero outside the grid)
-    unsigned long long raw[R + 2];
-    auto load_u = [&](int k) {
-      const double *uk = u + (long long)k * m + cc;
+  const int pbeg = (int)((long long)q * g.n / g.nch), pend = (int)((long long)(q + 1) * g.n / g.nch);
+  const bool cin = FULL || (unsigned)c < (unsigned)N;
+  const bool outc = lane >= 1 && lane <= kWsOut && cin;
+  const int nr = FULL ? R : min(R, N - i0);  // output rows inside the grid
+  const long long cc = cin ? c : 0;
+  // the scaling of output rows (t, t + 3): oscale, 0 outside the grid (so that they add
+  // nothing to the sums)
+  float2 osc[H];
 #pragma unroll
-      for (int e = 0; e < R + 2; e++) {
-        const int i = i0 - 1 + e;
-        const bool ok = cin && (unsigned)i < (unsigned)N;
-        raw[e] = ok ? (unsigned long long)__double_as_longlong(uk[(long long)i * N]) : 0ull;
+  for (int t = 0; t < H; t++)
+    osc[t] = make_float2(outc && t < nr ? A.oscale : 0.f, outc && t + H < nr ? A.oscale : 0.f);
+  const long long rb = (long long)(i0 - 1) * N + cc;  // row i0 - 1 of the lane's column
+  // the lane's column of one time step, rows i0 - 1 .. i0 + R (zero outside the grid)
+  unsigned long long raw[R + 2];
+  auto load_u = [&](int k) {
+    const double *uk = A.u + (long long)k * m + rb;
+#pragma unroll
+    for (int e = 0; e < R + 2; e++) {
+      const bool ok = FULL || (cin && (unsigned)(i0 - 1 + e) < (unsigned)N);
+      raw[e] = ok ? (unsigned long long)__double_as_longlong(uk[(long long)e * N]) : 0ull;
+    }
+  };
+  load_u(ws_step(g, pbeg));
+  DF2 un[H];  // u_{k+off} of rows (t, t + 3), in the previous step's units
+  int s_prev = 0;
+  bool bad_prev = false;
+  for (int p = pbeg; p < pend; p++) {
+    const int k = ws_step(g, p);
+    const bool first = p == pbeg;
+    const long long kx0 = (long long)k * m + rb + N;  // the lane's row i0 in plane k
+    // this step's fhat (cache) or f of the lane's points: 64-bit words
+    unsigned long long fb[R];
+#pragma unroll
+    for (int t = 0; t < R; t++) {
+      const bool ok = FULL || (outc && t < nr);
+      if (FMODE == 2)
+        fb[t] = ok ? *reinterpret_cast<const unsigned long long *>(A.fc_in + kx0 + (long long)t * N) : 0ull;
+      else
+        fb[t] = ok ? (unsigned long long)__double_as_longlong(A.f[kx0 + (long long)t * N]) : 0ull;
+    }
+    // first step of the item: u_{k+off} from memory (FP64, split below)
+    unsigned long long ub[R];
+    if (first) {
+      const int kp = (k + g.off + g.n) % g.n;
+      const double *up = A.u + (long long)kp * m + rb + N;
+#pragma unroll
+      for (int t = 0; t < R; t++)
+        ub[t] = (outc && t < nr) ? (unsigned long long)__double_as_longlong(up[(long long)t * N]) : 0ull;
+    }
+    // largest exponent of the warp tile (the largest high word without its sign bit has
+    // the largest exponent), then the limbs
+    unsigned em = 0;
+#pragma unroll
+    for (int e = 0; e < R + 2; e++) em = max(em, (unsigned)(raw[e] >> 32) & 0x7FFFFFFFu);
+    em = __reduce_max_sync(0xffffffffu, em) >> 20;
+    LimbBits lb[R + 2];
+#pragma unroll
+    for (int e = 0; e < R + 2; e++) lb[e] = limb_bits(raw[e], em);
+    Limbs2 Q[H + 2];
+#pragma unroll
+    for (int e = 0; e < H + 2; e++) Q[e] = limbs2(lb[e], lb[e + H]);
+    // the next step's column, while this one is computed
+    if (p + 1 < pend) load_u(ws_step(g, p + 1));
+    const float4 kb = A.kbd[k];
+    // (kappa/h^2) 2^-S and bd_k 2^-S multiply fixed-point values, bs_k 2^-S' those of the
+    // previous step (beyond S = 252, |u| < 2^-170: the products are 0)
+    const bool bad = em > 1081 + 126;  // Inf/NaN or |u| >= 2^186 in the tile
+    const int S = 1081 - (int)em, sc = S > 252 ? 252 : S;
+    const DF c3 = df_scale_down(A.ihd, sc);
+    const DF cb = df_scale_down(DF{kb.x, kb.y}, sc);
+    const DF cs = first ? DF{kb.z, kb.w} : df_scale_down(DF{kb.z, kb.w}, s_prev > 252 ? 252 : s_prev);
+    const DF2 c32 = {bc2(c3.hi), bc2(c3.lo)}, cb2 = {bc2(cb.hi), bc2(cb.lo)}, cs2 = {bc2(cs.hi), bc2(cs.lo)};
+    const bool nan_out = bad || (!first && bad_prev);
+    DF ck = {0.f, 0.f};
+    bool has_u0 = false;
+    if (FMODE != 2 && A.u0) {
+      const float2 c2 = A.ku0[k];
+      ck = DF{c2.x, c2.y};
+      has_u0 = c2.x != 0.f || c2.y != 0.f;
+    }
+    if (first) {
+#pragma unroll
+      for (int t = 0; t < H; t++) {
+        const DF a = split_bits((uint32_t)(ub[t] >> 32), (uint32_t)ub[t]);
+        const DF b = split_bits((uint32_t)(ub[t + H] >> 32), (uint32_t)ub[t + H]);
+        un[t] = DF2{make_float2(a.hi, b.hi), make_float2(a.lo, b.lo)};
       }
-    };
-    load_u(ws_step(g, pbeg));
-    DF un[R];  // u_{k+off} of the lane's points, in the previous step's units
-    int s_prev = 0;
-    bool bad_prev = false;
-    for (int p = pbeg; p < pend; p++) {
-      const int k = ws_step(g, p);
-      const bool first = p == pbeg;
-      const long long kx0 = (long long)k * m + (long long)i0 * N + cc;  // the lane's row i0 in plane k
-      // this step's fhat (cache) or f of the lane's points: 64-bit words
-      unsigned long long fb[R];
+    }
+    float2 rowr = make_float2(0.f, 0.f);
+    float rowf = 0.f;
 #pragma unroll
-      for (int t = 0; t < R; t++) {
-        const bool ok = outc && t < nr;
-        if (FMODE == 2)
-          fb[t] = ok ? *reinterpret_cast<const unsigned long long *>(fc_in + kx0 + (long long)t * N) : 0ull;
-        else
-          fb[t] = ok ? (unsigned long long)__double_as_longlong(f[kx0 + (long long)t * N]) : 0ull;
-      }
-      // first step of the item: u_{k+off} from memory (FP64, split below)
-      unsigned long long ub[R];
-      if (first) {
-        const int kp = (k + g.off + g.n) % g.n;
-        const double *up = u + (long long)kp * m + (long long)i0 * N + cc;
+    for (int t = 0; t < H; t++) {
+      // the exact stencil difference per limb, then as a float-float pair
+      const Limbs2 &U = Q[t], &C = Q[t + 1], &D = Q[t + 2];
+      const float2 a2 = stencil2(U.l2, C.l2, D.l2);
+      const float2 a1 = stencil2(U.l1, C.l1, D.l1);
+      const float2 a0 = stencil2(U.l0, C.l0, D.l0);
+      DF2 t1 = two_sum2(a2, a1);
+      t1.lo = add2(t1.lo, a0);
+      DF2 uc = fast_two_sum2(C.l2, C.l1);
+      uc.lo = add2(uc.lo, C.l0);
+      const DF2 unt = un[t];
+      un[t] = uc;
+      // fhat of rows t and t + 3
+      DF fa, fz;
 #pragma unroll
-        for (int t = 0; t < R; t++)
-          ub[t] = (outc && t < nr) ? (unsigned long long)__double_as_longlong(up[(long long)t * N]) : 0ull;
-      }
-      // largest exponent of the warp tile (the largest high word without its sign bit has
-      // the largest exponent), then the limbs
-      unsigned em = 0;
-#pragma unroll
-      for (int e = 0; e < R + 2; e++) em = max(em, (unsigned)(raw[e] >> 32) & 0x7FFFFFFFu);
-      em = __reduce_max_sync(0xffffffffu, em) >> 20;
-      float lx[R + 2], ly[R + 2], lz[R + 2];
-#pragma unroll
-      for (int e = 0; e < R + 2; e++) {
-        const float4 l4 = to_limbs(raw[e], em);
-        lx[e] = l4.x;
-        ly[e] = l4.y;
-        lz[e] = l4.z;
-      }
-      // the next step's column, while this one is computed
-      if (p + 1 < pend) load_u(ws_step(g, p + 1));
-      const float4 kb = kbd[k];
-      // (kappa/h^2) 2^-S and bd_k 2^-S multiply fixed-point values, bs_k 2^-S' those of the
-      // previous step (beyond S = 252, |u| < 2^-170: the products are 0)
-      const bool bad = em > 1081 + 126;  // Inf/NaN or |u| >= 2^186 in the tile
-      const int S = 1081 - (int)em, sc = S > 252 ? 252 : S;
-      const DF c3 = df_scale_down(ihd, sc);
-      const DF cb = df_scale_down(DF{kb.x, kb.y}, sc);
-      const DF cs = first ? DF{kb.z, kb.w} : df_scale_down(DF{kb.z, kb.w}, s_prev > 252 ? 252 : s_prev);
-      const bool nan_out = bad || (!first && bad_prev);
-      DF ck = {0.f, 0.f};
-      bool has_u0 = false;
-      if (FMODE != 2 && u0) {
-        const float2 c2 = ku0[k];
-        ck = DF{c2.x, c2.y};
-        has_u0 = c2.x != 0.f || c2.y != 0.f;
-      }
-      if (first) {
-#pragma unroll
-        for (int t = 0; t < R; t++) un[t] = split_bits((uint32_t)(ub[t] >> 32), (uint32_t)ub[t]);
-      }
-      float rowr = 0.f, rowf = 0.f;
-#pragma unroll
-      for (int t = 0; t < R; t++) {
-        // the exact stencil difference per limb, then as a float-float pair
-        const float hx = __shfl_up_sync(0xffffffffu, lx[t + 1], 1) + __shfl_down_sync(0xffffffffu, lx[t + 1], 1);
-        const float hy = __shfl_up_sync(0xffffffffu, ly[t + 1], 1) + __shfl_down_sync(0xffffffffu, ly[t + 1], 1);
-        const float hz = __shfl_up_sync(0xffffffffu, lz[t + 1], 1) + __shfl_down_sync(0xffffffffu, lz[t + 1], 1);
-        const float a2 = __fmaf_rn(4.f, lx[t + 1], -__fadd_rn(__fadd_rn(lx[t], lx[t + 2]), hx));
-        const float a1 = __fmaf_rn(4.f, ly[t + 1], -__fadd_rn(__fadd_rn(ly[t], ly[t + 2]), hy));
-        const float a0 = __fmaf_rn(4.f, lz[t + 1], -__fadd_rn(__fadd_rn(lz[t], lz[t + 2]), hz));
-        DF t1 = two_sum(a2, a1);
-        t1.lo = __fadd_rn(t1.lo, a0);
-        DF uc = fast_two_sum(lx[t + 1], ly[t + 1]);
-        uc.lo = __fadd_rn(uc.lo, lz[t + 1]);
-        const DF unt = un[t];
-        un[t] = uc;
-        const bool ok = outc && t < nr;
-        const long long kx = kx0 + (long long)t * N;
+      for (int h = 0; h < 2; h++) {
+        const int tt = t + h * H;
+        const bool ok = outc && tt < nr;
         DF fh;
         if (FMODE == 2) {
-          fh = DF{__uint_as_float((uint32_t)fb[t]), __uint_as_float((uint32_t)(fb[t] >> 32))};
+          fh = DF{__uint_as_float((uint32_t)fb[tt]), __uint_as_float((uint32_t)(fb[tt] >> 32))};
         } else {
-          fh = split_bits((uint32_t)(fb[t] >> 32), (uint32_t)fb[t]);
-          if (has_u0 && ok) fh = df_add(fh, df_mul(ck, split(u0[(long long)(i0 + t) * N + cc])));
-          if (FMODE == 1 && ok) fc_out[kx] = make_float2(fh.hi, fh.lo);
-        }
-        const DF p1 = df_mul_un(cb, uc), p2 = df_mul_un(cs, unt), p3 = df_mul_un(c3, t1);
-        // fhat - p1 - p2 - p3: the hi parts summed exactly, the low parts and errors in FP32
-        const float lo = __fsub_rn(fh.lo, __fadd_rn(__fadd_rn(p1.lo, p2.lo), p3.lo));
-        DF s = two_sum(fh.hi, -p1.hi);
-        float el = s.lo;
-        s = two_sum(s.hi, -p2.hi);
-        el = __fadd_rn(el, s.lo);
-        s = two_sum(s.hi, -p3.hi);
-        el = __fadd_rn(el, s.lo);
-        float rv = __fmul_rn(__fadd_rn(s.hi, __fadd_rn(lo, el)), oscale);
-        if (nan_out) rv = __int_as_float(0x7FC00000);
-        if (ok) {
-          r[kx] = rv;
-          rowr = __fmaf_rn(rv, rv, rowr);
-          if (want_f) {
-            const float fv = __fmul_rn(__fadd_rn(fh.hi, fh.lo), fscale);
+          fh = split_bits((uint32_t)(fb[tt] >> 32), (uint32_t)fb[tt]);
+          if (has_u0 && ok) fh = df_add(fh, df_mul(ck, split(A.u0[rb + (long long)(tt + 1) * N])));
+          if (FMODE == 1 && ok) A.fc_out[kx0 + (long long)tt * N] = make_float2(fh.hi, fh.lo);
+          if (A.want_f && ok) {
+            const float fv = __fmul_rn(__fadd_rn(fh.hi, fh.lo), A.fscale);
             rowf = __fmaf_rn(fv, fv, rowf);
           }
         }
+        if (h == 0) fa = fh;
+        else fz = fh;
       }
-      ar = df_add(ar, DF{rowr, 0.f});
-      if (want_f) af = df_add(af, DF{rowf, 0.f});
-      s_prev = S;
-      bad_prev = bad;
+      const DF2 fh = {make_float2(fa.hi, fz.hi), make_float2(fa.lo, fz.lo)};
+      const DF2 p1 = mul_un2(cb2, uc), p2 = mul_un2(cs2, unt), p3 = mul_un2(c32, t1);
+      // fhat - p1 - p2 - p3: the hi parts summed exactly, the low parts and errors in FP32
+      const float2 lo = sub2(fh.lo, add2(add2(p1.lo, p2.lo), p3.lo));
+      DF2 s = two_sum2(fh.hi, neg2(p1.hi));
+      float2 el = s.lo;
+      s = two_sum2(s.hi, neg2(p2.hi));
+      el = add2(el, s.lo);
+      s = two_sum2(s.hi, neg2(p3.hi));
+      el = add2(el, s.lo);
+      float2 o = osc[t];
+      if (nan_out) o = bc2(__int_as_float(0x7FC00000));
+      const float2 rv = mul2(add2(s.hi, add2(lo, el)), o);
+      if (outc && t < nr) A.r[kx0 + (long long)t * N] = rv.x;
+      if (outc && t + H < nr) A.r[kx0 + (long long)(t + H) * N] = rv.y;
+      rowr = fma2(rv, rv, rowr);
+    }
+    ar = df_add(ar, DF{__fadd_rn(rowr.x, rowr.y), 0.f});
+    if (A.want_f) af = df_add(af, DF{rowf, 0.f});
+    s_prev = S;
+    bad_prev = bad;
+  }
+}
+
+// FULL: the interior tiles (g.tx counts the interior strips, g.tiles = interior strips x
+// interior row blocks); else every tile but the interior ones.  CTA sums: float-float over
+// the warps, one conversion to FP64 per CTA.
+template <int FMODE, bool FULL>
+__global__ void __launch_bounds__(kWsThreads, 2)
+k_residual_ws(const __grid_constant__ WsGeom g, const __grid_constant__ WsArgs A,
+              double *__restrict__ part) {
+  constexpr int R = kWsR;
+  __shared__ float2 red[2][kWsWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  DF ar = {0.f, 0.f}, af = {0.f, 0.f};
+  for (int it = blockIdx.x * kWsWarps + warp; it < g.items; it += gridDim.x * kWsWarps) {
+    const int q = it / g.tiles, t0 = it - q * g.tiles;
+    if (FULL) {
+      const int by = 1 + t0 / g.tx, sx = 1 + t0 % g.tx;
+      ws_item<FMODE, true>(g, A, q, by * R, sx * kWsOut - 1 + lane, lane, ar, af);
+    } else {
+      const int by = t0 / g.tx, sx = t0 - by * g.tx;
+      const int i0 = by * R, c0 = sx * kWsOut - 1;
+      if (!ws_interior(g.N, i0, c0)) ws_item<FMODE, false>(g, A, q, i0, c0 + lane, lane, ar, af);
     }
   }
-  // CTA sums: float-float over the warps, one conversion to FP64 per CTA
   for (int o = 16; o > 0; o >>= 1) {
     ar = df_add(ar, df_shfl_down(ar, o));
     af = df_add(af, df_shfl_down(af, o));
@@ -229,12 +296,35 @@ k_residual_ws(WsGeom g, float *__restrict__ r, const double *__restrict__ u,
   }
 }
 
+// time-step runs: enough items for about eight per warp (the tail of a static
+// distribution then costs little), runs of at least two steps
+void ws_chunks(WsGeom &g, long long work_tiles, int blocks) {
+  const long long warps = (long long)blocks * kWsWarps;
+  g.nch = 1;
+  while (work_tiles * g.nch < 8 * warps && g.n / (2 * g.nch) >= 2) g.nch *= 2;
+  g.items = g.tiles * g.nch;
+}
+
+// the interior kernel on `blocks` CTAs (partial sums part[0 .. 2 blocks)), then the edge
+// kernel on `blocks_edge` CTAs (part[2 blocks ..))
 template <int FMODE>
-void launch_ws(cudaStream_t s, int blocks, const WsGeom &g, float *r, const double *u, const double *f,
-               const double *u0, const float4 *kbd, const float2 *ku0, float2 ihf, float oscale,
-               float fscale, bool want_f, double *part, const float2 *fc_in, float2 *fc_out) {
-  k_residual_ws<FMODE><<<blocks, kWsThreads, 0, s>>>(g, r, u, f, u0, kbd, ku0, ihf, oscale, fscale,
-                                                     want_f ? 1 : 0, part, fc_in, fc_out);
+void launch_ws(cudaStream_t s, int blocks, int blocks_edge, int N, int n, int off, const WsArgs &A,
+               double *part) {
+  WsGeom g;
+  g.N = N;
+  g.n = n;
+  g.off = off < 0 ? -1 : 1;
+  const int ty_in = (N - 1) / kWsR - 1, tx_in = (N - 31) / kWsOut;
+  WsGeom gi = g;
+  gi.tx = std::max(tx_in, 1);
+  gi.tiles = tx_in >= 1 && ty_in >= 1 ? tx_in * ty_in : 0;
+  ws_chunks(gi, gi.tiles, blocks);
+  k_residual_ws<FMODE, true><<<blocks, kWsThreads, 0, s>>>(gi, A, part);
+  WsGeom ge = g;
+  ge.tx = (N + kWsOut - 1) / kWsOut;
+  ge.tiles = ge.tx * ((N + kWsR - 1) / kWsR);
+  ws_chunks(ge, (long long)ge.tiles - gi.tiles, blocks_edge);
+  k_residual_ws<FMODE, false><<<blocks_edge, kWsThreads, 0, s>>>(ge, A, part + 2 * blocks);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -390,7 +480,8 @@ k_shift_residual_ws(int N, const double2 *__restrict__ z, const double2 *__restr
 
 }  // namespace
 
-int residual_fx_blocks(int num_sms) { return 2 * num_sms; }
+// two CTAs per SM for the interior tiles, one per SM for the edge tiles
+int residual_fx_blocks(int num_sms) { return 3 * num_sms; }
 
 // CTAs per shift of the shifted residuals: about eight waves of two CTAs per SM over all
 // shifts (the CTAs of a wave do equal work, so a last partial wave costs at most an
@@ -413,24 +504,14 @@ void launch_residual_fx(cudaStream_t s, int blocks, int N, int n, int off, float
                         const double *u, const double *f, const double *u0, const float4 *kbd,
                         const float2 *ku0, float oscale, float fscale, bool want_f, double *part,
                         const float2 *fc_in, float2 *fc_out) {
-  WsGeom g;
-  g.N = N;
-  g.n = n;
-  g.off = off < 0 ? -1 : 1;
-  g.tx = (N + kWsOut - 1) / kWsOut;
-  g.tiles = g.tx * ((N + kWsR - 1) / kWsR);
-  // time-step runs: enough items for about eight per warp (the tail of a static
-  // distribution then costs little), runs of at least two steps
-  const long long warps = (long long)blocks * kWsWarps;
-  g.nch = 1;
-  while ((long long)g.tiles * g.nch < 8 * warps && n / (2 * g.nch) >= 2) g.nch *= 2;
-  g.items = g.tiles * g.nch;
+  const WsArgs A{r, u, f, u0, kbd, ku0, DF{ihf.x, ihf.y}, oscale, fscale, want_f ? 1 : 0, fc_in, fc_out};
+  const int be = std::max(1, blocks / 3), bi = std::max(1, blocks - be);
   if (fc_in)
-    launch_ws<2>(s, blocks, g, r, u, f, u0, kbd, ku0, ihf, oscale, fscale, want_f, part, fc_in, nullptr);
+    launch_ws<2>(s, bi, be, N, n, off, A, part);
   else if (fc_out)
-    launch_ws<1>(s, blocks, g, r, u, f, u0, kbd, ku0, ihf, oscale, fscale, want_f, part, nullptr, fc_out);
+    launch_ws<1>(s, bi, be, N, n, off, A, part);
   else
-    launch_ws<0>(s, blocks, g, r, u, f, u0, kbd, ku0, ihf, oscale, fscale, want_f, part, nullptr, nullptr);
+    launch_ws<0>(s, bi, be, N, n, off, A, part);
 }
 
 }  // namespace pd
