@@ -337,61 +337,114 @@ void launch_ws(cudaStream_t s, int blocks, int blocks_edge, int N, int n, int of
 // 1..30) by kSwR rows of one shift; each complex component has its own fixed-point scale
 // (warp max of the tile's exponents), its exact stencil difference in three FP32 limbs,
 // and z itself in the tile's units from the limbs; lam_j z_j and the sums are float-float
-// with the constants scaled to those units.  The next tile's z is loaded while the
-// current one is computed.  Grid (gx, n): CTA x of shift j takes the tiles x, x + gx, ...
-// (one per warp); frozen shifts get a zero right-hand side and no sums.
+// with the constants scaled to those units.  The real and imaginary components are the
+// two components of the packed FP32x2 operations.  The next tile's z is loaded while the
+// current one is computed.  Interior tiles (every row and column read inside the grid)
+// and edge tiles are two kernels, compiled apart; in each, CTA x of shift j takes that
+// kernel's tiles x, x + gx, ... (one per warp); frozen shifts get a zero right-hand side
+// and no sums.
 constexpr int kSwR = 4;
 
+// interior tiles: rows i0 - 1 .. i0 + kSwR and columns c0 .. c0 + 31 inside the grid, i.e.
+// row blocks [1, ty_in], strips [1, tx_in]
+struct SwGeom {
+  int N, tx, ty, tx_in, ty_in;
+};
+__host__ __device__ __forceinline__ SwGeom sw_geom(int N) {
+  SwGeom g;
+  g.N = N;
+  g.tx = (N + kWsOut - 1) / kWsOut;
+  g.ty = (N + kSwR - 1) / kSwR;
+  g.tx_in = N > 31 ? (N - 31) / kWsOut : 0;
+  g.ty_in = N > 1 + kSwR ? (N - 1) / kSwR - 1 : 0;
+  if (g.tx_in == 0 || g.ty_in == 0) g.tx_in = g.ty_in = 0;
+  return g;
+}
+__host__ __device__ __forceinline__ int sw_tiles(const SwGeom &g, bool interior) {
+  const int in = g.tx_in * g.ty_in;
+  return interior ? in : g.tx * g.ty - in;
+}
+// tile t of the interior or of the edge set -> (row block, strip); the edge set is the rows
+// outside [1, ty_in] (all strips), then strip 0 and the strips beyond tx_in of the rows inside
+__device__ __forceinline__ void sw_tile(const SwGeom &g, bool interior, int t, int &by, int &sx) {
+  if (interior) {
+    by = 1 + t / g.tx_in;
+    sx = 1 + t % g.tx_in;
+    return;
+  }
+  const int e1 = (g.ty - g.ty_in) * g.tx;
+  if (t < e1) {
+    const int fr = t / g.tx;
+    sx = t - fr * g.tx;
+    by = fr == 0 ? 0 : g.ty_in + fr;
+  } else {
+    const int ns = g.tx - g.tx_in, e2 = t - e1;
+    by = 1 + e2 / ns;
+    const int k = e2 - (by - 1) * ns;
+    sx = k == 0 ? 0 : g.tx_in + k;
+  }
+}
+
+template <bool FULL>
 __global__ void __launch_bounds__(kWsThreads, 2)
 k_shift_residual_ws(int N, const double2 *__restrict__ z, const double2 *__restrict__ b,
                     const double2 *__restrict__ lam, double off, float oscale,
                     const float *__restrict__ sc, View out, const int *__restrict__ frozen,
-                    double *__restrict__ part) {
+                    double *__restrict__ part, int pstride, int poff) {
   constexpr int R = kSwR;
   __shared__ float2 red[kWsWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int j = blockIdx.y;
   const long long m = (long long)N * N;
-  const int tx = (N + kWsOut - 1) / kWsOut, tiles = tx * ((N + R - 1) / R);
+  const SwGeom g = sw_geom(N);
+  const int tiles = sw_tiles(g, FULL);
   float2 *o = reinterpret_cast<float2 *>(out.p) + (long long)j * out.plane;
+  double *pj = part + (long long)j * pstride + poff + blockIdx.x;
   const int t_first = blockIdx.x * kWsWarps + warp, t_step = gridDim.x * kWsWarps;
   if (frozen && frozen[j]) {
     for (int t = t_first; t < tiles; t += t_step) {
-      const int i0 = (t / tx) * R, c = (t % tx) * kWsOut - 1 + lane;
+      int by, sx;
+      sw_tile(g, FULL, t, by, sx);
+      const int i0 = by * R, c = sx * kWsOut - 1 + lane;
       if (lane >= 1 && lane <= kWsOut && c < N)
 #pragma unroll
         for (int q = 0; q < R; q++)
           if (i0 + q < N) o[(long long)(i0 + q) * out.pitch + c] = make_float2(0.f, 0.f);
     }
-    if (threadIdx.x == 0) part[(long long)j * gridDim.x + blockIdx.x] = 0.0;
+    if (threadIdx.x == 0) *pj = 0.0;
     return;
   }
   const double2 *zj = z + (long long)j * m, *bj = b + (long long)j * m;
   const double2 lj = lam[j];
   const DF lr = split(lj.x), li = split(lj.y), offd = split(off);
-  const float scj = sc[j];
+  const float2 scj = bc2(sc[j]), osc = bc2(oscale);
   DF ar = {0.f, 0.f};
   ulonglong2 raw[R + 2];
   auto load_z = [&](int t) {
-    const int i0 = (t / tx) * R, c = (t % tx) * kWsOut - 1 + lane;
-    const bool cin = (unsigned)c < (unsigned)N;
+    int by, sx;
+    sw_tile(g, FULL, t, by, sx);
+    const int i0 = by * R, c = sx * kWsOut - 1 + lane;
+    const bool cin = FULL || (unsigned)c < (unsigned)N;
+    const double2 *zc = zj + (long long)(i0 - 1) * N + (cin ? c : 0);
 #pragma unroll
     for (int e = 0; e < R + 2; e++) {
-      const int i = i0 - 1 + e;
-      const bool ok = cin && (unsigned)i < (unsigned)N;
-      raw[e] = ok ? *reinterpret_cast<const ulonglong2 *>(zj + (long long)i * N + c) : make_ulonglong2(0ull, 0ull);
+      const bool ok = FULL || (cin && (unsigned)(i0 - 1 + e) < (unsigned)N);
+      raw[e] = ok ? *reinterpret_cast<const ulonglong2 *>(zc + (long long)e * N) : make_ulonglong2(0ull, 0ull);
     }
   };
   if (t_first < tiles) load_z(t_first);
   for (int t = t_first; t < tiles; t += t_step) {
-    const int i0 = (t / tx) * R, c = (t % tx) * kWsOut - 1 + lane;
-    const bool outc = lane >= 1 && lane <= kWsOut && c < N;
-    const int nr = min(R, N - i0);
+    int by, sx;
+    sw_tile(g, FULL, t, by, sx);
+    const int i0 = by * R, c = sx * kWsOut - 1 + lane;
+    const bool outc = lane >= 1 && lane <= kWsOut && (FULL || c < N);
+    const int nr = FULL ? R : min(R, N - i0);
     double2 bq[R];
 #pragma unroll
     for (int q = 0; q < R; q++)
-      bq[q] = (outc && q < nr) ? bj[(long long)(i0 + q) * N + c] : make_double2(0.0, 0.0);
-    // largest exponent of each component over the warp tile, then the limbs
+      bq[q] = (FULL || (outc && q < nr)) ? bj[(long long)(i0 + q) * N + c] : make_double2(0.0, 0.0);
+    // largest exponent of each component over the warp tile, then the limbs (component x:
+    // real, y: imaginary)
     unsigned er = 0, ei = 0;
 #pragma unroll
     for (int e = 0; e < R + 2; e++) {
@@ -400,73 +453,54 @@ k_shift_residual_ws(int N, const double2 *__restrict__ z, const double2 *__restr
     }
     er = __reduce_max_sync(0xffffffffu, er) >> 20;
     ei = __reduce_max_sync(0xffffffffu, ei) >> 20;
-    float rx2[R + 2], rx1[R + 2], rx0[R + 2], ix2[R + 2], ix1[R + 2], ix0[R + 2];
+    Limbs2 Q[R + 2];
 #pragma unroll
-    for (int e = 0; e < R + 2; e++) {
-      const float4 a = to_limbs(raw[e].x, er), q = to_limbs(raw[e].y, ei);
-      rx2[e] = a.x;
-      rx1[e] = a.y;
-      rx0[e] = a.z;
-      ix2[e] = q.x;
-      ix1[e] = q.y;
-      ix0[e] = q.z;
-    }
+    for (int e = 0; e < R + 2; e++) Q[e] = limbs2(limb_bits(raw[e].x, er), limb_bits(raw[e].y, ei));
     if (t + t_step < tiles) load_z(t + t_step);  // the next tile, while this one is computed
     const bool bad = er > 1081 + 126 || ei > 1081 + 126;
     const int Sr = 1081 - (int)er, Si = 1081 - (int)ei;
     const int sr = Sr > 252 ? 252 : Sr, si = Si > 252 ? 252 : Si;
-    // constants in the units of the component they multiply
+    // constants in the units of the component they multiply: (lr zr, lr zi), (li zi, -li zr)
+    // and off (T1r, T1i)
     const DF qr = df_scale_down(offd, sr), qi = df_scale_down(offd, si);
     const DF lrr = df_scale_down(lr, sr), lri = df_scale_down(lr, si);
     const DF lir = df_scale_down(li, sr), lii = df_scale_down(li, si);
-    float rowr = 0.f;
+    const DF2 q2 = {make_float2(qr.hi, qi.hi), make_float2(qr.lo, qi.lo)};
+    const DF2 l1 = {make_float2(lrr.hi, lri.hi), make_float2(lrr.lo, lri.lo)};
+    const DF2 l2 = {make_float2(lii.hi, -lir.hi), make_float2(lii.lo, -lir.lo)};
+    const float2 scale = bad ? bc2(__int_as_float(0x7FC00000)) : scj;
+    float2 rowr = make_float2(0.f, 0.f);
 #pragma unroll
     for (int q = 0; q < R; q++) {
       // exact stencil differences of both components, as float-float pairs
-      const float h2r = __shfl_up_sync(0xffffffffu, rx2[q + 1], 1) + __shfl_down_sync(0xffffffffu, rx2[q + 1], 1);
-      const float h1r = __shfl_up_sync(0xffffffffu, rx1[q + 1], 1) + __shfl_down_sync(0xffffffffu, rx1[q + 1], 1);
-      const float h0r = __shfl_up_sync(0xffffffffu, rx0[q + 1], 1) + __shfl_down_sync(0xffffffffu, rx0[q + 1], 1);
-      const float h2i = __shfl_up_sync(0xffffffffu, ix2[q + 1], 1) + __shfl_down_sync(0xffffffffu, ix2[q + 1], 1);
-      const float h1i = __shfl_up_sync(0xffffffffu, ix1[q + 1], 1) + __shfl_down_sync(0xffffffffu, ix1[q + 1], 1);
-      const float h0i = __shfl_up_sync(0xffffffffu, ix0[q + 1], 1) + __shfl_down_sync(0xffffffffu, ix0[q + 1], 1);
-      DF tr = two_sum(__fmaf_rn(4.f, rx2[q + 1], -__fadd_rn(__fadd_rn(rx2[q], rx2[q + 2]), h2r)),
-                      __fmaf_rn(4.f, rx1[q + 1], -__fadd_rn(__fadd_rn(rx1[q], rx1[q + 2]), h1r)));
-      tr.lo = __fadd_rn(tr.lo, __fmaf_rn(4.f, rx0[q + 1], -__fadd_rn(__fadd_rn(rx0[q], rx0[q + 2]), h0r)));
-      DF ti = two_sum(__fmaf_rn(4.f, ix2[q + 1], -__fadd_rn(__fadd_rn(ix2[q], ix2[q + 2]), h2i)),
-                      __fmaf_rn(4.f, ix1[q + 1], -__fadd_rn(__fadd_rn(ix1[q], ix1[q + 2]), h1i)));
-      ti.lo = __fadd_rn(ti.lo, __fmaf_rn(4.f, ix0[q + 1], -__fadd_rn(__fadd_rn(ix0[q], ix0[q + 2]), h0i)));
-      // z in the tile's units
-      DF zr = fast_two_sum(rx2[q + 1], rx1[q + 1]);
-      zr.lo = __fadd_rn(zr.lo, rx0[q + 1]);
-      DF zi = fast_two_sum(ix2[q + 1], ix1[q + 1]);
-      zi.lo = __fadd_rn(zi.lo, ix0[q + 1]);
+      const Limbs2 &U = Q[q], &C = Q[q + 1], &D = Q[q + 2];
+      const float2 a2 = stencil2(U.l2, C.l2, D.l2);
+      const float2 a1 = stencil2(U.l1, C.l1, D.l1);
+      const float2 a0 = stencil2(U.l0, C.l0, D.l0);
+      DF2 T = two_sum2(a2, a1);
+      T.lo = add2(T.lo, a0);
+      // z in the tile's units, and with its components swapped
+      DF2 Z = fast_two_sum2(C.l2, C.l1);
+      Z.lo = add2(Z.lo, C.l0);
+      const DF2 Zs = {make_float2(Z.hi.y, Z.hi.x), make_float2(Z.lo.y, Z.lo.x)};
       const DF br = split(bq[q].x), bi = split(bq[q].y);
-      // real: br - lr zr + li zi - off T1r; imaginary: bi - lr zi - li zr - off T1i
-      const DF p1 = df_mul_un(lrr, zr), p2 = df_mul_un(lii, zi), p3 = df_mul_un(qr, tr);
-      const DF p4 = df_mul_un(lri, zi), p5 = df_mul_un(lir, zr), p6 = df_mul_un(qi, ti);
-      float lo = __fadd_rn(__fsub_rn(br.lo, p1.lo), __fsub_rn(p2.lo, p3.lo));
-      DF s1 = two_sum(br.hi, -p1.hi);
-      float el = s1.lo;
-      s1 = two_sum(s1.hi, p2.hi);
-      el = __fadd_rn(el, s1.lo);
-      s1 = two_sum(s1.hi, -p3.hi);
-      el = __fadd_rn(el, s1.lo);
-      float rxv = __fmul_rn(__fadd_rn(s1.hi, __fadd_rn(lo, el)), scj);
-      lo = __fsub_rn(bi.lo, __fadd_rn(__fadd_rn(p4.lo, p5.lo), p6.lo));
-      DF s2 = two_sum(bi.hi, -p4.hi);
-      el = s2.lo;
-      s2 = two_sum(s2.hi, -p5.hi);
-      el = __fadd_rn(el, s2.lo);
-      s2 = two_sum(s2.hi, -p6.hi);
-      el = __fadd_rn(el, s2.lo);
-      float ryv = __fmul_rn(__fadd_rn(s2.hi, __fadd_rn(lo, el)), scj);
-      if (bad) rxv = ryv = __int_as_float(0x7FC00000);
+      const DF2 B2 = {make_float2(br.hi, bi.hi), make_float2(br.lo, bi.lo)};
+      // (real, imaginary) = b - (lr zr, lr zi) + (li zi, -li zr) - off (T1r, T1i)
+      const DF2 P1 = mul_un2(l1, Z), P2 = mul_un2(l2, Zs), P3 = mul_un2(q2, T);
+      const float2 lo = add2(sub2(B2.lo, P1.lo), sub2(P2.lo, P3.lo));
+      DF2 s = two_sum2(B2.hi, neg2(P1.hi));
+      float2 el = s.lo;
+      s = two_sum2(s.hi, P2.hi);
+      el = add2(el, s.lo);
+      s = two_sum2(s.hi, neg2(P3.hi));
+      el = add2(el, s.lo);
+      const float2 rv = mul2(add2(s.hi, add2(lo, el)), scale);
       if (outc && q < nr) {
-        o[(long long)(i0 + q) * out.pitch + c] = make_float2(rxv * oscale, ryv * oscale);
-        rowr = __fmaf_rn(rxv, rxv, __fmaf_rn(ryv, ryv, rowr));
+        o[(long long)(i0 + q) * out.pitch + c] = mul2(rv, osc);
+        rowr = fma2(rv, rv, rowr);
       }
     }
-    ar = df_add(ar, DF{rowr, 0.f});
+    ar = df_add(ar, DF{__fadd_rn(rowr.x, rowr.y), 0.f});
   }
   for (int o2 = 16; o2 > 0; o2 >>= 1) ar = df_add(ar, df_shfl_down(ar, o2));
   if (lane == 0) red[warp] = make_float2(ar.hi, ar.lo);
@@ -474,7 +508,7 @@ k_shift_residual_ws(int N, const double2 *__restrict__ z, const double2 *__restr
   if (threadIdx.x == 0) {
     DF s0 = {0.f, 0.f};
     for (int w = 0; w < kWsWarps; w++) s0 = df_add(s0, DF{red[w].x, red[w].y});
-    part[(long long)j * gridDim.x + blockIdx.x] = (double)s0.hi + (double)s0.lo;
+    *pj = (double)s0.hi + (double)s0.lo;
   }
 }
 
@@ -485,19 +519,28 @@ int residual_fx_blocks(int num_sms) { return 3 * num_sms; }
 
 // CTAs per shift of the shifted residuals: about eight waves of two CTAs per SM over all
 // shifts (the CTAs of a wave do equal work, so a last partial wave costs at most an
-// eighth), but no more CTAs than give each warp one warp tile, nor more than grid rows
+// eighth), but no more CTAs than give each warp one warp tile, nor more than grid rows;
+// at least two (the interior and the edge tiles take at least one each)
 int shift_residual_blocks(int N, int n, int num_sms) {
   const int want = (16 * num_sms + n - 1) / n;
   const long long tiles = (long long)((N + kWsOut - 1) / kWsOut) * ((N + kSwR - 1) / kSwR);
   const int cap = (int)std::min<long long>(N, (tiles + kWsWarps - 1) / kWsWarps);
-  return std::max(1, std::min(want, cap));
+  return std::max(2, std::min(want, cap));
 }
 
+// gx CTAs per shift, split between the interior and the edge kernels in proportion to their
+// tiles (at least one each); part[j gx + x] = the sum of CTA x of shift j, the edge kernel's
+// CTAs after the interior kernel's
 void launch_shift_residual_fx(cudaStream_t s, int gx, int N, int n, const double2 *z, const double2 *b,
                               const double2 *lam, double off, float oscale, const float *sc, View out,
                               const int *frozen, double *part) {
-  dim3 grid(gx, n);
-  k_shift_residual_ws<<<grid, kWsThreads, 0, s>>>(N, z, b, lam, off, oscale, sc, out, frozen, part);
+  const SwGeom g = sw_geom(N);
+  const double fe = (double)sw_tiles(g, false) / ((double)g.tx * g.ty);
+  const int ge = std::min(gx - 1, std::max(1, (int)std::lround(gx * fe))), gi = gx - ge;
+  k_shift_residual_ws<true><<<dim3(gi, n), kWsThreads, 0, s>>>(N, z, b, lam, off, oscale, sc, out, frozen,
+                                                               part, gx, 0);
+  k_shift_residual_ws<false><<<dim3(ge, n), kWsThreads, 0, s>>>(N, z, b, lam, off, oscale, sc, out, frozen,
+                                                                part, gx, gi);
 }
 
 void launch_residual_fx(cudaStream_t s, int blocks, int N, int n, int off, float2 ihf, float *r,
