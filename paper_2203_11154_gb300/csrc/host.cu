@@ -931,7 +931,7 @@ void refine_eval_launch(RefRun &r) {
             launch_shift_residual(c->stream, gx, N, n, first ? nullptr : r.z, r.b, c->d_c1,
                                   c->kappa / (h * h), (float)rs(c, 0), c->d_rsc, view(B.b, N, B.P),
                                   first ? nullptr : c->d_frozen, first, c->d_srpart));
-  ck_launch(c);
+  ck_launch(c, !first && c->cfg.fx_residual ? 2 : 1);  // the fx residual: interior and edge kernels
   ck(c, cudaMemcpyAsync(c->h_srpart, c->d_srpart, (first ? 2 : 1) * (size_t)n * gx * sizeof(double),
                         cudaMemcpyDeviceToHost, c->stream));
   ck(c, cudaEventRecord(c->ev[0], c->stream));
@@ -1346,7 +1346,7 @@ void allatonce_norms(pd_ctx *c, double *r, const double *u, const double *f, con
               launch_allatonce_residual(c->stream, c->N, c->n, c->kappa, r, u, f, u0, c->d_u0coef,
                                         c->d_Bptr, c->d_Bcol, c->d_Bval, c->d_part));
     }
-    ck_launch(c);
+    ck_launch(c, fx ? 2 : 1);  // the fx residual: interior and edge kernels
     ck(c, cudaMemcpyAsync(c->h_part, c->d_part, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost,
                           c->stream));
     ck(c, cudaStreamSynchronize(c->stream));
@@ -1378,7 +1378,7 @@ void allatonce_norms(pd_ctx *c, double *r, const double *u, const double *f, con
     else
       launch_residual_bidiag(c->stream, c->N, c->n, c->boff, c->kappa, nullptr, r32, u, f, u0,
                              c->d_u0coef, c->d_bd, c->d_bs, false, c->d_part, 1.0);
-    ck_launch(c);
+    ck_launch(c, fx ? 2 : 1);
     ck(c, cudaStreamSynchronize(c->stream));
   }
 }
@@ -2445,7 +2445,7 @@ pd_status pd_shifted_residual32(pd_ctx *c, float *r32, const void *z, const void
       launch_shift_residual(c->stream, gx, N, n, static_cast<const double2 *>(z),
                             static_cast<const double2 *>(b), c->d_c1, c->kappa / (h * h), 1.0f, c->d_rsc,
                             out, nullptr, false, c->d_srpart);
-    ck_launch(c);
+    ck_launch(c, c->cfg.fx_residual ? 2 : 1);
     ck(c, cudaMemcpyAsync(c->h_srpart, c->d_srpart, (size_t)n * gx * sizeof(double), cudaMemcpyDeviceToHost,
                           c->stream));
     ck(c, cudaStreamSynchronize(c->stream));

@@ -52,11 +52,53 @@ constexpr int kWsOut = 30;   // output columns of a warp strip
 constexpr int kWsWarps = 8;  // warps per CTA
 constexpr int kWsThreads = 32 * kWsWarps;
 
-// item = chunk * tiles + tile, tile = row block * tx + strip; chunk q covers the positions
+// Tile sets of the warp-tile kernels (tiles of R rows by kWsOut output columns, strip sx
+// starting at column c0 = kWsOut sx - 1): a tile is interior when its rows i0 - 1 .. i0 + R
+// and the strip's 32 columns c0 .. c0 + 31 all lie inside the grid, i.e. row blocks
+// [1, ty_in] and strips [1, tx_in].  The edge set is the row blocks outside [1, ty_in] (all
+// strips), then strip 0 and the strips beyond tx_in of the row blocks inside.
+struct TileGeom {
+  int tx, ty, tx_in, ty_in;
+};
+__host__ __device__ __forceinline__ TileGeom tile_geom(int N, int R) {
+  TileGeom g;
+  g.tx = (N + kWsOut - 1) / kWsOut;
+  g.ty = (N + R - 1) / R;
+  g.tx_in = N > 31 ? (N - 31) / kWsOut : 0;
+  g.ty_in = N > 1 + R ? (N - 1) / R - 1 : 0;
+  if (g.tx_in == 0 || g.ty_in == 0) g.tx_in = g.ty_in = 0;
+  return g;
+}
+__host__ __device__ __forceinline__ int tile_count(const TileGeom &g, bool interior) {
+  const int in = g.tx_in * g.ty_in;
+  return interior ? in : g.tx * g.ty - in;
+}
+// tile t of the interior or the edge set -> (row block, strip)
+__device__ __forceinline__ void tile_at(const TileGeom &g, bool interior, int t, int &by, int &sx) {
+  if (interior) {
+    by = 1 + t / g.tx_in;
+    sx = 1 + t % g.tx_in;
+    return;
+  }
+  const int e1 = (g.ty - g.ty_in) * g.tx;
+  if (t < e1) {
+    const int fr = t / g.tx;
+    sx = t - fr * g.tx;
+    by = fr == 0 ? 0 : g.ty_in + fr;
+  } else {
+    const int ns = g.tx - g.tx_in, e2 = t - e1;
+    by = 1 + e2 / ns;
+    const int k = e2 - (by - 1) * ns;
+    sx = k == 0 ? 0 : g.tx_in + k;
+  }
+}
+
+// item = chunk * tiles + tile (tiles: the kernel's tile set); chunk q covers the positions
 // [q n / nch, (q + 1) n / nch) of the time walk, position p being step p (off = -1) or
 // n - 1 - p (off = +1)
 struct WsGeom {
-  int N, n, off, tx, tiles, nch, items;
+  int N, n, off, tiles, nch, items;
+  TileGeom tg;
 };
 
 __device__ __forceinline__ int ws_step(const WsGeom &g, int p) { return g.off < 0 ? p : g.n - 1 - p; }
@@ -85,13 +127,6 @@ __device__ __forceinline__ float2 shfl_sum2(float2 v) {
 // 4 c - (u + d + the horizontal neighbours of c) of one limb, exact
 __device__ __forceinline__ float2 stencil2(float2 u, float2 c, float2 d) {
   return fma2(bc2(4.f), c, neg2(add2(add2(u, d), shfl_sum2(c))));
-}
-
-// A tile is interior when its rows i0 - 1 .. i0 + kWsR and the strip's 32 columns c0 ..
-// c0 + 31 all lie inside the grid: row blocks by in [1, (N - 1) / kWsR - 1], strips sx in
-// [1, (N - 31) / kWsOut].
-__host__ __device__ __forceinline__ bool ws_interior(int N, int i0, int c0) {
-  return i0 >= 1 && i0 + kWsR < N && c0 >= 0 && c0 + 31 < N;
 }
 
 // One work item: the tile at rows i0.., the lane's column c, time-walk chunk q.  Output rows
@@ -254,9 +289,8 @@ __device__ __forceinline__ void ws_item(const WsGeom &g, const WsArgs &A, int q,
   }
 }
 
-// FULL: the interior tiles (g.tx counts the interior strips, g.tiles = interior strips x
-// interior row blocks); else every tile but the interior ones.  CTA sums: float-float over
-// the warps, one conversion to FP64 per CTA.
+// FULL: the interior tiles, else the edge tiles.  CTA sums: float-float over the warps, one
+// conversion to FP64 per CTA.
 template <int FMODE, bool FULL>
 __global__ void __launch_bounds__(kWsThreads, 2)
 k_residual_ws(const __grid_constant__ WsGeom g, const __grid_constant__ WsArgs A,
@@ -267,14 +301,9 @@ k_residual_ws(const __grid_constant__ WsGeom g, const __grid_constant__ WsArgs A
   DF ar = {0.f, 0.f}, af = {0.f, 0.f};
   for (int it = blockIdx.x * kWsWarps + warp; it < g.items; it += gridDim.x * kWsWarps) {
     const int q = it / g.tiles, t0 = it - q * g.tiles;
-    if (FULL) {
-      const int by = 1 + t0 / g.tx, sx = 1 + t0 % g.tx;
-      ws_item<FMODE, true>(g, A, q, by * R, sx * kWsOut - 1 + lane, lane, ar, af);
-    } else {
-      const int by = t0 / g.tx, sx = t0 - by * g.tx;
-      const int i0 = by * R, c0 = sx * kWsOut - 1;
-      if (!ws_interior(g.N, i0, c0)) ws_item<FMODE, false>(g, A, q, i0, c0 + lane, lane, ar, af);
-    }
+    int by, sx;
+    tile_at(g.tg, FULL, t0, by, sx);
+    ws_item<FMODE, FULL>(g, A, q, by * R, sx * kWsOut - 1 + lane, lane, ar, af);
   }
   for (int o = 16; o > 0; o >>= 1) {
     ar = df_add(ar, df_shfl_down(ar, o));
@@ -298,10 +327,10 @@ k_residual_ws(const __grid_constant__ WsGeom g, const __grid_constant__ WsArgs A
 
 // time-step runs: enough items for about eight per warp (the tail of a static
 // distribution then costs little), runs of at least two steps
-void ws_chunks(WsGeom &g, long long work_tiles, int blocks) {
+void ws_chunks(WsGeom &g, int blocks) {
   const long long warps = (long long)blocks * kWsWarps;
   g.nch = 1;
-  while (work_tiles * g.nch < 8 * warps && g.n / (2 * g.nch) >= 2) g.nch *= 2;
+  while ((long long)g.tiles * g.nch < 8 * warps && g.n / (2 * g.nch) >= 2) g.nch *= 2;
   g.items = g.tiles * g.nch;
 }
 
@@ -314,16 +343,13 @@ void launch_ws(cudaStream_t s, int blocks, int blocks_edge, int N, int n, int of
   g.N = N;
   g.n = n;
   g.off = off < 0 ? -1 : 1;
-  const int ty_in = (N - 1) / kWsR - 1, tx_in = (N - 31) / kWsOut;
-  WsGeom gi = g;
-  gi.tx = std::max(tx_in, 1);
-  gi.tiles = tx_in >= 1 && ty_in >= 1 ? tx_in * ty_in : 0;
-  ws_chunks(gi, gi.tiles, blocks);
+  g.tg = tile_geom(N, kWsR);
+  WsGeom gi = g, ge = g;
+  gi.tiles = tile_count(g.tg, true);
+  ws_chunks(gi, blocks);
   k_residual_ws<FMODE, true><<<blocks, kWsThreads, 0, s>>>(gi, A, part);
-  WsGeom ge = g;
-  ge.tx = (N + kWsOut - 1) / kWsOut;
-  ge.tiles = ge.tx * ((N + kWsR - 1) / kWsR);
-  ws_chunks(ge, (long long)ge.tiles - gi.tiles, blocks_edge);
+  ge.tiles = tile_count(g.tg, false);
+  ws_chunks(ge, blocks_edge);
   k_residual_ws<FMODE, false><<<blocks_edge, kWsThreads, 0, s>>>(ge, A, part + 2 * blocks);
 }
 
@@ -345,46 +371,6 @@ void launch_ws(cudaStream_t s, int blocks, int blocks_edge, int N, int n, int of
 // and no sums.
 constexpr int kSwR = 4;
 
-// interior tiles: rows i0 - 1 .. i0 + kSwR and columns c0 .. c0 + 31 inside the grid, i.e.
-// row blocks [1, ty_in], strips [1, tx_in]
-struct SwGeom {
-  int N, tx, ty, tx_in, ty_in;
-};
-__host__ __device__ __forceinline__ SwGeom sw_geom(int N) {
-  SwGeom g;
-  g.N = N;
-  g.tx = (N + kWsOut - 1) / kWsOut;
-  g.ty = (N + kSwR - 1) / kSwR;
-  g.tx_in = N > 31 ? (N - 31) / kWsOut : 0;
-  g.ty_in = N > 1 + kSwR ? (N - 1) / kSwR - 1 : 0;
-  if (g.tx_in == 0 || g.ty_in == 0) g.tx_in = g.ty_in = 0;
-  return g;
-}
-__host__ __device__ __forceinline__ int sw_tiles(const SwGeom &g, bool interior) {
-  const int in = g.tx_in * g.ty_in;
-  return interior ? in : g.tx * g.ty - in;
-}
-// tile t of the interior or of the edge set -> (row block, strip); the edge set is the rows
-// outside [1, ty_in] (all strips), then strip 0 and the strips beyond tx_in of the rows inside
-__device__ __forceinline__ void sw_tile(const SwGeom &g, bool interior, int t, int &by, int &sx) {
-  if (interior) {
-    by = 1 + t / g.tx_in;
-    sx = 1 + t % g.tx_in;
-    return;
-  }
-  const int e1 = (g.ty - g.ty_in) * g.tx;
-  if (t < e1) {
-    const int fr = t / g.tx;
-    sx = t - fr * g.tx;
-    by = fr == 0 ? 0 : g.ty_in + fr;
-  } else {
-    const int ns = g.tx - g.tx_in, e2 = t - e1;
-    by = 1 + e2 / ns;
-    const int k = e2 - (by - 1) * ns;
-    sx = k == 0 ? 0 : g.tx_in + k;
-  }
-}
-
 template <bool FULL>
 __global__ void __launch_bounds__(kWsThreads, 2)
 k_shift_residual_ws(int N, const double2 *__restrict__ z, const double2 *__restrict__ b,
@@ -396,15 +382,15 @@ k_shift_residual_ws(int N, const double2 *__restrict__ z, const double2 *__restr
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int j = blockIdx.y;
   const long long m = (long long)N * N;
-  const SwGeom g = sw_geom(N);
-  const int tiles = sw_tiles(g, FULL);
+  const TileGeom g = tile_geom(N, R);
+  const int tiles = tile_count(g, FULL);
   float2 *o = reinterpret_cast<float2 *>(out.p) + (long long)j * out.plane;
   double *pj = part + (long long)j * pstride + poff + blockIdx.x;
   const int t_first = blockIdx.x * kWsWarps + warp, t_step = gridDim.x * kWsWarps;
   if (frozen && frozen[j]) {
     for (int t = t_first; t < tiles; t += t_step) {
       int by, sx;
-      sw_tile(g, FULL, t, by, sx);
+      tile_at(g, FULL, t, by, sx);
       const int i0 = by * R, c = sx * kWsOut - 1 + lane;
       if (lane >= 1 && lane <= kWsOut && c < N)
 #pragma unroll
@@ -422,7 +408,7 @@ k_shift_residual_ws(int N, const double2 *__restrict__ z, const double2 *__restr
   ulonglong2 raw[R + 2];
   auto load_z = [&](int t) {
     int by, sx;
-    sw_tile(g, FULL, t, by, sx);
+    tile_at(g, FULL, t, by, sx);
     const int i0 = by * R, c = sx * kWsOut - 1 + lane;
     const bool cin = FULL || (unsigned)c < (unsigned)N;
     const double2 *zc = zj + (long long)(i0 - 1) * N + (cin ? c : 0);
@@ -435,7 +421,7 @@ k_shift_residual_ws(int N, const double2 *__restrict__ z, const double2 *__restr
   if (t_first < tiles) load_z(t_first);
   for (int t = t_first; t < tiles; t += t_step) {
     int by, sx;
-    sw_tile(g, FULL, t, by, sx);
+    tile_at(g, FULL, t, by, sx);
     const int i0 = by * R, c = sx * kWsOut - 1 + lane;
     const bool outc = lane >= 1 && lane <= kWsOut && (FULL || c < N);
     const int nr = FULL ? R : min(R, N - i0);
@@ -514,8 +500,8 @@ k_shift_residual_ws(int N, const double2 *__restrict__ z, const double2 *__restr
 
 }  // namespace
 
-// two CTAs per SM for the interior tiles, one per SM for the edge tiles
-int residual_fx_blocks(int num_sms) { return 3 * num_sms; }
+// two CTAs per SM for the interior tiles, two per SM for the edge tiles
+int residual_fx_blocks(int num_sms) { return 4 * num_sms; }
 
 // CTAs per shift of the shifted residuals: about eight waves of two CTAs per SM over all
 // shifts (the CTAs of a wave do equal work, so a last partial wave costs at most an
@@ -534,8 +520,8 @@ int shift_residual_blocks(int N, int n, int num_sms) {
 void launch_shift_residual_fx(cudaStream_t s, int gx, int N, int n, const double2 *z, const double2 *b,
                               const double2 *lam, double off, float oscale, const float *sc, View out,
                               const int *frozen, double *part) {
-  const SwGeom g = sw_geom(N);
-  const double fe = (double)sw_tiles(g, false) / ((double)g.tx * g.ty);
+  const TileGeom g = tile_geom(N, kSwR);
+  const double fe = (double)tile_count(g, false) / ((double)g.tx * g.ty);
   const int ge = std::min(gx - 1, std::max(1, (int)std::lround(gx * fe))), gi = gx - ge;
   k_shift_residual_ws<true><<<dim3(gi, n), kWsThreads, 0, s>>>(N, z, b, lam, off, oscale, sc, out, frozen,
                                                                part, gx, 0);
@@ -548,7 +534,7 @@ void launch_residual_fx(cudaStream_t s, int blocks, int N, int n, int off, float
                         const float2 *ku0, float oscale, float fscale, bool want_f, double *part,
                         const float2 *fc_in, float2 *fc_out) {
   const WsArgs A{r, u, f, u0, kbd, ku0, DF{ihf.x, ihf.y}, oscale, fscale, want_f ? 1 : 0, fc_in, fc_out};
-  const int be = std::max(1, blocks / 3), bi = std::max(1, blocks - be);
+  const int be = std::max(1, blocks / 2), bi = std::max(1, blocks - be);
   if (fc_in)
     launch_ws<2>(s, bi, be, N, n, off, A, part);
   else if (fc_out)
