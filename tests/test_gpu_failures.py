@@ -157,11 +157,11 @@ def test_refined_shifted_solve_does_not_depend_on_the_data_scale(scale):
 
 
 @pytest.mark.parametrize("fx", [0, 1])
-@pytest.mark.parametrize("N,n", [(127, 8), (255, 4)])
+@pytest.mark.parametrize("N,n", [(127, 8), (255, 4), (31, 3)])
 def test_shifted_residual32_against_long_double_oracle(fx, N, n):
     """The FP32 residual of eq. (2) the refined shifted solves hand to the multigrid, element
     by element against the oracle's long-double residual, on a random z and on a converged
-    one.  Without FP64 arithmetic (fx = 1) the bound is the FP32 rounding of r plus 2^-43
+    one (N = 31: every warp tile touches the grid's edge).  Without FP64 arithmetic (fx = 1) the bound is the FP32 rounding of r plus 2^-43
     of the terms and the fixed-point truncation ih2 2^-54 max|z_j| per component; the FP64
     formula (fx = 0) is bound by its rounding, 4 eps of the terms, and its FP32 output is
     truncated (not rounded) to 24 bits: 2^-23 |r|."""

@@ -221,10 +221,11 @@ def converged_iterate(N, n, tau, alpha, fhat, steps=3):
 
 
 @pytest.mark.parametrize("fx", [1, 0])
-@pytest.mark.parametrize("N,n,alpha", [(127, 8, 1e-3), (255, 16, 1e-2), (63, 5, 0.3)])
+@pytest.mark.parametrize("N,n,alpha", [(127, 8, 1e-3), (255, 16, 1e-2), (63, 5, 0.3), (31, 4, 1e-3)])
 def test_refinement_residual32(fx, N, n, alpha):
     """The FP32 residual the refinement hands to the forward transform, element by element
-    against the oracle's long-double residual, on a random and on a converged u.  Without
+    against the oracle's long-double residual, on a random and on a converged u (N = 31:
+    every warp tile touches the grid's edge; N = 63: one column of interior tiles).  Without
     FP64 arithmetic (fx = 1) the error bound is the FP32 rounding of r plus 2^-43 of the
     terms and the fixed-point truncation ih2 2^-54 max|u_k| — far below the FP64 rounding of
     the formula (4 eps of ih2 (4|u| + sum|nb|)), which bounds fx = 0."""
@@ -282,7 +283,7 @@ def fx_bound(N, n, tau, alpha, u, fhat, r_ld):
     return 2.0 ** -24 * np.abs(r_ld) + 2.0 ** -43 * T + ih2 * 2.0 ** -54 * umax
 
 
-@pytest.mark.parametrize("N,n,alpha", [(127, 8, 1e-3), (255, 16, 1e-2), (63, 5, 0.3)])
+@pytest.mark.parametrize("N,n,alpha", [(127, 8, 1e-3), (255, 16, 1e-2), (63, 5, 0.3), (31, 3, 0.1)])
 def test_refinement_residual32_transposed(N, n, alpha):
     """The same residual for the adjoint's transposed time matrix, whose kernel walks the
     time steps downwards: B^T = J B J with J the reversal of the time steps, so the
