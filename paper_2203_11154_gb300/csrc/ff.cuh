@@ -92,31 +92,12 @@ __device__ __forceinline__ unsigned long long shr64(unsigned long long x, unsign
 
 // FP64 bits -> the three limbs of its fixed-point value in units 2^-S, S = 1081 - emax:
 // v = m 2^(e - 1075 + S) = (m << 6) >> (emax - e) (m < 2^53, so m << 6 < 2^59; truncated
-// below a unit), cut into 21-bit pieces and made FP32 by the mantissa trick at the limb's
-// own exponent: the FP32 number X with t in the mantissa of 2^(23 + 21 j) is 2^(23 + 21 j)
-// + t 2^(21 j), and X - 2^(23 + 21 j) is exact (here times the sign, in one FMA).  Zero and subnormal
-// inputs (e = 0) are taken with the implicit bit: below 2^-1022 they only matter in a tile
-// with emax < 64, where every scaled coefficient is 0.
-__device__ __forceinline__ float4 to_limbs(unsigned long long bits, unsigned emax) {
-  const uint32_t hw = (uint32_t)(bits >> 32), lw = (uint32_t)bits;
-  const unsigned e = (hw >> 20) & 0x7FFu;
-  const unsigned long long m = ((unsigned long long)((hw & 0xFFFFFu) | 0x100000u) << 32) | lw;
-  const unsigned long long v = shr64(m << 6, emax - e);
-  const uint32_t vl = (uint32_t)v, vh = (uint32_t)(v >> 32);
-  const uint32_t t0 = vl & 0x1FFFFFu, t1 = __funnelshift_r(vl, vh, 21) & 0x1FFFFFu, t2 = vh >> 10;
-  // sign: sg = +-1; sg (X - 2^(23 + 21 j)) as one exact FMA
-  const float sg = __uint_as_float((hw & 0x80000000u) | 0x3F800000u);
-  constexpr uint32_t E2 = 192u << 23, E1 = 171u << 23, E0 = 150u << 23;
-  float4 l;
-  l.x = __fmaf_rn(sg, __uint_as_float(E2 | t2), __fmul_rn(sg, -0x1p65f));
-  l.y = __fmaf_rn(sg, __uint_as_float(E1 | t1), __fmul_rn(sg, -0x1p44f));
-  l.z = __fmaf_rn(sg, __uint_as_float(E0 | t0), __fmul_rn(sg, -0x1p23f));
-  l.w = 0.f;
-  return l;
-}
-
-// The integer part of to_limbs: the FP32 words X_j (t_j in the mantissa of 2^(23 + 21 j))
-// and the sign as +-1, so that the limbs are sg (X_j - 2^(23 + 21 j)).
+// below a unit), cut into 21-bit pieces t_j and made FP32 by the mantissa trick at the
+// limb's own exponent: the FP32 number X_j with t_j in the mantissa of 2^(23 + 21 j) is
+// 2^(23 + 21 j) + t_j 2^(21 j), and sg (X_j - 2^(23 + 21 j)) is exact (sg = +-1, the sign;
+// one FMA, see limbs2 below).  Zero and subnormal inputs (e = 0) are taken with the
+// implicit bit: below 2^-1022 they only matter in a tile with emax < 64, where every scaled
+// coefficient is 0.  limb_bits is the integer part: the words X_j and sg.
 struct LimbBits {
   uint32_t x2, x1, x0;
   float sg;
@@ -159,7 +140,7 @@ __device__ __forceinline__ DF2 mul_un2(DF2 c, DF2 x) {
   const float2 p = mul2(c.hi, x.hi);
   return {p, add2(fma2(c.hi, x.hi, neg2(p)), fma2(c.hi, x.lo, mul2(c.lo, x.hi)))};
 }
-// the three limbs of two values (components x and y), from their LimbBits
+// the three limbs of two values (components x and y) from their LimbBits: sg (X_j - 2^(23 + 21 j))
 struct Limbs2 {
   float2 l2, l1, l0;
 };

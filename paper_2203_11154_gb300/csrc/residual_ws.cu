@@ -21,12 +21,12 @@
 //     FP32 operation (FADD2 / FMUL2 / FFMA2), each component rounded exactly as the scalar
 //     operation, so the results are those of the scalar formulas bit for bit.
 //   - Interior and edge tiles are two kernels: the interior one (every row and column the
-//     tile reads inside the grid) loads without bounds checks; the edge one walks the
-//     remaining tiles in short runs of time steps.  Compiled apart, each keeps its state in
-//     registers (compiled together they spilled).
+//     tile reads inside the grid) loads without bounds checks; the edge one takes the
+//     remaining tiles (enumerated directly) in short runs of time steps.  Compiled apart,
+//     each keeps its state in registers (compiled together they spilled).
 //   - Fixed point: one scale per warp tile and step, 2^-S with S = 1081 - (largest biased
 //     exponent of the tile's (kWsR + 2) x 32 values, a warp max); every value becomes three
-//     exact FP32 limbs (ff::to_limbs), so the stencil difference 4 u_k - (sum of the
+//     exact FP32 limbs (ff::limb_bits, ff::limbs2), so the stencil difference 4 u_k - (sum of the
 //     neighbours), where the cancellation happens, is exact in FP32 arithmetic.
 //   - The other terms are float-float pairs: fhat (split from FP64 by bit operations, or
 //     read back from the float-float cache the first residual of a solve writes), the three
